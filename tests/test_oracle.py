@@ -1,0 +1,439 @@
+"""Pins of the FP64 CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the paper's
+printed tables, closed-form solutions, exact invariants, a Fourier-space
+restatement of the linearised scheme, or brute-force geometry.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as fh:
+        return json.load(fh)
+
+
+# --------------------------------------------------------------------------
+# Lattices and the collision matrix
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name,d,q", [("D2Q5", 2, 5), ("D3Q7", 3, 7)])
+def test_lattice_tables_match_paper(name, d, q):
+    g = _gold("lattices.json")[name]
+    cv, w, cs2 = O.lattice(d, q, 1.0)
+    assert np.array_equal(cv, np.array(g["c"], dtype=float))
+    assert np.allclose(w, g["w"], rtol=0, atol=1e-16)
+    assert cs2 == pytest.approx(g["cs2"], abs=1e-16)
+
+
+@pytest.mark.parametrize("d,q", [(2, 5), (3, 7)])
+@pytest.mark.parametrize("c", [1.0, 0.37])
+def test_lattice_isotropy(d, q, c):
+    """Eq. DdQq: sum w = 1, sum w c = 0, sum w c c = cs^2 I."""
+    cv, w, cs2 = O.lattice(d, q, c)
+    assert w.sum() == pytest.approx(1.0, abs=1e-15)
+    assert np.abs(w @ cv).max() < 1e-15
+    assert np.allclose(np.einsum("i,ia,ib->ab", w, cv, cv), cs2 * np.eye(d), atol=1e-15)
+
+
+def test_d2q5_basis_is_eq_4_2():
+    M, S = O.moment_basis(2, 5, 1.0, 1.0, 1.2, 0.9)
+    assert np.array_equal(M, np.array(_gold("lattices.json")["D2Q5"]["M"], dtype=float))
+    assert np.array_equal(S, [1.0, 1.2, 1.2, 0.9, 0.9])
+
+
+@pytest.mark.parametrize("d,q", [(2, 5), (3, 7)])
+@pytest.mark.parametrize("rates", [(1.0, 1.2, None), (0.8, 1.7, 0.5), (1.3, 0.7, 1.9)])
+def test_collision_matrix_requirements(d, q, rates):
+    """Eq. 3-6: e and c_beta are left eigenvectors of Lambda with s0, s1;
+    the spectrum is {s0, s1 (d times), s2 (q-1-d times)}."""
+    s0, s1, s2 = rates
+    s2 = O.s2_rule(s1) if s2 is None else s2
+    for c in (1.0, 0.29):
+        L = O.collision_matrix(d, q, c, s0, s1, s2)
+        cv, _, _ = O.lattice(d, q, c)
+        e = np.ones(q)
+        assert np.allclose(e @ L, s0 * e, atol=1e-13)
+        for b in range(d):
+            assert np.allclose(cv[:, b] @ L, s1 * cv[:, b], atol=1e-13)
+        ev = np.sort(np.linalg.eigvals(L).real)
+        want = np.sort([s0] + [s1] * d + [s2] * (q - 1 - d))
+        assert np.allclose(ev, want, atol=1e-12)
+        M, S = O.moment_basis(d, q, c, s0, s1, s2)
+        assert np.allclose(L, np.linalg.solve(M, np.diag(S) @ M), atol=1e-13)
+
+
+def test_s2_rule():
+    assert O.s2_rule(1.2) == pytest.approx(8 * 0.8 / 6.8)
+    # with s1 = 1.2 the rule gives (1/s1 - 1/2)(1/s2 - 1/2) = 3/16
+    s2 = O.s2_rule(1.2)
+    assert (1 / 1.2 - 0.5) * (1 / s2 - 0.5) == pytest.approx(3 / 16)
+
+
+# --------------------------------------------------------------------------
+# Fixed points and exact invariants
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("d,n,wall,lid", [
+    (2, (7, 5), (0, 0, 0), False),
+    (2, (6, 5), (1, 1, 0), False),
+    (3, (4, 5, 3), (0, 0, 0), False),
+    (3, (4, 3, 5), (1, 1, 1), False),
+])
+def test_rest_state_is_fixed_point(d, n, wall, lid):
+    pb = O.Problem(d=d, n=n, s1=1.3, wall=wall, lid=lid)
+    P, u = synth.rest_state(pb.N, d)
+    f = O.init(pb, P, u)
+    f0 = f.copy()
+    O.run(pb, f, 3)
+    assert np.abs(f - f0).max() <= 4e-16
+
+
+def _seeded_fields_2d(nx, ny, seed, amp=0.02):
+    rng = synth.SplitMix64(seed)
+    X, Y = synth.grid_coords((nx, ny))
+    P = 1.0 + 0.1 * amp * np.cos(2 * math.pi * X / nx + rng.uniform())
+    u = np.stack([amp * np.sin(2 * math.pi * (X / nx + 2 * Y / ny) + 6 * rng.uniform()),
+                  amp * np.cos(2 * math.pi * (3 * X / nx - Y / ny) + 6 * rng.uniform())])
+    return P, u
+
+
+def _seeded_fields_3d(n, seed, amp=0.02):
+    rng = synth.SplitMix64(seed)
+    X, Y, Z = synth.grid_coords(n)
+    ph = [6 * rng.uniform() for _ in range(4)]
+    P = 1.0 + 0.1 * amp * np.cos(2 * math.pi * Z / n[2] + ph[0])
+    u = np.stack([amp * np.sin(2 * math.pi * (X / n[0] + Y / n[1]) + ph[1]),
+                  amp * np.sin(2 * math.pi * (Y / n[1] - Z / n[2]) + ph[2]),
+                  amp * np.cos(2 * math.pi * (X / n[0] + Z / n[2]) + ph[3])])
+    return P, u
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_periodic_conservation(d):
+    """Lambda has e as left eigenvector (Eq. 3-6, 3-9): sum_x ubar_alpha is
+    conserved by collision and by periodic streaming."""
+    if d == 2:
+        pb = O.Problem(d=2, n=(12, 10), s1=1.6)
+        P, u = _seeded_fields_2d(12, 10, 7)
+    else:
+        pb = O.Problem(d=3, n=(6, 5, 4), s1=1.6)
+        P, u = _seeded_fields_3d((6, 5, 4), 7)
+    u = u + np.array([0.004, -0.003, 0.002][:d])[:, None]  # a non-zero mean flow
+    f = O.init(pb, P, u)
+    s0 = O.sums(pb, f)
+    O.run(pb, f, 50)
+    s1 = O.sums(pb, f)
+    assert np.abs(s1 - s0).max() < 1e-12 * pb.N
+    # and sum_x u is u's mean times N: not trivially zero for these fields
+    assert np.abs(s0[1:]).max() > 1e-3
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_divergence_identity(d):
+    """Eq. 3-15 with R = 0 makes Eq. 3-16a vanish at every node exactly:
+    sum_a sum_i c_{i,a} f^ne_{i,a} = 0 by construction of P."""
+    if d == 2:
+        pb = O.Problem(d=2, n=(9, 8), s1=1.1)
+        P, u = _seeded_fields_2d(9, 8, 3)
+    else:
+        pb = O.Problem(d=3, n=(5, 4, 6), s1=1.1)
+        P, u = _seeded_fields_3d((5, 4, 6), 3)
+    f = O.init(pb, P, u)
+    O.run(pb, f, 7)
+    D = O.derived(pb, f)
+    scale = np.abs(D["G"]).max()
+    assert scale > 1e-4
+    assert np.abs(D["div"]).max() < 1e-12 * max(1.0, scale)
+    # the trace of G is the divergence
+    assert np.allclose(np.einsum("aan->n", D["G"]), D["div"], atol=1e-14)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_continuity_set_never_feeds_back(d):
+    """Sec. 3.2 / Remark IV: u and P do not depend on the alpha = 0 set."""
+    if d == 2:
+        n = (8, 6)
+        P, u = _seeded_fields_2d(8, 6, 11)
+    else:
+        n = (4, 5, 3)
+        P, u = _seeded_fields_3d(n, 11)
+    out = []
+    for wr in (True, False):
+        pb = O.Problem(d=d, n=n, s1=1.4, with_rho=wr)
+        f = O.init(pb, P, u)
+        O.run(pb, f, 9)
+        out.append(O.macro(pb, f)[:2])
+    assert np.array_equal(out[0][0], out[1][0])
+    assert np.array_equal(out[0][1], out[1][1])
+
+
+# --------------------------------------------------------------------------
+# Linearised scheme in Fourier space (independent restatement)
+# --------------------------------------------------------------------------
+def _amplification(d, q, c_int, w, cs2, s, k, with_rho):
+    """A(k) of the scheme linearised about rest (P0 = rho0 = 1, u = 0):
+    push-streaming e^{-i k.c_i} after f -> f - Lam (f - E f)."""
+    if d == 2:
+        M = np.array(_gold("lattices.json")["D2Q5"]["M"], dtype=float)
+        S = np.diag([s[0], s[1], s[1], s[2], s[2]])
+    else:
+        cc = np.array(c_int, dtype=float)
+        c2 = (cc ** 2).sum(1)
+        M = np.stack([np.ones(q), cc[:, 0], cc[:, 1], cc[:, 2], 7 * c2 - 6,
+                      2 * cc[:, 0] ** 2 - cc[:, 1] ** 2 - cc[:, 2] ** 2,
+                      cc[:, 1] ** 2 - cc[:, 2] ** 2])
+        S = np.diag([s[0]] + [s[1]] * 3 + [s[2]] * 3)
+    Lam = np.linalg.inv(M) @ S @ M
+    alphas = list(range(0 if with_rho else 1, d + 1))
+    ns = len(alphas)
+    dim = ns * q
+    E = np.zeros((dim, dim))
+    cc = np.array(c_int, dtype=float)
+    # linear pressure deviation: dP = (1/d) sum_b sum_j c_{j,b} df_{j,b}
+    dP = np.zeros(dim)
+    for b in range(d):
+        a = alphas.index(b + 1)
+        dP[a * q:(a + 1) * q] += cc[:, b] / d
+    for a, al in enumerate(alphas):
+        for i in range(q):
+            row = a * q + i
+            if al == 0:
+                E[row, a * q:(a + 1) * q] += w[i]  # d rho
+                for b in range(d):  # rho0 c_i . du / cs2
+                    ab = alphas.index(b + 1)
+                    E[row, ab * q:(ab + 1) * q] += w[i] * cc[i, b] / cs2
+            else:
+                E[row, a * q:(a + 1) * q] += w[i]  # d u_alpha
+                E[row] += w[i] * cc[i, al - 1] * dP / cs2
+    C = np.eye(dim) - np.kron(np.eye(ns), Lam) @ (np.eye(dim) - E)
+    phase = np.exp(-1j * (cc @ np.asarray(k)))
+    D = np.diag(np.tile(phase, ns))
+    return D @ C, E
+
+
+@pytest.mark.parametrize("d,n,m", [(2, (16, 12), (1, 2)), (2, (10, 14), (2, -1)),
+                                   (3, (12, 10, 9), (1, 1, -1))])
+def test_linear_dispersion(d, n, m):
+    q = 5 if d == 2 else 7
+    s = (1.0, 1.35, 0.8)
+    cv, w, cs2 = O.lattice(d, q, 1.0)
+    k = [2 * math.pi * m[b] / n[b] for b in range(d)]
+    A, E = _amplification(d, q, cv, w, cs2, s, k, True)
+    eps = 1e-7
+    coords = synth.grid_coords(n)
+    phase = sum(k[b] * coords[b] for b in range(d))
+    amp = [0.7, -0.4, 0.5][:d]
+    u = np.stack([eps * amp[b] * np.cos(phase) for b in range(d)])
+    P = 1.0 + 0.3 * eps * np.cos(phase)
+    pb = O.Problem(d=d, n=n, s1=s[1], s2=s[2], s0=s[0])
+    f = O.init(pb, P, u)
+    rest = O.init(pb, *synth.rest_state(pb.N, d))
+    # linear initial deviation: E applied to a state carrying (d rho = 0, du, dP)
+    nsets = d + 1
+    # build the linear amplitude of f^eq deviation directly
+    f0hat = np.zeros(nsets * q)
+    for i in range(q):
+        f0hat[i] = w[i] * sum(cv[i, b] * eps * amp[b] for b in range(d)) / cs2
+        for al in range(1, d + 1):
+            f0hat[al * q + i] = w[i] * (eps * amp[al - 1] + cv[i, al - 1] * 0.3 * eps / cs2)
+    dev0 = (f - rest).reshape(nsets * q, pb.N)
+    pred0 = np.real(np.outer(f0hat, np.exp(1j * phase)))
+    assert np.abs(dev0 - pred0).max() < 1e-6 * np.abs(pred0).max()
+    nsteps = 25
+    O.run(pb, f, nsteps)
+    fhat = np.linalg.matrix_power(A, nsteps) @ f0hat
+    pred = np.real(np.outer(fhat, np.exp(1j * phase)))
+    dev = (f - rest).reshape(nsets * q, pb.N)
+    assert np.abs(pred).max() > 1e-3 * eps
+    assert np.abs(dev - pred).max() < 2e-5 * np.abs(pred).max()
+
+
+# --------------------------------------------------------------------------
+# Closed-form flows
+# --------------------------------------------------------------------------
+def _tg2d_error(N, U0, steps, nu=0.01):
+    s1 = 1.0 / (3 * nu + 0.5)
+    pb = O.Problem(d=2, n=(N, N), s1=s1)
+    P, u = synth.taylor_green_2d(N, U0)
+    f = O.init(pb, P, u)
+    O.run(pb, f, steps)
+    Pn, un, _ = O.macro(pb, f)
+    k = 2 * math.pi / N
+    dec = math.exp(-2 * nu * k * k * steps)
+    Pa, ua = synth.taylor_green_2d(N, U0 * dec)
+    X, Y = synth.grid_coords((N, N))
+    om = 2 * U0 * dec * k * np.sin(k * X) * np.sin(k * Y)
+    D = O.derived(pb, f)
+    return (O.rel_l2(ua, un), O.rel_l2(Pa - Pa.mean(), Pn - Pn.mean()),
+            O.rel_l2(om, D["omega"][0]))
+
+
+def test_taylor_green_2d_second_order():
+    """2D TG under diffusive scaling (U0 ~ dx, steps ~ dx^-2): the error of u,
+    P - mean(P) and omega falls by about 4 per halving of dx."""
+    e = [_tg2d_error(N, U0, st) for N, U0, st in ((32, 0.02, 250), (64, 0.01, 1000),
+                                                  (128, 0.005, 4000))]
+    for fld in range(3):
+        for a, b in zip(e[:-1], e[1:]):
+            assert 3.5 < a[fld] / b[fld] < 4.5, (fld, e)
+    assert e[1][0] < 0.02 and e[1][1] < 0.03 and e[1][2] < 0.03
+
+
+def test_taylor_green_3d_stokes_decay_second_order():
+    """3D TG at small U0 decays as exp(-3 nu k^2 t) (Stokes limit)."""
+    errs = []
+    nu = 0.01
+    for N, st in ((8, 100), (16, 400)):
+        s1 = 1.0 / (4 * nu + 0.5)
+        pb = O.Problem(d=3, n=(N, N, N), s1=s1, with_rho=False)
+        U0 = 1e-6
+        P, u = synth.taylor_green_3d(N, U0)
+        f = O.init(pb, P, u)
+        O.run(pb, f, st)
+        _, un, _ = O.macro(pb, f)
+        k = 2 * math.pi / N
+        errs.append(O.rel_l2(u * math.exp(-3 * nu * k * k * st), un))
+    assert errs[1] < 0.01
+    assert 3.3 < errs[0] / errs[1] < 4.7, errs
+
+
+def test_poiseuille_matches_paper():
+    """Sec. 4.1: E(u1) printed as 5.9427e-4; du1/dy, S_xy, omega exact up to
+    FP64 rounding (the paper quotes 9.75e-17; in FP64 the f^ne cancellation
+    with f ~ 0.5 leaves a floor of a few 1e-10)."""
+    g = _gold("paper_numbers.json")["poiseuille"]
+    N, nu, F1, s1 = g["N"], g["nu"], g["F1"], g["s1"]
+    dx = 1.0 / N
+    dt = (1 / s1 - 0.5) * dx * dx / (3 * nu)  # Eq. 3-13a with c_s^2 = dx^2/(3 dt^2)
+    F = np.zeros((2, N * N))
+    F[0] = F1
+    pb = O.Problem(d=2, n=(N, N), s1=s1, wall=(0, 1, 0), dx=dx, dt=dt, force=F)
+    f = O.init(pb, *synth.rest_state(N * N, 2))
+    O.run(pb, f, 22000)
+    _, un, _ = O.macro(pb, f)
+    D = O.derived(pb, f)
+    y = (np.arange(N) + 0.5) * dx
+    ua = np.repeat(F1 / (2 * nu) * (y - y * y), N)
+    gy = np.repeat(F1 / (2 * nu) * (1 - 2 * y), N)
+    assert O.rel_l2(ua, un[0]) == pytest.approx(g["E_u1"], rel=2e-3)
+    assert np.abs(un[1]).max() < 1e-13
+    assert O.rel_l2(gy, D["G"][0, 1]) < 1e-9
+    assert O.rel_l2(gy / 2, D["S"][1]) < 1e-9
+    assert O.rel_l2(-gy, D["omega"][0]) < 1e-9
+    assert np.abs(D["div"]).max() < 1e-12
+
+
+def _four_roll_mill(N, s1, U0=1e-4, nu=0.01, T=800.0):
+    dx = 2 * math.pi / N
+    dt = (1 / s1 - 0.5) * dx * dx / (3 * nu)
+    F = synth.four_roll_mill_force(N, U0, nu, dx)
+    pb = O.Problem(d=2, n=(N, N), s1=s1, dx=dx, dt=dt, force=F, with_rho=False)
+    f = O.init(pb, *synth.rest_state(N * N, 2))
+    O.run(pb, f, int(T / dt))
+    _, un, _ = O.macro(pb, f)
+    D = O.derived(pb, f)
+    X, Y = synth.grid_coords((N, N))
+    X, Y = X * dx, Y * dx
+    u1 = U0 * np.sin(X) * np.cos(Y)
+    u2 = -U0 * np.cos(X) * np.sin(Y)
+    Sxx = U0 * np.cos(X) * np.cos(Y)
+    om = 2 * U0 * np.sin(X) * np.sin(Y)
+    return dict(E_u1=O.rel_l2(u1, un[0]), E_u2=O.rel_l2(u2, un[1]),
+                E_Sxx=O.rel_l2(Sxx, D["S"][0]), E_Syy=O.rel_l2(-Sxx, D["S"][2]),
+                E_omega=O.rel_l2(om, D["omega"][0]), div=np.abs(D["div"]).max())
+
+
+def test_four_roll_mill_table1():
+    """Table 1 at 64^2 for s1 = 0.7, 1.2, 1.7 (within 0.1%)."""
+    g = _gold("paper_numbers.json")["four_roll_mill_table1"]
+    for j, s1 in enumerate(g["s1"]):
+        got = _four_roll_mill(g["N"], s1)
+        for key in ("E_u1", "E_u2", "E_Sxx", "E_Syy", "E_omega"):
+            assert got[key] == pytest.approx(g[key][j], rel=1e-3), (s1, key, got[key])
+
+
+def test_four_roll_mill_second_order():
+    """Fig. 13: second-order convergence of u, S and omega (N = 16, 32, 64)."""
+    e = [_four_roll_mill(N, 1.2) for N in (16, 32, 64)]
+    for key in ("E_u1", "E_Sxx", "E_omega"):
+        for a, b in zip(e[:-1], e[1:]):
+            assert 3.6 < a[key] / b[key] < 4.4, (key, a[key], b[key])
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_lid_couette_is_exact(d):
+    """A lid moving over a channel (Couette flow) has the linear profile
+    u = U (h + 1/2)/H; anti-halfway bounce-back reproduces it exactly."""
+    H, U = 12, 1e-3
+    if d == 2:
+        n, wall = (4, H), (0, 1, 0)
+    else:
+        n, wall = (3, 4, H), (0, 0, 1)
+    pb = O.Problem(d=d, n=n, s1=1.0, wall=wall, lid=True, lid_u=(U, 0, 0))
+    f = O.init(pb, *synth.rest_state(pb.N, d))
+    O.run(pb, f, 6000)
+    _, un, _ = O.macro(pb, f)
+    h = synth.grid_coords(n)[d - 1]
+    ua = U * (h + 0.5) / H
+    assert np.abs(un[0] - ua).max() < 1e-12 * U * 1e3
+    assert np.abs(un[1:]).max() < 1e-14
+
+
+def test_channel_3d_poiseuille():
+    """Body-force channel in D3Q7 with walls on z: parabolic profile, error
+    of order dx^2, and exact linear shear stress from f^ne."""
+    errs = []
+    for H in (8, 16):
+        nu, F = 1.0 / 12.0, 1e-6
+        s1 = 1.0 / (4 * nu + 0.5)
+        n = (3, 3, H)
+        N = 9 * H
+        Fld = np.zeros((3, N))
+        Fld[0] = F
+        pb = O.Problem(d=3, n=n, s1=s1, wall=(0, 0, 1), force=Fld)
+        f = O.init(pb, *synth.rest_state(N, 3))
+        O.run(pb, f, 40 * H * H)
+        _, un, _ = O.macro(pb, f)
+        D = O.derived(pb, f)
+        z = synth.grid_coords(n)[2] + 0.5
+        ua = F / (2 * nu) * z * (H - z)
+        errs.append(O.rel_l2(ua, un[0]))
+        gz = F / (2 * nu) * (H - 2 * z)
+        assert O.rel_l2(gz, D["G"][0, 2]) < 1e-8
+    assert errs[1] < 2e-3
+    assert errs[0] / errs[1] > 3.5 or errs[1] < 1e-12
+
+
+def test_mask_geometry_brute_force():
+    """Cavity masks: bit i when the link along c_i leaves the box; bit 7 on
+    links through the lid (the + face of the last axis)."""
+    nx, ny = 5, 4
+    pb = O.Problem(d=2, n=(nx, ny), s1=1.0, wall=(1, 1, 0), lid=True)
+    m = O.mask(pb).reshape(ny, nx)
+    for y in range(ny):
+        for x in range(nx):
+            want = 0
+            want |= (x == nx - 1) << 1
+            want |= (y == ny - 1) << 2
+            want |= (x == 0) << 3
+            want |= (y == 0) << 4
+            want |= (y == ny - 1) << 7
+            assert m[y, x] == want, (x, y)
+    n3 = (3, 4, 2)
+    pb = O.Problem(d=3, n=n3, s1=1.0, wall=(1, 0, 1), lid=True)
+    m = O.mask(pb).reshape(n3[2], n3[1], n3[0])
+    for z in range(n3[2]):
+        for y in range(n3[1]):
+            for x in range(n3[0]):
+                want = ((x == n3[0] - 1) << 1) | ((x == 0) << 2)
+                want |= ((z == n3[2] - 1) << 5) | ((z == 0) << 6)
+                want |= (z == n3[2] - 1) << 7
+                assert m[z, y, x] == want
