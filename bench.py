@@ -1,0 +1,354 @@
+"""Benchmark of the MDF-LBM fused MRT collide-and-stream step on GB300.
+
+Workload (the 4096^2 periodic 2D case): Taylor-Green vortex (U0 = 0.01) plus
+8 seeded divergence-free Fourier modes (seed 2108), D2Q5 x 3 distribution
+sets (alpha = 0, 1, 2), FP32 rest-shifted population storage, FP32 collision
+arithmetic, nu = 0.01 (s1 = 1/0.53), s2 from the paper's rule.
+
+One benchmark step = one epilogue period: 100 lattice updates, the first of
+which also writes the derived fields (P, u, du/dx, div, S, sigma, omega) of
+Eq. 2-7, 3-15 .. 3-19 in FP64.  value = lattice updates per second of the
+whole job in millions (MLUPS).  The populations (2 x 1.0 GB) are far larger
+than the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mdf|reference]
+
+Under torchrun each rank advances its own lattice (replicas; the method
+needs no exchange between independent lattices): value = sum over ranks of
+node updates / max over ranks of the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % HBM roofline vs FP64 oracle error; time-to-steady (warm vs cold)"
+N_GRID = 4096
+EPI_EVERY = 100
+NU = 0.01
+S1 = 1.0 / (3 * NU + 0.5)
+WORKLOAD = ("2D Taylor-Green + 8 seeded divergence-free modes (seed 2108), periodic "
+            "4096x4096, D2Q5 x 3 sets, FP32 rest-shifted storage, FP32 arithmetic, "
+            "epilogue every 100 steps")
+KERNEL_SOURCES = ("paper_2108_08591_gb300/csrc/mdf_kernels.cuh",
+                  "paper_2108_08591_gb300/csrc/mdf_lattice.cuh")
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _config(n_gpus: int, storage: str):
+    return {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "lattice": "D2Q5", "sets": 3,
+            "storage": storage, "steps_per_bench_step": EPI_EVERY,
+            "global_batch": n_gpus, "parallelism": f"replicas x{n_gpus}",
+            "l2": "inputs larger than L2 (2 x 1.0 GB populations), no flush"}
+
+
+def _kernel_sha() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_sha: str):
+    """DRAM bytes per launch of the step kernel from the committed ncu
+    summary, or None when the kernel changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if t.get("kernel_sha") != kernel_sha:
+        return None
+    return t.get("dram_bytes_per_launch_4096")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v == "Active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+def cpu_oracle_sample(steps: int = 2, warmup: int = 1):
+    """Time the FP64 CPU oracle, as it stands, on the benchmark workload:
+    the full 4096^2 lattice, `steps` timed updates after `warmup`."""
+    import oracle
+    import synth
+    P, u = synth.tg_plus_modes(N_GRID, U0=0.01, seed=2108)
+    pb = oracle.Problem(d=2, n=(N_GRID, N_GRID), s1=S1)
+    f = oracle.init(pb, P, u)
+    del P, u
+    oracle.run(pb, f, warmup)
+    t0 = time.perf_counter()
+    oracle.run(pb, f, steps)
+    dt = time.perf_counter() - t0
+    return {"value": N_GRID * N_GRID * steps / dt / 1e6, "unit": "MLUPS",
+            "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{steps} FP64 oracle updates of the full 4096^2 D2Q5x3 lattice "
+                      f"after {warmup} warm-up, OpenMP threads = {oracle.threads()}",
+            "seconds": dt}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import synth
+    oracle.build()
+    P, u = synth.tg_plus_modes(N_GRID, U0=0.01, seed=2108)
+    pb = oracle.Problem(d=2, n=(N_GRID, N_GRID), s1=S1)
+    f = oracle.init(pb, P, u)
+    del P, u
+    for _ in range(args.warmup):
+        oracle.run(pb, f, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.run(pb, f, 1)
+    dt = time.perf_counter() - t0
+    mlups = N_GRID * N_GRID * args.steps / dt / 1e6
+    cores = oracle.threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": mlups, "unit": "MLUPS",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(args.gpus, "f64 (oracle)"),
+        "cpu_baseline": {"value": mlups, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                         "sample": "each step: one FP64 oracle update of the full 4096^2 "
+                                   "D2Q5x3 lattice on the host cores"},
+        "e2e": {"value": mlups, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_mdf(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2108_08591_gb300 import Lattice, _build
+
+    rank, world, local = _dist()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+
+    P, u = synth.tg_plus_modes(N_GRID, U0=0.01, seed=2108)
+    N = N_GRID * N_GRID
+    stream = torch.cuda.current_stream()
+    lat = Lattice((N_GRID, N_GRID), s1=S1, storage=args.storage, stream=stream)
+    lat.init(P, u)
+    info = lat.info
+    fields = lat.alloc_fields(("P", "u", "G", "div", "S", "sigma", "omega"))
+
+    def bench_step(ev_a=None, ev_b=None):
+        lat.step_fields(1, fields)  # fused epilogue update
+        if ev_a is not None:
+            ev_a.record(stream)
+        lat.step(EPI_EVERY - 1)  # plain updates (CUDA-graph chunks)
+        if ev_b is not None:
+            ev_b.record(stream)
+
+    for _ in range(args.warmup):
+        bench_step()
+    torch.cuda.synchronize()
+
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    with sampler:
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        start.record(stream)
+        for k in range(args.steps):
+            bench_step(*evs[k])
+        stop.record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+    elapsed_ms = start.elapsed_time(stop)
+    plain_ms = sum(a.elapsed_time(b) for a, b in evs) / (args.steps * (EPI_EVERY - 1))
+    clocks = sampler.summary()
+
+    updates_local = args.steps * EPI_EVERY * N
+    t_max = elapsed_ms
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = updates_local * world / (t_max / 1e3) / 1e6
+
+    # end to end through the C-ABI with host buffers: every step copies the
+    # step's inputs (P, u) from pinned host memory, runs the 100 updates with
+    # the fused epilogue and reads (P, u) back to pinned host memory
+    e2e_steps = max(1, min(args.steps, 5))
+    Ph = torch.from_numpy(P).pin_memory().numpy()
+    uh = torch.from_numpy(np.ascontiguousarray(u)).pin_memory().numpy()
+    outP = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    outu = torch.empty((2, N), dtype=torch.float64).pin_memory().numpy()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.init(Ph, uh)
+        bench_step()
+        lat.fields_host(("P", "u"), out={"P": outP, "u": outu})
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = e2e_steps * EPI_EVERY * N * world / e2e_s / 1e6
+    lat.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    peak, peak_kind = _peaks()
+    bytes_per_launch = info.bytes_per_update * N
+    achieved = bytes_per_launch / (plain_ms / 1e3) / 1e9
+    sha = _kernel_sha()
+    traffic = _traffic(sha)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_oracle_sample()
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f16": "f16 storage / f32", "bf16": "bf16 storage / f32",
+                  "f64": "f64"}[args.storage],
+        "data": "synthetic", "config": _config(world, args.storage),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
+                     "kernel": "k_update<D2Q5,float,MODE_STEP,periodic>",
+                     "algorithmic_bytes_per_launch": bytes_per_launch,
+                     "avg_launch_ms": plain_ms, "kernel_sha": sha},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "MLUPS", "steps": e2e_steps,
+                "h2d_bytes_per_step": int(P.nbytes + u.nbytes),
+                "d2h_bytes_per_step": int(outP.nbytes + outu.nbytes)},
+        "gpu_launches": args.steps * EPI_EVERY,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("mdf", "reference"), default="mdf")
+    ap.add_argument("--storage", choices=("f32", "f16", "bf16"), default="f32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "mdf":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_mdf(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * mdf.h -- C-ABI of the GB300 (sm_103a) MDF-LBM library.
+ *
+ * The library advances the multiple-distribution-function lattice Boltzmann
+ * method of Chai, Shi & Zhan (arXiv 2108.08591) for the incompressible
+ * Navier-Stokes equations written as d+1 coupled convection-diffusion
+ * equations (Eq. 2-2): one D2Q5 (2D) or D3Q7 (3D) distribution set per
+ * equation, the MRT collision Lambda = M^-1 S_d M (Eq. 4-1 .. 4-3) and the
+ * evolution of Eq. 3-21 (diffusive scaling, lattice units dx = dt = c = 1).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns an mdf_status; nothing aborts the process.  On an
+ *     error, mdf_last_error(h) (or mdf_last_error(NULL) for a failed create)
+ *     returns a human-readable message.
+ *   - Node order is x fastest: n = x + nx*(y + ny*z).  A scalar field is
+ *     [N] doubles, a vector field [d][N], with N = nx*ny*nz and no padding.
+ *   - Device pointers passed in are owned by the caller and must stay valid
+ *     until the work enqueued on the library's stream has finished.
+ *   - All GPU work is enqueued on the stream given at create time (stream
+ *     ordered, asynchronous) unless a function says it synchronises.
+ *   - Lattice units: x_j = j, dt = 1; P0 = rho0 = 1 is the rest state.
+ */
+#ifndef MDF_H
+#define MDF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mdf_s *mdf_t;
+
+typedef enum {
+    MDF_OK = 0,
+    MDF_EINVAL = 1,          /* bad argument (null, size, rate outside (0,2), ...) */
+    MDF_ENOMEM = 2,          /* device or host allocation failed */
+    MDF_ECUDA = 3,           /* a CUDA call failed; see mdf_last_error */
+    MDF_EDIVERGED = 4,       /* a reduction met a non-finite value */
+    MDF_ETIMEOUT = 5,        /* a bounded device wait gave up */
+    MDF_ENOTCONVERGED = 6,   /* step cap reached before the tolerance */
+    MDF_EUNSUPPORTED = 7,    /* valid but not built (lattice, storage, ...) */
+    MDF_EIO = 8              /* checkpoint file error or checksum mismatch */
+} mdf_status;
+
+/* Population storage.  Populations are stored shifted by the rest state
+ * f_rest = f^eq(P0 = 1, u = 0) (Eq. 2-4), so the stored numbers are small;
+ * all collision arithmetic is FP32 except for MDF_F64 (FP64 throughout). */
+enum { MDF_F32 = 0, MDF_F16 = 1, MDF_BF16 = 2, MDF_F64 = 3 };
+
+/* Where a caller's array lives. */
+enum { MDF_HOST = 0, MDF_DEVICE = 1 };
+
+typedef struct {
+    int nx, ny, nz;          /* nodes per axis; nz = 1 when d = 2 */
+} mdf_grid;
+
+typedef struct {
+    double s0, s1, s2;       /* S_d = diag(s0, s1.., s2..) of Eq. 4-3; s2 < 0 selects
+                                the paper's rule s2 = 8(2 - s1)/(8 - s1) (Sec. 4.1).
+                                Viscosity nu = (1/s1 - 1/2) c_s^2 (Eq. 3-13a). */
+} mdf_rates;
+
+typedef struct {
+    int wall[3];             /* per axis: 0 periodic, 1 halfway walls at both ends */
+    int lid;                 /* 1: the + face of the last axis moves with lid_u */
+    double lid_u[3];         /* lid velocity (lattice units) */
+} mdf_bc;
+
+typedef struct {
+    int storage;             /* MDF_F32, MDF_F16, MDF_BF16 or MDF_F64 */
+    int with_rho;            /* 1: also carry the alpha = 0 (continuity) set, so d+1
+                                sets are advanced; 0: only the d velocity sets (the
+                                paper shows alpha = 0 can be omitted, Sec. 3.2) */
+    void *stream;            /* cudaStream_t to enqueue on; NULL = legacy default */
+} mdf_opts;
+
+/* Derived-field outputs, each a caller-owned array of doubles or NULL.
+ * Layout (N nodes, d dimensions):
+ *   P[N]        pressure, Eq. 3-15 (R = 0)
+ *   u[d][N]     velocity, Eq. 2-7
+ *   rho[N]      zeroth moment of the alpha = 0 set (needs with_rho = 1)
+ *   G[d][d][N]  G[a][b] = du_a/dx_b, Eq. 3-16
+ *   div[N]      velocity divergence, Eq. 3-16a
+ *   S[k][N]     strain rate, Eq. 3-17, upper triangle in row order
+ *               (2D: xx, xy, yy; 3D: xx, xy, xz, yy, yz, zz)
+ *   sigma[k][N] shear stress, Eq. 3-17a, same order (rho0 = 1)
+ *   omega[.][N] vorticity, Eq. 3-18/3-19: 2D du2/dx - du1/dy; 3D (wx, wy, wz)
+ * where = MDF_DEVICE: device pointers, filled asynchronously.
+ * where = MDF_HOST: host pointers; the call stages through device memory
+ * and synchronises the stream before returning. */
+typedef struct {
+    double *P, *u, *rho, *G, *div, *S, *sigma, *omega;
+    int where;
+} mdf_fields_t;
+
+/* Static facts about a handle. */
+typedef struct {
+    int d, q, nsets, storage;
+    int nx, ny, nz, pitch;   /* pitch: padded x extent of the device arrays */
+    long long nodes;         /* nx*ny*nz */
+    long long step;          /* time steps taken since the last init/load */
+    double bytes_per_update; /* algorithmic bytes per node update: one read and one
+                                write of every population (2 q nsets sizeof(T)) */
+    double s0, s1, s2;
+} mdf_info_t;
+
+/*
+ * mdf_create -- allocate a lattice of d+1 (or d) distribution sets.
+ *   g: grid (nx, ny >= 2; nz = 1 for d = 2, nz >= 2 for d = 3);
+ *   d: 2 (D2Q5, Sec. 2.2) or 3 (D3Q7, Sec. 2.2, MRT basis read analogously
+ *      to Eq. 4-2);  r: relaxation rates, each in (0, 2);
+ *   bc: periodic axes or anti-halfway bounce-back walls (Sec. 4), optional
+ *      moving lid;  o: storage, sets and stream.
+ * The library allocates and owns the population buffers (two of
+ * 2*q*nsets*pitch*ny*nz elements), the link mask and its scratch.  The state
+ * is undefined until mdf_init or mdf_load.  Errors: MDF_EINVAL,
+ * MDF_EUNSUPPORTED, MDF_ENOMEM, MDF_ECUDA; *h is NULL on error.
+ */
+mdf_status mdf_create(mdf_t *h, const mdf_grid *g, int d, const mdf_rates *r,
+                      const mdf_bc *bc, const mdf_opts *o);
+
+/* Release every resource of h (synchronises its stream).  NULL is ignored. */
+void mdf_destroy(mdf_t h);
+
+/*
+ * mdf_init -- set f = f^eq(P, u) at every node (Sec. 4: initialisation by
+ * the equilibrium of Eq. 2-4), for the alpha = 0 set with ubar_0 = rho0 = 1.
+ *   P[N], u[d][N]: FP64 arrays in `where` memory (MDF_HOST or MDF_DEVICE).
+ * Resets the step counter.  Host arrays are copied before the call returns;
+ * device arrays must stay valid until the stream reaches this work.
+ */
+mdf_status mdf_init(mdf_t h, const double *P, const double *u, int where);
+
+/*
+ * mdf_set_force -- body force Fbar_alpha(x) of Eq. 2-6 (F_i = w_i Fbar_alpha),
+ * added as dt w_i Fbar_alpha in Eq. 3-21.  F[d][N] FP64 in `where` memory,
+ * stored on the device in FP32; NULL removes the force.
+ */
+mdf_status mdf_set_force(mdf_t h, const double *F, int where);
+
+/* mdf_step -- advance n >= 0 time steps of Eq. 3-21 with streaming. */
+mdf_status mdf_step(mdf_t h, long long n);
+
+/*
+ * mdf_step_fields -- advance n >= 1 steps; the first update also writes the
+ * derived fields (Eq. 2-7, 3-15 .. 3-19) of the state it starts from, in the
+ * same pass over memory.  Equivalent to mdf_fields(h, out) followed by
+ * mdf_step(h, n).  out->where must be MDF_DEVICE.
+ */
+mdf_status mdf_step_fields(mdf_t h, long long n, const mdf_fields_t *out);
+
+/* mdf_fields -- derived fields of the current state (no step taken). */
+mdf_status mdf_fields(mdf_t h, const mdf_fields_t *out);
+
+/* mdf_moments -- P (Eq. 3-15), u (Eq. 2-7) and rho (nullable) on the device. */
+mdf_status mdf_moments(mdf_t h, double *P, double *u, double *rho);
+
+/* mdf_gradients -- Eq. 3-16 .. 3-19 on the device; each pointer nullable. */
+mdf_status mdf_gradients(mdf_t h, double *G, double *div, double *S, double *sigma,
+                         double *omega);
+
+/*
+ * mdf_sums -- sums[a] = sum over nodes of ubar_alpha (Eq. 2-7) for every
+ * carried set a (alpha = 0 first when with_rho = 1), reduced in FP64 in a
+ * fixed order (deterministic).  sums: host array of nsets doubles.
+ * Synchronises the stream.  MDF_EDIVERGED if a value is not finite.
+ */
+mdf_status mdf_sums(mdf_t h, double *sums);
+
+/*
+ * mdf_residual -- steady-state residual r = ||u - u_prev||_2 / ||u||_2 over
+ * all nodes in FP64, where u_prev is the velocity at the previous
+ * mdf_residual call (r = +inf on the first call after init/load).  *r on the
+ * host.  Synchronises.  MDF_EDIVERGED if u is not finite.
+ */
+mdf_status mdf_residual(mdf_t h, double *r);
+
+/* mdf_mask -- link mask [N] bytes to host memory: bit i set when the link
+ * from the node along c_i crosses a wall; bit 7 when it crosses the lid.
+ * Synchronises. */
+mdf_status mdf_mask(mdf_t h, unsigned char *host_out);
+
+/* mdf_save / mdf_load -- raw populations plus a header (grid, d, sets,
+ * storage, rates, boundary, step) and an FNV-1a checksum.  Load requires a
+ * handle created with the same configuration; MDF_EIO on a mismatch or a
+ * corrupt file.  Both synchronise.  A resumed run is bit-identical. */
+mdf_status mdf_save(mdf_t h, const char *path);
+mdf_status mdf_load(mdf_t h, const char *path);
+
+/* mdf_info -- static facts about h (host struct). */
+mdf_status mdf_info(mdf_t h, mdf_info_t *out);
+
+/* mdf_sync -- wait for all work enqueued on h's stream. */
+mdf_status mdf_sync(mdf_t h);
+
+/* mdf_last_error -- message of the last failure on h (NULL: of the calling
+ * thread's last failed mdf_create).  Never NULL. */
+const char *mdf_last_error(mdf_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDF_H */

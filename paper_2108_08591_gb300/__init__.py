@@ -1,0 +1,205 @@
+"""GB300-native MDF-LBM (Chai, Shi & Zhan, arXiv 2108.08591).
+
+Thin Python binding over the C-ABI of ``libmdf.so`` (include/mdf.h).  Every
+step of the method runs in the library's CUDA kernels; this module only
+marshals arguments.  PyTorch supplies device memory for outputs and the
+CUDA stream the library enqueues on.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Dict, Iterable, Optional, Sequence
+
+import numpy as np
+
+from . import _lib
+from ._lib import DEVICE, HOST, MdfError, STORAGE
+
+__all__ = ["Lattice", "MdfError", "FIELD_NAMES", "field_shapes", "s2_rule"]
+
+FIELD_NAMES = ("P", "u", "rho", "G", "div", "S", "sigma", "omega")
+
+
+def s2_rule(s1: float) -> float:
+    """The paper's default s2 = 8(2 - s1)/(8 - s1) (Sec. 4.1)."""
+    return 8.0 * (2.0 - s1) / (8.0 - s1)
+
+
+def field_shapes(d: int, N: int) -> Dict[str, tuple]:
+    nsym = 3 if d == 2 else 6
+    return {"P": (N,), "u": (d, N), "rho": (N,), "G": (d, d, N), "div": (N,),
+            "S": (nsym, N), "sigma": (nsym, N), "omega": ((1 if d == 2 else 3), N)}
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a contiguous FP64 numpy array or torch tensor (host or device)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.dtype == np.float64 and a.flags.c_contiguous, "need contiguous float64"
+        return a.ctypes.data
+    assert a.dtype.is_floating_point and a.element_size() == 8 and a.is_contiguous(), \
+        "need a contiguous float64 tensor"
+    return a.data_ptr()
+
+
+def _is_device(a) -> bool:
+    return not isinstance(a, np.ndarray) and a.is_cuda
+
+
+class Lattice:
+    """One MDF-LBM lattice: d + 1 (or d) D2Q5/D3Q7 distribution sets.
+
+    shape: (nx, ny) or (nx, ny, nz).  s1 sets the viscosity
+    nu = (1/s1 - 1/2) c_s^2 (Eq. 3-13a); s2 < 0 picks the paper's rule.
+    wall: per-axis halfway walls (anti-halfway bounce-back), lid: the + face
+    of the last axis moves with lid_u.  storage: 'f32', 'f16', 'bf16', 'f64'.
+    """
+
+    def __init__(self, shape: Sequence[int], s1: float, s2: float = -1.0, s0: float = 1.0,
+                 wall: Sequence[int] = (0, 0, 0), lid: bool = False,
+                 lid_u: Sequence[float] = (0.0, 0.0, 0.0), storage: str = "f32",
+                 with_rho: bool = True, stream=None):
+        import torch
+
+        self._lib = _lib.load()
+        self.d = len(shape)
+        if self.d not in (2, 3):
+            raise ValueError("shape must have 2 or 3 entries")
+        nx, ny = int(shape[0]), int(shape[1])
+        nz = int(shape[2]) if self.d == 3 else 1
+        self.shape = tuple(int(v) for v in shape)
+        self.N = nx * ny * nz
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        g = _lib.Grid(nx, ny, nz)
+        r = _lib.Rates(s0, s1, s2)
+        bc = _lib.BC()
+        w = list(wall) + [0] * (3 - len(wall))
+        bc.wall[:] = [int(v) for v in w[:3]]
+        bc.lid = int(bool(lid))
+        lu = list(lid_u) + [0.0] * (3 - len(lid_u))
+        bc.lid_u[:] = [float(v) for v in lu[:3]]
+        o = _lib.Opts(STORAGE[storage], int(bool(with_rho)), ctypes.c_void_p(sptr))
+        h = ctypes.c_void_p()
+        _lib.check(self._lib.mdf_create(ctypes.byref(h), ctypes.byref(g), self.d,
+                                        ctypes.byref(r), ctypes.byref(bc), ctypes.byref(o)))
+        self._h = h
+        self.with_rho = bool(with_rho)
+        self.storage = storage
+        self._keep = []  # device inputs that must outlive queued work
+
+    # ------------------------------------------------------------------
+    def _check(self, status: int):
+        _lib.check(status, self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mdf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def info(self) -> _lib.Info:
+        inf = _lib.Info()
+        self._check(self._lib.mdf_info(self._h, ctypes.byref(inf)))
+        return inf
+
+    # ------------------------------------------------------------------
+    def init(self, P, u):
+        """f = f^eq(P, u); P [N], u [d][N] FP64, numpy (host) or CUDA tensors."""
+        dev = _is_device(P)
+        if dev != _is_device(u):
+            raise ValueError("P and u must both be on the host or both on the device")
+        if dev:
+            self._keep = [P, u]
+        self._check(self._lib.mdf_init(self._h, _ptr(P), _ptr(u), DEVICE if dev else HOST))
+
+    def set_force(self, F):
+        """Body force Fbar [d][N] (Eq. 2-6); None removes it."""
+        if F is None:
+            self._check(self._lib.mdf_set_force(self._h, None, HOST))
+            return
+        self._check(self._lib.mdf_set_force(self._h, _ptr(F), DEVICE if _is_device(F) else HOST))
+
+    def step(self, n: int = 1):
+        self._check(self._lib.mdf_step(self._h, int(n)))
+
+    def _fields_struct(self, out: Dict[str, object], where: int) -> _lib.Fields:
+        f = _lib.Fields()
+        for k, v in out.items():
+            setattr(f, k, _ptr(v))
+        f.where = where
+        return f
+
+    def alloc_fields(self, names: Iterable[str] = FIELD_NAMES):
+        import torch
+        shapes = field_shapes(self.d, self.N)
+        return {k: torch.empty(shapes[k], dtype=torch.float64, device="cuda") for k in names
+                if k != "rho" or self.with_rho}
+
+    def step_fields(self, n: int, out: Dict[str, object]):
+        """n updates; the first also writes the fields of the starting state."""
+        f = self._fields_struct(out, DEVICE)
+        self._check(self._lib.mdf_step_fields(self._h, int(n), ctypes.byref(f)))
+
+    def fields(self, names: Iterable[str] = ("P", "u"), out: Optional[Dict[str, object]] = None):
+        """Derived fields of the current state as CUDA tensors (Eq. 2-7, 3-15 .. 3-19)."""
+        if out is None:
+            out = self.alloc_fields(names)
+        f = self._fields_struct(out, DEVICE)
+        self._check(self._lib.mdf_fields(self._h, ctypes.byref(f)))
+        return out
+
+    def fields_host(self, names: Iterable[str] = ("P", "u"), out=None) -> Dict[str, np.ndarray]:
+        """Derived fields copied to host numpy arrays (synchronises)."""
+        shapes = field_shapes(self.d, self.N)
+        if out is None:
+            out = {k: np.empty(shapes[k]) for k in names}
+        f = self._fields_struct(out, HOST)
+        self._check(self._lib.mdf_fields(self._h, ctypes.byref(f)))
+        return out
+
+    def moments(self):
+        o = self.fields(("P", "u", "rho") if self.with_rho else ("P", "u"))
+        return o["P"], o["u"], o.get("rho")
+
+    def gradients(self):
+        return self.fields(("G", "div", "S", "sigma", "omega"))
+
+    def sums(self) -> np.ndarray:
+        out = np.zeros(4)
+        self._check(self._lib.mdf_sums(self._h, out.ctypes.data))
+        return out[: self.info.nsets].copy()
+
+    def residual(self) -> float:
+        out = np.zeros(1)
+        self._check(self._lib.mdf_residual(self._h, out.ctypes.data))
+        return float(out[0])
+
+    def mask(self) -> np.ndarray:
+        m = np.zeros(self.N, dtype=np.uint8)
+        self._check(self._lib.mdf_mask(self._h, m.ctypes.data))
+        return m
+
+    def save(self, path: str):
+        self._check(self._lib.mdf_save(self._h, path.encode()))
+
+    def load(self, path: str):
+        self._check(self._lib.mdf_load(self._h, path.encode()))
+
+    def sync(self):
+        self._check(self._lib.mdf_sync(self._h))

@@ -1,0 +1,553 @@
+// Host side of the C-ABI declared in include/mdf.h: handle lifetime, buffer
+// management, launch sequencing (with CUDA-graph chunks for long runs),
+// FP64 reductions, checkpoints.  Every GPU step of the method runs in the
+// kernels of mdf_kernels.cuh; this file only marshals and sequences.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mdf.h"
+#include "mdf_internal.h"
+
+using namespace mdf;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+constexpr int kGraphChunk = 64;  // steps per captured graph (even: buffers return)
+
+size_t storage_bytes(int st) {
+  switch (st) {
+    case MDF_F32: return 4;
+    case MDF_F16: return 2;
+    case MDF_BF16: return 2;
+    case MDF_F64: return 8;
+  }
+  return 0;
+}
+
+}  // namespace
+
+struct mdf_s {
+  int d = 0, q = 0, nsets = 0, with_rho = 0, storage = 0;
+  int nx = 0, ny = 0, nz = 0, px = 0;
+  long long plane = 0, N = 0;
+  double s0 = 1, s1 = 1, s2 = 1;
+  mdf_bc bc{};
+  bool walls = false;
+  cudaStream_t stream = nullptr;
+  void *cur = nullptr, *nxt = nullptr;  // population buffers
+  uint8_t *mask = nullptr;
+  float *force = nullptr;
+  double *stage = nullptr;  // staging for host inputs/outputs
+  size_t stage_bytes = 0;
+  double *uprev = nullptr;  // residual memory [d][N]
+  bool have_prev = false;
+  double *partials = nullptr, *result = nullptr;
+  int *nonfinite = nullptr;
+  long long step = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};  // chunk starting from buffer 0 / 1
+  void *buf[2] = {nullptr, nullptr};
+  std::string err = "no error";
+
+  size_t pop_bytes() const { return (size_t)nsets * q * (size_t)plane * storage_bytes(storage); }
+};
+
+namespace {
+
+mdf_status fail(mdf_t h, mdf_status st, const char *fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  if (h) h->err = msg;
+  else g_create_error = msg;
+  return st;
+}
+
+#define CU(h, call)                                                                     \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail((h), MDF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+  } while (0)
+
+DevArgs base_args(const mdf_t h) {
+  DevArgs a;
+  std::memset(&a, 0, sizeof a);
+  a.fin = h->cur;
+  a.fout = h->nxt;
+  a.mask = h->walls ? h->mask : nullptr;
+  a.force = h->force;
+  a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.px = h->px;
+  a.plane = h->plane;
+  a.with_rho = h->with_rho;
+  a.s1 = h->s1; a.s2 = h->s2;
+  for (int b = 0; b < 3; ++b) a.lid_u[b] = h->bc.lid ? h->bc.lid_u[b] : 0.0;
+  a.partials = h->partials;
+  a.result = h->result;
+  a.nonfinite = h->nonfinite;
+  a.uprev = h->uprev;
+  return a;
+}
+
+cudaError_t launch_update(const mdf_t h, int mode, const DevArgs &a) {
+  return h->d == 2 ? launch_update_d2q5(h->storage, mode, h->walls, a, h->stream)
+                   : launch_update_d3q7(h->storage, mode, h->walls, a, h->stream);
+}
+
+cudaError_t launch_reduce(const mdf_t h, int kind, const DevArgs &a) {
+  return h->d == 2 ? launch_reduce_d2q5(h->storage, h->walls, kind, a, h->stream)
+                   : launch_reduce_d3q7(h->storage, h->walls, kind, a, h->stream);
+}
+
+void drop_graphs(mdf_t h) {
+  for (auto &g : h->graph)
+    if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+}
+
+mdf_status ensure_stage(mdf_t h, size_t bytes) {
+  if (h->stage_bytes >= bytes) return MDF_OK;
+  if (h->stage) { cudaStreamSynchronize(h->stream); cudaFree(h->stage); h->stage = nullptr; }
+  h->stage_bytes = 0;
+  cudaError_t e = cudaMalloc(&h->stage, bytes);
+  if (e != cudaSuccess) { cudaGetLastError(); return fail(h, MDF_ENOMEM, "staging %zu bytes: %s", bytes, cudaGetErrorString(e)); }
+  h->stage_bytes = bytes;
+  return MDF_OK;
+}
+
+// One plain update from cur to nxt, then swap.
+mdf_status one_update(mdf_t h, int mode, const mdf_fields_t *out) {
+  DevArgs a = base_args(h);
+  if (out) {
+    a.P = out->P; a.u = out->u; a.rho = out->rho; a.G = out->G; a.div = out->div;
+    a.S = out->S; a.sigma = out->sigma; a.omega = out->omega;
+  }
+  CU(h, launch_update(h, mode, a));
+  if (mode != MODE_FIELDS) { std::swap(h->cur, h->nxt); ++h->step; }
+  return MDF_OK;
+}
+
+// Capture kGraphChunk updates starting from buffer `which` into a graph.
+mdf_status build_graph(mdf_t h, int which) {
+  void *c0 = h->cur, *n0 = h->nxt;
+  h->cur = h->buf[which];
+  h->nxt = h->buf[1 - which];
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k) {
+      e = launch_update(h, MODE_STEP, base_args(h));
+      std::swap(h->cur, h->nxt);
+    }
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+    if (e == cudaSuccess) e = e2;
+  }
+  h->cur = c0;
+  h->nxt = n0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[which], g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    h->graph[which] = nullptr;
+    return fail(h, MDF_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+  }
+  return MDF_OK;
+}
+
+mdf_status run_steps(mdf_t h, long long n) {
+  // Graph chunks only on a real (non-legacy) stream: capture is not allowed
+  // on the legacy default stream.
+  const bool use_graph = h->stream != nullptr && n >= kGraphChunk;
+  while (use_graph && n >= kGraphChunk) {
+    const int which = h->cur == h->buf[0] ? 0 : 1;
+    if (!h->graph[which]) {
+      mdf_status st = build_graph(h, which);
+      if (st != MDF_OK) return st;
+    }
+    CU(h, cudaGraphLaunch(h->graph[which], h->stream));
+    n -= kGraphChunk;  // even chunk: cur/nxt end where they started
+    h->step += kGraphChunk;
+  }
+  for (; n > 0; --n) {
+    mdf_status st = one_update(h, MODE_STEP, nullptr);
+    if (st != MDF_OK) return st;
+  }
+  return MDF_OK;
+}
+
+bool fields_empty(const mdf_fields_t *o) {
+  return !(o->P || o->u || o->rho || o->G || o->div || o->S || o->sigma || o->omega);
+}
+
+mdf_status check_handle(mdf_t h) {
+  if (!h) return MDF_EINVAL;
+  return MDF_OK;
+}
+
+int nsym(int d) { return d == 2 ? 3 : 6; }
+
+uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t hsh = 1469598103934665603ull) {
+  for (size_t i = 0; i < n; ++i) { hsh ^= p[i]; hsh *= 1099511628211ull; }
+  return hsh;
+}
+
+struct CkptHeader {
+  char magic[8];
+  int32_t version, d, q, nsets, storage, nx, ny, nz, px, wall[3], lid;
+  double s0, s1, s2, lid_u[3];
+  int64_t step, payload;
+  uint64_t checksum;
+};
+
+}  // namespace
+
+extern "C" {
+
+mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
+                      const mdf_bc *bc, const mdf_opts *o) {
+  if (!out) return fail(nullptr, MDF_EINVAL, "null handle pointer");
+  *out = nullptr;
+  if (!g || !r) return fail(nullptr, MDF_EINVAL, "null grid or rates");
+  if (d != 2 && d != 3) return fail(nullptr, MDF_EINVAL, "d must be 2 or 3 (got %d)", d);
+  if (g->nx < 2 || g->ny < 2 || (d == 2 && g->nz != 1) || (d == 3 && g->nz < 2))
+    return fail(nullptr, MDF_EINVAL, "bad grid %d x %d x %d for d = %d", g->nx, g->ny, g->nz, d);
+  if ((long long)g->nx * g->ny * g->nz > (1LL << 40) || g->ny > 65535 || g->nz > 65535)
+    return fail(nullptr, MDF_EINVAL, "grid too large (ny, nz <= 65535)");
+  const double s1 = r->s1;
+  const double s2 = r->s2 < 0 ? 8.0 * (2.0 - s1) / (8.0 - s1) : r->s2;
+  if (!(s1 > 0 && s1 < 2) || !(s2 > 0 && s2 < 2) || !(r->s0 > 0 && r->s0 < 2))
+    return fail(nullptr, MDF_EINVAL, "relaxation rates must lie in (0, 2): s0=%g s1=%g s2=%g",
+                r->s0, s1, s2);
+  mdf_opts opts{};
+  opts.storage = MDF_F32;
+  opts.with_rho = 1;
+  if (o) opts = *o;
+  if (storage_bytes(opts.storage) == 0)
+    return fail(nullptr, MDF_EUNSUPPORTED, "unknown storage %d", opts.storage);
+
+  mdf_t h = new (std::nothrow) mdf_s;
+  if (!h) return fail(nullptr, MDF_ENOMEM, "host allocation");
+  h->d = d;
+  h->q = d == 2 ? 5 : 7;
+  h->with_rho = opts.with_rho ? 1 : 0;
+  h->nsets = d + h->with_rho;
+  h->storage = opts.storage;
+  h->nx = g->nx; h->ny = g->ny; h->nz = g->nz;
+  h->px = (g->nx + 31) / 32 * 32;
+  h->plane = (long long)h->px * g->ny * g->nz;
+  h->N = (long long)g->nx * g->ny * g->nz;
+  h->s0 = r->s0; h->s1 = s1; h->s2 = s2;
+  if (bc) h->bc = *bc;
+  for (int b = 0; b < 3; ++b) h->bc.wall[b] = (b < d && h->bc.wall[b]) ? 1 : 0;
+  h->walls = h->bc.wall[0] || h->bc.wall[1] || h->bc.wall[2];
+  if (h->bc.lid && !h->bc.wall[d - 1]) {
+    delete h;
+    return fail(nullptr, MDF_EINVAL, "a lid needs walls on the last axis");
+  }
+  h->stream = static_cast<cudaStream_t>(opts.stream);
+
+  const size_t pb = h->pop_bytes();
+  cudaError_t e = cudaMalloc(&h->buf[0], pb);
+  if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], pb);
+  if (e == cudaSuccess) e = cudaMalloc(&h->partials, sizeof(double) * kReduceBlocks * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&h->result, sizeof(double) * 4);
+  if (e == cudaSuccess) e = cudaMalloc(&h->nonfinite, sizeof(int));
+  if (e == cudaSuccess && h->walls) e = cudaMalloc(&h->mask, (size_t)h->plane);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, pb, h->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, pb, h->stream);
+  if (e == cudaSuccess && h->walls) {
+    e = cudaMemsetAsync(h->mask, 0, (size_t)h->plane, h->stream);
+    if (e == cudaSuccess) {
+      DevArgs a = base_args(h);
+      e = d == 2 ? launch_mask_d2q5(h->bc.wall, h->bc.lid, a, h->mask, h->stream)
+                 : launch_mask_d3q7(h->bc.wall, h->bc.lid, a, h->mask, h->stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    mdf_status st = e == cudaErrorMemoryAllocation ? MDF_ENOMEM : MDF_ECUDA;
+    fail(nullptr, st, "create: %s", cudaGetErrorString(e));
+    mdf_destroy(h);
+    return st;
+  }
+  h->cur = h->buf[0];
+  h->nxt = h->buf[1];
+  *out = h;
+  return MDF_OK;
+}
+
+void mdf_destroy(mdf_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
+  cudaFree(h->buf[0]); cudaFree(h->buf[1]); cudaFree(h->mask); cudaFree(h->force);
+  cudaFree(h->stage); cudaFree(h->uprev); cudaFree(h->partials); cudaFree(h->result);
+  cudaFree(h->nonfinite);
+  delete h;
+}
+
+mdf_status mdf_init(mdf_t h, const double *P, const double *u, int where) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!P || !u) return fail(h, MDF_EINVAL, "init: null P or u");
+  const size_t nb = sizeof(double) * (size_t)h->N;
+  DevArgs a = base_args(h);
+  if (where == MDF_HOST) {
+    mdf_status st = ensure_stage(h, nb * (1 + h->d));
+    if (st != MDF_OK) return st;
+    CU(h, cudaMemcpyAsync(h->stage, P, nb, cudaMemcpyHostToDevice, h->stream));
+    CU(h, cudaMemcpyAsync(h->stage + h->N, u, nb * h->d, cudaMemcpyHostToDevice, h->stream));
+    a.Pin = h->stage;
+    a.uin = h->stage + h->N;
+  } else if (where == MDF_DEVICE) {
+    a.Pin = P;
+    a.uin = u;
+  } else {
+    return fail(h, MDF_EINVAL, "init: bad `where` %d", where);
+  }
+  a.fout = h->cur;
+  CU(h, h->d == 2 ? launch_init_d2q5(h->storage, h->walls, a, h->stream)
+                  : launch_init_d3q7(h->storage, h->walls, a, h->stream));
+  if (where == MDF_HOST) CU(h, cudaStreamSynchronize(h->stream));
+  h->step = 0;
+  h->have_prev = false;
+  return MDF_OK;
+}
+
+mdf_status mdf_set_force(mdf_t h, const double *F, int where) {
+  if (check_handle(h)) return MDF_EINVAL;
+  CU(h, cudaStreamSynchronize(h->stream));
+  drop_graphs(h);  // captured launches hold the old force pointer
+  if (!F) {
+    cudaFree(h->force);
+    h->force = nullptr;
+    return MDF_OK;
+  }
+  if (!h->force) {
+    cudaError_t e = cudaMalloc(&h->force, sizeof(float) * (size_t)h->plane * h->d);
+    if (e != cudaSuccess) { cudaGetLastError(); h->force = nullptr; return fail(h, MDF_ENOMEM, "force: %s", cudaGetErrorString(e)); }
+    CU(h, cudaMemsetAsync(h->force, 0, sizeof(float) * (size_t)h->plane * h->d, h->stream));
+  }
+  const double *src = F;
+  const size_t nb = sizeof(double) * (size_t)h->N * h->d;
+  if (where == MDF_HOST) {
+    mdf_status st = ensure_stage(h, nb);
+    if (st != MDF_OK) return st;
+    CU(h, cudaMemcpyAsync(h->stage, F, nb, cudaMemcpyHostToDevice, h->stream));
+    src = h->stage;
+  } else if (where != MDF_DEVICE) {
+    return fail(h, MDF_EINVAL, "set_force: bad `where` %d", where);
+  }
+  CU(h, launch_pad_force(src, h->force, h->d, h->nx, h->ny, h->nz, h->px, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return MDF_OK;
+}
+
+mdf_status mdf_step(mdf_t h, long long n) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (n < 0) return fail(h, MDF_EINVAL, "step: n < 0");
+  return run_steps(h, n);
+}
+
+mdf_status mdf_step_fields(mdf_t h, long long n, const mdf_fields_t *out) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (n < 1 || !out) return fail(h, MDF_EINVAL, "step_fields: need n >= 1 and outputs");
+  if (out->where != MDF_DEVICE) return fail(h, MDF_EINVAL, "step_fields: outputs must be on the device");
+  if (out->rho && !h->with_rho) return fail(h, MDF_EINVAL, "rho requested without the alpha = 0 set");
+  mdf_status st = one_update(h, fields_empty(out) ? MODE_STEP : MODE_STEP_FIELDS, out);
+  if (st != MDF_OK) return st;
+  return run_steps(h, n - 1);
+}
+
+mdf_status mdf_fields(mdf_t h, const mdf_fields_t *out) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!out) return fail(h, MDF_EINVAL, "fields: null outputs");
+  if (out->rho && !h->with_rho) return fail(h, MDF_EINVAL, "rho requested without the alpha = 0 set");
+  if (fields_empty(out)) return MDF_OK;
+  if (out->where == MDF_DEVICE) return one_update(h, MODE_FIELDS, out);
+  if (out->where != MDF_HOST) return fail(h, MDF_EINVAL, "fields: bad `where`");
+  // host outputs: compute into staging, then copy each requested field back
+  const long long N = h->N;
+  const int d = h->d;
+  struct F { double *host; size_t count; } f[8] = {
+      {out->P, (size_t)N}, {out->u, (size_t)(d * N)}, {out->rho, (size_t)N},
+      {out->G, (size_t)(d * d * N)}, {out->div, (size_t)N}, {out->S, (size_t)(nsym(d) * N)},
+      {out->sigma, (size_t)(nsym(d) * N)}, {out->omega, (size_t)((d == 2 ? 1 : 3) * N)}};
+  size_t total = 0;
+  for (auto &x : f)
+    if (x.host) total += x.count;
+  mdf_status st = ensure_stage(h, total * sizeof(double));
+  if (st != MDF_OK) return st;
+  mdf_fields_t dev{};
+  dev.where = MDF_DEVICE;
+  double *p = h->stage;
+  double **slots[8] = {&dev.P, &dev.u, &dev.rho, &dev.G, &dev.div, &dev.S, &dev.sigma, &dev.omega};
+  for (int k = 0; k < 8; ++k)
+    if (f[k].host) { *slots[k] = p; p += f[k].count; }
+  st = one_update(h, MODE_FIELDS, &dev);
+  if (st != MDF_OK) return st;
+  for (int k = 0; k < 8; ++k)
+    if (f[k].host)
+      CU(h, cudaMemcpyAsync(f[k].host, *slots[k], f[k].count * sizeof(double),
+                            cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return MDF_OK;
+}
+
+mdf_status mdf_moments(mdf_t h, double *P, double *u, double *rho) {
+  mdf_fields_t o{};
+  o.P = P; o.u = u; o.rho = rho; o.where = MDF_DEVICE;
+  return mdf_fields(h, &o);
+}
+
+mdf_status mdf_gradients(mdf_t h, double *G, double *div, double *S, double *sigma,
+                         double *omega) {
+  mdf_fields_t o{};
+  o.G = G; o.div = div; o.S = S; o.sigma = sigma; o.omega = omega; o.where = MDF_DEVICE;
+  return mdf_fields(h, &o);
+}
+
+static mdf_status reduce(mdf_t h, int kind, double out[4]) {
+  DevArgs a = base_args(h);
+  CU(h, cudaMemsetAsync(h->nonfinite, 0, sizeof(int), h->stream));
+  CU(h, launch_reduce(h, kind, a));
+  CU(h, launch_reduce_final(a, kReduceBlocks, 4, h->stream));
+  int bad = 0;
+  CU(h, cudaMemcpyAsync(out, h->result, sizeof(double) * 4, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaMemcpyAsync(&bad, h->nonfinite, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  if (bad) return fail(h, MDF_EDIVERGED, "non-finite populations");
+  return MDF_OK;
+}
+
+mdf_status mdf_sums(mdf_t h, double *sums) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!sums) return fail(h, MDF_EINVAL, "sums: null output");
+  double r[4];
+  mdf_status st = reduce(h, RED_SUMS, r);
+  if (st != MDF_OK) return st;
+  for (int k = 0; k < h->nsets; ++k) sums[k] = r[k];
+  return MDF_OK;
+}
+
+mdf_status mdf_residual(mdf_t h, double *res) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!res) return fail(h, MDF_EINVAL, "residual: null output");
+  if (!h->uprev) {
+    cudaError_t e = cudaMalloc(&h->uprev, sizeof(double) * (size_t)h->N * h->d);
+    if (e != cudaSuccess) { cudaGetLastError(); h->uprev = nullptr; return fail(h, MDF_ENOMEM, "residual: %s", cudaGetErrorString(e)); }
+    h->have_prev = false;
+  }
+  double r[4];
+  mdf_status st = reduce(h, RED_RESIDUAL, r);
+  if (st != MDF_OK) return st;
+  if (!h->have_prev) {
+    h->have_prev = true;
+    *res = INFINITY;
+    return MDF_OK;
+  }
+  *res = r[1] > 0 ? std::sqrt(r[0] / r[1]) : (r[0] > 0 ? INFINITY : 0.0);
+  return MDF_OK;
+}
+
+mdf_status mdf_mask(mdf_t h, unsigned char *host_out) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!host_out) return fail(h, MDF_EINVAL, "mask: null output");
+  if (!h->walls) {
+    std::memset(host_out, 0, (size_t)h->N);
+    return MDF_OK;
+  }
+  std::vector<unsigned char> tmp((size_t)h->plane);
+  CU(h, cudaMemcpyAsync(tmp.data(), h->mask, (size_t)h->plane, cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  for (long long z = 0; z < h->nz; ++z)
+    for (long long y = 0; y < h->ny; ++y)
+      std::memcpy(host_out + (z * h->ny + y) * h->nx, tmp.data() + (z * h->ny + y) * h->px,
+                  (size_t)h->nx);
+  return MDF_OK;
+}
+
+static void fill_header(const mdf_t h, CkptHeader &hd) {
+  std::memset(&hd, 0, sizeof hd);
+  std::memcpy(hd.magic, "MDFLBM1", 8);
+  hd.version = 1;
+  hd.d = h->d; hd.q = h->q; hd.nsets = h->nsets; hd.storage = h->storage;
+  hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz; hd.px = h->px;
+  for (int b = 0; b < 3; ++b) { hd.wall[b] = h->bc.wall[b]; hd.lid_u[b] = h->bc.lid_u[b]; }
+  hd.lid = h->bc.lid;
+  hd.s0 = h->s0; hd.s1 = h->s1; hd.s2 = h->s2;
+  hd.step = h->step;
+  hd.payload = (int64_t)h->pop_bytes();
+}
+
+mdf_status mdf_save(mdf_t h, const char *path) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!path) return fail(h, MDF_EINVAL, "save: null path");
+  std::vector<unsigned char> buf(h->pop_bytes());
+  CU(h, cudaMemcpyAsync(buf.data(), h->cur, buf.size(), cudaMemcpyDeviceToHost, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  CkptHeader hd;
+  fill_header(h, hd);
+  hd.checksum = fnv1a(buf.data(), buf.size());
+  FILE *fp = std::fopen(path, "wb");
+  if (!fp) return fail(h, MDF_EIO, "save: cannot open %s", path);
+  bool ok = std::fwrite(&hd, sizeof hd, 1, fp) == 1 &&
+            std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+  ok = (std::fclose(fp) == 0) && ok;
+  return ok ? MDF_OK : fail(h, MDF_EIO, "save: write failed for %s", path);
+}
+
+mdf_status mdf_load(mdf_t h, const char *path) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!path) return fail(h, MDF_EINVAL, "load: null path");
+  FILE *fp = std::fopen(path, "rb");
+  if (!fp) return fail(h, MDF_EIO, "load: cannot open %s", path);
+  CkptHeader hd, want;
+  fill_header(h, want);
+  bool ok = std::fread(&hd, sizeof hd, 1, fp) == 1;
+  if (ok) {
+    want.step = hd.step;
+    want.checksum = hd.checksum;
+    ok = std::memcmp(&hd, &want, sizeof hd) == 0;
+  }
+  if (!ok) { std::fclose(fp); return fail(h, MDF_EIO, "load: header of %s does not match this handle", path); }
+  std::vector<unsigned char> buf(h->pop_bytes());
+  ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+  std::fclose(fp);
+  if (!ok) return fail(h, MDF_EIO, "load: short file %s", path);
+  if (fnv1a(buf.data(), buf.size()) != hd.checksum) return fail(h, MDF_EIO, "load: checksum mismatch in %s", path);
+  CU(h, cudaMemcpyAsync(h->cur, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  h->step = hd.step;
+  h->have_prev = false;
+  return MDF_OK;
+}
+
+mdf_status mdf_info(mdf_t h, mdf_info_t *out) {
+  if (check_handle(h) || !out) return MDF_EINVAL;
+  out->d = h->d; out->q = h->q; out->nsets = h->nsets; out->storage = h->storage;
+  out->nx = h->nx; out->ny = h->ny; out->nz = h->nz; out->pitch = h->px;
+  out->nodes = h->N;
+  out->step = h->step;
+  out->bytes_per_update = 2.0 * h->q * h->nsets * (double)storage_bytes(h->storage);
+  out->s0 = h->s0; out->s1 = h->s1; out->s2 = h->s2;
+  return MDF_OK;
+}
+
+mdf_status mdf_sync(mdf_t h) {
+  if (check_handle(h)) return MDF_EINVAL;
+  CU(h, cudaStreamSynchronize(h->stream));
+  return MDF_OK;
+}
+
+const char *mdf_last_error(mdf_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// Host/device interface between the C-ABI layer (mdf_api.cu) and the
+// per-lattice kernel translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdf {
+
+// Everything a kernel launch needs, as plain pointers and sizes.
+struct DevArgs {
+  const void *fin;               // current populations (post-collision, pre-stream)
+  void *fout;                    // next populations
+  const uint8_t *mask;           // link mask [plane] or null (periodic)
+  const float *force;            // [d][plane] body force or null
+  int nx, ny, nz, px;            // grid and padded x pitch
+  long long plane;               // px * ny * nz
+  int with_rho;                  // 1: set 0 is the alpha = 0 set
+  double s1, s2;                 // relaxation rates (s0 never acts: m0 = m0eq)
+  double lid_u[3];               // lid velocity
+  // derived-field outputs (dense [N] layout), each nullable
+  double *P, *u, *rho, *G, *div, *S, *sigma, *omega;
+  // init inputs (dense FP64 on the device)
+  const double *Pin, *uin;
+  // reductions
+  double *partials;              // [blocks][k] block partial sums
+  double *uprev;                 // [d][N] previous velocity (residual)
+  double *result;                // [k] final sums
+  int *nonfinite;                // set to 1 when a non-finite value is met
+};
+
+enum Mode { MODE_STEP = 0, MODE_STEP_FIELDS = 1, MODE_FIELDS = 2 };
+enum Storage { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2, ST_F64 = 3 };
+enum ReduceKind { RED_SUMS = 0, RED_RESIDUAL = 1 };
+
+// Kernel block width along x for the update kernels.
+constexpr int kBlockX = 128;
+// Blocks of the grid-stride reduction pass (a multiple of the 152 SMs).
+constexpr int kReduceBlocks = 152 * 4;
+constexpr int kReduceThreads = 256;
+
+// Per-lattice launchers (mdf_d2q5.cu, mdf_d3q7.cu).
+
+cudaError_t launch_update_d2q5(int storage, int mode, bool walls, const DevArgs &a,
+                               cudaStream_t s);
+cudaError_t launch_init_d2q5(int storage, bool walls, const DevArgs &a, cudaStream_t s);
+cudaError_t launch_reduce_d2q5(int storage, bool walls, int kind, const DevArgs &a,
+                               cudaStream_t s);
+cudaError_t launch_update_d3q7(int storage, int mode, bool walls, const DevArgs &a,
+                               cudaStream_t s);
+cudaError_t launch_init_d3q7(int storage, bool walls, const DevArgs &a, cudaStream_t s);
+cudaError_t launch_reduce_d3q7(int storage, bool walls, int kind, const DevArgs &a,
+                               cudaStream_t s);
+
+cudaError_t launch_mask_d2q5(const int wall[3], int lid, const DevArgs &a, uint8_t *mask,
+                             cudaStream_t s);
+cudaError_t launch_mask_d3q7(const int wall[3], int lid, const DevArgs &a, uint8_t *mask,
+                             cudaStream_t s);
+
+// Second reduction pass: sums `nblocks` x `k` partials in a fixed order.
+cudaError_t launch_reduce_final(const DevArgs &a, int nblocks, int k, cudaStream_t s);
+// Dense FP64 [d][N] -> padded FP32 [d][plane].
+cudaError_t launch_pad_force(const double *src, float *dst, int d, int nx, int ny, int nz,
+                             int px, cudaStream_t s);
+
+}  // namespace mdf

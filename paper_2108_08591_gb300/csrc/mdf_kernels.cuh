@@ -1,0 +1,431 @@
+// Kernel templates of the MDF-LBM stepper: fused pull-stream + moments +
+// MRT collision + store (Eq. 2-7, 3-15, 2-4, 3-21), the derived-field
+// epilogue (Eq. 3-16 .. 3-19), initialisation, link masks and FP64
+// reductions.  Instantiated per lattice in mdf_d2q5.cu / mdf_d3q7.cu.
+//
+// Memory layout (structure of arrays): set a, direction i, node (x, y, z)
+//   f[((a * Q + i) * plane) + (z * ny + y) * px + x],   plane = px * ny * nz,
+// with px = nx rounded up to a multiple of 32 so every row starts on a
+// 128-byte boundary.  Two buffers alternate (pull scheme): the current
+// buffer holds post-collision populations f*(x, t - 1); an update pulls
+// f_i(x, t) = f*_i(x - c_i, t - 1), collides and stores f*_i(x, t) at x in
+// the other buffer, so every population is read once and written once.
+// A link whose source x - c_i lies behind a wall is replaced by the
+// anti-halfway bounce-back of the node's own opposite population:
+//   f_i(x, t) = -f*_{opp(i)}(x, t - 1) + 2 w_i ubar_wall.
+#pragma once
+
+#include "mdf_internal.h"
+#include "mdf_lattice.cuh"
+
+namespace mdf {
+
+template <class TS> struct ComputeOf { using T = float; };
+template <> struct ComputeOf<double> { using T = double; };
+
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Index of the node x - c_i (periodic wrap on every axis; walls are masked).
+template <class L>
+__device__ __forceinline__ long long pull_src(const DevArgs &A, int x, int y, int z, int i) {
+  const int sx = wrap(x - L::c(i, 0), A.nx);
+  const int sy = wrap(y - L::c(i, 1), A.ny);
+  const int sz = L::D == 3 ? wrap(z - L::c(i, 2), A.nz) : z;
+  return ((long long)sz * A.ny + sy) * A.px + sx;
+}
+
+// Pull the Q populations of set `a` (carrying alpha) arriving at node idx.
+template <class L, class TS, bool WALLS>
+__device__ __forceinline__ void pull_set(const DevArgs &A, const TS *__restrict__ fin, int a,
+                                         int alpha, long long idx, const long long (&src)[L::Q],
+                                         uint8_t m, typename ComputeOf<TS>::T (&g)[L::Q]) {
+  using TC = typename ComputeOf<TS>::T;
+  const TS *base = fin + (long long)a * L::Q * A.plane;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    if (WALLS && i != 0 && ((m >> L::opp(i)) & 1)) {
+      // anti-halfway bounce-back; in shifted storage the alpha = 0 wall value
+      // rho0 and the rest shift cancel, leaving -g*_opp + 2 w_i u_wall(alpha)
+      TC v = -TC(Codec<TS>::load(base + (long long)L::opp(i) * A.plane + idx));
+      if (alpha >= 1 && i == L::opp(L::UP) && (m & 0x80u))
+        v += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+      g[i] = v;
+    } else {
+      g[i] = Codec<TS>::load(base + (long long)i * A.plane + src[i]);
+    }
+  }
+}
+
+// Derived fields of Eq. 2-7, 3-15 .. 3-19 at one node, in FP64, from the
+// pulled (pre-collision) shifted populations.  gv: the d velocity sets;
+// h: the alpha = 0 set (ignored unless with_rho).
+template <class L, class TC>
+__device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long long N,
+                                             const TC (&gv)[L::D][L::Q], const TC (&h)[L::Q]) {
+  constexpr int D = L::D, Q = L::Q;
+  double u[D], J[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) s += (double)gv[a][i];
+    u[a] = s;
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+      double t = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        if (L::c(i, b) != 0) t += L::c(i, b) * (double)gv[a][i];
+      J[a][b] = t;  // sum_i c_{i,b} g_{i,a}
+    }
+  }
+  double tr = 0.0, usq = 0.0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) { tr += J[a][a]; usq += u[a] * u[a]; }
+  const double Pp = (tr - usq) / D;  // Eq. 3-15, P' = P - P0, R = 0
+  if (A.P) A.P[n] = 1.0 + Pp;
+  if (A.u)
+#pragma unroll
+    for (int a = 0; a < D; ++a) A.u[a * N + n] = u[a];
+  if (A.rho && A.with_rho) {
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) s += (double)h[i];
+    A.rho[n] = 1.0 + s;
+  }
+  if (!(A.G || A.div || A.S || A.sigma || A.omega)) return;
+  // first moment of f^ne: sum_i c_{i,b} (f - f^eq)_{i,a} = J - u_a u_b - P' delta_ab
+  double mne[D][D];
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) mne[a][b] = J[a][b] - u[a] * u[b] - (a == b ? Pp : 0.0);
+  const double pref = -A.s1 / L::CS2;  // Eq. 3-16 with dt = 1
+  if (A.G)
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = 0; b < D; ++b) A.G[(a * D + b) * N + n] = pref * mne[a][b];
+  if (A.div) {
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) s += mne[a][a];
+    A.div[n] = pref * s;  // Eq. 3-16a
+  }
+  if (A.S || A.sigma) {
+    int k = 0;
+    const double sig = -(1.0 - 0.5 * A.s1);  // Eq. 3-17a with rho0 = 1
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int b = a; b < D; ++b, ++k) {
+        const double sym = mne[a][b] + mne[b][a];
+        if (A.S) A.S[k * N + n] = 0.5 * pref * sym;  // Eq. 3-17
+        if (A.sigma) A.sigma[k * N + n] = sig * sym;
+      }
+  }
+  if (A.omega) {  // Eq. 3-18, 3-19: omega = curl u
+    if (D == 2) {
+      A.omega[n] = pref * (mne[1][0] - mne[0][1]);
+    } else {
+      A.omega[n] = pref * (mne[2][1] - mne[1][2]);
+      A.omega[N + n] = pref * (mne[0][2] - mne[2][0]);
+      A.omega[2 * N + n] = pref * (mne[1][0] - mne[0][1]);
+    }
+  }
+}
+
+// One lattice update per thread-node: pull, moments, (fields), collide, store.
+template <class L, class TS, int MODE, bool WALLS>
+__global__ void __launch_bounds__(kBlockX) k_update(const DevArgs A) {
+  using TC = typename ComputeOf<TS>::T;
+  constexpr int D = L::D, Q = L::Q;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= A.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const long long idx = ((long long)z * A.ny + y) * A.px + x;
+  long long src[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) src[i] = pull_src<L>(A, x, y, z, i);
+  const uint8_t m = WALLS ? A.mask[idx] : uint8_t(0);
+  const TS *__restrict__ fin = static_cast<const TS *>(A.fin);
+  const int a1 = A.with_rho;  // set index of alpha = 1
+
+  TC g[D][Q], h[Q];
+#pragma unroll
+  for (int al = 1; al <= D; ++al) pull_set<L, TS, WALLS>(A, fin, a1 + al - 1, al, idx, src, m, g[al - 1]);
+  if (A.with_rho) pull_set<L, TS, WALLS>(A, fin, 0, 0, idx, src, m, h);
+
+  if (MODE != MODE_STEP) {
+    const long long N = (long long)A.nx * A.ny * A.nz;
+    const long long n = ((long long)z * A.ny + y) * A.nx + x;
+    write_fields<L, TC>(A, n, N, g, h);
+    if (MODE == MODE_FIELDS) return;
+  }
+
+  // Eq. 2-7: u_alpha = sum_i f_{i,alpha} (the rest shift has zero sum);
+  // Eq. 3-15: P' = (1/d)(sum_alpha sum_i c_{i,alpha} g_{i,alpha} - |u|^2).
+  TC u[D], tr = TC(0), usq = TC(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    TC s = TC(0), t = TC(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      s += g[a][i];
+      if (L::c(i, a) != 0) t += TC(L::c(i, a)) * g[a][i];
+    }
+    u[a] = s;
+    tr += t;
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) usq += u[a] * u[a];
+  const TC Pp = (tr - usq) * TC(1.0 / D);
+  const TC s1 = TC(A.s1), s2 = TC(A.s2);
+  TS *__restrict__ fout = static_cast<TS *>(A.fout);
+
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    TC jeq[D];  // Eq. 3-7a: sum_i c_i f^eq = u_alpha u + P E_alpha (shifted: P')
+#pragma unroll
+    for (int b = 0; b < D; ++b) jeq[b] = u[a] * u[b] + (a == b ? Pp : TC(0));
+    const TC F = A.force ? TC(__ldg(A.force + a * A.plane + idx)) : TC(0);
+    L::relax(g[a], jeq, s1, s2, F);
+    TS *base = fout + (long long)(a1 + a) * Q * A.plane + idx;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Codec<TS>::store(base + (long long)i * A.plane, g[a][i]);
+  }
+  if (A.with_rho) {
+    TC r = TC(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) r += h[i];
+    TC jeq[D];  // ubar_0 u with ubar_0 = rho0 + rho'
+#pragma unroll
+    for (int b = 0; b < D; ++b) jeq[b] = (TC(1) + r) * u[b];
+    L::relax(h, jeq, s1, s2, TC(0));
+    TS *base = fout + idx;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) Codec<TS>::store(base + (long long)i * A.plane, h[i]);
+  }
+}
+
+// Shifted equilibrium g^eq_i of set alpha at dense node n (Eq. 2-4 minus
+// the rest state): alpha >= 1: w_i [u_a + (c_i.u u_a + c_{i,a} P')/c_s^2];
+// alpha = 0 (ubar_0 = rho0 = 1): w_i c_i.u / c_s^2.
+template <class L>
+__device__ __forceinline__ double geq(const DevArgs &A, long long N, long long n, int alpha, int i) {
+  double cu = 0.0;
+#pragma unroll
+  for (int b = 0; b < L::D; ++b)
+    if (L::c(i, b) != 0) cu += L::c(i, b) * A.uin[b * N + n];
+  if (alpha == 0) return L::w(i) * cu / L::CS2;
+  const double ua = A.uin[(alpha - 1) * N + n];
+  const double Pp = A.Pin[n] - 1.0;
+  return L::w(i) * (ua + (cu * ua + L::c(i, alpha - 1) * Pp) / L::CS2);
+}
+
+// Initial state f = f^eq(P, u) written in pull form: the value stored at x
+// for direction i is the one the first update pulls into x + c_i, and for a
+// wall link the one whose bounce-back returns f^eq_opp(i)(x).
+template <class L, class TS, bool WALLS>
+__global__ void __launch_bounds__(kBlockX) k_init(const DevArgs A) {
+  constexpr int D = L::D, Q = L::Q;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= A.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const long long idx = ((long long)z * A.ny + y) * A.px + x;
+  const long long N = (long long)A.nx * A.ny * A.nz;
+  const long long n = ((long long)z * A.ny + y) * A.nx + x;
+  const uint8_t m = WALLS ? A.mask[idx] : uint8_t(0);
+  TS *fout = static_cast<TS *>(A.fout);
+  const int nsets = D + A.with_rho;
+  for (int a = 0; a < nsets; ++a) {
+    const int alpha = a + 1 - A.with_rho;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      double v;
+      if (WALLS && i != 0 && ((m >> i) & 1)) {
+        v = -geq<L>(A, N, n, alpha, L::opp(i));
+        if (alpha >= 1 && i == L::UP && (m & 0x80u)) v += 2.0 * L::w(i) * A.lid_u[alpha - 1];
+      } else {
+        const int tx = wrap(x + L::c(i, 0), A.nx);
+        const int ty = wrap(y + L::c(i, 1), A.ny);
+        const int tz = D == 3 ? wrap(z + L::c(i, 2), A.nz) : z;
+        v = geq<L>(A, N, ((long long)tz * A.ny + ty) * A.nx + tx, alpha, i);
+      }
+      fout[((long long)a * Q + i) * A.plane + idx] = Codec<TS>::enc(v);
+    }
+  }
+}
+
+// Block-wide FP64 sum of k values (fixed order: deterministic).
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double *out) {
+  __shared__ double sh[K][kReduceThreads / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    double s = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) sh[k][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    double s = 0.0;
+    for (int w = 0; w < kReduceThreads / 32; ++w) s += sh[threadIdx.x][w];
+    out[threadIdx.x] = s;
+  }
+}
+
+// Grid-stride FP64 reduction over all nodes.
+//   RED_SUMS:     partial[k] = sum_x ubar_k (k over carried sets, Eq. 2-7)
+//   RED_RESIDUAL: partial[0] = sum |u - uprev|^2, partial[1] = sum |u|^2, uprev <- u
+template <class L, class TS, bool WALLS, int KIND>
+__global__ void __launch_bounds__(kReduceThreads) k_reduce(const DevArgs A) {
+  using TC = typename ComputeOf<TS>::T;
+  constexpr int D = L::D, Q = L::Q;
+  const long long N = (long long)A.nx * A.ny * A.nz;
+  const TS *__restrict__ fin = static_cast<const TS *>(A.fin);
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  bool bad = false;
+  for (long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x; n < N;
+       n += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(n % A.nx);
+    const int y = (int)((n / A.nx) % A.ny);
+    const int z = (int)(n / ((long long)A.nx * A.ny));
+    const long long idx = ((long long)z * A.ny + y) * A.px + x;
+    long long src[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) src[i] = pull_src<L>(A, x, y, z, i);
+    const uint8_t m = WALLS ? A.mask[idx] : uint8_t(0);
+    const int nsets = D + A.with_rho;
+#pragma unroll
+    for (int a = 0; a < D + 1; ++a) {
+      if (a >= nsets) break;
+      const int alpha = a + 1 - A.with_rho;
+      TC g[Q];
+      pull_set<L, TS, WALLS>(A, fin, a, alpha, idx, src, m, g);
+      double s = 0.0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) s += (double)g[i];
+      if (alpha == 0) s += 1.0;  // the rest shift of the alpha = 0 set sums to rho0
+      bad |= !isfinite(s);
+      if (KIND == RED_SUMS) {
+        acc[a] += s;
+      } else if (alpha >= 1) {
+        double *up = A.uprev + (long long)(alpha - 1) * N + n;
+        const double dlt = s - *up;
+        acc[0] += dlt * dlt;
+        acc[1] += s * s;
+        *up = s;
+      }
+    }
+  }
+  block_sum<4>(acc, A.partials + (long long)blockIdx.x * 4);
+  if (bad) atomicExch(A.nonfinite, 1);
+}
+
+template <class L>
+__global__ void k_mask(const DevArgs A, int wx, int wy, int wz, int lid, uint8_t *mask) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= A.nx) return;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int pos[3] = {x, y, z}, ext[3] = {A.nx, A.ny, A.nz}, wall[3] = {wx, wy, wz};
+  uint8_t m = 0;
+#pragma unroll
+  for (int i = 1; i < L::Q; ++i) {
+#pragma unroll
+    for (int b = 0; b < L::D; ++b) {
+      const int t = pos[b] + L::c(i, b);
+      if (wall[b] && (t < 0 || t >= ext[b])) {
+        m |= uint8_t(1u << i);
+        if (lid && b == L::D - 1 && t >= ext[b]) m |= 0x80u;
+      }
+    }
+  }
+  mask[((long long)z * A.ny + y) * A.px + x] = m;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side dispatch over storage / mode / walls for one lattice.
+// ---------------------------------------------------------------------------
+inline dim3 node_grid(const DevArgs &a) {
+  return dim3((unsigned)((a.nx + kBlockX - 1) / kBlockX), (unsigned)a.ny, (unsigned)a.nz);
+}
+
+template <class L, class TS>
+cudaError_t update_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
+  const dim3 grid = node_grid(a), block(kBlockX);
+  if (walls) {
+    if (mode == MODE_STEP) k_update<L, TS, MODE_STEP, true><<<grid, block, 0, s>>>(a);
+    else if (mode == MODE_STEP_FIELDS) k_update<L, TS, MODE_STEP_FIELDS, true><<<grid, block, 0, s>>>(a);
+    else k_update<L, TS, MODE_FIELDS, true><<<grid, block, 0, s>>>(a);
+  } else {
+    if (mode == MODE_STEP) k_update<L, TS, MODE_STEP, false><<<grid, block, 0, s>>>(a);
+    else if (mode == MODE_STEP_FIELDS) k_update<L, TS, MODE_STEP_FIELDS, false><<<grid, block, 0, s>>>(a);
+    else k_update<L, TS, MODE_FIELDS, false><<<grid, block, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t update_lattice(int storage, int mode, bool walls, const DevArgs &a, cudaStream_t s) {
+  switch (storage) {
+    case ST_F32: return update_t<L, float>(mode, walls, a, s);
+    case ST_F16: return update_t<L, __half>(mode, walls, a, s);
+    case ST_BF16: return update_t<L, __nv_bfloat16>(mode, walls, a, s);
+    case ST_F64: return update_t<L, double>(mode, walls, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class L, class TS>
+cudaError_t init_t(bool walls, const DevArgs &a, cudaStream_t s) {
+  if (walls) k_init<L, TS, true><<<node_grid(a), kBlockX, 0, s>>>(a);
+  else k_init<L, TS, false><<<node_grid(a), kBlockX, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t init_lattice(int storage, bool walls, const DevArgs &a, cudaStream_t s) {
+  switch (storage) {
+    case ST_F32: return init_t<L, float>(walls, a, s);
+    case ST_F16: return init_t<L, __half>(walls, a, s);
+    case ST_BF16: return init_t<L, __nv_bfloat16>(walls, a, s);
+    case ST_F64: return init_t<L, double>(walls, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class L, class TS>
+cudaError_t reduce_t(bool walls, int kind, const DevArgs &a, cudaStream_t s) {
+  const int nb = kReduceBlocks;
+  if (kind == RED_SUMS) {
+    if (walls) k_reduce<L, TS, true, RED_SUMS><<<nb, kReduceThreads, 0, s>>>(a);
+    else k_reduce<L, TS, false, RED_SUMS><<<nb, kReduceThreads, 0, s>>>(a);
+  } else {
+    if (walls) k_reduce<L, TS, true, RED_RESIDUAL><<<nb, kReduceThreads, 0, s>>>(a);
+    else k_reduce<L, TS, false, RED_RESIDUAL><<<nb, kReduceThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <class L>
+cudaError_t reduce_lattice(int storage, bool walls, int kind, const DevArgs &a, cudaStream_t s) {
+  switch (storage) {
+    case ST_F32: return reduce_t<L, float>(walls, kind, a, s);
+    case ST_F16: return reduce_t<L, __half>(walls, kind, a, s);
+    case ST_BF16: return reduce_t<L, __nv_bfloat16>(walls, kind, a, s);
+    case ST_F64: return reduce_t<L, double>(walls, kind, a, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <class L>
+cudaError_t mask_lattice(const int wall[3], int lid, const DevArgs &a, uint8_t *mask,
+                         cudaStream_t s) {
+  k_mask<L><<<node_grid(a), kBlockX, 0, s>>>(a, wall[0], wall[1], wall[2], lid, mask);
+  return cudaGetLastError();
+}
+
+}  // namespace mdf

@@ -1,0 +1,135 @@
+// Lattice traits, storage codecs and the per-node MRT collision of the
+// MDF-LBM (Chai, Shi & Zhan, arXiv 2108.08591) for the GPU kernels.
+//
+// Populations are stored shifted by the rest state f_rest = f^eq(P0=1, u=0):
+//   g_{i,a} = f_{i,a} - w_i [delta_{a0} rho0 + c_{i,a} P0 / c_s^2].
+// The collision is linear in f once f^eq is fixed, so it acts on g exactly as
+// on f with every equilibrium moment shifted the same way (P -> P' = P - P0,
+// ubar_0 -> rho' = ubar_0 - rho0).  Lattice units: dx = dt = c = 1.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace mdf {
+
+// ---------------------------------------------------------------------------
+// Storage codecs: populations are held as T in HBM and computed in TC.
+// ---------------------------------------------------------------------------
+template <class T> struct Codec;
+template <> struct Codec<float> {
+  static __device__ __forceinline__ float load(const float *p) { return __ldg(p); }
+  static __device__ __forceinline__ void store(float *p, float v) { __stcs(p, v); }
+  static __device__ __forceinline__ float enc(double v) { return (float)v; }
+};
+template <> struct Codec<double> {
+  static __device__ __forceinline__ double load(const double *p) { return __ldg(p); }
+  static __device__ __forceinline__ void store(double *p, double v) { __stcs(p, v); }
+  static __device__ __forceinline__ double enc(double v) { return v; }
+};
+template <> struct Codec<__half> {
+  static __device__ __forceinline__ float load(const __half *p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ void store(__half *p, float v) { *p = __float2half_rn(v); }
+  static __device__ __forceinline__ __half enc(double v) { return __float2half_rn((float)v); }
+};
+template <> struct Codec<__nv_bfloat16> {
+  static __device__ __forceinline__ float load(const __nv_bfloat16 *p) {
+    return __bfloat162float(__ldg(p));
+  }
+  static __device__ __forceinline__ void store(__nv_bfloat16 *p, float v) {
+    *p = __float2bfloat16_rn(v);
+  }
+  static __device__ __forceinline__ __nv_bfloat16 enc(double v) {
+    return __float2bfloat16_rn((float)v);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// D2Q5 (Sec. 2.2): c_0..c_4 = (0,0),(1,0),(0,1),(-1,0),(0,-1);
+// w_0 = 1/3, w_1..4 = 1/6; c_s^2 = 1/3.  MRT basis of Eq. 4-2 (c = 1):
+//   m0 = sum g, m1 = g1 - g3, m2 = g2 - g4, m3 = g1 - g2 + g3 - g4,
+//   m4 = -4 g0 + g1 + g2 + g3 + g4;  S_d = diag(s0, s1, s1, s2, s2) (Eq. 4-3).
+// Rows of M are orthogonal with squared norms (5, 2, 2, 4, 20), so
+// M^-1 = M^T diag(1/5, 1/2, 1/2, 1/4, 1/20).
+// Equilibrium moments (Eq. 2-4 with Eq. 3-7a): m3eq = 0, m4eq = -(2/3) m0.
+// ---------------------------------------------------------------------------
+struct D2Q5 {
+  static constexpr int D = 2, Q = 5;
+  static constexpr double CS2 = 1.0 / 3.0;
+  __host__ __device__ static constexpr int c(int i, int b) {
+    return b == 0 ? (i == 1 ? 1 : i == 3 ? -1 : 0) : b == 1 ? (i == 2 ? 1 : i == 4 ? -1 : 0) : 0;
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : i == 1 ? 3 : i == 2 ? 4 : i == 3 ? 1 : 2;
+  }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 1.0 / 3.0 : 1.0 / 6.0; }
+  // direction that points through the + face of the last axis (the lid)
+  static constexpr int UP = 2;
+
+  // In-place MRT relaxation of one set: g <- g - M^-1 S (M g - m^eq) + w F.
+  // jeq[b]: equilibrium first moment (shifted); F: source Fbar_alpha.
+  template <class TC>
+  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F) {
+    const TC m0 = g[0] + g[1] + g[2] + g[3] + g[4];
+    const TC d1 = s1 * ((g[1] - g[3]) - jeq[0]);
+    const TC d2 = s1 * ((g[2] - g[4]) - jeq[1]);
+    const TC d3 = s2 * ((g[1] + g[3]) - (g[2] + g[4]));
+    const TC d4 = s2 * ((g[1] + g[2] + g[3] + g[4]) - TC(4) * g[0] + TC(2.0 / 3.0) * m0);
+    const TC h1 = TC(0.5) * d1, h2 = TC(0.5) * d2, q3 = TC(0.25) * d3, e4 = TC(0.05) * d4;
+    const TC Fw = F * TC(1.0 / 6.0);
+    g[0] = g[0] + TC(0.2) * d4 + F * TC(1.0 / 3.0);
+    g[1] = g[1] - h1 - q3 - e4 + Fw;
+    g[2] = g[2] - h2 + q3 - e4 + Fw;
+    g[3] = g[3] + h1 - q3 - e4 + Fw;
+    g[4] = g[4] + h2 + q3 - e4 + Fw;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// D3Q7 (Sec. 2.2): c_0 = 0, c_1,2 = +-x, c_3,4 = +-y, c_5,6 = +-z;
+// w_0 = 1/4, w_1..6 = 1/8; c_s^2 = 1/4.  The paper prints M for D2Q5 only;
+// the analogous orthogonal basis used here is
+//   m0 = sum g, m1..3 = first moments, m4 = 7|c|^2 - 6 (-6 g0 + sum_{i>0} g),
+//   m5 = 2cx^2 - cy^2 - cz^2, m6 = cy^2 - cz^2;  S_d = diag(s0, s1 x3, s2 x3),
+// squared row norms (7, 2, 2, 2, 42, 12, 4); m4eq = -(3/4) m0, m5eq = m6eq = 0.
+// ---------------------------------------------------------------------------
+struct D3Q7 {
+  static constexpr int D = 3, Q = 7;
+  static constexpr double CS2 = 0.25;
+  __host__ __device__ static constexpr int c(int i, int b) {
+    return b == 0 ? (i == 1 ? 1 : i == 2 ? -1 : 0)
+         : b == 1 ? (i == 3 ? 1 : i == 4 ? -1 : 0)
+                  : (i == 5 ? 1 : i == 6 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int opp(int i) {
+    return i == 0 ? 0 : (i & 1) ? i + 1 : i - 1;
+  }
+  __host__ __device__ static constexpr double w(int i) { return i == 0 ? 0.25 : 0.125; }
+  static constexpr int UP = 5;
+
+  template <class TC>
+  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F) {
+    const TC sx = g[1] + g[2], sy = g[3] + g[4], sz = g[5] + g[6];
+    const TC m0 = g[0] + sx + sy + sz;
+    const TC d1 = s1 * ((g[1] - g[2]) - jeq[0]);
+    const TC d2 = s1 * ((g[3] - g[4]) - jeq[1]);
+    const TC d3 = s1 * ((g[5] - g[6]) - jeq[2]);
+    const TC d4 = s2 * ((sx + sy + sz) - TC(6) * g[0] + TC(0.75) * m0);
+    const TC d5 = s2 * (TC(2) * sx - sy - sz);
+    const TC d6 = s2 * (sy - sz);
+    const TC h1 = TC(0.5) * d1, h2 = TC(0.5) * d2, h3 = TC(0.5) * d3;
+    const TC e4 = d4 * TC(1.0 / 42.0);
+    const TC ex = d5 * TC(1.0 / 6.0), eo = d5 * TC(1.0 / 12.0), q6 = TC(0.25) * d6;
+    const TC Fw = F * TC(0.125);
+    g[0] = g[0] + d4 * TC(1.0 / 7.0) + F * TC(0.25);
+    g[1] = g[1] - h1 - e4 - ex + Fw;
+    g[2] = g[2] + h1 - e4 - ex + Fw;
+    g[3] = g[3] - h2 - e4 + eo - q6 + Fw;
+    g[4] = g[4] + h2 - e4 + eo - q6 + Fw;
+    g[5] = g[5] - h3 - e4 + eo + q6 + Fw;
+    g[6] = g[6] + h3 - e4 + eo + q6 + Fw;
+  }
+};
+
+}  // namespace mdf

@@ -181,3 +181,26 @@ def cavity_batch(count: int = 64, seed: int = 2108, sides=(65, 129, 257, 513),
 
 def rest_state(N: int, d: int, P0: float = 1.0):
     return np.full(N, P0), np.zeros((d, N))
+
+
+def smooth_fields(n: Tuple[int, ...], seed: int, amp: float = 0.02, mean_flow: bool = True):
+    """Seeded smooth periodic (P, u) on any grid shape (2D or 3D).
+
+    A few low Fourier modes with SplitMix64 phases; the velocity is not
+    divergence-free on purpose (it exercises the pressure and the
+    compressible transient of the scheme).  Returns (P [N], u [d][N]).
+    """
+    rng = SplitMix64(seed)
+    d = len(n)
+    C = grid_coords(tuple(n))
+    two_pi = 2.0 * math.pi
+    ph = [two_pi * rng.uniform() for _ in range(2 * d + 1)]
+    P = 1.0 + 0.1 * amp * np.cos(two_pi * C[0] / n[0] + ph[0]) * np.cos(two_pi * C[1] / n[1] + ph[1])
+    u = np.empty((d, C[0].size))
+    for a in range(d):
+        b = (a + 1) % d
+        arg = two_pi * ((a + 1) * C[a] / n[a] + (2 - a % 2) * C[b] / n[b]) + ph[2 + a]
+        u[a] = amp * np.sin(arg)
+        if mean_flow:
+            u[a] += 0.1 * amp * (1.0 - 2.0 * rng.uniform())
+    return P, u

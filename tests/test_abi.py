@@ -1,0 +1,72 @@
+"""CPU-side checks of the C-ABI library: it loads, exports every entry point
+declared in include/*.h, and rejects bad arguments before touching a GPU."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(mdf_[a-z0-9_]+)\s*\(", text))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2108_08591_gb300 import _build, _lib
+    _build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for want in ("mdf_create", "mdf_init", "mdf_step", "mdf_moments", "mdf_gradients"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in sorted(_declared()):
+        assert hasattr(lib, name), name
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2108_08591_gb300 import _lib
+    assert _declared() <= set(_lib.SIGNATURES)
+
+
+def test_invalid_arguments_are_rejected_without_a_gpu(lib):
+    from paper_2108_08591_gb300 import _lib
+    h = ctypes.c_void_p()
+    g = _lib.Grid(8, 8, 1)
+    r = _lib.Rates(1.0, 1.2, -1.0)
+    # bad dimension
+    assert lib.mdf_create(ctypes.byref(h), ctypes.byref(g), 4, ctypes.byref(r), None, None) == _lib.EINVAL
+    assert b"d must be" in lib.mdf_last_error(None)
+    # relaxation rate outside (0, 2)
+    bad = _lib.Rates(1.0, 2.5, -1.0)
+    assert lib.mdf_create(ctypes.byref(h), ctypes.byref(g), 2, ctypes.byref(bad), None, None) == _lib.EINVAL
+    # grid too small / nz mismatch
+    g2 = _lib.Grid(1, 8, 1)
+    assert lib.mdf_create(ctypes.byref(h), ctypes.byref(g2), 2, ctypes.byref(r), None, None) == _lib.EINVAL
+    g3 = _lib.Grid(8, 8, 4)
+    assert lib.mdf_create(ctypes.byref(h), ctypes.byref(g3), 2, ctypes.byref(r), None, None) == _lib.EINVAL
+    # lid without walls on the last axis
+    bc = _lib.BC()
+    bc.lid = 1
+    assert lib.mdf_create(ctypes.byref(h), ctypes.byref(g), 2, ctypes.byref(r), ctypes.byref(bc), None) == _lib.EINVAL
+    # unknown storage
+    o = _lib.Opts(9, 1, None)
+    assert lib.mdf_create(ctypes.byref(h), ctypes.byref(g), 2, ctypes.byref(r), None, ctypes.byref(o)) == _lib.EUNSUPPORTED
+    assert h.value is None
+    # null handles
+    assert lib.mdf_step(None, 1) == _lib.EINVAL
+    assert lib.mdf_init(None, None, None, 0) == _lib.EINVAL
+    lib.mdf_destroy(None)

@@ -1,0 +1,339 @@
+"""GPU-vs-oracle parity of the MDF-LBM stepper through the C-ABI.
+
+Tolerances (relative L2, Sec. 4's E_L2; the pressure by its fluctuation
+P - mean(P)):
+  * FP64 storage (FP64 arithmetic): u, P within 1e-10; derived fields within
+    1e-8 (the oracle itself carries ~1e-12 cancellation noise in f^ne).
+  * FP32 storage: u, P within 1e-5.  Derived fields within 1e-4: one FP32
+    rounding of a shifted population (|g| ~ 3e-3, ulp ~ 2e-10) against the
+    first moment of f^ne (~1e-4 .. 1e-5 at these sizes) gives ~1e-6 per node.
+  * FP16 storage: u, P within 2e-3.  BF16: reported, within 2e-2.
+Masks are compared byte for byte.
+"""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests._harness import errors, rel, rel_p, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+NU = 0.01
+S1_TG = 1.0 / (3 * NU + 0.5)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_08591_gb300 import _build
+    _build.build()
+
+
+def _tol(storage):
+    return {"f64": (1e-10, 1e-8), "f32": (1e-5, 1e-4), "f16": (2e-3, 5e-2),
+            "bf16": (2e-2, 3e-1)}[storage]
+
+
+# --------------------------------------------------------------------------
+# 2D periodic
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_taylor_green_64_matches_oracle(storage):
+    """64^2 Taylor-Green plus 8 seeded modes, 1000 steps (the small 2D case)."""
+    n, steps = 64, 1000
+    P, u = synth.tg_plus_modes(n, U0=0.01, seed=2108)
+    got = run_gpu((n, n), P, u, steps, S1_TG, storage=storage)
+    ref = run_oracle((n, n), P, u, steps, S1_TG)
+    e = errors(ref, got)
+    tu, tg = _tol(storage)
+    assert e["u"] < tu and e["P"] < tu, e
+    for k in ("G", "S", "sigma", "omega"):
+        assert e[k] < tg, (k, e)
+    assert e["rho"] < (1e-12 if storage == "f64" else 1e-6)
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+def test_ragged_grid_2d(storage):
+    """Grid spanning several 128-wide blocks with a ragged tail (nx = 300) and
+    a padded pitch; smooth seeded fields with a mean flow."""
+    shape, steps, s1 = (300, 37), 150, 1.55
+    P, u = synth.smooth_fields(shape, seed=5, amp=0.02)
+    got = run_gpu(shape, P, u, steps, s1, storage=storage)
+    ref = run_oracle(shape, P, u, steps, s1)
+    e = errors(ref, got)
+    tu, tg = _tol(storage)
+    print(storage, e)
+    assert e["u"] < tu and e["P"] < tu, e
+    assert e["G"] < tg and e["omega"] < tg, e
+
+
+def test_without_continuity_set_is_identical():
+    """u, P and every derived field do not depend on the alpha = 0 set."""
+    shape = (70, 45)
+    P, u = synth.smooth_fields(shape, seed=9)
+    a = run_gpu(shape, P, u, 40, 1.3, with_rho=True)
+    b = run_gpu(shape, P, u, 40, 1.3, with_rho=False)
+    for k in ("P", "u", "G", "div", "S", "sigma", "omega"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+# --------------------------------------------------------------------------
+# 3D periodic
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_d3q7_ragged_matches_oracle(storage):
+    shape, steps, s1 = (150, 20, 18), 60, 1.45
+    P, u = synth.smooth_fields(shape, seed=13)
+    got = run_gpu(shape, P, u, steps, s1, storage=storage)
+    ref = run_oracle(shape, P, u, steps, s1)
+    e = errors(ref, got)
+    tu, tg = _tol(storage)
+    assert e["u"] < tu and e["P"] < tu, e
+    for k in ("G", "S", "sigma", "omega"):
+        assert e[k] < tg, (k, e)
+
+
+def test_taylor_green_3d_matches_oracle():
+    n, steps = 32, 200
+    nu = 1.0 / 40
+    s1 = 1.0 / (4 * nu + 0.5)
+    P, u = synth.taylor_green_3d(n, U0=0.05)
+    got = run_gpu((n, n, n), P, u, steps, s1, storage="f32")
+    ref = run_oracle((n, n, n), P, u, steps, s1)
+    e = errors(ref, got)
+    assert e["u"] < 1e-5 and e["P"] < 1e-5, e
+    assert e["omega"] < 1e-4, e
+
+
+# --------------------------------------------------------------------------
+# Walls, lid, force
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_lid_driven_cavity_2d(storage):
+    """Anti-halfway bounce-back walls and a moving lid on a 67 x 53 cavity."""
+    shape, steps, s1 = (67, 53), 400, 1.6
+    P, u = synth.rest_state(67 * 53, 2)
+    kw = dict(wall=(1, 1, 0), lid=True, lid_u=(0.05, 0.0, 0.0))
+    got = run_gpu(shape, P, u, steps, s1, storage=storage, **kw)
+    ref = run_oracle(shape, P, u, steps, s1, **kw)
+    assert np.array_equal(got["mask"], ref["mask"])
+    e = errors(ref, got)
+    tu, tg = _tol(storage)
+    assert e["u"] < tu and e["P"] < tu, e
+    assert e["G"] < tg and e["omega"] < tg, e
+
+
+def test_cavity_3d_and_non_rest_init():
+    """3D box with walls on every face, lid on +z, from a non-rest state."""
+    shape, steps, s1 = (37, 21, 19), 120, 1.4
+    P, u = synth.smooth_fields(shape, seed=21, amp=0.01)
+    kw = dict(wall=(1, 1, 1), lid=True, lid_u=(0.03, -0.01, 0.0))
+    got = run_gpu(shape, P, u, steps, s1, storage="f64", **kw)
+    ref = run_oracle(shape, P, u, steps, s1, **kw)
+    assert np.array_equal(got["mask"], ref["mask"])
+    e = errors(ref, got)
+    assert e["u"] < 1e-10 and e["P"] < 1e-10, e
+
+
+def test_mixed_walls_and_force():
+    """Periodic x, walls on y, a non-uniform body force (Eq. 2-6)."""
+    shape, steps, s1 = (40, 33), 500, 1.2
+    X, Y = synth.grid_coords(shape)
+    F = np.stack([1e-5 * (1.0 + 0.5 * np.cos(2 * np.pi * X / 40)), 2e-6 * np.sin(2 * np.pi * Y / 33)])
+    P, u = synth.rest_state(shape[0] * shape[1], 2)
+    for storage, tol in (("f64", 1e-10), ("f32", 1e-5)):
+        got = run_gpu(shape, P, u, steps, s1, storage=storage, wall=(0, 1, 0), force=F)
+        ref = run_oracle(shape, P, u, steps, s1, wall=(0, 1, 0), force=F)
+        e = errors(ref, got)
+        assert e["u"] < tol and e["P"] < max(tol, 1e-5), (storage, e)
+
+
+# --------------------------------------------------------------------------
+# Fused epilogue, reductions, checkpoints, edges
+# --------------------------------------------------------------------------
+def test_fused_fields_equal_separate_pass():
+    import torch
+    from paper_2108_08591_gb300 import Lattice
+    shape = (129, 40)
+    P, u = synth.smooth_fields(shape, seed=3)
+    a = Lattice(shape, s1=1.3)
+    b = Lattice(shape, s1=1.3)
+    a.init(P, u)
+    b.init(P, u)
+    a.step(7)
+    b.step(7)
+    fa = a.alloc_fields()
+    a.step_fields(5, fa)
+    fb = b.fields(list(fa.keys()))
+    b.step(5)
+    torch.cuda.synchronize()
+    for k in fa:
+        assert torch.equal(fa[k], fb[k]), k
+    ua = a.fields_host(("u",))["u"]
+    ub = b.fields_host(("u",))["u"]
+    assert np.array_equal(ua, ub)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_conservation_sums(d):
+    from paper_2108_08591_gb300 import Lattice
+    shape = (45, 38) if d == 2 else (20, 17, 12)
+    P, u = synth.smooth_fields(shape, seed=4)
+    pb = O.Problem(d=d, n=shape, s1=1.5)
+    ref0 = O.sums(pb, O.init(pb, P, u))
+    for storage, tol in (("f64", 1e-13), ("f32", 1e-6)):
+        lat = Lattice(shape, s1=1.5, storage=storage)
+        lat.init(P, u)
+        s0 = lat.sums()
+        lat.step(200)
+        s1 = lat.sums()
+        lat.close()
+        scale = np.abs(ref0).max()
+        assert np.abs(s0 - ref0).max() < tol * scale, (storage, s0, ref0)
+        assert np.abs(s1 - s0).max() < tol * scale, (storage, s1, s0)
+
+
+def test_residual_matches_definition():
+    from paper_2108_08591_gb300 import Lattice
+    shape = (64, 48)
+    P, u = synth.smooth_fields(shape, seed=8)
+    lat = Lattice(shape, s1=1.7, storage="f64")
+    lat.init(P, u)
+    assert lat.residual() == float("inf")
+    u0 = lat.fields_host(("u",))["u"]
+    lat.step(10)
+    r = lat.residual()
+    u1 = lat.fields_host(("u",))["u"]
+    want = np.linalg.norm(u1 - u0) / np.linalg.norm(u1)
+    assert r == pytest.approx(want, rel=1e-10)
+    lat.close()
+
+
+def test_nonfinite_is_reported():
+    from paper_2108_08591_gb300 import Lattice, MdfError
+    shape = (32, 16)
+    P, u = synth.rest_state(512, 2)
+    P[77] = np.nan
+    lat = Lattice(shape, s1=1.2)
+    lat.init(P, u)
+    with pytest.raises(MdfError, match="EDIVERGED"):
+        lat.sums()
+    lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_checkpoint_resume_is_bit_identical(storage):
+    from paper_2108_08591_gb300 import Lattice, MdfError
+    shape = (50, 30)
+    P, u = synth.smooth_fields(shape, seed=2)
+    a = Lattice(shape, s1=1.4, storage=storage)
+    a.init(P, u)
+    a.step(33)
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "ck.mdf")
+        a.save(path)
+        a.step(40)
+        b = Lattice(shape, s1=1.4, storage=storage)
+        b.load(path)
+        assert b.info.step == 33
+        b.step(40)
+        assert np.array_equal(a.fields_host(("u", "P", "G"))["G"], b.fields_host(("u", "P", "G"))["G"])
+        # corrupt file is rejected
+        raw = bytearray(open(path, "rb").read())
+        raw[-5] ^= 0xFF
+        open(path, "wb").write(bytes(raw))
+        with pytest.raises(MdfError, match="EIO"):
+            b.load(path)
+        # a handle of another configuration refuses the file
+        c = Lattice(shape, s1=1.41, storage=storage)
+        a.save(path)
+        with pytest.raises(MdfError, match="EIO"):
+            c.load(path)
+        b.close()
+        c.close()
+    a.close()
+
+
+@pytest.mark.parametrize("shape", [(2, 2), (3, 2), (33, 2), (2, 2, 2), (5, 3, 2)])
+def test_smallest_grids(shape):
+    P, u = synth.smooth_fields(shape, seed=1)
+    got = run_gpu(shape, P, u, 25, 1.1, storage="f64")
+    ref = run_oracle(shape, P, u, 25, 1.1)
+    e = errors(ref, got)
+    assert e["u"] < 1e-10, e
+
+
+def test_zero_steps_and_graph_chunks():
+    """n = 0 is a no-op; long runs (graph chunks of 64 plus a remainder)
+    equal the same number of single steps."""
+    import torch
+    from paper_2108_08591_gb300 import Lattice
+    shape = (96, 20)
+    P, u = synth.smooth_fields(shape, seed=6)
+    s = torch.cuda.Stream()  # graphs are captured on a non-legacy stream only
+    a = Lattice(shape, s1=1.3, stream=s)
+    b = Lattice(shape, s1=1.3, stream=s)
+    a.init(P, u)
+    b.init(P, u)
+    a.step(0)
+    a.step(64 * 2 + 13)
+    for _ in range(64 * 2 + 13):
+        b.step(1)
+    assert np.array_equal(a.fields_host(("u",))["u"], b.fields_host(("u",))["u"])
+    assert a.info.step == b.info.step == 141
+    a.close()
+    b.close()
+
+
+# --------------------------------------------------------------------------
+# Full size (4096^2, the benchmark's configuration): sampled parity
+# --------------------------------------------------------------------------
+def test_full_size_4096_sampled_parity():
+    """4096^2 D2Q5 x 3, FP32 storage, Taylor-Green + 8 modes, run as the
+    benchmark runs it (fused epilogue update, then graph chunks).  After n
+    steps a node depends only on nodes within distance n, so the oracle runs
+    a periodic (2n+1)^2 window around each sampled node."""
+    import torch
+    from paper_2108_08591_gb300 import Lattice
+    n, steps = 4096, 71
+    P, u = synth.tg_plus_modes(n, U0=0.01, seed=2108)
+    lat = Lattice((n, n), s1=S1_TG, storage="f32")
+    lat.init(P, u)
+    fl = lat.alloc_fields(("P", "u", "G", "div"))
+    lat.step_fields(steps, fl)
+    out = lat.fields(("P", "u", "G", "omega", "div"))
+    torch.cuda.synchronize()
+    # fields of the initial state from the fused update: divergence identity
+    G0 = fl["G"].cpu().numpy()
+    assert np.abs(fl["div"].cpu().numpy()).max() < 1e-9 * np.abs(G0).max()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    assert np.abs(got["div"]).max() < 1e-9 * np.abs(got["G"]).max()
+    lat.close()
+    rng = synth.SplitMix64(77)
+    pts = [(rng.randint(0, n - 1), rng.randint(0, n - 1)) for _ in range(12)] + [(0, 0), (n - 1, n - 1)]
+    half = steps
+    ref_u, got_u, ref_P, got_P, ref_w, got_w = [], [], [], [], [], []
+    for cx, cy in pts:
+        Pw, uw = synth.window(n, [P, u], cx, cy, half)
+        W = 2 * half + 1
+        pb = O.Problem(d=2, n=(W, W), s1=S1_TG)
+        f = O.init(pb, Pw, uw)
+        O.run(pb, f, steps)
+        c = half * W + half
+        Pr, ur, _ = O.macro(pb, f)
+        D = O.derived(pb, f)
+        g = cy * n + cx
+        ref_u.append(ur[:, c]); got_u.append(got["u"][:, g])
+        ref_P.append(Pr[c] - 1.0); got_P.append(got["P"][g] - 1.0)
+        ref_w.append(D["omega"][0, c]); got_w.append(got["omega"][0, g])
+    assert rel(np.array(ref_u), np.array(got_u)) < 1e-5
+    assert rel(np.array(ref_P), np.array(got_P)) < 1e-5
+    assert rel(np.array(ref_w), np.array(got_w)) < 1e-3
