@@ -35,7 +35,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % HBM roofline vs FP64 oracle error; time-to-steady (warm vs cold)"
-N_GRID = 4096
+N_GRID = 4096  # --grid overrides it (small cases for profiling)
 EPI_EVERY = 100
 NU = 0.01
 S1 = 1.0 / (3 * NU + 0.5)
@@ -342,7 +342,13 @@ def main():
     ap.add_argument("--impl", choices=("mdf", "reference"), default="mdf")
     ap.add_argument("--storage", choices=("f32", "f16", "bf16"), default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=4096,
+                    help="lattice side (default 4096; smaller sides are profiling cases)")
     args = ap.parse_args()
+    global N_GRID, WORKLOAD
+    if args.grid != N_GRID:
+        WORKLOAD = WORKLOAD.replace("4096x4096", f"{args.grid}x{args.grid}")
+        N_GRID = args.grid
     if args.warmup < 3 and args.impl == "mdf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

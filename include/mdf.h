@@ -133,7 +133,8 @@ mdf_status mdf_init(mdf_t h, const double *P, const double *u, int where);
 /*
  * mdf_set_force -- body force Fbar_alpha(x) of Eq. 2-6 (F_i = w_i Fbar_alpha),
  * added as dt w_i Fbar_alpha in Eq. 3-21.  F[d][N] FP64 in `where` memory,
- * stored on the device in FP32; NULL removes the force.
+ * stored on the device in the compute precision (FP32; FP64 for MDF_F64
+ * storage); NULL removes the force.
  */
 mdf_status mdf_set_force(mdf_t h, const double *F, int where);
 

@@ -44,7 +44,7 @@ struct mdf_s {
   cudaStream_t stream = nullptr;
   void *cur = nullptr, *nxt = nullptr;  // population buffers
   uint8_t *mask = nullptr;
-  float *force = nullptr;
+  void *force = nullptr;  // FP32, or FP64 with FP64 storage
   double *stage = nullptr;  // staging for host inputs/outputs
   size_t stage_bytes = 0;
   double *uprev = nullptr;  // residual memory [d][N]
@@ -331,10 +331,12 @@ mdf_status mdf_set_force(mdf_t h, const double *F, int where) {
     h->force = nullptr;
     return MDF_OK;
   }
+  const bool f64 = h->storage == MDF_F64;
+  const size_t fbytes = (f64 ? sizeof(double) : sizeof(float)) * (size_t)h->plane * h->d;
   if (!h->force) {
-    cudaError_t e = cudaMalloc(&h->force, sizeof(float) * (size_t)h->plane * h->d);
+    cudaError_t e = cudaMalloc(&h->force, fbytes);
     if (e != cudaSuccess) { cudaGetLastError(); h->force = nullptr; return fail(h, MDF_ENOMEM, "force: %s", cudaGetErrorString(e)); }
-    CU(h, cudaMemsetAsync(h->force, 0, sizeof(float) * (size_t)h->plane * h->d, h->stream));
+    CU(h, cudaMemsetAsync(h->force, 0, fbytes, h->stream));
   }
   const double *src = F;
   const size_t nb = sizeof(double) * (size_t)h->N * h->d;
@@ -346,7 +348,7 @@ mdf_status mdf_set_force(mdf_t h, const double *F, int where) {
   } else if (where != MDF_DEVICE) {
     return fail(h, MDF_EINVAL, "set_force: bad `where` %d", where);
   }
-  CU(h, launch_pad_force(src, h->force, h->d, h->nx, h->ny, h->nz, h->px, h->stream));
+  CU(h, launch_pad_force(src, h->force, f64, h->d, h->nx, h->ny, h->nz, h->px, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   return MDF_OK;
 }

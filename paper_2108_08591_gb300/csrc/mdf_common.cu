@@ -30,7 +30,8 @@ cudaError_t launch_reduce_final(const DevArgs &a, int nblocks, int k, cudaStream
   return cudaGetLastError();
 }
 
-__global__ void k_pad_force(const double *__restrict__ src, float *__restrict__ dst, int d, int nx,
+template <class T>
+__global__ void k_pad_force(const double *__restrict__ src, T *__restrict__ dst, int d, int nx,
                             int ny, int nz, int px) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= nx) return;
@@ -38,13 +39,14 @@ __global__ void k_pad_force(const double *__restrict__ src, float *__restrict__ 
   const long long N = (long long)nx * ny * nz, plane = (long long)px * ny * nz;
   const long long n = ((long long)z * ny + y) * nx + x;
   const long long idx = ((long long)z * ny + y) * px + x;
-  for (int b = 0; b < d; ++b) dst[b * plane + idx] = (float)src[b * N + n];
+  for (int b = 0; b < d; ++b) dst[b * plane + idx] = (T)src[b * N + n];
 }
 
-cudaError_t launch_pad_force(const double *src, float *dst, int d, int nx, int ny, int nz, int px,
-                             cudaStream_t s) {
+cudaError_t launch_pad_force(const double *src, void *dst, bool f64, int d, int nx, int ny, int nz,
+                             int px, cudaStream_t s) {
   dim3 grid((unsigned)((nx + kBlockX - 1) / kBlockX), (unsigned)ny, (unsigned)nz);
-  k_pad_force<<<grid, kBlockX, 0, s>>>(src, dst, d, nx, ny, nz, px);
+  if (f64) k_pad_force<double><<<grid, kBlockX, 0, s>>>(src, (double *)dst, d, nx, ny, nz, px);
+  else k_pad_force<float><<<grid, kBlockX, 0, s>>>(src, (float *)dst, d, nx, ny, nz, px);
   return cudaGetLastError();
 }
 

@@ -12,7 +12,7 @@ struct DevArgs {
   const void *fin;               // current populations (post-collision, pre-stream)
   void *fout;                    // next populations
   const uint8_t *mask;           // link mask [plane] or null (periodic)
-  const float *force;            // [d][plane] body force or null
+  const void *force;             // [d][plane] body force (compute type) or null
   int nx, ny, nz, px;            // grid and padded x pitch
   long long plane;               // px * ny * nz
   int with_rho;                  // 1: set 0 is the alpha = 0 set
@@ -59,8 +59,8 @@ cudaError_t launch_mask_d3q7(const int wall[3], int lid, const DevArgs &a, uint8
 
 // Second reduction pass: sums `nblocks` x `k` partials in a fixed order.
 cudaError_t launch_reduce_final(const DevArgs &a, int nblocks, int k, cudaStream_t s);
-// Dense FP64 [d][N] -> padded FP32 [d][plane].
-cudaError_t launch_pad_force(const double *src, float *dst, int d, int nx, int ny, int nz,
-                             int px, cudaStream_t s);
+// Dense FP64 [d][N] -> padded [d][plane] in FP32 (f64 = false) or FP64.
+cudaError_t launch_pad_force(const double *src, void *dst, bool f64, int d, int nx, int ny,
+                             int nz, int px, cudaStream_t s);
 
 }  // namespace mdf

@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kBlockX) k_update(const DevArgs A) {
     TC jeq[D];  // Eq. 3-7a: sum_i c_i f^eq = u_alpha u + P E_alpha (shifted: P')
 #pragma unroll
     for (int b = 0; b < D; ++b) jeq[b] = u[a] * u[b] + (a == b ? Pp : TC(0));
-    const TC F = A.force ? TC(__ldg(A.force + a * A.plane + idx)) : TC(0);
+    const TC F = A.force ? __ldg(static_cast<const TC *>(A.force) + a * A.plane + idx) : TC(0);
     L::relax(g[a], jeq, s1, s2, F);
     TS *base = fout + (long long)(a1 + a) * Q * A.plane + idx;
 #pragma unroll

@@ -7,7 +7,10 @@ P - mean(P)):
   * FP32 storage: u, P within 1e-5.  Derived fields within 1e-4: one FP32
     rounding of a shifted population (|g| ~ 3e-3, ulp ~ 2e-10) against the
     first moment of f^ne (~1e-4 .. 1e-5 at these sizes) gives ~1e-6 per node.
-  * FP16 storage: u, P within 2e-3.  BF16: reported, within 2e-2.
+  * FP16 storage: u within 2e-3.  The pressure fluctuation P' ~ U^2 is
+    carried by populations of size ~U, so rest-shifted FP16 resolves it only
+    to ~2e-3 .. 5e-3 relative: bound 5e-3.  BF16 (8-bit significand):
+    reported, u within 2e-2, P within 5e-2.
 Masks are compared byte for byte.
 """
 import os
@@ -36,8 +39,9 @@ def _built():
 
 
 def _tol(storage):
-    return {"f64": (1e-10, 1e-8), "f32": (1e-5, 1e-4), "f16": (2e-3, 5e-2),
-            "bf16": (2e-2, 3e-1)}[storage]
+    """(u, P - mean P, derived fields) bounds per storage type."""
+    return {"f64": (1e-10, 1e-10, 1e-8), "f32": (1e-5, 1e-5, 1e-4),
+            "f16": (2e-3, 5e-3, 5e-2), "bf16": (2e-2, 5e-2, 3e-1)}[storage]
 
 
 # --------------------------------------------------------------------------
@@ -51,8 +55,8 @@ def test_taylor_green_64_matches_oracle(storage):
     got = run_gpu((n, n), P, u, steps, S1_TG, storage=storage)
     ref = run_oracle((n, n), P, u, steps, S1_TG)
     e = errors(ref, got)
-    tu, tg = _tol(storage)
-    assert e["u"] < tu and e["P"] < tu, e
+    tu, tp, tg = _tol(storage)
+    assert e["u"] < tu and e["P"] < tp, e
     for k in ("G", "S", "sigma", "omega"):
         assert e[k] < tg, (k, e)
     assert e["rho"] < (1e-12 if storage == "f64" else 1e-6)
@@ -67,9 +71,9 @@ def test_ragged_grid_2d(storage):
     got = run_gpu(shape, P, u, steps, s1, storage=storage)
     ref = run_oracle(shape, P, u, steps, s1)
     e = errors(ref, got)
-    tu, tg = _tol(storage)
+    tu, tp, tg = _tol(storage)
     print(storage, e)
-    assert e["u"] < tu and e["P"] < tu, e
+    assert e["u"] < tu and e["P"] < tp, e
     assert e["G"] < tg and e["omega"] < tg, e
 
 
@@ -93,8 +97,8 @@ def test_d3q7_ragged_matches_oracle(storage):
     got = run_gpu(shape, P, u, steps, s1, storage=storage)
     ref = run_oracle(shape, P, u, steps, s1)
     e = errors(ref, got)
-    tu, tg = _tol(storage)
-    assert e["u"] < tu and e["P"] < tu, e
+    tu, tp, tg = _tol(storage)
+    assert e["u"] < tu and e["P"] < tp, e
     for k in ("G", "S", "sigma", "omega"):
         assert e[k] < tg, (k, e)
 
@@ -124,8 +128,8 @@ def test_lid_driven_cavity_2d(storage):
     ref = run_oracle(shape, P, u, steps, s1, **kw)
     assert np.array_equal(got["mask"], ref["mask"])
     e = errors(ref, got)
-    tu, tg = _tol(storage)
-    assert e["u"] < tu and e["P"] < tu, e
+    tu, tp, tg = _tol(storage)
+    assert e["u"] < tu and e["P"] < tp, e
     assert e["G"] < tg and e["omega"] < tg, e
 
 
@@ -147,11 +151,13 @@ def test_mixed_walls_and_force():
     X, Y = synth.grid_coords(shape)
     F = np.stack([1e-5 * (1.0 + 0.5 * np.cos(2 * np.pi * X / 40)), 2e-6 * np.sin(2 * np.pi * Y / 33)])
     P, u = synth.rest_state(shape[0] * shape[1], 2)
-    for storage, tol in (("f64", 1e-10), ("f32", 1e-5)):
+    # the pressure fluctuation of this flow is ~1e-7, so FP32 storage
+    # rounding (~1e-11 absolute) leaves ~1e-5 relative on it: bound 5e-5
+    for storage, tol, tolp in (("f64", 1e-10, 1e-10), ("f32", 1e-5, 5e-5)):
         got = run_gpu(shape, P, u, steps, s1, storage=storage, wall=(0, 1, 0), force=F)
         ref = run_oracle(shape, P, u, steps, s1, wall=(0, 1, 0), force=F)
         e = errors(ref, got)
-        assert e["u"] < tol and e["P"] < max(tol, 1e-5), (storage, e)
+        assert e["u"] < tol and e["P"] < tolp, (storage, e)
 
 
 # --------------------------------------------------------------------------
