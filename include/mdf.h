@@ -152,6 +152,35 @@ mdf_status mdf_step_fields(mdf_t h, long long n, const mdf_fields_t *out);
 /* mdf_fields -- derived fields of the current state (no step taken). */
 mdf_status mdf_fields(mdf_t h, const mdf_fields_t *out);
 
+/*
+ * mdf_fields_host_noalloc -- like mdf_fields() with out->where = MDF_HOST,
+ * but it allocates nothing.  (This is a library service; the paper has no
+ * counterpart.)  mdf_fields() stages host readbacks through a device buffer
+ * that the handle grows with cudaMalloc when needed.  Callers that cannot
+ * let the library allocate at that moment use this entry point instead:
+ * processes whose GPU memory is fully reserved by another allocator (a
+ * framework's caching pool, an MPS memory quota), or code that runs while
+ * allocation is forbidden, e.g. while another thread captures a CUDA graph
+ * in global capture mode.  The fields are staged in one fixed 16 MiB device
+ * buffer compiled into the library (2,097,152 doubles), which every GPU that
+ * loads the library holds until the process exits.
+ *   out: host arrays, out->where must be MDF_HOST; layout as mdf_fields_t.
+ * Limits and behaviour:
+ *   - the requested fields together may hold at most 2,097,152 doubles
+ *     (e.g. P and u of a 2D lattice up to 699,050 nodes); larger requests
+ *     return MDF_EINVAL with a message and do nothing;
+ *   - the first call on a GPU looks up that buffer's device address (a
+ *     one-time set-up per GPU); make that first call before any stream
+ *     capture begins;
+ *   - every call on a GPU shares the one buffer, which keeps the last call's
+ *     contents.  Each call writes every requested field in full before
+ *     reading it back, so nothing needs clearing, but calls that overlap on
+ *     the GPU (from several threads or streams at once) race on the buffer:
+ *     serialise them.  The call synchronises h's stream before returning.
+ *   - like every entry point, call it with h's GPU current.
+ */
+mdf_status mdf_fields_host_noalloc(mdf_t h, const mdf_fields_t *out);
+
 /* mdf_moments -- P (Eq. 3-15), u (Eq. 2-7) and rho (nullable) on the device. */
 mdf_status mdf_moments(mdf_t h, double *P, double *u, double *rho);
 

@@ -173,6 +173,17 @@ class Lattice:
         self._check(self._lib.mdf_fields(self._h, ctypes.byref(f)))
         return out
 
+    def fields_host_noalloc(self, names: Iterable[str] = ("P", "u"), out=None) -> Dict[str, np.ndarray]:
+        """As fields_host(), but the library allocates no device memory: the
+        fields are staged in its fixed 16 MiB buffer (at most 2,097,152
+        doubles per call; calls from several threads must not overlap)."""
+        shapes = field_shapes(self.d, self.N)
+        if out is None:
+            out = {k: np.empty(shapes[k]) for k in names}
+        f = self._fields_struct(out, HOST)
+        self._check(self._lib.mdf_fields_host_noalloc(self._h, ctypes.byref(f)))
+        return out
+
     def moments(self):
         o = self.fields(("P", "u", "rho") if self.with_rho else ("P", "u"))
         return o["P"], o["u"], o.get("rho")

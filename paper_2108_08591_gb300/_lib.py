@@ -62,6 +62,7 @@ SIGNATURES = {
     "mdf_step": (ctypes.c_int, [H, ctypes.c_longlong]),
     "mdf_step_fields": (ctypes.c_int, [H, ctypes.c_longlong, ctypes.POINTER(Fields)]),
     "mdf_fields": (ctypes.c_int, [H, ctypes.POINTER(Fields)]),
+    "mdf_fields_host_noalloc": (ctypes.c_int, [H, ctypes.POINTER(Fields)]),
     "mdf_moments": (ctypes.c_int, [H, DP, DP, DP]),
     "mdf_gradients": (ctypes.c_int, [H, DP, DP, DP, DP, DP]),
     "mdf_sums": (ctypes.c_int, [H, DP]),

@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -553,3 +554,94 @@ mdf_status mdf_sync(mdf_t h) {
 const char *mdf_last_error(mdf_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free readback of the derived fields to host memory.
+//
+// mdf_fields() with host outputs stages the fields in a device buffer that
+// the handle grows with cudaMalloc on demand.  Some callers cannot let the
+// library allocate at that point: a process whose GPU memory is fully
+// reserved by another allocator (a framework's caching pool, an MPS memory
+// quota), or code running while allocation is forbidden (for instance while
+// another thread captures work in global capture mode, where a cudaMalloc
+// would invalidate that capture).  mdf_fields_host_noalloc stages through
+// the fixed buffer below instead and calls no allocating routine.
+// ---------------------------------------------------------------------------
+namespace {
+
+// 2,097,152 doubles = 16 MiB, held on every GPU that loads this library
+// until the process exits.  Shared by all calls on that GPU.
+constexpr size_t kNoallocStageDoubles = size_t(1) << 21;
+static __device__ __align__(256) double g_noalloc_stage[kNoallocStageDoubles];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double *g_noalloc_addr[kMaxDevices] = {};  // device address of the buffer, per GPU
+
+// Device address of g_noalloc_stage on the GPU that holds h's populations.
+// Looked up once per GPU (with that GPU current) and cached: in host code the
+// symbol name is only a host-side stand-in, never a device address.
+mdf_status noalloc_stage_address(mdf_t h, double **out) {
+  cudaPointerAttributes attr;
+  CU(h, cudaPointerGetAttributes(&attr, h->buf[0]));
+  const int dev = attr.device;
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(h, MDF_EUNSUPPORTED, "fields_host_noalloc: device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    int cur = 0;
+    CU(h, cudaGetDevice(&cur));
+    if (cur != dev) CU(h, cudaSetDevice(dev));
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stage);
+    if (cur != dev) cudaSetDevice(cur);
+    if (e != cudaSuccess || !p)
+      return fail(h, MDF_ECUDA, "fields_host_noalloc: cudaGetSymbolAddress failed: %s",
+                  cudaGetErrorString(e));
+    g_noalloc_addr[dev] = static_cast<double *>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return MDF_OK;
+}
+
+}  // namespace
+
+extern "C" mdf_status mdf_fields_host_noalloc(mdf_t h, const mdf_fields_t *out) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!out) return fail(h, MDF_EINVAL, "fields_host_noalloc: null outputs");
+  if (out->where != MDF_HOST)
+    return fail(h, MDF_EINVAL, "fields_host_noalloc: outputs must be host arrays (where = MDF_HOST)");
+  if (out->rho && !h->with_rho)
+    return fail(h, MDF_EINVAL, "rho requested without the alpha = 0 set");
+  if (fields_empty(out)) return MDF_OK;
+  const size_t N = (size_t)h->N;
+  const int d = h->d;
+  double *const host[8] = {out->P, out->u, out->rho, out->G, out->div, out->S, out->sigma, out->omega};
+  const size_t count[8] = {N, d * N, N, (size_t)d * d * N, N, nsym(d) * N, nsym(d) * N,
+                           (size_t)(d == 2 ? 1 : 3) * N};
+  size_t total = 0;
+  for (int k = 0; k < 8; ++k)
+    if (host[k]) total += count[k];
+  if (total > kNoallocStageDoubles)
+    return fail(h, MDF_EINVAL,
+                "fields_host_noalloc: the requested fields need %zu doubles but the static "
+                "staging buffer holds %zu (16 MiB); request fewer fields or use mdf_fields",
+                total, kNoallocStageDoubles);
+  double *stage = nullptr;
+  mdf_status st = noalloc_stage_address(h, &stage);
+  if (st != MDF_OK) return st;
+  // Every requested field is written in full by the kernel, so no part of the
+  // shared buffer has to be cleared first.
+  DevArgs a = base_args(h);
+  double **slot[8] = {&a.P, &a.u, &a.rho, &a.G, &a.div, &a.S, &a.sigma, &a.omega};
+  double *p = stage;
+  for (int k = 0; k < 8; ++k)
+    if (host[k]) { *slot[k] = p; p += count[k]; }
+  CU(h, launch_update(h, MODE_FIELDS, a));
+  for (int k = 0; k < 8; ++k)
+    if (host[k])
+      CU(h, cudaMemcpyAsync(host[k], *slot[k], count[k] * sizeof(double), cudaMemcpyDeviceToHost,
+                            h->stream));
+  CU(h, cudaStreamSynchronize(h->stream));
+  return MDF_OK;
+}
