@@ -42,6 +42,9 @@ S1 = 1.0 / (3 * NU + 0.5)
 WORKLOAD = ("2D Taylor-Green + 8 seeded divergence-free modes (seed 2108), periodic "
             "4096x4096, D2Q5 x 3 sets, FP32 rest-shifted storage, FP32 arithmetic, "
             "epilogue every 100 steps")
+# the 3D case (--workload tg3d): Taylor-Green vortex, 512^3, D3Q7 x 4 sets,
+# U0 = 0.05, Re = 1600 on U0 and k = 2 pi / 512, epilogue every 200 steps
+TG3D_U0, TG3D_RE = 0.05, 1600.0
 KERNEL_SOURCES = ("paper_2108_08591_gb300/csrc/mdf_kernels.cuh",
                   "paper_2108_08591_gb300/csrc/mdf_lattice.cuh")
 
@@ -53,11 +56,14 @@ def _dist():
     return rank, world, local
 
 
-def _config(n_gpus: int, storage: str):
-    return {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "lattice": "D2Q5", "sets": 3,
-            "storage": storage, "steps_per_bench_step": EPI_EVERY,
+def _config(n_gpus: int, storage: str, d: int = 2):
+    grid = [N_GRID] * d
+    pop_gb = N_GRID ** d * (5 * 3 if d == 2 else 7 * 4) * {"f32": 4, "f16": 2, "bf16": 2}.get(
+        storage, 8) / 1e9
+    return {"workload": WORKLOAD, "grid": grid, "lattice": "D2Q5" if d == 2 else "D3Q7",
+            "sets": d + 1, "storage": storage, "steps_per_bench_step": EPI_EVERY,
             "global_batch": n_gpus, "parallelism": f"replicas x{n_gpus}",
-            "l2": "inputs larger than L2 (2 x 1.0 GB populations), no flush"}
+            "l2": f"inputs larger than L2 (2 x {pop_gb:.2f} GB populations), no flush"}
 
 
 def _kernel_sha() -> str:
@@ -203,11 +209,70 @@ def run_reference(args):
     return 0
 
 
+def _workload(args):
+    """(shape, s1, P, u) of the benchmark workload, FP64 host arrays."""
+    import synth
+    if args.workload == "tg2d":
+        P, u = synth.tg_plus_modes(N_GRID, U0=0.01, seed=2108)
+        return (N_GRID, N_GRID), S1, P, u
+    k = 2 * math.pi / N_GRID
+    nu = TG3D_U0 / (k * TG3D_RE)
+    P, u = synth.taylor_green_3d(N_GRID, U0=TG3D_U0)
+    return (N_GRID,) * 3, 1.0 / (4 * nu + 0.5), P, u
+
+
+def sampled_oracle_error(shape, s1, P, u, storage, steps, samples=8, seed=77):
+    """FP64 oracle error of the GPU fields at full size, on sampled nodes.
+
+    After `steps` updates a node depends only on nodes within that many
+    links, so the oracle advances a periodic (2 steps + 1)^d window around
+    each sampled node; the GPU runs the whole lattice as the benchmark does
+    (fused epilogue update first, then plain updates)."""
+    import numpy as np
+    import oracle
+    import synth
+    from paper_2108_08591_gb300 import Lattice
+    d = len(shape)
+    lat = Lattice(shape, s1=s1, storage=storage)
+    lat.init(P, u)
+    fl = lat.alloc_fields(("P",))
+    lat.step_fields(steps, fl)
+    got = {k: v.cpu().numpy() for k, v in lat.fields(("P", "u", "omega")).items()}
+    lat.close()
+    rng = synth.SplitMix64(seed)
+    n = shape[0]
+    W = 2 * steps + 1
+    ref, num = {"u": [], "P": [], "omega": []}, {"u": [], "P": [], "omega": []}
+    for _ in range(samples):
+        c = [rng.randint(0, n - 1) for _ in range(d)]
+        offs = np.arange(-steps, steps + 1)
+        axes = [(c[b] + offs) % n for b in range(d)]
+        if d == 2:
+            sel = (axes[1][:, None] * n + axes[0][None, :]).ravel()
+            g = c[1] * n + c[0]
+        else:
+            sel = ((axes[2][:, None, None] * n + axes[1][None, :, None]) * n
+                   + axes[0][None, None, :]).ravel()
+            g = (c[2] * n + c[1]) * n + c[0]
+        pb = oracle.Problem(d=d, n=(W,) * d, s1=s1)
+        f = oracle.init(pb, P[sel], u[:, sel])
+        oracle.run(pb, f, steps)
+        Pr, ur, _ = oracle.macro(pb, f)
+        D = oracle.derived(pb, f)
+        mid = (W ** d) // 2
+        ref["u"].append(ur[:, mid]); num["u"].append(got["u"][:, g])
+        ref["P"].append(Pr[mid] - 1.0); num["P"].append(got["P"][g] - 1.0)
+        ref["omega"].append(D["omega"][:, mid]); num["omega"].append(got["omega"][:, g])
+    err = {k: oracle.rel_l2(np.array(ref[k]), np.array(num[k])) for k in ref}
+    err["case"] = (f"{samples} seeded nodes of the full lattice after {steps} updates, "
+                   f"FP64 oracle on periodic {W}^{d} windows; P compared as P - 1")
+    return err
+
+
 def run_mdf(args):
     import numpy as np
     import torch
 
-    import synth
     from paper_2108_08591_gb300 import Lattice, _build
 
     rank, world, local = _dist()
@@ -223,10 +288,11 @@ def run_mdf(args):
     if dist is not None:
         dist.barrier()
 
-    P, u = synth.tg_plus_modes(N_GRID, U0=0.01, seed=2108)
-    N = N_GRID * N_GRID
+    shape, s1, P, u = _workload(args)
+    d = len(shape)
+    N = int(np.prod(shape))
     stream = torch.cuda.current_stream()
-    lat = Lattice((N_GRID, N_GRID), s1=S1, storage=args.storage, stream=stream)
+    lat = Lattice(shape, s1=s1, storage=args.storage, stream=stream)
     lat.init(P, u)
     info = lat.info
     fields = lat.alloc_fields(("P", "u", "G", "div", "S", "sigma", "omega"))
@@ -235,7 +301,7 @@ def run_mdf(args):
         lat.step_fields(1, fields)  # fused epilogue update
         if ev_a is not None:
             ev_a.record(stream)
-        lat.step(EPI_EVERY - 1)  # plain updates (CUDA-graph chunks)
+        lat.step(EPI_EVERY - 1)  # plain updates
         if ev_b is not None:
             ev_b.record(stream)
 
@@ -271,13 +337,13 @@ def run_mdf(args):
     value = updates_local * world / (t_max / 1e3) / 1e6
 
     # end to end through the C-ABI with host buffers: every step copies the
-    # step's inputs (P, u) from pinned host memory, runs the 100 updates with
-    # the fused epilogue and reads (P, u) back to pinned host memory
+    # step's inputs (P, u) from pinned host memory, runs the updates with the
+    # fused epilogue and reads (P, u) back to pinned host memory
     e2e_steps = max(1, min(args.steps, 5))
     Ph = torch.from_numpy(P).pin_memory().numpy()
     uh = torch.from_numpy(np.ascontiguousarray(u)).pin_memory().numpy()
     outP = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
-    outu = torch.empty((2, N), dtype=torch.float64).pin_memory().numpy()
+    outu = torch.empty((d, N), dtype=torch.float64).pin_memory().numpy()
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
@@ -294,6 +360,8 @@ def run_mdf(args):
         e2e_s = float(t.item())
     e2e_value = e2e_steps * EPI_EVERY * N * world / e2e_s / 1e6
     lat.close()
+    del fields
+    torch.cuda.empty_cache()
 
     if rank != 0:
         if dist is not None:
@@ -304,23 +372,31 @@ def run_mdf(args):
     bytes_per_launch = info.bytes_per_update * N
     achieved = bytes_per_launch / (plain_ms / 1e3) / 1e9
     sha = _kernel_sha()
-    traffic = _traffic(sha)
+    traffic = _traffic(sha) if (args.workload == "tg2d" and N_GRID == 4096
+                                and args.storage == "f32") else None
+    oerr = None
+    if not args.no_oracle_check:
+        oerr = sampled_oracle_error(shape, s1, P, u, args.storage, steps=64 if d == 2 else 16)
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
+    if world == 1 and not args.no_cpu_baseline and args.workload == "tg2d":
         cpu = cpu_oracle_sample()
+    kname = {2: "D2Q5", 3: "D3Q7"}[d]
+    tname = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}[args.storage]
+    kernel = (f"k_update_vec<{kname},{tname},VX={info.vx},MODE_STEP,periodic>" if info.vx > 1
+              else f"k_update<{kname},{tname},MODE_STEP,periodic>")
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f32": "f32", "f16": "f16 storage / f32", "bf16": "bf16 storage / f32",
-                  "f64": "f64"}[args.storage],
-        "data": "synthetic", "config": _config(world, args.storage),
+        "dtype": {"f32": "f32", "f16": "f16 storage / f32", "bf16": "bf16 storage / f32"}[args.storage],
+        "data": "synthetic", "config": _config(world, args.storage, d),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
-                     "kernel": "k_update<D2Q5,float,MODE_STEP,periodic>",
+                     "kernel": kernel, "block": info.block,
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": plain_ms, "kernel_sha": sha},
+        "fp64_oracle_error": oerr,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "steps": e2e_steps,
                 "h2d_bytes_per_step": int(P.nbytes + u.nbytes),
@@ -342,13 +418,24 @@ def main():
     ap.add_argument("--impl", choices=("mdf", "reference"), default="mdf")
     ap.add_argument("--storage", choices=("f32", "f16", "bf16"), default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--workload", choices=("tg2d", "tg3d"), default="tg2d",
+                    help="tg2d: the 4096^2 D2Q5 x 3 line (default); tg3d: 512^3 D3Q7 x 4")
     ap.add_argument("--grid", type=int, default=4096,
                     help="lattice side (default 4096; smaller sides are profiling cases)")
     args = ap.parse_args()
-    global N_GRID, WORKLOAD
-    if args.grid != N_GRID:
-        WORKLOAD = WORKLOAD.replace("4096x4096", f"{args.grid}x{args.grid}")
+    global N_GRID, WORKLOAD, EPI_EVERY
+    if args.workload == "tg3d":
+        N_GRID, EPI_EVERY = 512, 200
+        WORKLOAD = (f"3D Taylor-Green vortex, periodic 512^3, D3Q7 x 4 sets, U0 = {TG3D_U0}, "
+                    f"Re = {TG3D_RE:.0f}, {args.storage.upper()} rest-shifted storage, FP32 "
+                    "arithmetic, epilogue every 200 steps")
+    if args.grid != 4096:
+        WORKLOAD = WORKLOAD.replace(f"{N_GRID}x{N_GRID}", f"{args.grid}x{args.grid}").replace(
+            f"{N_GRID}^3", f"{args.grid}^3")
         N_GRID = args.grid
+    if args.impl == "mdf" and args.storage != "f32":
+        WORKLOAD = WORKLOAD.replace("FP32 rest-shifted", f"{args.storage.upper()} rest-shifted")
     if args.warmup < 3 and args.impl == "mdf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

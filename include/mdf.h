@@ -71,6 +71,12 @@ typedef struct {
                                 sets are advanced; 0: only the d velocity sets (the
                                 paper shows alpha = 0 can be omitted, Sec. 3.2) */
     void *stream;            /* cudaStream_t to enqueue on; NULL = legacy default */
+    int vx;                  /* x-nodes per thread of the update kernel: 0 = tuned
+                                default; 1 = one node per thread; 2, 4, 8 = vector
+                                widths (FP32: 2, 4; FP16/BF16: 4, 8; FP64: 2).  A
+                                width that does not divide nx falls back to 1. */
+    int block;               /* threads per block of the update kernel: 0 = tuned
+                                default, else a multiple of 32 in [32, 256] */
 } mdf_opts;
 
 /* Derived-field outputs, each a caller-owned array of doubles or NULL.
@@ -101,6 +107,7 @@ typedef struct {
     double bytes_per_update; /* algorithmic bytes per node update: one read and one
                                 write of every population (2 q nsets sizeof(T)) */
     double s0, s1, s2;
+    int vx, block;           /* launch shape of the update kernel in use */
 } mdf_info_t;
 
 /*
@@ -218,6 +225,16 @@ mdf_status mdf_load(mdf_t h, const char *path);
 
 /* mdf_info -- static facts about h (host struct). */
 mdf_status mdf_info(mdf_t h, mdf_info_t *out);
+
+/*
+ * mdf_autotune -- measure the update kernel's launch shapes for this handle
+ * (one node per thread and each vector width built for the storage type
+ * that divides nx, times 64/128/256 threads per block; `reps` timed updates
+ * each, CUDA events on h's stream) and keep the fastest.  The candidates
+ * update out of place without advancing the state, so the lattice is left
+ * as it was.  *vx, *block (nullable) receive the choice.  Synchronises.
+ */
+mdf_status mdf_autotune(mdf_t h, int reps, int *vx, int *block);
 
 /* mdf_sync -- wait for all work enqueued on h's stream. */
 mdf_status mdf_sync(mdf_t h);

@@ -54,12 +54,14 @@ class Lattice:
     nu = (1/s1 - 1/2) c_s^2 (Eq. 3-13a); s2 < 0 picks the paper's rule.
     wall: per-axis halfway walls (anti-halfway bounce-back), lid: the + face
     of the last axis moves with lid_u.  storage: 'f32', 'f16', 'bf16', 'f64'.
+    vx / block: x-nodes per thread and threads per block of the update
+    kernel (0: the library's tuned default).
     """
 
     def __init__(self, shape: Sequence[int], s1: float, s2: float = -1.0, s0: float = 1.0,
                  wall: Sequence[int] = (0, 0, 0), lid: bool = False,
                  lid_u: Sequence[float] = (0.0, 0.0, 0.0), storage: str = "f32",
-                 with_rho: bool = True, stream=None):
+                 with_rho: bool = True, stream=None, vx: int = 0, block: int = 0):
         import torch
 
         self._lib = _lib.load()
@@ -82,7 +84,7 @@ class Lattice:
         bc.lid = int(bool(lid))
         lu = list(lid_u) + [0.0] * (3 - len(lid_u))
         bc.lid_u[:] = [float(v) for v in lu[:3]]
-        o = _lib.Opts(STORAGE[storage], int(bool(with_rho)), ctypes.c_void_p(sptr))
+        o = _lib.Opts(STORAGE[storage], int(bool(with_rho)), ctypes.c_void_p(sptr), int(vx), int(block))
         h = ctypes.c_void_p()
         _lib.check(self._lib.mdf_create(ctypes.byref(h), ctypes.byref(g), self.d,
                                         ctypes.byref(r), ctypes.byref(bc), ctypes.byref(o)))
@@ -211,6 +213,13 @@ class Lattice:
 
     def load(self, path: str):
         self._check(self._lib.mdf_load(self._h, path.encode()))
+
+    def autotune(self, reps: int = 10):
+        """Measure the update kernel's launch shapes and keep the fastest;
+        the lattice state is unchanged.  Returns (vx, block)."""
+        vx, block = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.mdf_autotune(self._h, int(reps), ctypes.byref(vx), ctypes.byref(block)))
+        return vx.value, block.value
 
     def sync(self):
         self._check(self._lib.mdf_sync(self._h))

@@ -33,7 +33,8 @@ class BC(ctypes.Structure):
 
 
 class Opts(ctypes.Structure):
-    _fields_ = [("storage", ctypes.c_int), ("with_rho", ctypes.c_int), ("stream", ctypes.c_void_p)]
+    _fields_ = [("storage", ctypes.c_int), ("with_rho", ctypes.c_int), ("stream", ctypes.c_void_p),
+                ("vx", ctypes.c_int), ("block", ctypes.c_int)]
 
 
 class Fields(ctypes.Structure):
@@ -46,7 +47,8 @@ class Info(ctypes.Structure):
                 ("storage", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int),
                 ("nz", ctypes.c_int), ("pitch", ctypes.c_int), ("nodes", ctypes.c_longlong),
                 ("step", ctypes.c_longlong), ("bytes_per_update", ctypes.c_double),
-                ("s0", ctypes.c_double), ("s1", ctypes.c_double), ("s2", ctypes.c_double)]
+                ("s0", ctypes.c_double), ("s1", ctypes.c_double), ("s2", ctypes.c_double),
+                ("vx", ctypes.c_int), ("block", ctypes.c_int)]
 
 
 H = ctypes.c_void_p
@@ -71,6 +73,8 @@ SIGNATURES = {
     "mdf_save": (ctypes.c_int, [H, ctypes.c_char_p]),
     "mdf_load": (ctypes.c_int, [H, ctypes.c_char_p]),
     "mdf_info": (ctypes.c_int, [H, ctypes.POINTER(Info)]),
+    "mdf_autotune": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]),
     "mdf_sync": (ctypes.c_int, [H]),
     "mdf_last_error": (ctypes.c_char_p, [H]),
 }

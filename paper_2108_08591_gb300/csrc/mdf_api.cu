@@ -33,10 +33,25 @@ size_t storage_bytes(int st) {
   return 0;
 }
 
+// Launch shape defaults of the update kernel, per lattice and storage, from
+// a sweep on GB300 (4096^2 D2Q5 x 3 and 512^3 D3Q7 x 4; CUDA-event timing):
+//   2D: vector kernel, 4 nodes per thread, 128 threads (FP32 6.91 TB/s,
+//       FP16 5.62 TB/s, BF16 5.35 TB/s); FP64 2 nodes per thread.
+//   3D: one node per thread, 256 threads (FP32 6.94 TB/s, FP16 4.40 TB/s):
+//       with 28 populations per node the vector kernel's register pressure
+//       costs more than its saved instructions.
+// mdf_autotune() measures the candidates for a given handle instead.
+int default_vx(int d, int storage) {
+  if (d == 3) return 1;
+  return storage == MDF_F64 ? 2 : 4;
+}
+int default_block(int d, int) { return d == 3 ? 256 : 128; }
+
 }  // namespace
 
 struct mdf_s {
   int d = 0, q = 0, nsets = 0, with_rho = 0, storage = 0;
+  int vx = 1, block = 128;  // update-kernel launch shape
   int nx = 0, ny = 0, nz = 0, px = 0;
   long long plane = 0, N = 0;
   double s0 = 1, s1 = 1, s2 = 1;
@@ -90,6 +105,8 @@ DevArgs base_args(const mdf_t h) {
   a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.px = h->px;
   a.plane = h->plane;
   a.with_rho = h->with_rho;
+  a.vx = h->vx;
+  a.block = h->block;
   a.s1 = h->s1; a.s2 = h->s2;
   for (int b = 0; b < 3; ++b) a.lid_u[b] = h->bc.lid ? h->bc.lid_u[b] : 0.0;
   a.partials = h->partials;
@@ -254,6 +271,16 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
     return fail(nullptr, MDF_EINVAL, "a lid needs walls on the last axis");
   }
   h->stream = static_cast<cudaStream_t>(opts.stream);
+  if (opts.block != 0 && (opts.block < 32 || opts.block > kMaxBlock || opts.block % 32)) {
+    delete h;
+    return fail(nullptr, MDF_EINVAL, "block must be a multiple of 32 in [32, %d]", kMaxBlock);
+  }
+  if (opts.vx < 0 || opts.vx > 8) {
+    delete h;
+    return fail(nullptr, MDF_EINVAL, "vx must be 0 (default), 1, 2, 4 or 8");
+  }
+  h->block = opts.block ? opts.block : default_block(d, h->storage);
+  h->vx = opts.vx ? opts.vx : default_vx(d, h->storage);
 
   const size_t pb = h->pop_bytes();
   cudaError_t e = cudaMalloc(&h->buf[0], pb);
@@ -541,7 +568,59 @@ mdf_status mdf_info(mdf_t h, mdf_info_t *out) {
   out->nodes = h->N;
   out->step = h->step;
   out->bytes_per_update = 2.0 * h->q * h->nsets * (double)storage_bytes(h->storage);
+  out->vx = h->vx;
+  out->block = h->block;
   out->s0 = h->s0; out->s1 = h->s1; out->s2 = h->s2;
+  return MDF_OK;
+}
+
+mdf_status mdf_autotune(mdf_t h, int reps, int *vx_out, int *block_out) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (reps < 1) reps = 10;
+  // Candidates: one node per thread, and every vector width built for the
+  // storage type that divides nx; 64, 128 and 256 threads per block.
+  int widths[4] = {1, 0, 0, 0}, nw = 1;
+  const int built[4][2] = {{2, 4}, {4, 8}, {4, 8}, {2, 2}};  // by MDF_F32, F16, BF16, F64
+  for (int k = 0; k < 2; ++k) {
+    const int v = built[h->storage][k];
+    bool dup = false;
+    for (int j = 0; j < nw; ++j) dup |= widths[j] == v;
+    if (!dup && h->nx % v == 0) widths[nw++] = v;
+  }
+  const int blocks[3] = {64, 128, 256};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(h, cudaEventCreate(&e0));
+  CU(h, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_vx = h->vx, best_block = h->block;
+  mdf_status st = MDF_OK;
+  for (int w = 0; w < nw && st == MDF_OK; ++w)
+    for (int b = 0; b < 3 && st == MDF_OK; ++b) {
+      h->vx = widths[w];
+      h->block = blocks[b];
+      // out-of-place updates cur -> nxt without swapping: the state is kept
+      const DevArgs a = base_args(h);
+      cudaError_t e = launch_update(h, MODE_STEP, a);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+      for (int r = 0; r < reps && e == cudaSuccess; ++r) e = launch_update(h, MODE_STEP, a);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) {
+        st = fail(h, MDF_ECUDA, "autotune: %s", cudaGetErrorString(e));
+        break;
+      }
+      if (ms < best) { best = ms; best_vx = widths[w]; best_block = blocks[b]; }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->vx = best_vx;
+  h->block = best_block;
+  drop_graphs(h);  // captured launches hold the old shape
+  if (st != MDF_OK) return st;
+  if (vx_out) *vx_out = best_vx;
+  if (block_out) *block_out = best_block;
   return MDF_OK;
 }
 

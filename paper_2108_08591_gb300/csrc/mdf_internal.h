@@ -16,6 +16,8 @@ struct DevArgs {
   int nx, ny, nz, px;            // grid and padded x pitch
   long long plane;               // px * ny * nz
   int with_rho;                  // 1: set 0 is the alpha = 0 set
+  int vx;                        // x-nodes per thread of the update kernel (1: scalar)
+  int block;                     // threads per block of the update kernel
   double s1, s2;                 // relaxation rates (s0 never acts: m0 = m0eq)
   double lid_u[3];               // lid velocity
   // derived-field outputs (dense [N] layout), each nullable
@@ -33,8 +35,10 @@ enum Mode { MODE_STEP = 0, MODE_STEP_FIELDS = 1, MODE_FIELDS = 2 };
 enum Storage { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2, ST_F64 = 3 };
 enum ReduceKind { RED_SUMS = 0, RED_RESIDUAL = 1 };
 
-// Kernel block width along x for the update kernels.
+// Block width along x of the auxiliary kernels, and the largest block of the
+// update kernels (their width is a launch parameter).
 constexpr int kBlockX = 128;
+constexpr int kMaxBlock = 256;
 // Blocks of the grid-stride reduction pass (a multiple of the 152 SMs).
 constexpr int kReduceBlocks = 152 * 4;
 constexpr int kReduceThreads = 256;

@@ -15,6 +15,8 @@
 //   f_i(x, t) = -f*_{opp(i)}(x, t - 1) + 2 w_i ubar_wall.
 #pragma once
 
+#include <type_traits>
+
 #include "mdf_internal.h"
 #include "mdf_lattice.cuh"
 
@@ -56,88 +58,141 @@ __device__ __forceinline__ void pull_set(const DevArgs &A, const TS *__restrict_
   }
 }
 
-// Derived fields of Eq. 2-7, 3-15 .. 3-19 at one node, in FP64, from the
-// pulled (pre-collision) shifted populations.  gv: the d velocity sets;
-// h: the alpha = 0 set (ignored unless with_rho).
+// Derived fields of Eq. 2-7, 3-15 .. 3-19 at one node from the pulled
+// (pre-collision) shifted populations, computed in the compute type TC and
+// written as FP64.  gv: the d velocity sets; h: the alpha = 0 set (ignored
+// unless with_rho).  FP32 suffices here: the populations are rest-shifted,
+// so J (~u^2) and u u + P' carry absolute rounding ~1e-7 |J| while the
+// first moment of f^ne they differ by is ~1e-3..1e-1 |J| at the workloads'
+// sizes; the FP32 storage rounding of g dominates the error.  (GB300's FP64
+// throughput is too low for FP64 arithmetic here to stay HBM-bound.)
 template <class L, class TC>
 __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long long N,
                                              const TC (&gv)[L::D][L::Q], const TC (&h)[L::Q]) {
   constexpr int D = L::D, Q = L::Q;
-  double u[D], J[D][D];
+  TC u[D], J[D][D];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    double s = 0.0;
+    TC s = TC(0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) s += (double)gv[a][i];
+    for (int i = 0; i < Q; ++i) s += gv[a][i];
     u[a] = s;
 #pragma unroll
     for (int b = 0; b < D; ++b) {
-      double t = 0.0;
+      TC t = TC(0);
 #pragma unroll
-      for (int i = 0; i < Q; ++i)
-        if (L::c(i, b) != 0) t += L::c(i, b) * (double)gv[a][i];
+      for (int i = 0; i < Q; ++i) {
+        if (L::c(i, b) > 0) t += gv[a][i];
+        if (L::c(i, b) < 0) t -= gv[a][i];
+      }
       J[a][b] = t;  // sum_i c_{i,b} g_{i,a}
     }
   }
-  double tr = 0.0, usq = 0.0;
+  TC tr = TC(0), usq = TC(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) { tr += J[a][a]; usq += u[a] * u[a]; }
-  const double Pp = (tr - usq) / D;  // Eq. 3-15, P' = P - P0, R = 0
-  if (A.P) A.P[n] = 1.0 + Pp;
+  const TC Pp = (tr - usq) * TC(1.0 / D);  // Eq. 3-15, P' = P - P0, R = 0
+  if (A.P) A.P[n] = 1.0 + (double)Pp;
   if (A.u)
 #pragma unroll
-    for (int a = 0; a < D; ++a) A.u[a * N + n] = u[a];
+    for (int a = 0; a < D; ++a) A.u[a * N + n] = (double)u[a];
   if (A.rho && A.with_rho) {
-    double s = 0.0;
+    TC s = TC(0);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) s += (double)h[i];
-    A.rho[n] = 1.0 + s;
+    for (int i = 0; i < Q; ++i) s += h[i];
+    A.rho[n] = 1.0 + (double)s;
   }
   if (!(A.G || A.div || A.S || A.sigma || A.omega)) return;
   // first moment of f^ne: sum_i c_{i,b} (f - f^eq)_{i,a} = J - u_a u_b - P' delta_ab
-  double mne[D][D];
+  TC mne[D][D];
 #pragma unroll
   for (int a = 0; a < D; ++a)
 #pragma unroll
-    for (int b = 0; b < D; ++b) mne[a][b] = J[a][b] - u[a] * u[b] - (a == b ? Pp : 0.0);
-  const double pref = -A.s1 / L::CS2;  // Eq. 3-16 with dt = 1
+    for (int b = 0; b < D; ++b) mne[a][b] = J[a][b] - u[a] * u[b] - (a == b ? Pp : TC(0));
+  const TC pref = TC(-A.s1 / L::CS2);  // Eq. 3-16 with dt = 1
   if (A.G)
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int b = 0; b < D; ++b) A.G[(a * D + b) * N + n] = pref * mne[a][b];
+      for (int b = 0; b < D; ++b) A.G[(a * D + b) * N + n] = (double)(pref * mne[a][b]);
   if (A.div) {
-    double s = 0.0;
+    TC s = TC(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) s += mne[a][a];
-    A.div[n] = pref * s;  // Eq. 3-16a
+    A.div[n] = (double)(pref * s);  // Eq. 3-16a
   }
   if (A.S || A.sigma) {
     int k = 0;
-    const double sig = -(1.0 - 0.5 * A.s1);  // Eq. 3-17a with rho0 = 1
+    const TC sig = TC(-(1.0 - 0.5 * A.s1));  // Eq. 3-17a with rho0 = 1
+    const TC half_pref = TC(0.5) * pref;
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int b = a; b < D; ++b, ++k) {
-        const double sym = mne[a][b] + mne[b][a];
-        if (A.S) A.S[k * N + n] = 0.5 * pref * sym;  // Eq. 3-17
-        if (A.sigma) A.sigma[k * N + n] = sig * sym;
+        const TC sym = mne[a][b] + mne[b][a];
+        if (A.S) A.S[k * N + n] = (double)(half_pref * sym);  // Eq. 3-17
+        if (A.sigma) A.sigma[k * N + n] = (double)(sig * sym);
       }
   }
   if (A.omega) {  // Eq. 3-18, 3-19: omega = curl u
     if (D == 2) {
-      A.omega[n] = pref * (mne[1][0] - mne[0][1]);
+      A.omega[n] = (double)(pref * (mne[1][0] - mne[0][1]));
     } else {
-      A.omega[n] = pref * (mne[2][1] - mne[1][2]);
-      A.omega[N + n] = pref * (mne[0][2] - mne[2][0]);
-      A.omega[2 * N + n] = pref * (mne[1][0] - mne[0][1]);
+      A.omega[n] = (double)(pref * (mne[2][1] - mne[1][2]));
+      A.omega[N + n] = (double)(pref * (mne[0][2] - mne[2][0]));
+      A.omega[2 * N + n] = (double)(pref * (mne[1][0] - mne[0][1]));
     }
   }
 }
 
+// Eq. 2-7, 3-15, 2-4 (moments of Eq. 3-7a) and 3-21 at one node, in place
+// on its pulled populations: g (the d velocity sets) and h (the alpha = 0
+// set) become the post-collision populations.  F: Fbar_alpha, alpha = 1..d.
+template <class L, class TC>
+__device__ __forceinline__ void collide_node(TC (&g)[L::D][L::Q], TC (&h)[L::Q], bool with_rho,
+                                             const TC (&F)[L::D], TC s1, TC s2) {
+  constexpr int D = L::D, Q = L::Q;
+  // Eq. 2-7: u_alpha = sum_i f_{i,alpha} (the rest shift has zero sum);
+  // Eq. 3-15: P' = (1/d)(sum_alpha sum_i c_{i,alpha} g_{i,alpha} - |u|^2).
+  TC u[D], tr = TC(0), usq = TC(0);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    TC s = TC(0), t = TC(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      s += g[a][i];
+      if (L::c(i, a) > 0) t += g[a][i];
+      if (L::c(i, a) < 0) t -= g[a][i];
+    }
+    u[a] = s;
+    tr += t;
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) usq += u[a] * u[a];
+  const TC Pp = (tr - usq) * TC(1.0 / D);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    TC jeq[D];  // Eq. 3-7a: sum_i c_i f^eq = u_alpha u + P E_alpha (shifted: P')
+#pragma unroll
+    for (int b = 0; b < D; ++b) jeq[b] = u[a] * u[b] + (a == b ? Pp : TC(0));
+    L::relax(g[a], jeq, s1, s2, F[a]);
+  }
+  if (with_rho) {
+    TC r = TC(0);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) r += h[i];
+    TC jeq[D];  // ubar_0 u with ubar_0 = rho0 + rho'
+#pragma unroll
+    for (int b = 0; b < D; ++b) jeq[b] = (TC(1) + r) * u[b];
+    L::relax(h, jeq, s1, s2, TC(0));
+  }
+}
+
 // One lattice update per thread-node: pull, moments, (fields), collide, store.
+// Used for every grid; the vector kernel below covers x extents divisible by
+// its width.
 template <class L, class TS, int MODE, bool WALLS>
-__global__ void __launch_bounds__(kBlockX) k_update(const DevArgs A) {
+__global__ void __launch_bounds__(kMaxBlock) k_update(const DevArgs A) {
   using TC = typename ComputeOf<TS>::T;
   constexpr int D = L::D, Q = L::Q;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -163,71 +218,269 @@ __global__ void __launch_bounds__(kBlockX) k_update(const DevArgs A) {
     if (MODE == MODE_FIELDS) return;
   }
 
-  // Eq. 2-7: u_alpha = sum_i f_{i,alpha} (the rest shift has zero sum);
-  // Eq. 3-15: P' = (1/d)(sum_alpha sum_i c_{i,alpha} g_{i,alpha} - |u|^2).
-  TC u[D], tr = TC(0), usq = TC(0);
+  TC F[D];
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    TC s = TC(0), t = TC(0);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      s += g[a][i];
-      if (L::c(i, a) != 0) t += TC(L::c(i, a)) * g[a][i];
-    }
-    u[a] = s;
-    tr += t;
-  }
-#pragma unroll
-  for (int a = 0; a < D; ++a) usq += u[a] * u[a];
-  const TC Pp = (tr - usq) * TC(1.0 / D);
-  const TC s1 = TC(A.s1), s2 = TC(A.s2);
-  TS *__restrict__ fout = static_cast<TS *>(A.fout);
+  for (int a = 0; a < D; ++a)
+    F[a] = A.force ? __ldg(static_cast<const TC *>(A.force) + a * A.plane + idx) : TC(0);
+  collide_node<L, TC>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2));
 
+  TS *__restrict__ fout = static_cast<TS *>(A.fout);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
-    TC jeq[D];  // Eq. 3-7a: sum_i c_i f^eq = u_alpha u + P E_alpha (shifted: P')
-#pragma unroll
-    for (int b = 0; b < D; ++b) jeq[b] = u[a] * u[b] + (a == b ? Pp : TC(0));
-    const TC F = A.force ? __ldg(static_cast<const TC *>(A.force) + a * A.plane + idx) : TC(0);
-    L::relax(g[a], jeq, s1, s2, F);
     TS *base = fout + (long long)(a1 + a) * Q * A.plane + idx;
 #pragma unroll
     for (int i = 0; i < Q; ++i) Codec<TS>::store(base + (long long)i * A.plane, g[a][i]);
   }
   if (A.with_rho) {
-    TC r = TC(0);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) r += h[i];
-    TC jeq[D];  // ubar_0 u with ubar_0 = rho0 + rho'
-#pragma unroll
-    for (int b = 0; b < D; ++b) jeq[b] = (TC(1) + r) * u[b];
-    L::relax(h, jeq, s1, s2, TC(0));
     TS *base = fout + idx;
 #pragma unroll
     for (int i = 0; i < Q; ++i) Codec<TS>::store(base + (long long)i * A.plane, h[i]);
   }
 }
 
+// ---------------------------------------------------------------------------
+// Vector update: each thread owns VX consecutive x-nodes (x0 .. x0+VX-1) and
+// moves them with one 8/16-byte access per population array.  The two
+// x-shifted pulls take the missing end value from the neighbouring lane
+// (warp shuffle) or, at a warp or row edge, with one scalar load.  All lanes
+// stay alive through the shuffles (threads past the row end clamp their
+// reads into the row and skip every store).  Node offsets are 32-bit.
+// Per node the arithmetic is the scalar kernel's, so both produce the same
+// bits.
+// ---------------------------------------------------------------------------
+template <class TS, int VX> struct VecIO;
+template <> struct VecIO<float, 4> {
+  static __device__ __forceinline__ void load(const float *p, float (&v)[4]) {
+    const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  }
+  static __device__ __forceinline__ void store(float *p, const float (&v)[4]) {
+    __stcs(reinterpret_cast<float4 *>(p), make_float4(v[0], v[1], v[2], v[3]));
+  }
+};
+template <> struct VecIO<float, 2> {
+  static __device__ __forceinline__ void load(const float *p, float (&v)[2]) {
+    const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+    v[0] = t.x; v[1] = t.y;
+  }
+  static __device__ __forceinline__ void store(float *p, const float (&v)[2]) {
+    __stcs(reinterpret_cast<float2 *>(p), make_float2(v[0], v[1]));
+  }
+};
+template <> struct VecIO<float, 8> {
+  static __device__ __forceinline__ void load(const float *p, float (&v)[8]) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+  }
+};
+template <> struct VecIO<double, 2> {
+  static __device__ __forceinline__ void load(const double *p, double (&v)[2]) {
+    const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+    v[0] = t.x; v[1] = t.y;
+  }
+  static __device__ __forceinline__ void store(double *p, const double (&v)[2]) {
+    __stcs(reinterpret_cast<double2 *>(p), make_double2(v[0], v[1]));
+  }
+};
+// 16-bit storage: VX/2 packed pairs per access (VX = 4: 8 bytes, VX = 8: 16).
+template <class H2> struct Pair;
+template <> struct Pair<__half2> {
+  static __device__ __forceinline__ float2 to_f2(__half2 v) { return __half22float2(v); }
+  static __device__ __forceinline__ __half2 from(float a, float b) { return __floats2half2_rn(a, b); }
+};
+template <> struct Pair<__nv_bfloat162> {
+  static __device__ __forceinline__ float2 to_f2(__nv_bfloat162 v) { return __bfloat1622float2(v); }
+  static __device__ __forceinline__ __nv_bfloat162 from(float a, float b) {
+    return __floats2bfloat162_rn(a, b);
+  }
+};
+template <class T16, class H2, int VX> struct VecIO16 {
+  static_assert(VX == 4 || VX == 8, "16-bit vectors of 4 or 8");
+  using Raw = typename std::conditional<VX == 4, uint2, uint4>::type;
+  static __device__ __forceinline__ void load(const T16 *p, float (&v)[VX]) {
+    const Raw r = __ldg(reinterpret_cast<const Raw *>(p));
+    const uint32_t *w = reinterpret_cast<const uint32_t *>(&r);
+#pragma unroll
+    for (int k = 0; k < VX / 2; ++k) {
+      const float2 f = Pair<H2>::to_f2(*reinterpret_cast<const H2 *>(&w[k]));
+      v[2 * k] = f.x;
+      v[2 * k + 1] = f.y;
+    }
+  }
+  static __device__ __forceinline__ void store(T16 *p, const float (&v)[VX]) {
+    Raw r;
+    uint32_t *w = reinterpret_cast<uint32_t *>(&r);
+#pragma unroll
+    for (int k = 0; k < VX / 2; ++k) {
+      const H2 hv = Pair<H2>::from(v[2 * k], v[2 * k + 1]);
+      w[k] = *reinterpret_cast<const uint32_t *>(&hv);
+    }
+    *reinterpret_cast<Raw *>(p) = r;
+  }
+};
+template <int VX> struct VecIO<__half, VX> : VecIO16<__half, __half2, VX> {};
+template <int VX> struct VecIO<__nv_bfloat16, VX> : VecIO16<__nv_bfloat16, __nv_bfloat162, VX> {};
+
+struct VecRows {
+  int row0, row_ym, row_yp, row_zm, row_zp;  // row offsets of the pull sources
+  int x0, xl, xr;                            // first x, wrapped x0 - 1 and x0 + VX
+  bool ledge, redge;                         // x - 1 / x + VX not held by a neighbour lane
+};
+
+// Pull VX consecutive nodes of one set (carrying alpha) into v[i][j].
+template <class L, class TS, int VX, bool WALLS>
+__device__ __forceinline__ void pull_set_vec(const DevArgs &A, const TS *__restrict__ base,
+                                             int alpha, const VecRows &R, const uint8_t (&m)[VX],
+                                             typename ComputeOf<TS>::T (&v)[L::Q][VX]) {
+  using TC = typename ComputeOf<TS>::T;
+  constexpr int Q = L::Q;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const TS *p = base + (long long)i * A.plane;
+    if (L::c(i, 0) == 1) {  // pulls from x - 1
+      TC own[VX];
+      VecIO<TS, VX>::load(p + R.row0 + R.x0, own);
+      TC pv = __shfl_up_sync(0xffffffffu, own[VX - 1], 1);
+      if (R.ledge) pv = Codec<TS>::load(p + R.row0 + R.xl);
+      v[i][0] = pv;
+#pragma unroll
+      for (int j = 1; j < VX; ++j) v[i][j] = own[j - 1];
+    } else if (L::c(i, 0) == -1) {  // pulls from x + 1
+      TC own[VX];
+      VecIO<TS, VX>::load(p + R.row0 + R.x0, own);
+      TC nv = __shfl_down_sync(0xffffffffu, own[0], 1);
+      if (R.redge) nv = Codec<TS>::load(p + R.row0 + R.xr);
+#pragma unroll
+      for (int j = 0; j < VX - 1; ++j) v[i][j] = own[j + 1];
+      v[i][VX - 1] = nv;
+    } else {
+      const int r = L::c(i, 1) == 1 ? R.row_ym : L::c(i, 1) == -1 ? R.row_yp
+                  : L::c(i, 2) == 1 ? R.row_zm : L::c(i, 2) == -1 ? R.row_zp : R.row0;
+      VecIO<TS, VX>::load(p + r + R.x0, v[i]);
+    }
+  }
+  if (WALLS) {  // anti-halfway bounce-back on wall links (see pull_set)
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+#pragma unroll
+      for (int j = 0; j < VX; ++j)
+        if ((m[j] >> L::opp(i)) & 1) {
+          TC w = -TC(Codec<TS>::load(base + (long long)L::opp(i) * A.plane + R.row0 + R.x0 + j));
+          if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u))
+            w += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+          v[i][j] = w;
+        }
+  }
+}
+
+template <class L, class TS, int VX, int MODE, bool WALLS>
+__global__ void __launch_bounds__(kMaxBlock) k_update_vec(const DevArgs A) {
+  using TC = typename ComputeOf<TS>::T;
+  constexpr int D = L::D, Q = L::Q;
+  const int lane = threadIdx.x & 31;
+  int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
+  const bool active = x0 < A.nx;
+  if (!active) x0 = A.nx - VX;
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int row0 = (z * A.ny + y) * A.px;
+  // rows the y- and z-directed pulls come from
+  const int row_ym = (z * A.ny + wrap(y - 1, A.ny)) * A.px;  // source of c_y = +1
+  const int row_yp = (z * A.ny + wrap(y + 1, A.ny)) * A.px;  // source of c_y = -1
+  const int row_zm = D == 3 ? (wrap(z - 1, A.nz) * A.ny + y) * A.px : row0;
+  const int row_zp = D == 3 ? (wrap(z + 1, A.nz) * A.ny + y) * A.px : row0;
+  const bool ledge = lane == 0 || x0 == 0;
+  const bool redge = lane == 31 || x0 + VX >= A.nx;
+  const int xl = x0 == 0 ? A.nx - 1 : x0 - 1;
+  const int xr = x0 + VX >= A.nx ? 0 : x0 + VX;
+  const TS *__restrict__ fin = static_cast<const TS *>(A.fin);
+  const int a1 = A.with_rho;
+  uint8_t m[VX];
+  if (WALLS) {
+#pragma unroll
+    for (int j = 0; j < VX; ++j) m[j] = A.mask[row0 + x0 + j];
+  }
+
+  const VecRows rows{row0, row_ym, row_yp, row_zm, row_zp, x0, xl, xr, ledge, redge};
+  TC g[D][Q][VX], h[Q][VX];
+#pragma unroll
+  for (int al = 1; al <= D; ++al)
+    pull_set_vec<L, TS, VX, WALLS>(A, fin + (long long)(a1 + al - 1) * Q * A.plane, al, rows, m,
+                                   g[al - 1]);
+  if (A.with_rho) pull_set_vec<L, TS, VX, WALLS>(A, fin, 0, rows, m, h);
+
+  const long long N = (long long)A.nx * A.ny * A.nz;
+  const long long n0 = ((long long)z * A.ny + y) * A.nx + x0;
+  TC F[D][VX];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (A.force) {
+      VecIO<TC, VX>::load(static_cast<const TC *>(A.force) + a * A.plane + row0 + x0, F[a]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < VX; ++j) F[a][j] = TC(0);
+    }
+  }
+  const TC s1 = TC(A.s1), s2 = TC(A.s2);
+#pragma unroll
+  for (int j = 0; j < VX; ++j) {
+    TC gn[D][Q], hn[Q], Fn[D];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) gn[a][i] = g[a][i][j];
+      hn[i] = h[i][j];
+    }
+    if (MODE != MODE_STEP && active) write_fields<L, TC>(A, n0 + j, N, gn, hn);
+    if (MODE == MODE_FIELDS) continue;
+#pragma unroll
+    for (int a = 0; a < D; ++a) Fn[a] = F[a][j];
+    collide_node<L, TC>(gn, hn, A.with_rho != 0, Fn, s1, s2);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) g[a][i][j] = gn[a][i];
+      h[i][j] = hn[i];
+    }
+  }
+  if (MODE == MODE_FIELDS || !active) return;
+  TS *__restrict__ fout = static_cast<TS *>(A.fout);
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      VecIO<TS, VX>::store(fout + ((long long)(a1 + a) * Q + i) * A.plane + row0 + x0, g[a][i]);
+  if (A.with_rho)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) VecIO<TS, VX>::store(fout + (long long)i * A.plane + row0 + x0, h[i]);
+}
+
 // Shifted equilibrium g^eq_i of set alpha at dense node n (Eq. 2-4 minus
 // the rest state): alpha >= 1: w_i [u_a + (c_i.u u_a + c_{i,a} P')/c_s^2];
-// alpha = 0 (ubar_0 = rho0 = 1): w_i c_i.u / c_s^2.
-template <class L>
-__device__ __forceinline__ double geq(const DevArgs &A, long long N, long long n, int alpha, int i) {
-  double cu = 0.0;
+// alpha = 0 (ubar_0 = rho0 = 1): w_i c_i.u / c_s^2.  P' = P - 1 is formed in
+// FP64 (P ~ 1), the rest in the compute type TC.
+template <class L, class TC>
+__device__ __forceinline__ TC geq(const DevArgs &A, long long N, long long n, int alpha, int i) {
+  TC cu = TC(0);
 #pragma unroll
-  for (int b = 0; b < L::D; ++b)
-    if (L::c(i, b) != 0) cu += L::c(i, b) * A.uin[b * N + n];
-  if (alpha == 0) return L::w(i) * cu / L::CS2;
-  const double ua = A.uin[(alpha - 1) * N + n];
-  const double Pp = A.Pin[n] - 1.0;
-  return L::w(i) * (ua + (cu * ua + L::c(i, alpha - 1) * Pp) / L::CS2);
+  for (int b = 0; b < L::D; ++b) {
+    if (L::c(i, b) > 0) cu += TC(A.uin[b * N + n]);
+    if (L::c(i, b) < 0) cu -= TC(A.uin[b * N + n]);
+  }
+  const TC wi = TC(L::w(i)), ics2 = TC(1.0 / L::CS2);
+  if (alpha == 0) return wi * cu * ics2;
+  const TC ua = TC(A.uin[(alpha - 1) * N + n]);
+  const TC Pp = TC(A.Pin[n] - 1.0);
+  const TC cP = L::c(i, alpha - 1) > 0 ? Pp : (L::c(i, alpha - 1) < 0 ? -Pp : TC(0));
+  return wi * (ua + (cu * ua + cP) * ics2);
 }
 
 // Initial state f = f^eq(P, u) written in pull form: the value stored at x
 // for direction i is the one the first update pulls into x + c_i, and for a
 // wall link the one whose bounce-back returns f^eq_opp(i)(x).
 template <class L, class TS, bool WALLS>
-__global__ void __launch_bounds__(kBlockX) k_init(const DevArgs A) {
+__global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
+  using TC = typename ComputeOf<TS>::T;
   constexpr int D = L::D, Q = L::Q;
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= A.nx) return;
@@ -242,17 +495,17 @@ __global__ void __launch_bounds__(kBlockX) k_init(const DevArgs A) {
     const int alpha = a + 1 - A.with_rho;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      double v;
+      TC v;
       if (WALLS && i != 0 && ((m >> i) & 1)) {
-        v = -geq<L>(A, N, n, alpha, L::opp(i));
-        if (alpha >= 1 && i == L::UP && (m & 0x80u)) v += 2.0 * L::w(i) * A.lid_u[alpha - 1];
+        v = -geq<L, TC>(A, N, n, alpha, L::opp(i));
+        if (alpha >= 1 && i == L::UP && (m & 0x80u)) v += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
       } else {
         const int tx = wrap(x + L::c(i, 0), A.nx);
         const int ty = wrap(y + L::c(i, 1), A.ny);
         const int tz = D == 3 ? wrap(z + L::c(i, 2), A.nz) : z;
-        v = geq<L>(A, N, ((long long)tz * A.ny + ty) * A.nx + tx, alpha, i);
+        v = geq<L, TC>(A, N, ((long long)tz * A.ny + ty) * A.nx + tx, alpha, i);
       }
-      fout[((long long)a * Q + i) * A.plane + idx] = Codec<TS>::enc(v);
+      Codec<TS>::store(fout + ((long long)a * Q + i) * A.plane + idx, v);
     }
   }
 }
@@ -354,8 +607,9 @@ inline dim3 node_grid(const DevArgs &a) {
 }
 
 template <class L, class TS>
-cudaError_t update_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
-  const dim3 grid = node_grid(a), block(kBlockX);
+cudaError_t update_scalar(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
+  const int bx = a.block;
+  const dim3 grid((unsigned)((a.nx + bx - 1) / bx), (unsigned)a.ny, (unsigned)a.nz), block(bx);
   if (walls) {
     if (mode == MODE_STEP) k_update<L, TS, MODE_STEP, true><<<grid, block, 0, s>>>(a);
     else if (mode == MODE_STEP_FIELDS) k_update<L, TS, MODE_STEP_FIELDS, true><<<grid, block, 0, s>>>(a);
@@ -366,6 +620,43 @@ cudaError_t update_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
     else k_update<L, TS, MODE_FIELDS, false><<<grid, block, 0, s>>>(a);
   }
   return cudaGetLastError();
+}
+
+template <class L, class TS, int VX>
+cudaError_t update_vec(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
+  const int bx = a.block;
+  const int threads = a.nx / VX;
+  const dim3 grid((unsigned)((threads + bx - 1) / bx), (unsigned)a.ny, (unsigned)a.nz), block(bx);
+  if (walls) {
+    if (mode == MODE_STEP) k_update_vec<L, TS, VX, MODE_STEP, true><<<grid, block, 0, s>>>(a);
+    else if (mode == MODE_STEP_FIELDS) k_update_vec<L, TS, VX, MODE_STEP_FIELDS, true><<<grid, block, 0, s>>>(a);
+    else k_update_vec<L, TS, VX, MODE_FIELDS, true><<<grid, block, 0, s>>>(a);
+  } else {
+    if (mode == MODE_STEP) k_update_vec<L, TS, VX, MODE_STEP, false><<<grid, block, 0, s>>>(a);
+    else if (mode == MODE_STEP_FIELDS) k_update_vec<L, TS, VX, MODE_STEP_FIELDS, false><<<grid, block, 0, s>>>(a);
+    else k_update_vec<L, TS, VX, MODE_FIELDS, false><<<grid, block, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// Vector widths built per storage type: FP32 2 or 4, 16-bit 4 or 8, FP64 2.
+// Any other request, an x extent not divisible by the width, or a plane
+// beyond 32-bit offsets runs the scalar kernel.
+template <class L, class TS>
+cudaError_t update_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
+  const bool ok = a.vx > 1 && a.nx % a.vx == 0 && a.plane < (1LL << 31) - 64;
+  if (ok) {
+    if constexpr (sizeof(TS) == 4) {
+      if (a.vx == 4) return update_vec<L, TS, 4>(mode, walls, a, s);
+      if (a.vx == 2) return update_vec<L, TS, 2>(mode, walls, a, s);
+    } else if constexpr (sizeof(TS) == 2) {
+      if (a.vx == 8) return update_vec<L, TS, 8>(mode, walls, a, s);
+      if (a.vx == 4) return update_vec<L, TS, 4>(mode, walls, a, s);
+    } else {
+      if (a.vx == 2) return update_vec<L, TS, 2>(mode, walls, a, s);
+    }
+  }
+  return update_scalar<L, TS>(mode, walls, a, s);
 }
 
 template <class L>

@@ -77,6 +77,17 @@ def test_ragged_grid_2d(storage):
     assert e["G"] < tg and e["omega"] < tg, e
 
 
+@pytest.mark.parametrize("d", [2, 3])
+def test_divergence_identity_fp64(d):
+    """Eq. 3-15 with R = 0 makes Eq. 3-16a vanish at every node; with FP64
+    storage and arithmetic the GPU fields show it to rounding."""
+    shape = (128, 96) if d == 2 else (40, 24, 20)
+    P, u = synth.smooth_fields(shape, seed=23)
+    got = run_gpu(shape, P, u, 30, 1.7, storage="f64", names=("G", "div"))
+    assert np.abs(got["G"]).max() > 1e-4
+    assert np.abs(got["div"]).max() < 1e-12 * np.abs(got["G"]).max()
+
+
 def test_without_continuity_set_is_identical():
     """u, P and every derived field do not depend on the alpha = 0 set."""
     shape = (70, 45)
@@ -317,11 +328,16 @@ def test_full_size_4096_sampled_parity():
     lat.step_fields(steps, fl)
     out = lat.fields(("P", "u", "G", "omega", "div"))
     torch.cuda.synchronize()
-    # fields of the initial state from the fused update: divergence identity
-    G0 = fl["G"].cpu().numpy()
-    assert np.abs(fl["div"].cpu().numpy()).max() < 1e-9 * np.abs(G0).max()
+    # fields of the initial state from the fused update: f = f^eq there, so
+    # f^ne and every gradient vanish up to FP32 storage rounding (~1e-9
+    # against |grad u| ~ 1.5e-5 of the flow)
+    assert np.abs(fl["G"].cpu().numpy()).max() < 1e-8
+    assert np.abs(fl["div"].cpu().numpy()).max() < 1e-8
+    # after 71 updates: divergence identity (exact in exact arithmetic; FP32
+    # epilogue arithmetic leaves a few 1e-6 of |G|)
     got = {k: v.cpu().numpy() for k, v in out.items()}
-    assert np.abs(got["div"]).max() < 1e-9 * np.abs(got["G"]).max()
+    assert np.abs(got["G"]).max() > 1e-6
+    assert np.abs(got["div"]).max() < 5e-5 * np.abs(got["G"]).max()
     lat.close()
     rng = synth.SplitMix64(77)
     pts = [(rng.randint(0, n - 1), rng.randint(0, n - 1)) for _ in range(12)] + [(0, 0), (n - 1, n - 1)]
@@ -343,3 +359,59 @@ def test_full_size_4096_sampled_parity():
     assert rel(np.array(ref_u), np.array(got_u)) < 1e-5
     assert rel(np.array(ref_P), np.array(got_P)) < 1e-5
     assert rel(np.array(ref_w), np.array(got_w)) < 1e-3
+
+
+# --------------------------------------------------------------------------
+# Vector kernel (VX x-nodes per thread) against the one-node-per-thread kernel
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("d,storage,vx", [
+    (2, "f32", 4), (2, "f32", 2), (2, "f16", 8), (2, "bf16", 4), (2, "f64", 2),
+    (3, "f32", 4), (3, "f32", 2), (3, "f16", 4), (3, "bf16", 8), (3, "f64", 2),
+])
+@pytest.mark.parametrize("walls", [False, True])
+def test_vector_kernel_is_bitwise_the_scalar_kernel(d, storage, vx, walls):
+    """Same per-node arithmetic, so the same bits: x extents of several warps
+    with a partial last warp (264 = 33 x 8), the row wrap, walls and lid."""
+    from paper_2108_08591_gb300 import Lattice
+    shape = (264, 9) if d == 2 else (264, 5, 4)
+    P, u = synth.smooth_fields(shape, seed=17)
+    kw = {}
+    if walls:
+        kw = dict(wall=(1, 1, 1)[:d] + (0,) * (3 - d), lid=True, lid_u=(0.02, 0.01, 0.0))
+    outs = []
+    for v in (1, vx):
+        lat = Lattice(shape, s1=1.35, storage=storage, vx=v, block=64, **kw)
+        lat.init(P, u)
+        lat.step(5)
+        f1 = lat.fields_host(("P", "u", "G", "rho"))
+        fl = lat.alloc_fields(("P", "u", "omega"))
+        lat.step_fields(7, fl)
+        f2 = {k: t.cpu().numpy() for k, t in fl.items()}
+        f3 = lat.fields_host(("P", "u", "G", "S", "sigma", "omega", "div"))
+        outs.append((f1, f2, f3))
+        lat.close()
+    for a, b in zip(outs[0], outs[1]):
+        for k in a:
+            assert np.array_equal(a[k], b[k]), (k, np.abs(a[k] - b[k]).max())
+
+
+def test_autotune_keeps_the_state_and_the_bits():
+    from paper_2108_08591_gb300 import Lattice
+    shape = (256, 40)
+    P, u = synth.smooth_fields(shape, seed=29)
+    a = Lattice(shape, s1=1.5, vx=1, block=128)
+    b = Lattice(shape, s1=1.5)
+    for lat in (a, b):
+        lat.init(P, u)
+        lat.step(3)
+    before = b.fields_host(("u", "P"))
+    vx, block = b.autotune(reps=3)
+    assert vx in (1, 2, 4) and block in (64, 128, 256)
+    assert (b.info.vx, b.info.block) == (vx, block)
+    after = b.fields_host(("u", "P"))
+    assert np.array_equal(before["u"], after["u"]) and np.array_equal(before["P"], after["P"])
+    a.step(20)
+    b.step(20)
+    assert np.array_equal(a.fields_host(("u",))["u"], b.fields_host(("u",))["u"])
+    a.close()
+    b.close()
