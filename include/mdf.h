@@ -41,10 +41,18 @@ typedef enum {
     MDF_EIO = 8              /* checkpoint file error or checksum mismatch */
 } mdf_status;
 
-/* Population storage.  Populations are stored shifted by the rest state
- * f_rest = f^eq(P0 = 1, u = 0) (Eq. 2-4), so the stored numbers are small;
- * all collision arithmetic is FP32 except for MDF_F64 (FP64 throughout). */
-enum { MDF_F32 = 0, MDF_F16 = 1, MDF_BF16 = 2, MDF_F64 = 3 };
+/* Population storage.  All collision arithmetic is FP32 except for MDF_F64
+ * (FP64 throughout).
+ *   MDF_F32, MDF_F16, MDF_BF16, MDF_F64: populations stored shifted by the
+ *     rest state f_rest = f^eq(P0 = 1, u = 0) (Eq. 2-4), so the stored
+ *     numbers are O(U) instead of O(1).
+ *   MDF_F16EQ, MDF_BF16EQ: equilibrium-shifted 16-bit storage: each node keeps
+ *     its post-collision non-equilibrium part f* - f^eq(M) in 16 bits (FP16
+ *     scaled by 2^14) plus its moments M = (u, P - P0[, rho - rho0]) in FP32;
+ *     a pull adds back f^eq of the source node's M.  The 16-bit rounding then
+ *     falls on f^ne only, so P and the Eq. 3-16 gradients stay accurate.
+ *     Bytes per node update: 4 q nsets + 8 (d + 1 + with_rho). */
+enum { MDF_F32 = 0, MDF_F16 = 1, MDF_BF16 = 2, MDF_F64 = 3, MDF_F16EQ = 4, MDF_BF16EQ = 5 };
 
 /* Where a caller's array lives. */
 enum { MDF_HOST = 0, MDF_DEVICE = 1 };
@@ -66,15 +74,16 @@ typedef struct {
 } mdf_bc;
 
 typedef struct {
-    int storage;             /* MDF_F32, MDF_F16, MDF_BF16 or MDF_F64 */
+    int storage;             /* one of the MDF_F32 .. MDF_BF16EQ storage types */
     int with_rho;            /* 1: also carry the alpha = 0 (continuity) set, so d+1
                                 sets are advanced; 0: only the d velocity sets (the
                                 paper shows alpha = 0 can be omitted, Sec. 3.2) */
     void *stream;            /* cudaStream_t to enqueue on; NULL = legacy default */
     int vx;                  /* x-nodes per thread of the update kernel: 0 = tuned
                                 default; 1 = one node per thread; 2, 4, 8 = vector
-                                widths (FP32: 2, 4; FP16/BF16: 4, 8; FP64: 2).  A
-                                width that does not divide nx falls back to 1. */
+                                widths (FP32: 2, 4; FP16/BF16: 4, 8; FP64: 2;
+                                *EQ: 2, 4).  A width that does not divide nx falls
+                                back to 1. */
     int block;               /* threads per block of the update kernel: 0 = tuned
                                 default, else a multiple of 32 in [32, 256] */
 } mdf_opts;

@@ -16,7 +16,7 @@ LIB_PATH = os.path.join(_HERE, "libmdf.so")
 OK, EINVAL, ENOMEM, ECUDA, EDIVERGED, ETIMEOUT, ENOTCONVERGED, EUNSUPPORTED, EIO = range(9)
 STATUS_NAMES = ["MDF_OK", "MDF_EINVAL", "MDF_ENOMEM", "MDF_ECUDA", "MDF_EDIVERGED",
                 "MDF_ETIMEOUT", "MDF_ENOTCONVERGED", "MDF_EUNSUPPORTED", "MDF_EIO"]
-STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3}
+STORAGE = {"f32": 0, "f16": 1, "bf16": 2, "f64": 3, "f16eq": 4, "bf16eq": 5}
 HOST, DEVICE = 0, 1
 
 

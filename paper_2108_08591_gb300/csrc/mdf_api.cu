@@ -29,9 +29,13 @@ size_t storage_bytes(int st) {
     case MDF_F16: return 2;
     case MDF_BF16: return 2;
     case MDF_F64: return 8;
+    case MDF_F16EQ: return 2;
+    case MDF_BF16EQ: return 2;
   }
   return 0;
 }
+
+bool eq_storage(int st) { return st == MDF_F16EQ || st == MDF_BF16EQ; }
 
 // Launch shape defaults of the update kernel, per lattice and storage, from
 // a sweep on GB300 (4096^2 D2Q5 x 3 and 512^3 D3Q7 x 4; CUDA-event timing):
@@ -43,6 +47,7 @@ size_t storage_bytes(int st) {
 // mdf_autotune() measures the candidates for a given handle instead.
 int default_vx(int d, int storage) {
   if (d == 3) return 1;
+  if (storage == MDF_F16EQ || storage == MDF_BF16EQ) return 2;
   return storage == MDF_F64 ? 2 : 4;
 }
 int default_block(int d, int) { return d == 3 ? 256 : 128; }
@@ -70,9 +75,13 @@ struct mdf_s {
   long long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // chunk starting from buffer 0 / 1
   void *buf[2] = {nullptr, nullptr};
+  void *mac[2] = {nullptr, nullptr};  // node moments of equilibrium-shifted storage
+  int kmom = 0;                       // moment slots per node (0 for other storage)
   std::string err = "no error";
 
   size_t pop_bytes() const { return (size_t)nsets * q * (size_t)plane * storage_bytes(storage); }
+  size_t mom_bytes() const { return (size_t)kmom * (size_t)plane * sizeof(float); }
+  int cur_index() const { return cur == buf[0] ? 0 : 1; }
 };
 
 namespace {
@@ -109,6 +118,8 @@ DevArgs base_args(const mdf_t h) {
   a.block = h->block;
   a.s1 = h->s1; a.s2 = h->s2;
   for (int b = 0; b < 3; ++b) a.lid_u[b] = h->bc.lid ? h->bc.lid_u[b] : 0.0;
+  a.min = h->mac[h->cur_index()];
+  a.mout = h->mac[1 - h->cur_index()];
   a.partials = h->partials;
   a.result = h->result;
   a.nonfinite = h->nonfinite;
@@ -279,6 +290,13 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
     delete h;
     return fail(nullptr, MDF_EINVAL, "vx must be 0 (default), 1, 2, 4 or 8");
   }
+  if (eq_storage(h->storage)) {
+    h->kmom = d + 1 + h->with_rho;
+    if (h->plane >= (1LL << 31) - 64) {
+      delete h;
+      return fail(nullptr, MDF_EUNSUPPORTED, "equilibrium-shifted storage needs < 2^31 padded nodes");
+    }
+  }
   h->block = opts.block ? opts.block : default_block(d, h->storage);
   h->vx = opts.vx ? opts.vx : default_vx(d, h->storage);
 
@@ -289,6 +307,10 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
   if (e == cudaSuccess) e = cudaMalloc(&h->result, sizeof(double) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&h->nonfinite, sizeof(int));
   if (e == cudaSuccess && h->walls) e = cudaMalloc(&h->mask, (size_t)h->plane);
+  if (e == cudaSuccess && h->kmom) e = cudaMalloc(&h->mac[0], h->mom_bytes());
+  if (e == cudaSuccess && h->kmom) e = cudaMalloc(&h->mac[1], h->mom_bytes());
+  if (e == cudaSuccess && h->kmom) e = cudaMemsetAsync(h->mac[0], 0, h->mom_bytes(), h->stream);
+  if (e == cudaSuccess && h->kmom) e = cudaMemsetAsync(h->mac[1], 0, h->mom_bytes(), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, pb, h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, pb, h->stream);
   if (e == cudaSuccess && h->walls) {
@@ -318,6 +340,7 @@ void mdf_destroy(mdf_t h) {
   cudaStreamSynchronize(h->stream);
   drop_graphs(h);
   cudaFree(h->buf[0]); cudaFree(h->buf[1]); cudaFree(h->mask); cudaFree(h->force);
+  cudaFree(h->mac[0]); cudaFree(h->mac[1]);
   cudaFree(h->stage); cudaFree(h->uprev); cudaFree(h->partials); cudaFree(h->result);
   cudaFree(h->nonfinite);
   delete h;
@@ -342,6 +365,7 @@ mdf_status mdf_init(mdf_t h, const double *P, const double *u, int where) {
     return fail(h, MDF_EINVAL, "init: bad `where` %d", where);
   }
   a.fout = h->cur;
+  a.mout = h->mac[h->cur_index()];
   CU(h, h->d == 2 ? launch_init_d2q5(h->storage, h->walls, a, h->stream)
                   : launch_init_d3q7(h->storage, h->walls, a, h->stream));
   if (where == MDF_HOST) CU(h, cudaStreamSynchronize(h->stream));
@@ -515,14 +539,17 @@ static void fill_header(const mdf_t h, CkptHeader &hd) {
   hd.lid = h->bc.lid;
   hd.s0 = h->s0; hd.s1 = h->s1; hd.s2 = h->s2;
   hd.step = h->step;
-  hd.payload = (int64_t)h->pop_bytes();
+  hd.payload = (int64_t)(h->pop_bytes() + h->mom_bytes());
 }
 
 mdf_status mdf_save(mdf_t h, const char *path) {
   if (check_handle(h)) return MDF_EINVAL;
   if (!path) return fail(h, MDF_EINVAL, "save: null path");
-  std::vector<unsigned char> buf(h->pop_bytes());
-  CU(h, cudaMemcpyAsync(buf.data(), h->cur, buf.size(), cudaMemcpyDeviceToHost, h->stream));
+  std::vector<unsigned char> buf(h->pop_bytes() + h->mom_bytes());
+  CU(h, cudaMemcpyAsync(buf.data(), h->cur, h->pop_bytes(), cudaMemcpyDeviceToHost, h->stream));
+  if (h->kmom)
+    CU(h, cudaMemcpyAsync(buf.data() + h->pop_bytes(), h->mac[h->cur_index()], h->mom_bytes(),
+                          cudaMemcpyDeviceToHost, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   CkptHeader hd;
   fill_header(h, hd);
@@ -549,12 +576,15 @@ mdf_status mdf_load(mdf_t h, const char *path) {
     ok = std::memcmp(&hd, &want, sizeof hd) == 0;
   }
   if (!ok) { std::fclose(fp); return fail(h, MDF_EIO, "load: header of %s does not match this handle", path); }
-  std::vector<unsigned char> buf(h->pop_bytes());
+  std::vector<unsigned char> buf(h->pop_bytes() + h->mom_bytes());
   ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
   std::fclose(fp);
   if (!ok) return fail(h, MDF_EIO, "load: short file %s", path);
   if (fnv1a(buf.data(), buf.size()) != hd.checksum) return fail(h, MDF_EIO, "load: checksum mismatch in %s", path);
-  CU(h, cudaMemcpyAsync(h->cur, buf.data(), buf.size(), cudaMemcpyHostToDevice, h->stream));
+  CU(h, cudaMemcpyAsync(h->cur, buf.data(), h->pop_bytes(), cudaMemcpyHostToDevice, h->stream));
+  if (h->kmom)
+    CU(h, cudaMemcpyAsync(h->mac[h->cur_index()], buf.data() + h->pop_bytes(), h->mom_bytes(),
+                          cudaMemcpyHostToDevice, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   h->step = hd.step;
   h->have_prev = false;
@@ -567,7 +597,8 @@ mdf_status mdf_info(mdf_t h, mdf_info_t *out) {
   out->nx = h->nx; out->ny = h->ny; out->nz = h->nz; out->pitch = h->px;
   out->nodes = h->N;
   out->step = h->step;
-  out->bytes_per_update = 2.0 * h->q * h->nsets * (double)storage_bytes(h->storage);
+  out->bytes_per_update = 2.0 * h->q * h->nsets * (double)storage_bytes(h->storage) +
+                         2.0 * 4.0 * h->kmom;
   out->vx = h->vx;
   out->block = h->block;
   out->s0 = h->s0; out->s1 = h->s1; out->s2 = h->s2;
@@ -580,7 +611,8 @@ mdf_status mdf_autotune(mdf_t h, int reps, int *vx_out, int *block_out) {
   // Candidates: one node per thread, and every vector width built for the
   // storage type that divides nx; 64, 128 and 256 threads per block.
   int widths[4] = {1, 0, 0, 0}, nw = 1;
-  const int built[4][2] = {{2, 4}, {4, 8}, {4, 8}, {2, 2}};  // by MDF_F32, F16, BF16, F64
+  // by MDF_F32, F16, BF16, F64, F16EQ, BF16EQ
+  const int built[6][2] = {{2, 4}, {4, 8}, {4, 8}, {2, 2}, {2, 4}, {2, 4}};
   for (int k = 0; k < 2; ++k) {
     const int v = built[h->storage][k];
     bool dup = false;

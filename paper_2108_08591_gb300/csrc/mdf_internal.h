@@ -13,6 +13,8 @@ struct DevArgs {
   void *fout;                    // next populations
   const uint8_t *mask;           // link mask [plane] or null (periodic)
   const void *force;             // [d][plane] body force (compute type) or null
+  const void *min;               // moments [K][plane] read (equilibrium-shifted storage)
+  void *mout;                    // moments written
   int nx, ny, nz, px;            // grid and padded x pitch
   long long plane;               // px * ny * nz
   int with_rho;                  // 1: set 0 is the alpha = 0 set
@@ -32,7 +34,7 @@ struct DevArgs {
 };
 
 enum Mode { MODE_STEP = 0, MODE_STEP_FIELDS = 1, MODE_FIELDS = 2 };
-enum Storage { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2, ST_F64 = 3 };
+enum Storage { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2, ST_F64 = 3, ST_F16EQ = 4, ST_BF16EQ = 5 };
 enum ReduceKind { RED_SUMS = 0, RED_RESIDUAL = 1 };
 
 // Block width along x of the auxiliary kernels, and the largest block of the

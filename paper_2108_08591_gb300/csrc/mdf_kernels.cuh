@@ -150,7 +150,8 @@ __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long
 // set) become the post-collision populations.  F: Fbar_alpha, alpha = 1..d.
 template <class L, class TC>
 __device__ __forceinline__ void collide_node(TC (&g)[L::D][L::Q], TC (&h)[L::Q], bool with_rho,
-                                             const TC (&F)[L::D], TC s1, TC s2) {
+                                             const TC (&F)[L::D], TC s1, TC s2,
+                                             TC (&M)[L::D + 2]) {
   constexpr int D = L::D, Q = L::Q;
   // Eq. 2-7: u_alpha = sum_i f_{i,alpha} (the rest shift has zero sum);
   // Eq. 3-15: P' = (1/d)(sum_alpha sum_i c_{i,alpha} g_{i,alpha} - |u|^2).
@@ -171,6 +172,10 @@ __device__ __forceinline__ void collide_node(TC (&g)[L::D][L::Q], TC (&h)[L::Q],
   for (int a = 0; a < D; ++a) usq += u[a] * u[a];
   const TC Pp = (tr - usq) * TC(1.0 / D);
 #pragma unroll
+  for (int a = 0; a < D; ++a) M[a] = u[a];
+  M[D] = Pp;
+  M[D + 1] = TC(0);
+#pragma unroll
   for (int a = 0; a < D; ++a) {
     TC jeq[D];  // Eq. 3-7a: sum_i c_i f^eq = u_alpha u + P E_alpha (shifted: P')
 #pragma unroll
@@ -184,6 +189,7 @@ __device__ __forceinline__ void collide_node(TC (&g)[L::D][L::Q], TC (&h)[L::Q],
     TC jeq[D];  // ubar_0 u with ubar_0 = rho0 + rho'
 #pragma unroll
     for (int b = 0; b < D; ++b) jeq[b] = (TC(1) + r) * u[b];
+    M[D + 1] = r;
     L::relax(h, jeq, s1, s2, TC(0));
   }
 }
@@ -222,7 +228,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_update(const DevArgs A) {
 #pragma unroll
   for (int a = 0; a < D; ++a)
     F[a] = A.force ? __ldg(static_cast<const TC *>(A.force) + a * A.plane + idx) : TC(0);
-  collide_node<L, TC>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2));
+  TC M[D + 2];
+  collide_node<L, TC>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M);
 
   TS *__restrict__ fout = static_cast<TS *>(A.fout);
 #pragma unroll
@@ -296,8 +303,9 @@ template <> struct Pair<__nv_bfloat162> {
   }
 };
 template <class T16, class H2, int VX> struct VecIO16 {
-  static_assert(VX == 4 || VX == 8, "16-bit vectors of 4 or 8");
-  using Raw = typename std::conditional<VX == 4, uint2, uint4>::type;
+  static_assert(VX == 2 || VX == 4 || VX == 8, "16-bit vectors of 2, 4 or 8");
+  using Raw = typename std::conditional<VX == 2, uint32_t,
+              typename std::conditional<VX == 4, uint2, uint4>::type>::type;
   static __device__ __forceinline__ void load(const T16 *p, float (&v)[VX]) {
     const Raw r = __ldg(reinterpret_cast<const Raw *>(p));
     const uint32_t *w = reinterpret_cast<const uint32_t *>(&r);
@@ -318,6 +326,15 @@ template <class T16, class H2, int VX> struct VecIO16 {
     }
     *reinterpret_cast<Raw *>(p) = r;
   }
+};
+// one element: the scalar codec
+template <class T16, class H2> struct VecIO16<T16, H2, 1> {
+  static __device__ __forceinline__ void load(const T16 *p, float (&v)[1]) { v[0] = Codec<T16>::load(p); }
+  static __device__ __forceinline__ void store(T16 *p, const float (&v)[1]) { Codec<T16>::store(p, v[0]); }
+};
+template <> struct VecIO<float, 1> {
+  static __device__ __forceinline__ void load(const float *p, float (&v)[1]) { v[0] = __ldg(p); }
+  static __device__ __forceinline__ void store(float *p, const float (&v)[1]) { __stcs(p, v[0]); }
 };
 template <int VX> struct VecIO<__half, VX> : VecIO16<__half, __half2, VX> {};
 template <int VX> struct VecIO<__nv_bfloat16, VX> : VecIO16<__nv_bfloat16, __nv_bfloat162, VX> {};
@@ -435,7 +452,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_vec(const DevArgs A) {
     if (MODE == MODE_FIELDS) continue;
 #pragma unroll
     for (int a = 0; a < D; ++a) Fn[a] = F[a][j];
-    collide_node<L, TC>(gn, hn, A.with_rho != 0, Fn, s1, s2);
+    TC M[D + 2];
+    collide_node<L, TC>(gn, hn, A.with_rho != 0, Fn, s1, s2, M);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
 #pragma unroll
@@ -599,6 +617,12 @@ __global__ void k_mask(const DevArgs A, int wx, int wy, int wz, int lid, uint8_t
   mask[((long long)z * A.ny + y) * A.px + x] = m;
 }
 
+}  // namespace mdf
+
+#include "mdf_eq.cuh"
+
+namespace mdf {
+
 // ---------------------------------------------------------------------------
 // Host-side dispatch over storage / mode / walls for one lattice.
 // ---------------------------------------------------------------------------
@@ -659,9 +683,37 @@ cudaError_t update_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
   return update_scalar<L, TS>(mode, walls, a, s);
 }
 
+template <class L, class TS, int VX>
+cudaError_t update_eq_vx(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
+  const int bx = a.block;
+  const int threads = a.nx / VX;
+  const dim3 grid((unsigned)((threads + bx - 1) / bx), (unsigned)a.ny, (unsigned)a.nz), block(bx);
+  if (walls) {
+    if (mode == MODE_STEP) k_update_eq<L, TS, VX, MODE_STEP, true><<<grid, block, 0, s>>>(a);
+    else if (mode == MODE_STEP_FIELDS) k_update_eq<L, TS, VX, MODE_STEP_FIELDS, true><<<grid, block, 0, s>>>(a);
+    else k_update_eq<L, TS, VX, MODE_FIELDS, true><<<grid, block, 0, s>>>(a);
+  } else {
+    if (mode == MODE_STEP) k_update_eq<L, TS, VX, MODE_STEP, false><<<grid, block, 0, s>>>(a);
+    else if (mode == MODE_STEP_FIELDS) k_update_eq<L, TS, VX, MODE_STEP_FIELDS, false><<<grid, block, 0, s>>>(a);
+    else k_update_eq<L, TS, VX, MODE_FIELDS, false><<<grid, block, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+// Equilibrium-shifted storage: widths 1, 2 or 4 (a width that does not
+// divide nx runs with 1).
+template <class L, class TS>
+cudaError_t update_eq_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
+  if (a.vx == 4 && a.nx % 4 == 0) return update_eq_vx<L, TS, 4>(mode, walls, a, s);
+  if (a.vx == 2 && a.nx % 2 == 0) return update_eq_vx<L, TS, 2>(mode, walls, a, s);
+  return update_eq_vx<L, TS, 1>(mode, walls, a, s);
+}
+
 template <class L>
 cudaError_t update_lattice(int storage, int mode, bool walls, const DevArgs &a, cudaStream_t s) {
   switch (storage) {
+    case ST_F16EQ: return update_eq_t<L, __half>(mode, walls, a, s);
+    case ST_BF16EQ: return update_eq_t<L, __nv_bfloat16>(mode, walls, a, s);
     case ST_F32: return update_t<L, float>(mode, walls, a, s);
     case ST_F16: return update_t<L, __half>(mode, walls, a, s);
     case ST_BF16: return update_t<L, __nv_bfloat16>(mode, walls, a, s);
@@ -677,9 +729,18 @@ cudaError_t init_t(bool walls, const DevArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class L, class TS>
+cudaError_t init_eq_t(bool walls, const DevArgs &a, cudaStream_t s) {
+  if (walls) k_init_eq<L, TS, true><<<node_grid(a), kBlockX, 0, s>>>(a);
+  else k_init_eq<L, TS, false><<<node_grid(a), kBlockX, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <class L>
 cudaError_t init_lattice(int storage, bool walls, const DevArgs &a, cudaStream_t s) {
   switch (storage) {
+    case ST_F16EQ: return init_eq_t<L, __half>(walls, a, s);
+    case ST_BF16EQ: return init_eq_t<L, __nv_bfloat16>(walls, a, s);
     case ST_F32: return init_t<L, float>(walls, a, s);
     case ST_F16: return init_t<L, __half>(walls, a, s);
     case ST_BF16: return init_t<L, __nv_bfloat16>(walls, a, s);
@@ -701,9 +762,24 @@ cudaError_t reduce_t(bool walls, int kind, const DevArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <class L, class TS>
+cudaError_t reduce_eq_t(bool walls, int kind, const DevArgs &a, cudaStream_t s) {
+  const int nb = kReduceBlocks;
+  if (kind == RED_SUMS) {
+    if (walls) k_reduce_eq<L, TS, true, RED_SUMS><<<nb, kReduceThreads, 0, s>>>(a);
+    else k_reduce_eq<L, TS, false, RED_SUMS><<<nb, kReduceThreads, 0, s>>>(a);
+  } else {
+    if (walls) k_reduce_eq<L, TS, true, RED_RESIDUAL><<<nb, kReduceThreads, 0, s>>>(a);
+    else k_reduce_eq<L, TS, false, RED_RESIDUAL><<<nb, kReduceThreads, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
 template <class L>
 cudaError_t reduce_lattice(int storage, bool walls, int kind, const DevArgs &a, cudaStream_t s) {
   switch (storage) {
+    case ST_F16EQ: return reduce_eq_t<L, __half>(walls, kind, a, s);
+    case ST_BF16EQ: return reduce_eq_t<L, __nv_bfloat16>(walls, kind, a, s);
     case ST_F32: return reduce_t<L, float>(walls, kind, a, s);
     case ST_F16: return reduce_t<L, __half>(walls, kind, a, s);
     case ST_BF16: return reduce_t<L, __nv_bfloat16>(walls, kind, a, s);

@@ -41,7 +41,8 @@ def _built():
 def _tol(storage):
     """(u, P - mean P, derived fields) bounds per storage type."""
     return {"f64": (1e-10, 1e-10, 1e-8), "f32": (1e-5, 1e-5, 1e-4),
-            "f16": (2e-3, 5e-3, 5e-2), "bf16": (2e-2, 5e-2, 3e-1)}[storage]
+            "f16": (2e-3, 5e-3, 5e-2), "bf16": (2e-2, 5e-2, 3e-1),
+            "f16eq": (1e-4, 1e-3, 1e-2), "bf16eq": (1e-3, 1e-2, 5e-2)}[storage]
 
 
 # --------------------------------------------------------------------------
@@ -62,7 +63,7 @@ def test_taylor_green_64_matches_oracle(storage):
     assert e["rho"] < (1e-12 if storage == "f64" else 1e-6)
 
 
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16", "f16eq", "bf16eq"])
 def test_ragged_grid_2d(storage):
     """Grid spanning several 128-wide blocks with a ragged tail (nx = 300) and
     a padded pitch; smooth seeded fields with a mean flow."""
@@ -101,7 +102,7 @@ def test_without_continuity_set_is_identical():
 # --------------------------------------------------------------------------
 # 3D periodic
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "f16eq", "bf16eq"])
 def test_d3q7_ragged_matches_oracle(storage):
     shape, steps, s1 = (150, 20, 18), 60, 1.45
     P, u = synth.smooth_fields(shape, seed=13)
@@ -109,6 +110,7 @@ def test_d3q7_ragged_matches_oracle(storage):
     ref = run_oracle(shape, P, u, steps, s1)
     e = errors(ref, got)
     tu, tp, tg = _tol(storage)
+    print(storage, e)
     assert e["u"] < tu and e["P"] < tp, e
     for k in ("G", "S", "sigma", "omega"):
         assert e[k] < tg, (k, e)
@@ -129,7 +131,7 @@ def test_taylor_green_3d_matches_oracle():
 # --------------------------------------------------------------------------
 # Walls, lid, force
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("storage", ["f64", "f32"])
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16eq"])
 def test_lid_driven_cavity_2d(storage):
     """Anti-halfway bounce-back walls and a moving lid on a 67 x 53 cavity."""
     shape, steps, s1 = (67, 53), 400, 1.6
@@ -206,7 +208,7 @@ def test_conservation_sums(d):
     P, u = synth.smooth_fields(shape, seed=4)
     pb = O.Problem(d=d, n=shape, s1=1.5)
     ref0 = O.sums(pb, O.init(pb, P, u))
-    for storage, tol in (("f64", 1e-13), ("f32", 1e-6)):
+    for storage, tol in (("f64", 1e-13), ("f32", 1e-6), ("f16eq", 1e-5)):
         lat = Lattice(shape, s1=1.5, storage=storage)
         lat.init(P, u)
         s0 = lat.sums()
@@ -246,7 +248,7 @@ def test_nonfinite_is_reported():
     lat.close()
 
 
-@pytest.mark.parametrize("storage", ["f32", "bf16"])
+@pytest.mark.parametrize("storage", ["f32", "bf16", "f16eq"])
 def test_checkpoint_resume_is_bit_identical(storage):
     from paper_2108_08591_gb300 import Lattice, MdfError
     shape = (50, 30)
@@ -367,6 +369,7 @@ def test_full_size_4096_sampled_parity():
 @pytest.mark.parametrize("d,storage,vx", [
     (2, "f32", 4), (2, "f32", 2), (2, "f16", 8), (2, "bf16", 4), (2, "f64", 2),
     (3, "f32", 4), (3, "f32", 2), (3, "f16", 4), (3, "bf16", 8), (3, "f64", 2),
+    (2, "f16eq", 2), (2, "f16eq", 4), (2, "bf16eq", 4), (3, "f16eq", 2), (3, "bf16eq", 4),
 ])
 @pytest.mark.parametrize("walls", [False, True])
 def test_vector_kernel_is_bitwise_the_scalar_kernel(d, storage, vx, walls):
