@@ -58,8 +58,8 @@ def _dist():
 
 def _config(n_gpus: int, storage: str, d: int = 2):
     grid = [N_GRID] * d
-    pop_gb = N_GRID ** d * (5 * 3 if d == 2 else 7 * 4) * {"f32": 4, "f16": 2, "bf16": 2}.get(
-        storage, 8) / 1e9
+    pop_gb = N_GRID ** d * (5 * 3 if d == 2 else 7 * 4) * {"f32": 4, "f16": 2, "bf16": 2,
+                                                           "f16eq": 2, "bf16eq": 2}.get(storage, 8) / 1e9
     return {"workload": WORKLOAD, "grid": grid, "lattice": "D2Q5" if d == 2 else "D3Q7",
             "sets": d + 1, "storage": storage, "steps_per_bench_step": EPI_EVERY,
             "global_batch": n_gpus, "parallelism": f"replicas x{n_gpus}",
@@ -381,14 +381,21 @@ def run_mdf(args):
     if world == 1 and not args.no_cpu_baseline and args.workload == "tg2d":
         cpu = cpu_oracle_sample()
     kname = {2: "D2Q5", 3: "D3Q7"}[d]
-    tname = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16"}[args.storage]
-    kernel = (f"k_update_vec<{kname},{tname},VX={info.vx},MODE_STEP,periodic>" if info.vx > 1
-              else f"k_update<{kname},{tname},MODE_STEP,periodic>")
+    tname = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16", "f16eq": "__half",
+             "bf16eq": "__nv_bfloat16"}[args.storage]
+    if args.storage.endswith("eq"):
+        kernel = f"k_update_eq<{kname},{tname},VX={info.vx},MODE_STEP,periodic>"
+    elif info.vx > 1:
+        kernel = f"k_update_vec<{kname},{tname},VX={info.vx},MODE_STEP,periodic>"
+    else:
+        kernel = f"k_update<{kname},{tname},MODE_STEP,periodic>"
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f32": "f32", "f16": "f16 storage / f32", "bf16": "bf16 storage / f32"}[args.storage],
+        "dtype": {"f32": "f32", "f16": "f16 storage / f32", "bf16": "bf16 storage / f32",
+                  "f16eq": "f16 equilibrium-shifted storage + f32 moments / f32",
+                  "bf16eq": "bf16 equilibrium-shifted storage + f32 moments / f32"}[args.storage],
         "data": "synthetic", "config": _config(world, args.storage, d),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
@@ -416,7 +423,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("mdf", "reference"), default="mdf")
-    ap.add_argument("--storage", choices=("f32", "f16", "bf16"), default="f32")
+    ap.add_argument("--storage", choices=("f32", "f16", "bf16", "f16eq", "bf16eq"), default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--workload", choices=("tg2d", "tg3d"), default="tg2d",
@@ -428,14 +435,17 @@ def main():
     if args.workload == "tg3d":
         N_GRID, EPI_EVERY = 512, 200
         WORKLOAD = (f"3D Taylor-Green vortex, periodic 512^3, D3Q7 x 4 sets, U0 = {TG3D_U0}, "
-                    f"Re = {TG3D_RE:.0f}, {args.storage.upper()} rest-shifted storage, FP32 "
+                    f"Re = {TG3D_RE:.0f}, FP32 rest-shifted storage, FP32 "
                     "arithmetic, epilogue every 200 steps")
     if args.grid != 4096:
         WORKLOAD = WORKLOAD.replace(f"{N_GRID}x{N_GRID}", f"{args.grid}x{args.grid}").replace(
             f"{N_GRID}^3", f"{args.grid}^3")
         N_GRID = args.grid
     if args.impl == "mdf" and args.storage != "f32":
-        WORKLOAD = WORKLOAD.replace("FP32 rest-shifted", f"{args.storage.upper()} rest-shifted")
+        name = {"f16": "FP16 rest-shifted", "bf16": "BF16 rest-shifted",
+                "f16eq": "FP16 equilibrium-shifted (+FP32 moments)",
+                "bf16eq": "BF16 equilibrium-shifted (+FP32 moments)"}[args.storage]
+        WORKLOAD = WORKLOAD.replace("FP32 rest-shifted", name).replace("F32 rest-shifted", name)
     if args.warmup < 3 and args.impl == "mdf":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
