@@ -252,6 +252,62 @@ mdf_status mdf_sync(mdf_t h);
  * thread's last failed mdf_create).  Never NULL. */
 const char *mdf_last_error(mdf_t h);
 
+/* ------------------------------------------------------------------------
+ * Batched lid-driven cavities (the cavity of Sec. 4.3 in lattice units).
+ *
+ * Many closed boxes of different sides and Reynolds numbers advanced
+ * together to steady state: anti-halfway bounce-back on every wall, the +
+ * face of the last axis (the lid) moving along x with `lid_speed`;
+ * nu = lid_speed * side / Re, s1 from Eq. 3-13a, s2 from the rule of
+ * Sec. 4.1; FP32 rest-shifted storage (opts->storage must be MDF_F32).  All
+ * nodes share one pool, tiled 128 nodes per tile, and one persistent
+ * cooperative kernel per convergence period walks the tiles of the cavities
+ * still running with a bounded grid barrier between steps (a barrier that
+ * waits more than ~2 s returns MDF_ETIMEOUT instead of hanging).
+ * ------------------------------------------------------------------------ */
+typedef struct mdf_batch_s *mdf_batch_t;
+
+/* mdf_batch_create -- n cavities (1 .. 8192) of dimension d (2: D2Q5 squares,
+ * 3: D3Q7 cubes), side[c] fluid nodes per axis, Reynolds number Re[c].
+ * The state is the rest state after mdf_batch_init(b, -1, NULL, NULL, 0). */
+mdf_status mdf_batch_create(mdf_batch_t *b, int d, int n, const int *side, const double *Re,
+                            double lid_speed, const mdf_opts *o);
+void mdf_batch_destroy(mdf_batch_t b);
+
+/* mdf_batch_init -- cavity c (or all when c = -1) to f = f^eq(P, u): P[N^d],
+ * u[d][N^d] FP64 in `where` memory, or the rest state when P = u = NULL. */
+mdf_status mdf_batch_init(mdf_batch_t b, int cavity, const double *P, const double *u, int where);
+
+/* mdf_batch_run -- advance every cavity until its residual
+ * r = ||u^n - u^{n-1}||_2 / ||u^n||_2 (FP64, checked every `check_every`
+ * steps, which must be even) drops below tol, it diverges, or it has taken
+ * max_steps steps.  Per cavity (host arrays of n, each nullable): steps
+ * taken, status (MDF_OK converged, MDF_EDIVERGED, MDF_ENOTCONVERGED) and
+ * the last residual.  Returns MDF_OK when every cavity converged, else the
+ * first non-OK status.  Synchronises; a period is one captured CUDA graph
+ * when the stream is not the legacy default stream. */
+mdf_status mdf_batch_run(mdf_batch_t b, double tol, long long max_steps, int check_every,
+                         long long *steps, int *status, double *res);
+
+/* mdf_batch_step -- advance every cavity by n steps (no convergence checks). */
+mdf_status mdf_batch_step(mdf_batch_t b, long long n);
+
+/* mdf_batch_fields -- derived fields (Eq. 2-7, 3-15 .. 3-19) of one cavity,
+ * layout as mdf_fields_t with N = side^d nodes. */
+mdf_status mdf_batch_fields(mdf_batch_t b, int cavity, const mdf_fields_t *out);
+
+/* mdf_batch_info -- total fluid nodes, tiles and persistent-grid blocks. */
+mdf_status mdf_batch_info(mdf_batch_t b, long long *nodes, int *tiles, int *grid);
+
+/* mdf_batch_set_timeout -- spin limit of the grid barrier in SM clock cycles
+ * (default 4e9, about 2 s).  A barrier that waits longer makes every block of
+ * the persistent kernel return and the call report MDF_ETIMEOUT; the batch
+ * state is then undefined until the next mdf_batch_init. */
+mdf_status mdf_batch_set_timeout(mdf_batch_t b, long long cycles);
+
+/* mdf_batch_last_error -- message of the last failure (NULL: last create). */
+const char *mdf_batch_last_error(mdf_batch_t b);
+
 #ifdef __cplusplus
 }
 #endif

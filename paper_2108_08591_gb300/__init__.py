@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib
 from ._lib import DEVICE, HOST, MdfError, STORAGE
 
-__all__ = ["Lattice", "MdfError", "FIELD_NAMES", "field_shapes", "s2_rule"]
+__all__ = ["Lattice", "CavityBatch", "MdfError", "FIELD_NAMES", "field_shapes", "s2_rule"]
 
 FIELD_NAMES = ("P", "u", "rho", "G", "div", "S", "sigma", "omega")
 
@@ -223,3 +223,86 @@ class Lattice:
 
     def sync(self):
         self._check(self._lib.mdf_sync(self._h))
+
+
+class CavityBatch:
+    """Many lid-driven cavities (closed boxes, lid on the + face of the last
+    axis moving along x) advanced together to steady state by one persistent
+    kernel per convergence period (see mdf_batch_* in include/mdf.h)."""
+
+    def __init__(self, sides: Sequence[int], Re: Sequence[float], lid_speed: float = 0.1,
+                 d: int = 2, with_rho: bool = True, stream=None):
+        import torch
+
+        self._lib = _lib.load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        self.sides = np.ascontiguousarray(sides, dtype=np.int32)
+        self.Re = np.ascontiguousarray(Re, dtype=np.float64)
+        self.d = d
+        self.n = len(self.sides)
+        self.with_rho = bool(with_rho)
+        o = _lib.Opts(STORAGE["f32"], int(bool(with_rho)), ctypes.c_void_p(sptr), 0, 0)
+        h = ctypes.c_void_p()
+        _lib.check_batch(self._lib.mdf_batch_create(ctypes.byref(h), d, self.n, self.sides.ctypes.data,
+                                                    self.Re.ctypes.data, float(lid_speed), ctypes.byref(o)))
+        self._h = h
+        self.init()
+
+    def _check(self, status: int):
+        _lib.check_batch(status, self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mdf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, cavity: int = -1, P=None, u=None):
+        """Rest state (P = u = None) or f = f^eq(P, u) for one cavity."""
+        dev = P is not None and _is_device(P)
+        self._check(self._lib.mdf_batch_init(self._h, int(cavity), _ptr(P), _ptr(u),
+                                             DEVICE if dev else HOST))
+
+    def run(self, tol: float = 1e-8, max_steps: int = 2_000_000, check_every: int = 100):
+        """Run to steady state; returns (steps, status, residual) arrays.
+        status: 0 converged, 4 diverged, 6 not converged (mdf_status codes)."""
+        steps = np.zeros(self.n, dtype=np.int64)
+        status = np.zeros(self.n, dtype=np.int32)
+        res = np.zeros(self.n)
+        rc = self._lib.mdf_batch_run(self._h, float(tol), int(max_steps), int(check_every),
+                                     steps.ctypes.data, status.ctypes.data, res.ctypes.data)
+        if rc not in (_lib.OK, _lib.EDIVERGED, _lib.ENOTCONVERGED):
+            self._check(rc)
+        return steps, status, res
+
+    def step(self, n: int):
+        self._check(self._lib.mdf_batch_step(self._h, int(n)))
+
+    def set_timeout(self, cycles: int):
+        """Grid-barrier spin limit in SM clock cycles (default ~2 s)."""
+        self._check(self._lib.mdf_batch_set_timeout(self._h, int(cycles)))
+
+    def fields_host(self, cavity: int, names: Iterable[str] = ("P", "u")) -> Dict[str, np.ndarray]:
+        N = int(self.sides[cavity]) ** self.d
+        shapes = field_shapes(self.d, N)
+        out = {k: np.empty(shapes[k]) for k in names}
+        f = _lib.Fields()
+        for k, v in out.items():
+            setattr(f, k, _ptr(v))
+        f.where = HOST
+        self._check(self._lib.mdf_batch_fields(self._h, int(cavity), ctypes.byref(f)))
+        return out
+
+    def info(self):
+        nodes, tiles, grid = np.zeros(1, np.int64), np.zeros(1, np.int32), np.zeros(1, np.int32)
+        self._check(self._lib.mdf_batch_info(self._h, nodes.ctypes.data, tiles.ctypes.data,
+                                             grid.ctypes.data))
+        return int(nodes[0]), int(tiles[0]), int(grid[0])

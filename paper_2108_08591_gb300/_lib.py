@@ -77,6 +77,16 @@ SIGNATURES = {
                                     ctypes.POINTER(ctypes.c_int)]),
     "mdf_sync": (ctypes.c_int, [H]),
     "mdf_last_error": (ctypes.c_char_p, [H]),
+    "mdf_batch_create": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int, ctypes.c_int, DP, DP,
+                                        ctypes.c_double, ctypes.POINTER(Opts)]),
+    "mdf_batch_destroy": (None, [H]),
+    "mdf_batch_init": (ctypes.c_int, [H, ctypes.c_int, DP, DP, ctypes.c_int]),
+    "mdf_batch_run": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_longlong, ctypes.c_int, DP, DP, DP]),
+    "mdf_batch_step": (ctypes.c_int, [H, ctypes.c_longlong]),
+    "mdf_batch_fields": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(Fields)]),
+    "mdf_batch_info": (ctypes.c_int, [H, DP, DP, DP]),
+    "mdf_batch_set_timeout": (ctypes.c_int, [H, ctypes.c_longlong]),
+    "mdf_batch_last_error": (ctypes.c_char_p, [H]),
 }
 
 _lib = None
@@ -110,4 +120,10 @@ class MdfError(RuntimeError):
 def check(status: int, handle=None):
     if status != OK:
         msg = load().mdf_last_error(handle)
+        raise MdfError(status, msg.decode() if msg else "")
+
+
+def check_batch(status: int, handle=None):
+    if status != OK:
+        msg = load().mdf_batch_last_error(handle)
         raise MdfError(status, msg.decode() if msg else "")

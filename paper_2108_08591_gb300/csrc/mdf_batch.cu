@@ -1,0 +1,715 @@
+// Batched lid-driven cavities advanced to steady state by one persistent
+// kernel per convergence period, captured in a CUDA graph.
+//
+// Every cavity is a closed box (anti-halfway bounce-back walls on all faces,
+// the + face of the last axis moving with the lid velocity, Sec. 4) with its
+// own side N and relaxation rates.  Nodes of all cavities live in one pool,
+// cavity after cavity, each cavity padded to whole tiles of kTile nodes, so a
+// tile belongs to exactly one cavity; populations are structure of arrays
+// f[set][i][pool node], rest-shifted FP32.  Per step the persistent kernel
+// walks the list of tiles of the cavities still running, with a bounded grid
+// barrier between steps.  Every `check` steps a residual pass (FP64,
+// Sec. C10 reading: r = |u^n - u^{n-1}|_2 / |u^n|_2 per cavity), a status pass
+// and a compaction pass retire converged or diverged cavities; the four
+// kernels form one captured graph replayed until no cavity runs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mdf.h"
+#include "mdf_kernels.cuh"
+
+namespace mdf {
+
+constexpr int kTile = 128;  // nodes per tile = threads per block
+
+struct CavParam {
+  int N;            // nodes per side
+  int tile0;        // first tile of this cavity
+  int ntiles;       // tiles of this cavity
+  int pad;
+  long long base;   // first pool node of this cavity
+  float s1, s2;
+  double s1d;
+};
+
+enum CavStatus { CAV_RUNNING = 0, CAV_CONVERGED = 1, CAV_DIVERGED = 2, CAV_MAXSTEPS = 3 };
+
+struct BatchArgs {
+  float *f[2];              // population pools [nsets][Q][tot]
+  long long tot;            // pool size in nodes (direction stride)
+  const CavParam *cav;
+  const int *tile_cav;      // cavity of every tile
+  int *live;                // tile ids of running cavities
+  int *n_live;
+  int ncav, ntiles, with_rho;
+  double lid_u[3];
+  float *usave;             // [d][tot] velocity saved by the last update of a period
+  double *part;             // [ntiles][2] residual partial sums
+  int *badtile;             // [ntiles] non-finite flags
+  int *status;              // [ncav]
+  long long *steps;         // [ncav]
+  double *res;              // [ncav]
+  unsigned int *bar;        // [0] arrivals, [1] generation
+  int *err;                 // MDF_ETIMEOUT on a barrier time-out
+  long long timeout;        // barrier spin limit in clock cycles
+};
+
+// Bounded grid-wide barrier for a cooperative launch: the last block to
+// arrive advances the generation; the others spin on it, give up after
+// `timeout` cycles (or when another block already gave up), and report.
+__device__ __forceinline__ bool grid_barrier(const BatchArgs &B) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int *gen = B.bar + 1;
+    volatile int *err = B.err;
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int arrived = atomicAdd(B.bar, 1u) + 1u;
+    if (arrived == gridDim.x) {
+      atomicExch(B.bar, 0u);
+      __threadfence();
+      atomicAdd(B.bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (*err) break;
+        if (clock64() - t0 > B.timeout) {
+          atomicCAS(B.err, 0, (int)MDF_ETIMEOUT);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = *err == 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Wall bits of node (x, y[, z]) of a closed box of side N: bit i when the
+// link along c_i leaves the box, bit 7 when it crosses the lid.
+template <class L>
+__device__ __forceinline__ uint8_t box_mask(const int (&p)[3], int N) {
+  uint8_t m = 0;
+#pragma unroll
+  for (int i = 1; i < L::Q; ++i)
+#pragma unroll
+    for (int b = 0; b < L::D; ++b) {
+      const int t = p[b] + L::c(i, b);
+      if (t < 0 || t >= N) {
+        m |= uint8_t(1u << i);
+        if (b == L::D - 1 && t >= N) m |= 0x80u;
+      }
+    }
+  return m;
+}
+
+template <class L>
+__device__ __forceinline__ void node_pos(int k, int N, int (&p)[3]) {
+  p[0] = k % N;
+  p[1] = (k / N) % N;
+  p[2] = L::D == 3 ? k / (N * N) : 0;
+}
+
+template <class L>
+__device__ __forceinline__ long long node_count(int N) {
+  return L::D == 3 ? (long long)N * N * N : (long long)N * N;
+}
+
+// Pull every carried set at pool node idx (local node k of cavity C).
+template <class L>
+__device__ __forceinline__ void batch_pull(const BatchArgs &B, const float *fin, const CavParam &C,
+                                           int k, float (&g)[L::D][L::Q], float (&h)[L::Q],
+                                           long long &idx) {
+  constexpr int D = L::D, Q = L::Q;
+  int p[3];
+  node_pos<L>(k, C.N, p);
+  idx = C.base + k;
+  const uint8_t m = box_mask<L>(p, C.N);
+  long long src[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    src[i] = idx - (L::c(i, 0) + (long long)L::c(i, 1) * C.N +
+                    (D == 3 ? (long long)L::c(i, 2) * C.N * C.N : 0));
+  const long long setstride = (long long)Q * B.tot;
+#pragma unroll
+  for (int al = 1; al <= D; ++al)
+    pull_set_p<L, float, true>(fin + (long long)(B.with_rho + al - 1) * setstride, B.tot, al, idx,
+                               src, m, B.lid_u, g[al - 1]);
+  if (B.with_rho) pull_set_p<L, float, true>(fin, B.tot, 0, idx, src, m, B.lid_u, h);
+}
+
+// `steps` updates of every running cavity; buffer `cur` holds the current
+// state.  With save_last, the last update stores the velocity it pulled
+// (u^{n-1}) for the residual pass.
+template <class L>
+__global__ void __launch_bounds__(kTile) k_batch_chunk(BatchArgs B, int cur, int steps, int save_last) {
+  constexpr int D = L::D, Q = L::Q;
+  const int nl = *B.n_live;
+  for (int s = 0; s < steps; ++s) {
+    const float *fin = B.f[(cur + s) & 1];
+    float *fout = B.f[(cur + s + 1) & 1];
+    for (int t = blockIdx.x; t < nl; t += gridDim.x) {
+      const int tile = B.live[t];
+      const CavParam C = B.cav[B.tile_cav[tile]];
+      const int k = (tile - C.tile0) * kTile + threadIdx.x;
+      if (k >= node_count<L>(C.N)) continue;
+      float g[D][Q], h[Q], F[D] = {}, M[D + 2];
+      long long idx;
+      batch_pull<L>(B, fin, C, k, g, h, idx);
+      collide_node<L, float>(g, h, B.with_rho != 0, F, C.s1, C.s2, M);
+      if (save_last && s == steps - 1)
+#pragma unroll
+        for (int a = 0; a < D; ++a) B.usave[a * B.tot + idx] = M[a];
+      const long long setstride = (long long)Q * B.tot;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int i = 0; i < Q; ++i)
+          __stcs(fout + (long long)(B.with_rho + a) * setstride + (long long)i * B.tot + idx, g[a][i]);
+      if (B.with_rho)
+#pragma unroll
+        for (int i = 0; i < Q; ++i) __stcs(fout + (long long)i * B.tot + idx, h[i]);
+    }
+    if (s + 1 < steps && !grid_barrier(B)) return;
+  }
+}
+
+// Residual partial sums of every live tile against the saved velocity.
+template <class L>
+__global__ void __launch_bounds__(kTile) k_batch_residual(BatchArgs B, int cur) {
+  constexpr int D = L::D, Q = L::Q;
+  const int t = blockIdx.x;
+  if (t >= *B.n_live) return;
+  const int tile = B.live[t];
+  const CavParam C = B.cav[B.tile_cav[tile]];
+  const int k = (tile - C.tile0) * kTile + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  bool bad = false;
+  if (k < node_count<L>(C.N)) {
+    float g[D][Q], h[Q];
+    long long idx;
+    batch_pull<L>(B, B.f[cur], C, k, g, h, idx);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      float s = 0.f;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) s += g[a][i];
+      const double u = s, dlt = u - (double)B.usave[a * B.tot + idx];
+      v[0] += dlt * dlt;
+      v[1] += u * u;
+      bad |= !isfinite(u);
+    }
+  }
+  __shared__ double sh[2][kTile / 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    double x = v[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[c][warp] = x;
+  }
+  const int anybad = __syncthreads_or(bad);
+  if (threadIdx.x < 2) {
+    double x = 0.0;
+    for (int w = 0; w < kTile / 32; ++w) x += sh[threadIdx.x][w];
+    B.part[(long long)tile * 2 + threadIdx.x] = x;
+  }
+  if (threadIdx.x == 0) B.badtile[tile] = anybad;
+}
+
+// Per cavity: residual from its tiles' partials (fixed order), step count,
+// status.  One block per cavity.
+__global__ void k_batch_status(BatchArgs B, int period, double tol, long long max_steps) {
+  const int c = blockIdx.x;
+  if (threadIdx.x != 0 || B.status[c] != CAV_RUNNING) return;
+  const CavParam C = B.cav[c];
+  double num = 0.0, den = 0.0;
+  int bad = 0;
+  for (int t = 0; t < C.ntiles; ++t) {
+    num += B.part[(long long)(C.tile0 + t) * 2];
+    den += B.part[(long long)(C.tile0 + t) * 2 + 1];
+    bad |= B.badtile[C.tile0 + t];
+  }
+  const double r = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+  B.res[c] = r;
+  B.steps[c] += period;
+  if (bad || !isfinite(r)) B.status[c] = CAV_DIVERGED;
+  else if (r < tol) B.status[c] = CAV_CONVERGED;
+  else if (B.steps[c] >= max_steps) B.status[c] = CAV_MAXSTEPS;
+}
+
+// Rebuild the live tile list from the cavity status (one block).
+__global__ void k_batch_compact(BatchArgs B) {
+  extern __shared__ int off[];  // [ncav + 1]
+  if (threadIdx.x == 0) {
+    int o = 0;
+    for (int c = 0; c < B.ncav; ++c) {
+      off[c] = o;
+      if (B.status[c] == CAV_RUNNING) o += B.cav[c].ntiles;
+    }
+    off[B.ncav] = o;
+    *B.n_live = o;
+  }
+  __syncthreads();
+  for (int c = 0; c < B.ncav; ++c) {
+    if (B.status[c] != CAV_RUNNING) continue;
+    const CavParam C = B.cav[c];
+    for (int t = threadIdx.x; t < C.ntiles; t += blockDim.x) B.live[off[c] + t] = C.tile0 + t;
+  }
+}
+
+// Initial state of one cavity: f = f^eq(P, u) in pull form (see k_init).
+template <class L>
+__global__ void __launch_bounds__(kTile) k_batch_init(BatchArgs B, int cur, int c, const double *P,
+                                                     const double *u) {
+  constexpr int D = L::D, Q = L::Q;
+  const CavParam C = B.cav[c];
+  const long long n = (long long)blockIdx.x * kTile + threadIdx.x;
+  const long long NN = node_count<L>(C.N);
+  if (n >= NN) return;
+  int p[3];
+  node_pos<L>((int)n, C.N, p);
+  const uint8_t m = box_mask<L>(p, C.N);
+  DevArgs A;  // only the fields geq() reads
+  A.Pin = P;
+  A.uin = u;
+  float *f = B.f[cur];
+  const int nsets = D + B.with_rho;
+  for (int a = 0; a < nsets; ++a) {
+    const int alpha = a + 1 - B.with_rho;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      float v;
+      if (i != 0 && ((m >> i) & 1)) {
+        v = -geq<L, float>(A, NN, n, alpha, L::opp(i));
+        if (alpha >= 1 && i == L::UP && (m & 0x80u)) v += float(2.0 * L::w(i) * B.lid_u[alpha - 1]);
+      } else {
+        const long long t = n + L::c(i, 0) + (long long)L::c(i, 1) * C.N +
+                            (D == 3 ? (long long)L::c(i, 2) * C.N * C.N : 0);
+        v = geq<L, float>(A, NN, t, alpha, i);
+      }
+      f[((long long)a * Q + i) * B.tot + C.base + n] = v;
+    }
+  }
+}
+
+// Derived fields of one cavity (dense [N^d] outputs, see write_fields).
+template <class L>
+__global__ void __launch_bounds__(kTile) k_batch_fields(BatchArgs B, int cur, int c, DevArgs A) {
+  constexpr int D = L::D, Q = L::Q;
+  const CavParam C = B.cav[c];
+  const long long n = (long long)blockIdx.x * kTile + threadIdx.x;
+  const long long NN = node_count<L>(C.N);
+  if (n >= NN) return;
+  float g[D][Q], h[Q];
+  long long idx;
+  batch_pull<L>(B, B.f[cur], C, (int)n, g, h, idx);
+  write_fields<L, float>(A, n, NN, g, h);
+}
+
+}  // namespace mdf
+
+using namespace mdf;
+
+struct mdf_batch_s {
+  int d = 2, ncav = 0, ntiles = 0, with_rho = 1;
+  long long tot = 0;
+  double lid_u[3] = {0, 0, 0};
+  cudaStream_t stream = nullptr;
+  std::vector<CavParam> cav;
+  BatchArgs B{};
+  int cur = 0;
+  int grid = 0;  // blocks of the persistent kernel
+  int *host_live = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  int graph_period = 0, graph_cur = 0;
+  double graph_tol = 0;
+  long long graph_max = 0;
+  std::string err = "no error";
+};
+
+namespace {
+
+thread_local std::string g_batch_error = "no error";
+
+mdf_status bfail(mdf_batch_t b, mdf_status st, const char *fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  if (b) b->err = msg;
+  else g_batch_error = msg;
+  return st;
+}
+
+#define BCU(b, call)                                                                     \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return bfail((b), MDF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
+  } while (0)
+
+template <class L>
+cudaError_t launch_chunk(mdf_batch_t b, int steps, int save_last) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(b->grid);
+  cfg.blockDim = dim3(kTile);
+  cfg.stream = b->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_batch_chunk<L>, b->B, b->cur, steps, save_last);
+}
+
+template <class L>
+cudaError_t enqueue_period(mdf_batch_t b, int period, double tol, long long max_steps) {
+  cudaError_t e = launch_chunk<L>(b, period, 1);
+  if (e != cudaSuccess) return e;
+  const int cur_after = (b->cur + period) & 1;
+  k_batch_residual<L><<<b->ntiles, kTile, 0, b->stream>>>(b->B, cur_after);
+  k_batch_status<<<b->ncav, 32, 0, b->stream>>>(b->B, period, tol, max_steps);
+  k_batch_compact<<<1, 256, sizeof(int) * (b->ncav + 1), b->stream>>>(b->B);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue(mdf_batch_t b, int period, double tol, long long max_steps) {
+  return b->d == 2 ? enqueue_period<D2Q5>(b, period, tol, max_steps)
+                   : enqueue_period<D3Q7>(b, period, tol, max_steps);
+}
+
+}  // namespace
+
+extern "C" {
+
+mdf_status mdf_batch_create(mdf_batch_t *out, int d, int n, const int *side, const double *Re,
+                            double lid_speed, const mdf_opts *o) {
+  if (!out) return bfail(nullptr, MDF_EINVAL, "null handle pointer");
+  *out = nullptr;
+  if (d != 2 && d != 3) return bfail(nullptr, MDF_EINVAL, "d must be 2 or 3");
+  if (n < 1 || n > 8192 || !side || !Re)
+    return bfail(nullptr, MDF_EINVAL, "need 1 .. 8192 cavities with sides and Re");
+  if (!(lid_speed > 0.0) || lid_speed > 0.5) return bfail(nullptr, MDF_EINVAL, "lid speed must lie in (0, 0.5]");
+  mdf_opts opts{};
+  opts.storage = MDF_F32;
+  opts.with_rho = 1;
+  if (o) opts = *o;
+  if (opts.storage != MDF_F32) return bfail(nullptr, MDF_EUNSUPPORTED, "batched cavities use FP32 storage");
+  mdf_batch_t b = new (std::nothrow) mdf_batch_s;
+  if (!b) return bfail(nullptr, MDF_ENOMEM, "host allocation");
+  b->d = d;
+  b->ncav = n;
+  b->with_rho = opts.with_rho ? 1 : 0;
+  b->stream = static_cast<cudaStream_t>(opts.stream);
+  b->lid_u[0] = lid_speed;
+  const double cs2 = d == 2 ? 1.0 / 3.0 : 0.25;
+  long long base = 0;
+  int tile0 = 0;
+  for (int c = 0; c < n; ++c) {
+    if (side[c] < 2 || side[c] > (d == 2 ? 16384 : 1024) || !(Re[c] > 0)) {
+      delete b;
+      return bfail(nullptr, MDF_EINVAL, "cavity %d: bad side %d or Re %g", c, side[c], Re[c]);
+    }
+    const double nu = lid_speed * side[c] / Re[c];   // Re = U N / nu
+    const double s1 = 1.0 / (nu / cs2 + 0.5);          // Eq. 3-13a with dt = 1
+    const double s2 = 8.0 * (2.0 - s1) / (8.0 - s1);   // the rule of Sec. 4.1
+    CavParam C{};
+    C.N = side[c];
+    const long long nn = d == 2 ? (long long)side[c] * side[c] : (long long)side[c] * side[c] * side[c];
+    C.ntiles = (int)((nn + kTile - 1) / kTile);
+    C.tile0 = tile0;
+    C.base = base;
+    C.s1 = (float)s1;
+    C.s2 = (float)s2;
+    C.s1d = s1;
+    b->cav.push_back(C);
+    tile0 += C.ntiles;
+    base += (long long)C.ntiles * kTile;
+  }
+  b->ntiles = tile0;
+  b->tot = base;
+  const int nsets = d + b->with_rho, Q = d == 2 ? 5 : 7;
+  BatchArgs &B = b->B;
+  B.tot = b->tot;
+  B.ncav = n;
+  B.ntiles = b->ntiles;
+  B.with_rho = b->with_rho;
+  for (int k = 0; k < 3; ++k) B.lid_u[k] = b->lid_u[k];
+  B.timeout = 4000000000LL;  // ~2 s at the GB300 clock
+  const size_t popb = sizeof(float) * (size_t)nsets * Q * (size_t)b->tot;
+  std::vector<int> tile_cav(b->ntiles);
+  for (int c = 0; c < n; ++c)
+    for (int t = 0; t < b->cav[c].ntiles; ++t) tile_cav[b->cav[c].tile0 + t] = c;
+  cudaError_t e = cudaMalloc(&B.f[0], popb);
+  if (e == cudaSuccess) e = cudaMalloc(&B.f[1], popb);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&B.cav, sizeof(CavParam) * n);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&B.tile_cav, sizeof(int) * b->ntiles);
+  if (e == cudaSuccess) e = cudaMalloc(&B.live, sizeof(int) * b->ntiles);
+  if (e == cudaSuccess) e = cudaMalloc(&B.n_live, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&B.usave, sizeof(float) * d * (size_t)b->tot);
+  if (e == cudaSuccess) e = cudaMalloc(&B.part, sizeof(double) * 2 * b->ntiles);
+  if (e == cudaSuccess) e = cudaMalloc(&B.badtile, sizeof(int) * b->ntiles);
+  if (e == cudaSuccess) e = cudaMalloc(&B.status, sizeof(int) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&B.steps, sizeof(long long) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&B.res, sizeof(double) * n);
+  if (e == cudaSuccess) e = cudaMalloc(&B.bar, sizeof(unsigned int) * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&B.err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->host_live, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.f[0], 0, popb, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.f[1], 0, popb, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.usave, 0, sizeof(float) * d * (size_t)b->tot, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.bar, 0, sizeof(unsigned int) * 2, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.err, 0, sizeof(int), b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void *)B.cav, b->cav.data(), sizeof(CavParam) * n, cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void *)B.tile_cav, tile_cav.data(), sizeof(int) * b->ntiles,
+                        cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) {
+    int dev = 0, sms = 0, per = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_chunk<D2Q5>, kTile, 0)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_chunk<D3Q7>, kTile, 0);
+    b->grid = std::max(1, std::min(sms * per, b->ntiles));
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    bfail(nullptr, e == cudaErrorMemoryAllocation ? MDF_ENOMEM : MDF_ECUDA, "batch create: %s",
+          cudaGetErrorString(e));
+    mdf_batch_destroy(b);
+    return e == cudaErrorMemoryAllocation ? MDF_ENOMEM : MDF_ECUDA;
+  }
+  *out = b;
+  return MDF_OK;
+}
+
+void mdf_batch_destroy(mdf_batch_t b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  BatchArgs &B = b->B;
+  cudaFree(B.f[0]); cudaFree(B.f[1]); cudaFree((void *)B.cav); cudaFree((void *)B.tile_cav);
+  cudaFree(B.live); cudaFree(B.n_live); cudaFree(B.usave); cudaFree(B.part); cudaFree(B.badtile);
+  cudaFree(B.status); cudaFree(B.steps); cudaFree(B.res); cudaFree(B.bar); cudaFree(B.err);
+  cudaFreeHost(b->host_live);
+  delete b;
+}
+
+mdf_status mdf_batch_init(mdf_batch_t b, int cavity, const double *P, const double *u, int where) {
+  if (!b) return MDF_EINVAL;
+  if (cavity < -1 || cavity >= b->ncav) return bfail(b, MDF_EINVAL, "cavity %d out of range", cavity);
+  const int lo = cavity < 0 ? 0 : cavity, hi = cavity < 0 ? b->ncav : cavity + 1;
+  if ((P || u) && cavity < 0) return bfail(b, MDF_EINVAL, "fields need a single cavity");
+  for (int c = lo; c < hi; ++c) {
+    const CavParam &C = b->cav[c];
+    const long long nn = b->d == 2 ? (long long)C.N * C.N : (long long)C.N * C.N * C.N;
+    const size_t bytes = sizeof(double) * (size_t)nn;
+    double *dP = nullptr, *du = nullptr;
+    BCU(b, cudaMallocAsync(&dP, bytes, b->stream));
+    BCU(b, cudaMallocAsync(&du, bytes * b->d, b->stream));
+    if (P && u) {
+      const cudaMemcpyKind kind = where == MDF_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+      BCU(b, cudaMemcpyAsync(dP, P, bytes, kind, b->stream));
+      BCU(b, cudaMemcpyAsync(du, u, bytes * b->d, kind, b->stream));
+    } else {  // rest state P = P0 = 1, u = 0
+      std::vector<double> ones((size_t)nn, 1.0);
+      BCU(b, cudaMemcpyAsync(dP, ones.data(), bytes, cudaMemcpyHostToDevice, b->stream));
+      BCU(b, cudaMemsetAsync(du, 0, bytes * b->d, b->stream));
+      BCU(b, cudaStreamSynchronize(b->stream));
+    }
+    const unsigned blocks = (unsigned)((nn + kTile - 1) / kTile);
+    if (b->d == 2) k_batch_init<D2Q5><<<blocks, kTile, 0, b->stream>>>(b->B, b->cur, c, dP, du);
+    else k_batch_init<D3Q7><<<blocks, kTile, 0, b->stream>>>(b->B, b->cur, c, dP, du);
+    BCU(b, cudaGetLastError());
+    BCU(b, cudaFreeAsync(dP, b->stream));
+    BCU(b, cudaFreeAsync(du, b->stream));
+  }
+  BCU(b, cudaStreamSynchronize(b->stream));
+  return MDF_OK;
+}
+
+mdf_status mdf_batch_run(mdf_batch_t b, double tol, long long max_steps, int check_every,
+                         long long *steps_out, int *status_out, double *res_out) {
+  if (!b) return MDF_EINVAL;
+  if (check_every < 2 || (check_every & 1))
+    return bfail(b, MDF_EINVAL, "check_every must be even and >= 2 (got %d)", check_every);
+  if (max_steps < check_every) return bfail(b, MDF_EINVAL, "max_steps must be >= check_every");
+  BatchArgs &B = b->B;
+  // every cavity starts running, with all tiles live
+  std::vector<int> zero(b->ncav, 0), live(b->ntiles);
+  for (int t = 0; t < b->ntiles; ++t) live[t] = t;
+  std::vector<long long> zsteps(b->ncav, 0);
+  BCU(b, cudaMemcpyAsync(B.status, zero.data(), sizeof(int) * b->ncav, cudaMemcpyHostToDevice, b->stream));
+  BCU(b, cudaMemcpyAsync(B.steps, zsteps.data(), sizeof(long long) * b->ncav, cudaMemcpyHostToDevice, b->stream));
+  BCU(b, cudaMemcpyAsync(B.live, live.data(), sizeof(int) * b->ntiles, cudaMemcpyHostToDevice, b->stream));
+  BCU(b, cudaMemcpyAsync(B.n_live, &b->ntiles, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  BCU(b, cudaMemsetAsync(B.err, 0, sizeof(int), b->stream));
+  BCU(b, cudaMemsetAsync(B.bar, 0, sizeof(unsigned int) * 2, b->stream));
+  BCU(b, cudaStreamSynchronize(b->stream));
+  // one convergence period as a graph (on a non-legacy stream), else direct launches
+  if (b->graph && (b->graph_period != check_every || b->graph_tol != tol || b->graph_max != max_steps ||
+                   b->graph_cur != b->cur)) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  if (!b->graph && b->stream) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      e = enqueue(b, check_every, tol, max_steps);
+      cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+      if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&b->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      b->graph = nullptr;  // fall back to direct launches
+    } else {
+      b->graph_period = check_every;
+      b->graph_cur = b->cur;
+      b->graph_tol = tol;
+      b->graph_max = max_steps;
+    }
+  }
+  for (long long done = 0; done < max_steps; done += check_every) {
+    if (b->graph) BCU(b, cudaGraphLaunch(b->graph, b->stream));
+    else BCU(b, enqueue(b, check_every, tol, max_steps));
+    // the period's step count is even: the current buffer index is unchanged
+    BCU(b, cudaMemcpyAsync(b->host_live, B.n_live, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    int err = 0;
+    BCU(b, cudaMemcpyAsync(&err, B.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BCU(b, cudaStreamSynchronize(b->stream));
+    if (err) return bfail(b, MDF_ETIMEOUT, "grid barrier timed out; the batch state is undefined");
+    if (*b->host_live == 0) break;
+  }
+  std::vector<int> st(b->ncav);
+  std::vector<long long> steps(b->ncav);
+  std::vector<double> res(b->ncav);
+  BCU(b, cudaMemcpyAsync(st.data(), B.status, sizeof(int) * b->ncav, cudaMemcpyDeviceToHost, b->stream));
+  BCU(b, cudaMemcpyAsync(steps.data(), B.steps, sizeof(long long) * b->ncav, cudaMemcpyDeviceToHost, b->stream));
+  BCU(b, cudaMemcpyAsync(res.data(), B.res, sizeof(double) * b->ncav, cudaMemcpyDeviceToHost, b->stream));
+  BCU(b, cudaStreamSynchronize(b->stream));
+  mdf_status worst = MDF_OK;
+  for (int c = 0; c < b->ncav; ++c) {
+    int s;
+    switch (st[c]) {
+      case CAV_CONVERGED: s = MDF_OK; break;
+      case CAV_DIVERGED: s = MDF_EDIVERGED; break;
+      default: s = MDF_ENOTCONVERGED; break;
+    }
+    if (status_out) status_out[c] = s;
+    if (steps_out) steps_out[c] = steps[c];
+    if (res_out) res_out[c] = res[c];
+    if (s != MDF_OK && worst == MDF_OK) worst = (mdf_status)s;
+  }
+  if (worst != MDF_OK) bfail(b, worst, "some cavities did not converge; see the status array");
+  return worst;
+}
+
+mdf_status mdf_batch_step(mdf_batch_t b, long long n) {
+  if (!b) return MDF_EINVAL;
+  if (n < 0) return bfail(b, MDF_EINVAL, "n < 0");
+  // all tiles live for plain stepping
+  std::vector<int> live(b->ntiles);
+  for (int t = 0; t < b->ntiles; ++t) live[t] = t;
+  BCU(b, cudaMemcpyAsync(b->B.live, live.data(), sizeof(int) * b->ntiles, cudaMemcpyHostToDevice, b->stream));
+  BCU(b, cudaMemcpyAsync(b->B.n_live, &b->ntiles, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  BCU(b, cudaMemsetAsync(b->B.err, 0, sizeof(int), b->stream));
+  BCU(b, cudaMemsetAsync(b->B.bar, 0, sizeof(unsigned int) * 2, b->stream));
+  const int chunk = 1 << 20;
+  while (n > 0) {
+    const int s = (int)std::min<long long>(n, chunk);
+    BCU(b, b->d == 2 ? launch_chunk<D2Q5>(b, s, 0) : launch_chunk<D3Q7>(b, s, 0));
+    b->cur = (b->cur + s) & 1;
+    n -= s;
+  }
+  int err = 0;
+  BCU(b, cudaMemcpyAsync(&err, b->B.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  BCU(b, cudaStreamSynchronize(b->stream));
+  if (err) return bfail(b, MDF_ETIMEOUT, "grid barrier timed out");
+  return MDF_OK;
+}
+
+mdf_status mdf_batch_fields(mdf_batch_t b, int cavity, const mdf_fields_t *out) {
+  if (!b || !out) return MDF_EINVAL;
+  if (cavity < 0 || cavity >= b->ncav) return bfail(b, MDF_EINVAL, "cavity %d out of range", cavity);
+  if (out->rho && !b->with_rho) return bfail(b, MDF_EINVAL, "rho needs the alpha = 0 set");
+  const CavParam &C = b->cav[cavity];
+  const int d = b->d;
+  const long long nn = d == 2 ? (long long)C.N * C.N : (long long)C.N * C.N * C.N;
+  const int nsym = d == 2 ? 3 : 6;
+  double *const host[8] = {out->P, out->u, out->rho, out->G, out->div, out->S, out->sigma, out->omega};
+  const size_t count[8] = {(size_t)nn, (size_t)(d * nn), (size_t)nn, (size_t)(d * d * nn), (size_t)nn,
+                           (size_t)(nsym * nn), (size_t)(nsym * nn), (size_t)((d == 2 ? 1 : 3) * nn)};
+  DevArgs A;
+  std::memset(&A, 0, sizeof A);
+  A.s1 = C.s1d;
+  A.with_rho = b->with_rho;
+  double **slot[8] = {&A.P, &A.u, &A.rho, &A.G, &A.div, &A.S, &A.sigma, &A.omega};
+  double *stage = nullptr;
+  size_t total = 0;
+  for (int k = 0; k < 8; ++k)
+    if (host[k]) total += count[k];
+  if (out->where == MDF_HOST && total) BCU(b, cudaMallocAsync(&stage, total * sizeof(double), b->stream));
+  double *p = stage;
+  for (int k = 0; k < 8; ++k)
+    if (host[k]) {
+      *slot[k] = out->where == MDF_HOST ? p : host[k];
+      p += count[k];
+    }
+  const unsigned blocks = (unsigned)((nn + kTile - 1) / kTile);
+  if (d == 2) k_batch_fields<D2Q5><<<blocks, kTile, 0, b->stream>>>(b->B, b->cur, cavity, A);
+  else k_batch_fields<D3Q7><<<blocks, kTile, 0, b->stream>>>(b->B, b->cur, cavity, A);
+  BCU(b, cudaGetLastError());
+  if (out->where == MDF_HOST) {
+    for (int k = 0; k < 8; ++k)
+      if (host[k])
+        BCU(b, cudaMemcpyAsync(host[k], *slot[k], count[k] * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
+    if (stage) BCU(b, cudaFreeAsync(stage, b->stream));
+    BCU(b, cudaStreamSynchronize(b->stream));
+  }
+  return MDF_OK;
+}
+
+mdf_status mdf_batch_info(mdf_batch_t b, long long *nodes, int *tiles, int *grid) {
+  if (!b) return MDF_EINVAL;
+  long long nn = 0;
+  for (const CavParam &C : b->cav)
+    nn += b->d == 2 ? (long long)C.N * C.N : (long long)C.N * C.N * C.N;
+  if (nodes) *nodes = nn;
+  if (tiles) *tiles = b->ntiles;
+  if (grid) *grid = b->grid;
+  return MDF_OK;
+}
+
+mdf_status mdf_batch_set_timeout(mdf_batch_t b, long long cycles) {
+  if (!b) return MDF_EINVAL;
+  if (cycles < 0) return bfail(b, MDF_EINVAL, "timeout must be >= 0 cycles");
+  b->B.timeout = cycles;
+  if (b->graph) {  // the captured kernels hold the old value
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+  return MDF_OK;
+}
+
+const char *mdf_batch_last_error(mdf_batch_t b) { return b ? b->err.c_str() : g_batch_error.c_str(); }
+
+}  // extern "C"

@@ -36,26 +36,37 @@ __device__ __forceinline__ long long pull_src(const DevArgs &A, int x, int y, in
   return ((long long)sz * A.ny + sy) * A.px + sx;
 }
 
-// Pull the Q populations of set `a` (carrying alpha) arriving at node idx.
+// Pull the Q populations of one set (carrying alpha, stored from `base` with
+// direction stride `stride`) arriving at node idx.
 template <class L, class TS, bool WALLS>
-__device__ __forceinline__ void pull_set(const DevArgs &A, const TS *__restrict__ fin, int a,
-                                         int alpha, long long idx, const long long (&src)[L::Q],
-                                         uint8_t m, typename ComputeOf<TS>::T (&g)[L::Q]) {
+__device__ __forceinline__ void pull_set_p(const TS *__restrict__ base, long long stride,
+                                           int alpha, long long idx,
+                                           const long long (&src)[L::Q], uint8_t m,
+                                           const double (&lid_u)[3],
+                                           typename ComputeOf<TS>::T (&g)[L::Q]) {
   using TC = typename ComputeOf<TS>::T;
-  const TS *base = fin + (long long)a * L::Q * A.plane;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
     if (WALLS && i != 0 && ((m >> L::opp(i)) & 1)) {
       // anti-halfway bounce-back; in shifted storage the alpha = 0 wall value
       // rho0 and the rest shift cancel, leaving -g*_opp + 2 w_i u_wall(alpha)
-      TC v = -TC(Codec<TS>::load(base + (long long)L::opp(i) * A.plane + idx));
+      TC v = -TC(Codec<TS>::load(base + (long long)L::opp(i) * stride + idx));
       if (alpha >= 1 && i == L::opp(L::UP) && (m & 0x80u))
-        v += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+        v += TC(2.0 * L::w(i) * lid_u[alpha - 1]);
       g[i] = v;
     } else {
-      g[i] = Codec<TS>::load(base + (long long)i * A.plane + src[i]);
+      g[i] = Codec<TS>::load(base + (long long)i * stride + src[i]);
     }
   }
+}
+
+// Pull the Q populations of set `a` (carrying alpha) arriving at node idx.
+template <class L, class TS, bool WALLS>
+__device__ __forceinline__ void pull_set(const DevArgs &A, const TS *__restrict__ fin, int a,
+                                         int alpha, long long idx, const long long (&src)[L::Q],
+                                         uint8_t m, typename ComputeOf<TS>::T (&g)[L::Q]) {
+  pull_set_p<L, TS, WALLS>(fin + (long long)a * L::Q * A.plane, A.plane, alpha, idx, src, m,
+                           A.lid_u, g);
 }
 
 // Derived fields of Eq. 2-7, 3-15 .. 3-19 at one node from the pulled

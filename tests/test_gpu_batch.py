@@ -1,0 +1,134 @@
+"""Batched lid-driven cavities (persistent cooperative kernel) through the
+C-ABI: bitwise against the single-lattice path, against the FP64 oracle,
+convergence bookkeeping and failure reporting."""
+import numpy as np
+import pytest
+
+import synth
+from tests._harness import errors, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+U = 0.1
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_08591_gb300 import _build
+    _build.build()
+
+
+def _rates(N, Re, d=2):
+    cs2 = 1.0 / 3.0 if d == 2 else 0.25
+    nu = U * N / Re
+    s1 = 1.0 / (nu / cs2 + 0.5)
+    return s1, 8.0 * (2.0 - s1) / (8.0 - s1)
+
+
+@pytest.mark.parametrize("d,sides,Res", [(2, [17, 24, 40], [100.0, 400.0, 1000.0]),
+                                         (3, [10, 13], [50.0, 200.0])])
+def test_batch_is_bitwise_the_single_lattice(d, sides, Res):
+    from paper_2108_08591_gb300 import CavityBatch, Lattice
+    names = ("P", "u", "G", "omega")
+    b = CavityBatch(sides, Res, lid_speed=U, d=d)
+    b.step(150)
+    for c, (N, Re) in enumerate(zip(sides, Res)):
+        s1, s2 = _rates(N, Re, d)
+        wall = (1, 1, 1)[:d]
+        lat = Lattice((N,) * d, s1=s1, s2=s2, wall=wall, lid=True, lid_u=(U, 0, 0))
+        lat.init(*synth.rest_state(N ** d, d))
+        lat.step(150)
+        want = lat.fields_host(names)
+        got = b.fields_host(c, names)
+        lat.close()
+        for k in names:
+            assert np.array_equal(want[k], got[k]), (c, k, np.abs(want[k] - got[k]).max())
+    b.close()
+
+
+def test_batch_matches_oracle():
+    from paper_2108_08591_gb300 import CavityBatch
+    sides, Res, steps = [19, 26], [150.0, 600.0], 300
+    b = CavityBatch(sides, Res, lid_speed=U)
+    b.step(steps)
+    for c, (N, Re) in enumerate(zip(sides, Res)):
+        s1, s2 = _rates(N, Re)
+        ref = run_oracle((N, N), *synth.rest_state(N * N, 2), steps, s1, s2=s2, wall=(1, 1, 0),
+                         lid=True, lid_u=(U, 0, 0))
+        got = b.fields_host(c, ("P", "u", "G", "S", "sigma", "omega"))
+        e = errors(ref, got)
+        assert e["u"] < 1e-5 and e["P"] < 1e-5, (c, e)
+        assert e["G"] < 1e-4 and e["omega"] < 1e-4, (c, e)
+    b.close()
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_run_to_steady_state(graph):
+    """Low-Re cavities converge; the residual and the step count follow the
+    definition; the final state equals a plain run of the same length."""
+    import torch
+    from paper_2108_08591_gb300 import CavityBatch, Lattice
+    sides, Res = [12, 16, 21], [5.0, 10.0, 20.0]
+    stream = torch.cuda.Stream() if graph else None
+    b = CavityBatch(sides, Res, lid_speed=U, stream=stream)
+    steps, status, res = b.run(tol=1e-7, max_steps=200000, check_every=50)
+    assert (status == 0).all(), (steps, status, res)
+    assert (steps % 50 == 0).all() and (steps > 0).all()
+    assert (res < 1e-7).all()
+    for c, (N, Re) in enumerate(zip(sides, Res)):
+        s1, s2 = _rates(N, Re)
+        lat = Lattice((N, N), s1=s1, s2=s2, wall=(1, 1), lid=True, lid_u=(U, 0, 0))
+        lat.init(*synth.rest_state(N * N, 2))
+        # the steady residual: u after and before the last step
+        lat.step(int(steps[c]) - 1)
+        u0 = lat.fields_host(("u",))["u"]
+        lat.step(1)
+        u1 = lat.fields_host(("u",))["u"]
+        assert res[c] == pytest.approx(np.linalg.norm(u1 - u0) / np.linalg.norm(u1), rel=1e-4)
+        if c != 0:  # cavity 0 converged first and stopped while the others ran on
+            pass
+        got = b.fields_host(c, ("u",))["u"]
+        assert np.array_equal(got, u1), c
+        lat.close()
+    b.close()
+
+
+def test_batch_reports_divergence_and_step_cap():
+    from paper_2108_08591_gb300 import CavityBatch
+    sides, Res = [14, 14], [50.0, 300.0]
+    b = CavityBatch(sides, Res, lid_speed=U)
+    P, u = synth.rest_state(14 * 14, 2)
+    P[37] = np.nan
+    b.init(0, P, u)
+    steps, status, res = b.run(tol=1e-12, max_steps=400, check_every=100)
+    assert status[0] == 4  # MDF_EDIVERGED
+    assert status[1] == 6 and steps[1] == 400  # MDF_ENOTCONVERGED at the cap
+    b.close()
+
+
+def test_batch_rejects_bad_arguments():
+    from paper_2108_08591_gb300 import CavityBatch, MdfError
+    with pytest.raises(MdfError, match="EINVAL"):
+        CavityBatch([1, 10], [100.0, 100.0])
+    b = CavityBatch([10], [100.0])
+    with pytest.raises(MdfError, match="EINVAL"):
+        b.run(check_every=33)
+    b.close()
+
+
+def test_barrier_timeout_is_reported_not_hung():
+    """A zero spin limit makes the first waiting block give up at once: every
+    block returns, the host reads MDF_ETIMEOUT, and the GPU stays usable."""
+    from paper_2108_08591_gb300 import CavityBatch, MdfError
+    b = CavityBatch([40, 33, 50], [100.0, 200.0, 300.0])
+    b.set_timeout(0)
+    with pytest.raises(MdfError, match="ETIMEOUT"):
+        b.step(20)
+    b.set_timeout(4_000_000_000)
+    b.init()
+    b.step(20)  # usable again
+    assert np.isfinite(b.fields_host(0, ("u",))["u"]).all()
+    b.close()
