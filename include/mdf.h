@@ -279,9 +279,9 @@ void mdf_batch_destroy(mdf_batch_t b);
 mdf_status mdf_batch_init(mdf_batch_t b, int cavity, const double *P, const double *u, int where);
 
 /* mdf_batch_run -- advance every cavity until its residual
- * r = ||u^n - u^{n-1}||_2 / ||u^n||_2 (FP64, checked every `check_every`
- * steps, which must be even) drops below tol, it diverges, or it has taken
- * max_steps steps.  Per cavity (host arrays of n, each nullable): steps
+ * r = ||u^n - u^{n-R}||_2 / (R ||u^n||_2), the mean per-step relative change
+ * of u over the check period R = check_every (even), computed in FP64, drops
+ * below tol, it diverges, or it has taken max_steps steps.  Per cavity (host arrays of n, each nullable): steps
  * taken, status (MDF_OK converged, MDF_EDIVERGED, MDF_ENOTCONVERGED) and
  * the last residual.  Returns MDF_OK when every cavity converged, else the
  * first non-OK status.  Synchronises; a period is one captured CUDA graph

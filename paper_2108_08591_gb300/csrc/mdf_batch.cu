@@ -8,10 +8,12 @@
 // tile belongs to exactly one cavity; populations are structure of arrays
 // f[set][i][pool node], rest-shifted FP32.  Per step the persistent kernel
 // walks the list of tiles of the cavities still running, with a bounded grid
-// barrier between steps.  Every `check` steps a residual pass (FP64,
-// Sec. C10 reading: r = |u^n - u^{n-1}|_2 / |u^n|_2 per cavity), a status pass
-// and a compaction pass retire converged or diverged cavities; the four
-// kernels form one captured graph replayed until no cavity runs.
+// barrier between steps.  Every R = `check` steps a residual pass (FP64:
+// r = |u^n - u^{n-R}|_2 / (R |u^n|_2) per cavity, the mean per-step relative
+// change over the period, which FP32 rounding noise does not floor near
+// 1e-7 as the single-step difference does), a status pass and a compaction
+// pass retire converged or diverged cavities; the four kernels form one
+// captured graph replayed until no cavity runs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,7 +52,7 @@ struct BatchArgs {
   int *n_live;
   int ncav, ntiles, with_rho;
   double lid_u[3];
-  float *usave;             // [d][tot] velocity saved by the last update of a period
+  float *usave;             // [d][tot] velocity saved by the first update of a period
   double *part;             // [ntiles][2] residual partial sums
   int *badtile;             // [ntiles] non-finite flags
   int *status;              // [ncav]
@@ -149,10 +151,10 @@ __device__ __forceinline__ void batch_pull(const BatchArgs &B, const float *fin,
 }
 
 // `steps` updates of every running cavity; buffer `cur` holds the current
-// state.  With save_last, the last update stores the velocity it pulled
-// (u^{n-1}) for the residual pass.
+// state.  With save_first, the first update stores the velocity it pulled
+// (u at the start of the period) for the residual pass.
 template <class L>
-__global__ void __launch_bounds__(kTile) k_batch_chunk(BatchArgs B, int cur, int steps, int save_last) {
+__global__ void __launch_bounds__(kTile) k_batch_chunk(BatchArgs B, int cur, int steps, int save_first) {
   constexpr int D = L::D, Q = L::Q;
   const int nl = *B.n_live;
   for (int s = 0; s < steps; ++s) {
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(kTile) k_batch_chunk(BatchArgs B, int cur, int
       long long idx;
       batch_pull<L>(B, fin, C, k, g, h, idx);
       collide_node<L, float>(g, h, B.with_rho != 0, F, C.s1, C.s2, M);
-      if (save_last && s == steps - 1)
+      if (save_first && s == 0)
 #pragma unroll
         for (int a = 0; a < D; ++a) B.usave[a * B.tot + idx] = M[a];
       const long long setstride = (long long)Q * B.tot;
@@ -241,7 +243,7 @@ __global__ void k_batch_status(BatchArgs B, int period, double tol, long long ma
     den += B.part[(long long)(C.tile0 + t) * 2 + 1];
     bad |= B.badtile[C.tile0 + t];
   }
-  const double r = den > 0.0 ? sqrt(num / den) : (num > 0.0 ? INFINITY : 0.0);
+  const double r = den > 0.0 ? sqrt(num / den) / period : (num > 0.0 ? INFINITY : 0.0);
   B.res[c] = r;
   B.steps[c] += period;
   if (bad || !isfinite(r)) B.status[c] = CAV_DIVERGED;
@@ -362,7 +364,7 @@ mdf_status bfail(mdf_batch_t b, mdf_status st, const char *fmt, ...) {
   } while (0)
 
 template <class L>
-cudaError_t launch_chunk(mdf_batch_t b, int steps, int save_last) {
+cudaError_t launch_chunk(mdf_batch_t b, int steps, int save_first) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->grid);
   cfg.blockDim = dim3(kTile);
@@ -372,7 +374,7 @@ cudaError_t launch_chunk(mdf_batch_t b, int steps, int save_last) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_batch_chunk<L>, b->B, b->cur, steps, save_last);
+  return cudaLaunchKernelEx(&cfg, k_batch_chunk<L>, b->B, b->cur, steps, save_first);
 }
 
 template <class L>
