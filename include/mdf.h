@@ -308,6 +308,59 @@ mdf_status mdf_batch_set_timeout(mdf_batch_t b, long long cycles);
 /* mdf_batch_last_error -- message of the last failure (NULL: last create). */
 const char *mdf_batch_last_error(mdf_batch_t b);
 
+/* ------------------------------------------------------------------------
+ * Learned warm start: a U-Net mapping cavity parameters to an approximate
+ * steady (P - P0, u, v) field that seeds mdf_batch_init.  Not part of the
+ * paper's method: a data-driven initial state for it.  Trained on the GPU by
+ * the library's own BF16 tensor-core convolution kernels (FP32
+ * accumulation, FP32 master weights, Adam).
+ *   level l = 0 .. levels-1 (channels[l]): two 3x3 convolutions with ReLU,
+ *     2x2 average pooling between levels; decoder: nearest 2x upsampling,
+ *     concatenation with the encoder output of the level, two convolutions
+ *     with ReLU; head: one linear 3x3 convolution to `cout` channels.
+ * Tensors are NHWC FP32 on the device: x[B][H][W][cin] (unused input
+ * channels zero), y[B][H][W][cout]; targets t[B][H][W][cout_used].
+ * ------------------------------------------------------------------------ */
+typedef struct mdf_ws_s *mdf_ws_t;
+
+/* H, W divisible by 2^(levels-1); cin, cout, channels[] multiples of 16;
+ * weights He-uniform from SplitMix64(seed), biases 0; buffers for up to
+ * max_batch samples; work on `stream` (cudaStream_t, may be NULL). */
+mdf_status mdf_ws_create(mdf_ws_t *w, int H, int W, int levels, const int *channels, int cin,
+                         int cout, int cout_used, int max_batch, unsigned long long seed,
+                         void *stream);
+void mdf_ws_destroy(mdf_ws_t w);
+long long mdf_ws_param_count(mdf_ws_t w);
+/* Parameters (FP32) per convolution in forward order e0a, e0b, ..,
+ * e{L-1}b, d{L-2}a, d{L-2}b, .., d0a, d0b, head: weights [Cout][3][3][Cin]
+ * then biases.  get: parameters and the last gradients to host (nullable). */
+mdf_status mdf_ws_get_params(mdf_ws_t w, float *host, float *grad_host);
+/* set: parameters from host; resets the Adam moments. */
+mdf_status mdf_ws_set_params(mdf_ws_t w, const float *host);
+/* y = net(x) for B <= max_batch samples (device pointers). */
+mdf_status mdf_ws_forward(mdf_ws_t w, const float *x, int B, float *y);
+/* One step: forward, MSE loss against t, backward, and (lr > 0) Adam with
+ * beta = (0.9, 0.999), eps = 1e-8.  *loss (nullable, host) gets the loss;
+ * asking for it synchronises. */
+mdf_status mdf_ws_train_step(mdf_ws_t w, const float *x, const float *t, int B, float lr,
+                             double *loss);
+const char *mdf_ws_last_error(mdf_ws_t w);
+
+/* The network's convolution kernels on caller-owned device buffers (NHWC
+ * BF16 activations, [Cout][3][3][Cin] BF16 weights; Cin, Cout % 8 == 0):
+ *   fwd:   y = conv(x) + bias (ReLU if relu), to y (BF16) and/or yf (FP32);
+ *   wgrad: dw[Cout][9 Cin] (FP32) = sum over pixels of dz x im2col(x), with
+ *          `part` a scratch of mdf_nn_wgrad_scratch(...) floats;
+ *   dgrad: dx (BF16) = gradient of the input for dz, with `wt` a BF16 scratch
+ *          of Cout * 9 * Cin elements. */
+mdf_status mdf_nn_conv_fwd(const void *x, const void *w, const float *bias, void *y, float *yf,
+                           int B, int H, int W, int Cin, int Cout, int relu, void *stream);
+long long mdf_nn_wgrad_scratch(int B, int H, int W, int Cin, int Cout);
+mdf_status mdf_nn_conv_wgrad(const void *x, const void *dz, float *dw, float *part, int B, int H,
+                             int W, int Cin, int Cout, void *stream);
+mdf_status mdf_nn_conv_dgrad(const void *dz, const void *w, void *wt, void *dx, int B, int H, int W,
+                             int Cin, int Cout, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

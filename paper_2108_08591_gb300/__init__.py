@@ -306,3 +306,100 @@ class CavityBatch:
         self._check(self._lib.mdf_batch_info(self._h, nodes.ctypes.data, tiles.ctypes.data,
                                              grid.ctypes.data))
         return int(nodes[0]), int(tiles[0]), int(grid[0])
+
+
+class WarmStartNet:
+    """The warm-start U-Net (mdf_ws_* in include/mdf.h): forward, training
+    step and parameters; tensors are CUDA float32 NHWC."""
+
+    def __init__(self, H: int, W: int, channels: Sequence[int] = (32, 64, 128, 256), cin: int = 16,
+                 cout: int = 16, cout_used: int = 3, max_batch: int = 8, seed: int = 2108,
+                 stream=None):
+        import torch
+
+        self._lib = _lib.load()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        ch = np.ascontiguousarray(channels, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _lib.check_ws(self._lib.mdf_ws_create(ctypes.byref(h), H, W, len(ch), ch.ctypes.data, cin, cout,
+                                              cout_used, max_batch, seed, ctypes.c_void_p(sptr)))
+        self._h = h
+        self.H, self.W, self.channels = H, W, tuple(int(c) for c in channels)
+        self.cin, self.cout, self.cout_used, self.max_batch = cin, cout, cout_used, max_batch
+
+    def _check(self, status: int):
+        _lib.check_ws(status, self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mdf_ws_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nparam(self) -> int:
+        return int(self._lib.mdf_ws_param_count(self._h))
+
+    def get_params(self, grads: bool = False):
+        p = np.empty(self.nparam, dtype=np.float32)
+        g = np.empty(self.nparam, dtype=np.float32) if grads else None
+        self._check(self._lib.mdf_ws_get_params(self._h, p.ctypes.data,
+                                                None if g is None else g.ctypes.data))
+        return (p, g) if grads else p
+
+    def set_params(self, p: np.ndarray):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        self._check(self._lib.mdf_ws_set_params(self._h, p.ctypes.data))
+
+    def forward(self, x):
+        import torch
+        y = torch.empty((x.shape[0], self.H, self.W, self.cout), dtype=torch.float32, device=x.device)
+        self._check(self._lib.mdf_ws_forward(self._h, x.data_ptr(), x.shape[0], y.data_ptr()))
+        return y
+
+    def train_step(self, x, t, lr: float, want_loss: bool = True):
+        loss = np.zeros(1)
+        self._check(self._lib.mdf_ws_train_step(self._h, x.data_ptr(), t.data_ptr(), x.shape[0],
+                                                float(lr), loss.ctypes.data if want_loss else None))
+        return float(loss[0]) if want_loss else None
+
+
+def conv3x3_bf16(x, w, bias=None, relu=False, out_fp32=True):
+    """The library's tensor-core convolution on CUDA tensors (bf16 x, w)."""
+    import torch
+    lib = _lib.load()
+    B, H, W, Cin = x.shape
+    Cout = w.shape[0]
+    y = torch.empty((B, H, W, Cout), device=x.device,
+                    dtype=torch.float32 if out_fp32 else torch.bfloat16)
+    s = torch.cuda.current_stream().cuda_stream
+    _lib.check(lib.mdf_nn_conv_fwd(x.data_ptr(), w.data_ptr(), None if bias is None else bias.data_ptr(),
+                                   None if out_fp32 else y.data_ptr(), y.data_ptr() if out_fp32 else None,
+                                   B, H, W, Cin, Cout, int(relu), ctypes.c_void_p(s)))
+    return y
+
+
+def conv3x3_bf16_backward(x, w, dz):
+    """(dx bf16, dw fp32) of the library's convolution kernels."""
+    import torch
+    lib = _lib.load()
+    B, H, W, Cin = x.shape
+    Cout = w.shape[0]
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    part = torch.empty(int(lib.mdf_nn_wgrad_scratch(B, H, W, Cin, Cout)), dtype=torch.float32, device=x.device)
+    dw = torch.empty((Cout, 3, 3, Cin), dtype=torch.float32, device=x.device)
+    _lib.check(lib.mdf_nn_conv_wgrad(x.data_ptr(), dz.data_ptr(), dw.data_ptr(), part.data_ptr(), B, H, W,
+                                     Cin, Cout, s))
+    wt = torch.empty(Cout * 9 * Cin, dtype=torch.bfloat16, device=x.device)
+    dx = torch.empty((B, H, W, Cin), dtype=torch.bfloat16, device=x.device)
+    _lib.check(lib.mdf_nn_conv_dgrad(dz.data_ptr(), w.data_ptr(), wt.data_ptr(), dx.data_ptr(), B, H, W,
+                                     Cin, Cout, s))
+    return dx, dw

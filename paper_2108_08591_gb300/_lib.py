@@ -87,6 +87,23 @@ SIGNATURES = {
     "mdf_batch_info": (ctypes.c_int, [H, DP, DP, DP]),
     "mdf_batch_set_timeout": (ctypes.c_int, [H, ctypes.c_longlong]),
     "mdf_batch_last_error": (ctypes.c_char_p, [H]),
+    "mdf_ws_create": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int, ctypes.c_int, ctypes.c_int, DP,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_ulonglong, ctypes.c_void_p]),
+    "mdf_ws_destroy": (None, [H]),
+    "mdf_ws_param_count": (ctypes.c_longlong, [H]),
+    "mdf_ws_get_params": (ctypes.c_int, [H, DP, DP]),
+    "mdf_ws_set_params": (ctypes.c_int, [H, DP]),
+    "mdf_ws_forward": (ctypes.c_int, [H, DP, ctypes.c_int, DP]),
+    "mdf_ws_train_step": (ctypes.c_int, [H, DP, DP, ctypes.c_int, ctypes.c_float, DP]),
+    "mdf_ws_last_error": (ctypes.c_char_p, [H]),
+    "mdf_nn_conv_fwd": (ctypes.c_int, [DP, DP, DP, DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "mdf_nn_wgrad_scratch": (ctypes.c_longlong, [ctypes.c_int] * 5),
+    "mdf_nn_conv_wgrad": (ctypes.c_int, [DP, DP, DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    "mdf_nn_conv_dgrad": (ctypes.c_int, [DP, DP, DP, DP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
 }
 
 _lib = None
@@ -120,6 +137,12 @@ class MdfError(RuntimeError):
 def check(status: int, handle=None):
     if status != OK:
         msg = load().mdf_last_error(handle)
+        raise MdfError(status, msg.decode() if msg else "")
+
+
+def check_ws(status: int, handle=None):
+    if status != OK:
+        msg = load().mdf_ws_last_error(handle)
         raise MdfError(status, msg.decode() if msg else "")
 
 

@@ -1,0 +1,484 @@
+// Warm-start network runtime: a U-Net that maps cavity parameters to an
+// approximate steady (P - P0, u, v), trained on the GPU with the tensor-core
+// convolution kernels of mdf_nn.cuh.  Host code here only sequences kernels
+// and owns buffers.
+//
+// Architecture (L levels, channels C_0 .. C_{L-1}, 3x3 convolutions):
+//   encoder l:  in -> conv(C_l)+ReLU -> conv(C_l)+ReLU = s_l -> (l < L-1) 2x2 avg pool
+//   decoder l = L-2 .. 0:  [upsample2(level l+1 output), s_l] -> conv(C_l)+ReLU
+//                          -> conv(C_l)+ReLU
+//   head: conv(Cout) on the level-0 decoder output; loss = MSE over the
+//   first `cout_used` output channels.
+// The encoder's second convolution of level l < L-1 writes s_l straight into
+// the channel slice [C_{l+1}, C_{l+1} + C_l) of the decoder's concatenation
+// buffer, so no copy is made.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mdf.h"
+#include "mdf_nn.cuh"
+
+using namespace mdfnn;
+
+namespace {
+
+thread_local std::string g_ws_error = "no error";
+
+struct Layer {
+  int cin, cout, relu, level;
+  long long woff, boff;  // offsets of weights / bias in the parameter vector
+};
+
+inline unsigned grid1(long long n, int b = 256) { return (unsigned)((n + b - 1) / b); }
+
+// SplitMix64 (Steele, Lea & Flood 2014) for the weight initialisation.
+inline uint64_t splitmix(uint64_t &s) {
+  s += 0x9E3779B97F4A7C15ull;
+  uint64_t z = s;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct mdf_ws_s {
+  int H = 0, W = 0, L = 0, cin = 0, cout = 0, cout_used = 0, maxb = 0;
+  std::vector<int> C;
+  std::vector<Layer> layers;  // e0a e0b e1a e1b ... d{L-2}a d{L-2}b ... d0a d0b head
+  long long nparam = 0;
+  cudaStream_t stream = nullptr;
+  float *p32 = nullptr, *g32 = nullptr, *m = nullptr, *v = nullptr;
+  bf16 *pbf = nullptr;  // BF16 copy (biases unused)
+  long long adam_step = 0;
+  // activations
+  bf16 *xin = nullptr;
+  std::vector<bf16 *> a, pool, cat, sdeep, da, db;  // per level
+  float *yf = nullptr;
+  // gradients / scratch
+  bf16 *dyh = nullptr, *wt = nullptr, *gA = nullptr, *gB = nullptr, *gC = nullptr;
+  std::vector<bf16 *> dcat;
+  float *part = nullptr;
+  double *lpart = nullptr;
+  long long part_n = 0, wt_n = 0, gbuf_n = 0;
+  std::string err = "no error";
+
+  int Hl(int l) const { return H >> l; }
+  int Wl(int l) const { return W >> l; }
+  long long Ml(int l, int B) const { return (long long)B * Hl(l) * Wl(l); }
+  const Layer &enc(int l, int k) const { return layers[2 * l + k]; }
+  const Layer &dec(int l, int k) const { return layers[2 * L + 2 * (L - 2 - l) + k]; }
+  const Layer &head() const { return layers.back(); }
+};
+
+namespace {
+
+mdf_status wfail(mdf_ws_t w, mdf_status st, const char *fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  if (w) w->err = msg;
+  else g_ws_error = msg;
+  return st;
+}
+
+#define WCU(w, call)                                                                    \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return wfail((w), MDF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+  } while (0)
+
+cudaError_t conv_fwd(cudaStream_t s, const bf16 *x, const bf16 *w, const float *bias, bf16 *y,
+                     float *yf, int B, int H, int W, int Cin, int Cout, int ldy, int yoff,
+                     int relu) {
+  ConvArgs a{x, w, bias, y, yf, B, H, W, Cin, Cout, ldy, yoff, relu};
+  const long long M = (long long)B * H * W;
+  dim3 grid((unsigned)((M + CBM - 1) / CBM), (unsigned)((Cout + CBN - 1) / CBN));
+  k_conv_fwd<<<grid, 128, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+int pix_per_split(long long M) { return M >= 8192 ? 2048 : 256; }
+
+cudaError_t conv_wgrad(cudaStream_t s, const bf16 *x, const bf16 *dz, float *part, float *dw,
+                       int B, int H, int W, int Cin, int Cout) {
+  const long long M = (long long)B * H * W;
+  const int pps = pix_per_split(M);
+  const int splits = (int)((M + pps - 1) / pps);
+  const int K = 9 * Cin;
+  WgradArgs a{x, dz, part, B, H, W, Cin, Cout, pps};
+  dim3 grid((unsigned)((K + 63) / 64), (unsigned)((Cout + 63) / 64), (unsigned)splits);
+  k_conv_wgrad<<<grid, 128, 0, s>>>(a);
+  const long long n = (long long)Cout * K;
+  k_sum_splits<<<grid1(n), 256, 0, s>>>(part, splits, n, dw, 0);
+  return cudaGetLastError();
+}
+
+long long wgrad_part_size(long long M, int Cin, int Cout) {
+  const int pps = pix_per_split(M);
+  return ((M + pps - 1) / pps) * (long long)Cout * 9 * Cin;
+}
+
+cudaError_t conv_dgrad(cudaStream_t s, const bf16 *dz, const bf16 *w, bf16 *wt, bf16 *dx, int B,
+                       int H, int W, int Cin, int Cout) {
+  const long long n = (long long)Cout * 9 * Cin;
+  k_flip_weights<<<grid1(n), 256, 0, s>>>(w, Cout, Cin, wt);
+  return conv_fwd(s, dz, wt, nullptr, dx, nullptr, B, H, W, Cout, Cin, Cin, 0, 0);
+}
+
+}  // namespace
+
+extern "C" {
+
+mdf_status mdf_ws_create(mdf_ws_t *out, int H, int W, int levels, const int *channels, int cin,
+                         int cout, int cout_used, int max_batch, unsigned long long seed,
+                         void *stream) {
+  if (!out) return wfail(nullptr, MDF_EINVAL, "null handle pointer");
+  *out = nullptr;
+  if (levels < 2 || levels > 8 || !channels) return wfail(nullptr, MDF_EINVAL, "need 2..8 levels");
+  if (H % (1 << (levels - 1)) || W % (1 << (levels - 1)) || H < 8 || W < 8)
+    return wfail(nullptr, MDF_EINVAL, "H and W must be divisible by 2^(levels-1)");
+  if (cin % 16 || cout % 16 || cout_used < 1 || cout_used > cout)
+    return wfail(nullptr, MDF_EINVAL, "cin, cout must be multiples of 16, 1 <= cout_used <= cout");
+  for (int l = 0; l < levels; ++l)
+    if (channels[l] % 16 || channels[l] <= 0) return wfail(nullptr, MDF_EINVAL, "channels must be multiples of 16");
+  if (max_batch < 1) return wfail(nullptr, MDF_EINVAL, "max_batch >= 1");
+  mdf_ws_t w = new (std::nothrow) mdf_ws_s;
+  if (!w) return wfail(nullptr, MDF_ENOMEM, "host allocation");
+  w->H = H; w->W = W; w->L = levels; w->cin = cin; w->cout = cout; w->cout_used = cout_used;
+  w->maxb = max_batch;
+  w->C.assign(channels, channels + levels);
+  w->stream = static_cast<cudaStream_t>(stream);
+  const int L = levels;
+  long long off = 0;
+  auto add = [&](int ci, int co, int relu, int level) {
+    Layer ly{ci, co, relu, level, off, off + (long long)co * 9 * ci};
+    off = ly.boff + co;
+    w->layers.push_back(ly);
+  };
+  int c = cin;
+  for (int l = 0; l < L; ++l) {
+    add(c, w->C[l], 1, l);
+    add(w->C[l], w->C[l], 1, l);
+    c = w->C[l];
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    add(w->C[l + 1] + w->C[l], w->C[l], 1, l);
+    add(w->C[l], w->C[l], 1, l);
+  }
+  add(w->C[0], cout, 0, 0);
+  w->nparam = off;
+
+  // He-uniform weights (bound sqrt(6 / fan_in)), zero biases
+  std::vector<float> p(w->nparam, 0.f);
+  uint64_t st = seed;
+  for (const Layer &ly : w->layers) {
+    const double bound = std::sqrt(6.0 / (9.0 * ly.cin));
+    for (long long i = 0; i < (long long)ly.cout * 9 * ly.cin; ++i) {
+      const double u = (splitmix(st) >> 11) * (1.0 / 9007199254740992.0);
+      p[ly.woff + i] = (float)((2.0 * u - 1.0) * bound);
+    }
+  }
+  const int B = max_batch;
+  long long part_n = 0, wt_n = 0, gbuf = 0;
+  for (const Layer &ly : w->layers) {
+    part_n = std::max(part_n, wgrad_part_size(w->Ml(ly.level, B), ly.cin, ly.cout));
+    wt_n = std::max(wt_n, (long long)ly.cout * 9 * ly.cin);
+    gbuf = std::max(gbuf, w->Ml(ly.level, B) * std::max(ly.cin, ly.cout));
+  }
+  w->part_n = part_n;
+  w->wt_n = wt_n;
+  w->gbuf_n = gbuf;
+  cudaError_t e = cudaSuccess;
+  auto alloc = [&](void **ptr, size_t bytes) {
+    if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(*ptr, 0, bytes, w->stream);
+  };
+  const size_t np = (size_t)w->nparam;
+  alloc((void **)&w->p32, np * 4);
+  alloc((void **)&w->g32, np * 4);
+  alloc((void **)&w->m, np * 4);
+  alloc((void **)&w->v, np * 4);
+  alloc((void **)&w->pbf, np * 2);
+  alloc((void **)&w->xin, (size_t)w->Ml(0, B) * cin * 2);
+  w->a.assign(L, nullptr); w->pool.assign(L, nullptr); w->cat.assign(L, nullptr);
+  w->sdeep.assign(L, nullptr); w->da.assign(L, nullptr); w->db.assign(L, nullptr);
+  w->dcat.assign(L, nullptr);
+  for (int l = 0; l < L; ++l) {
+    const size_t Mp = (size_t)w->Ml(l, B);
+    alloc((void **)&w->a[l], Mp * w->C[l] * 2);
+    if (l > 0) alloc((void **)&w->pool[l], Mp * w->C[l - 1] * 2);
+    if (l < L - 1) {
+      alloc((void **)&w->cat[l], Mp * (w->C[l + 1] + w->C[l]) * 2);
+      alloc((void **)&w->dcat[l], Mp * (w->C[l + 1] + w->C[l]) * 2);
+      alloc((void **)&w->da[l], Mp * w->C[l] * 2);
+      alloc((void **)&w->db[l], Mp * w->C[l] * 2);
+    } else {
+      alloc((void **)&w->sdeep[l], Mp * w->C[l] * 2);
+    }
+  }
+  alloc((void **)&w->yf, (size_t)w->Ml(0, B) * cout * 4);
+  alloc((void **)&w->dyh, (size_t)w->Ml(0, B) * cout * 2);
+  alloc((void **)&w->wt, (size_t)wt_n * 2);
+  alloc((void **)&w->gA, (size_t)gbuf * 2);
+  alloc((void **)&w->gB, (size_t)gbuf * 2);
+  alloc((void **)&w->gC, (size_t)gbuf * 2);
+  alloc((void **)&w->part, (size_t)part_n * 4);
+  alloc((void **)&w->lpart, (size_t)grid1(w->Ml(0, B) * cout) * 8);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w->p32, p.data(), np * 4, cudaMemcpyHostToDevice, w->stream);
+  if (e == cudaSuccess) {
+    k_f32_to_bf16<<<grid1(w->nparam), 256, 0, w->stream>>>(w->p32, w->pbf, w->nparam);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(w->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    const mdf_status s = e == cudaErrorMemoryAllocation ? MDF_ENOMEM : MDF_ECUDA;
+    wfail(nullptr, s, "ws create: %s", cudaGetErrorString(e));
+    mdf_ws_destroy(w);
+    return s;
+  }
+  *out = w;
+  return MDF_OK;
+}
+
+void mdf_ws_destroy(mdf_ws_t w) {
+  if (!w) return;
+  cudaStreamSynchronize(w->stream);
+  for (void *p : {(void *)w->p32, (void *)w->g32, (void *)w->m, (void *)w->v, (void *)w->pbf,
+                  (void *)w->xin, (void *)w->yf, (void *)w->dyh, (void *)w->wt, (void *)w->gA,
+                  (void *)w->gB, (void *)w->gC, (void *)w->part, (void *)w->lpart})
+    cudaFree(p);
+  for (auto *vec : {&w->a, &w->pool, &w->cat, &w->sdeep, &w->da, &w->db, &w->dcat})
+    for (bf16 *p : *vec) cudaFree(p);
+  delete w;
+}
+
+long long mdf_ws_param_count(mdf_ws_t w) { return w ? w->nparam : 0; }
+
+// Parameter vector layout: per layer in forward order (e0a, e0b, ..., e{L-1}b,
+// d{L-2}a, d{L-2}b, ..., d0a, d0b, head), weights [Cout][3][3][Cin] then bias.
+mdf_status mdf_ws_get_params(mdf_ws_t w, float *host, float *grad_host) {
+  if (!w) return MDF_EINVAL;
+  if (host) WCU(w, cudaMemcpyAsync(host, w->p32, w->nparam * 4, cudaMemcpyDeviceToHost, w->stream));
+  if (grad_host) WCU(w, cudaMemcpyAsync(grad_host, w->g32, w->nparam * 4, cudaMemcpyDeviceToHost, w->stream));
+  WCU(w, cudaStreamSynchronize(w->stream));
+  return MDF_OK;
+}
+
+mdf_status mdf_ws_set_params(mdf_ws_t w, const float *host) {
+  if (!w || !host) return MDF_EINVAL;
+  WCU(w, cudaMemcpyAsync(w->p32, host, w->nparam * 4, cudaMemcpyHostToDevice, w->stream));
+  k_f32_to_bf16<<<grid1(w->nparam), 256, 0, w->stream>>>(w->p32, w->pbf, w->nparam);
+  WCU(w, cudaGetLastError());
+  WCU(w, cudaMemsetAsync(w->m, 0, w->nparam * 4, w->stream));
+  WCU(w, cudaMemsetAsync(w->v, 0, w->nparam * 4, w->stream));
+  w->adam_step = 0;
+  WCU(w, cudaStreamSynchronize(w->stream));
+  return MDF_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Forward pass of B samples already in w->xin; output in w->yf (FP32).
+mdf_status forward(mdf_ws_t w, int B) {
+  const int L = w->L;
+  cudaStream_t s = w->stream;
+  const bf16 *in = w->xin;
+  int cin = w->cin;
+  for (int l = 0; l < L; ++l) {
+    const Layer &la = w->enc(l, 0), &lb = w->enc(l, 1);
+    const int H = w->Hl(l), W = w->Wl(l);
+    if (l > 0) {  // pool s_{l-1} (a slice of cat_{l-1})
+      const int ld = w->C[l] + w->C[l - 1];
+      k_avgpool2<<<grid1(w->Ml(l, B) * w->C[l - 1]), 256, 0, s>>>(w->cat[l - 1], ld, w->C[l], B,
+                                                                   2 * H, 2 * W, w->C[l - 1], w->pool[l]);
+      in = w->pool[l];
+      cin = w->C[l - 1];
+    }
+    WCU(w, conv_fwd(s, in, w->pbf + la.woff, w->p32 + la.boff, w->a[l], nullptr, B, H, W, cin,
+                    la.cout, la.cout, 0, 1));
+    if (l < L - 1)
+      WCU(w, conv_fwd(s, w->a[l], w->pbf + lb.woff, w->p32 + lb.boff, w->cat[l], nullptr, B, H, W,
+                      lb.cin, lb.cout, w->C[l + 1] + w->C[l], w->C[l + 1], 1));
+    else
+      WCU(w, conv_fwd(s, w->a[l], w->pbf + lb.woff, w->p32 + lb.boff, w->sdeep[l], nullptr, B, H, W,
+                      lb.cin, lb.cout, lb.cout, 0, 1));
+  }
+  for (int l = L - 2; l >= 0; --l) {
+    const Layer &la = w->dec(l, 0), &lb = w->dec(l, 1);
+    const int H = w->Hl(l), W = w->Wl(l);
+    const int ld = w->C[l + 1] + w->C[l];
+    const bf16 *below = (l + 1 == L - 1) ? w->sdeep[l + 1] : w->db[l + 1];
+    k_upsample2<<<grid1(w->Ml(l, B) * w->C[l + 1]), 256, 0, s>>>(below, B, H / 2, W / 2, w->C[l + 1],
+                                                                  w->cat[l], ld);
+    WCU(w, conv_fwd(s, w->cat[l], w->pbf + la.woff, w->p32 + la.boff, w->da[l], nullptr, B, H, W, ld,
+                    la.cout, la.cout, 0, 1));
+    WCU(w, conv_fwd(s, w->da[l], w->pbf + lb.woff, w->p32 + lb.boff, w->db[l], nullptr, B, H, W,
+                    lb.cin, lb.cout, lb.cout, 0, 1));
+  }
+  const Layer &hd = w->head();
+  WCU(w, conv_fwd(s, w->db[0], w->pbf + hd.woff, w->p32 + hd.boff, nullptr, w->yf, B, w->H, w->W,
+                  hd.cin, hd.cout, hd.cout, 0, 0));
+  return MDF_OK;
+}
+
+// Backward of one convolution: dz = dout (x) relu'(out) (or dout when linear),
+// weight and bias gradients, and (when dx) the input gradient.
+mdf_status conv_back(mdf_ws_t w, const Layer &ly, int B, const bf16 *x, const bf16 *out, int ldo,
+                     int ooff, const bf16 *dout, int lddo, int dooff, bf16 *dz, bf16 *dx) {
+  cudaStream_t s = w->stream;
+  const int H = w->Hl(ly.level), W = w->Wl(ly.level);
+  const long long M = w->Ml(ly.level, B);
+  const bf16 *dzp = dout;
+  if (ly.relu) {
+    k_relu_bwd<<<grid1(M * ly.cout), 256, 0, s>>>(dout, lddo, dooff, out, ldo, ooff, dz, M, ly.cout);
+    dzp = dz;
+  }
+  WCU(w, conv_wgrad(s, x, dzp, w->part, w->g32 + ly.woff, B, H, W, ly.cin, ly.cout));
+  k_bias_grad<<<ly.cout, 256, 0, s>>>(dzp, (int)M, ly.cout, w->g32 + ly.boff);
+  if (dx) WCU(w, conv_dgrad(s, dzp, w->pbf + ly.woff, w->wt, dx, B, H, W, ly.cin, ly.cout));
+  return MDF_OK;
+}
+
+mdf_status backward(mdf_ws_t w, int B) {
+  const int L = w->L;
+  cudaStream_t s = w->stream;
+  mdf_status st;
+  // head (linear): dz = dyh; d(db_0) -> gA
+  const Layer &hd = w->head();
+  if ((st = conv_back(w, hd, B, w->db[0], nullptr, 0, 0, w->dyh, hd.cout, 0, nullptr, w->gA))) return st;
+  bf16 *dout = w->gA;  // gradient of the level-l decoder output
+  for (int l = 0; l <= L - 2; ++l) {
+    const Layer &la = w->dec(l, 0), &lb = w->dec(l, 1);
+    const int ld = w->C[l + 1] + w->C[l];
+    if ((st = conv_back(w, lb, B, w->da[l], w->db[l], lb.cout, 0, dout, lb.cout, 0, w->gB, w->gC))) return st;
+    if ((st = conv_back(w, la, B, w->cat[l], w->da[l], la.cout, 0, w->gC, la.cout, 0, w->gB, w->dcat[l]))) return st;
+    // gradient of the tensor upsampled into cat_l: level l+1's output
+    const int Hn = w->Hl(l + 1), Wn = w->Wl(l + 1);
+    k_upsample2_bwd<<<grid1(w->Ml(l + 1, B) * w->C[l + 1]), 256, 0, s>>>(w->dcat[l], ld, B, Hn, Wn,
+                                                                       w->C[l + 1], w->gA);
+    dout = w->gA;
+  }
+  // encoder, deepest first; `dout` holds the gradient of s_{L-1}
+  for (int l = L - 1; l >= 0; --l) {
+    const Layer &la = w->enc(l, 0), &lb = w->enc(l, 1);
+    const int H = w->Hl(l), W = w->Wl(l);
+    const bf16 *sl;
+    int lds, soff;
+    if (l < L - 1) {
+      // gradient of s_l = pooled path (in gA, level l+1 sized) + skip slice of dcat_l
+      k_avgpool2_bwd_add<<<grid1(w->Ml(l, B) * w->C[l]), 256, 0, s>>>(
+          w->gA, w->dcat[l], w->C[l + 1] + w->C[l], w->C[l + 1], B, H, W, w->C[l], w->gB);
+      WCU(w, cudaMemcpyAsync(w->gA, w->gB, w->Ml(l, B) * w->C[l] * 2, cudaMemcpyDeviceToDevice, s));
+      sl = w->cat[l];
+      lds = w->C[l + 1] + w->C[l];
+      soff = w->C[l + 1];
+    } else {
+      sl = w->sdeep[l];
+      lds = w->C[l];
+      soff = 0;
+    }
+    if ((st = conv_back(w, lb, B, w->a[l], sl, lds, soff, w->gA, w->C[l], 0, w->gB, w->gC))) return st;
+    const bf16 *xin = l == 0 ? w->xin : w->pool[l];
+    if ((st = conv_back(w, la, B, xin, w->a[l], la.cout, 0, w->gC, la.cout, 0, w->gB,
+                        l == 0 ? nullptr : w->gA)))
+      return st;
+  }
+  return MDF_OK;
+}
+
+mdf_status load_input(mdf_ws_t w, const float *x, int B) {
+  const long long n = w->Ml(0, B) * w->cin;
+  k_f32_to_bf16<<<grid1(n), 256, 0, w->stream>>>(x, w->xin, n);
+  WCU(w, cudaGetLastError());
+  return MDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mdf_status mdf_ws_forward(mdf_ws_t w, const float *x, int B, float *y) {
+  if (!w || !x || !y) return MDF_EINVAL;
+  if (B < 1 || B > w->maxb) return wfail(w, MDF_EINVAL, "batch %d outside [1, %d]", B, w->maxb);
+  mdf_status st = load_input(w, x, B);
+  if (st == MDF_OK) st = forward(w, B);
+  if (st != MDF_OK) return st;
+  WCU(w, cudaMemcpyAsync(y, w->yf, w->Ml(0, B) * w->cout * 4, cudaMemcpyDeviceToDevice, w->stream));
+  return MDF_OK;
+}
+
+mdf_status mdf_ws_train_step(mdf_ws_t w, const float *x, const float *t, int B, float lr,
+                             double *loss) {
+  if (!w || !x || !t) return MDF_EINVAL;
+  if (B < 1 || B > w->maxb) return wfail(w, MDF_EINVAL, "batch %d outside [1, %d]", B, w->maxb);
+  mdf_status st = load_input(w, x, B);
+  if (st == MDF_OK) st = forward(w, B);
+  if (st != MDF_OK) return st;
+  const long long n = w->Ml(0, B) * w->cout;
+  const unsigned nb = grid1(n);
+  k_mse<<<nb, 256, 0, w->stream>>>(w->yf, w->cout, t, w->cout_used, w->Ml(0, B), w->dyh, w->lpart);
+  WCU(w, cudaGetLastError());
+  if ((st = backward(w, B))) return st;
+  if (lr > 0.f) {
+    ++w->adam_step;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)w->adam_step), c2 = 1.f - std::pow(b2, (float)w->adam_step);
+    k_adam<<<grid1(w->nparam), 256, 0, w->stream>>>(w->p32, w->g32, w->m, w->v, w->pbf, w->nparam, lr,
+                                                     b1, b2, 1e-8f, c1, c2);
+    WCU(w, cudaGetLastError());
+  }
+  if (loss) {
+    std::vector<double> parts(nb);
+    WCU(w, cudaMemcpyAsync(parts.data(), w->lpart, nb * 8, cudaMemcpyDeviceToHost, w->stream));
+    WCU(w, cudaStreamSynchronize(w->stream));
+    double sum = 0.0;
+    for (double p : parts) sum += p;
+    *loss = sum / (double)(w->Ml(0, B) * w->cout_used);
+  }
+  return MDF_OK;
+}
+
+// Raw kernels on caller-owned device buffers (for tests and benchmarks).
+// x, dz, w, y, dx: BF16 arrays; yf, dw: FP32; part: FP32 scratch of
+// mdf_nn_wgrad_scratch(...) floats; wt: BF16 scratch of Cout * 9 * Cin.
+mdf_status mdf_nn_conv_fwd(const void *x, const void *w, const float *bias, void *y, float *yf,
+                           int B, int H, int W, int Cin, int Cout, int relu, void *stream) {
+  if (!x || !w || (!y && !yf) || Cin % 8 || Cout % 8 || B < 1 || H < 1 || W < 1) return MDF_EINVAL;
+  return conv_fwd((cudaStream_t)stream, (const bf16 *)x, (const bf16 *)w, bias, (bf16 *)y, yf, B, H,
+                  W, Cin, Cout, Cout, 0, relu) == cudaSuccess ? MDF_OK : MDF_ECUDA;
+}
+
+long long mdf_nn_wgrad_scratch(int B, int H, int W, int Cin, int Cout) {
+  return wgrad_part_size((long long)B * H * W, Cin, Cout);
+}
+
+mdf_status mdf_nn_conv_wgrad(const void *x, const void *dz, float *dw, float *part, int B, int H,
+                             int W, int Cin, int Cout, void *stream) {
+  if (!x || !dz || !dw || !part || Cin % 8 || Cout % 8) return MDF_EINVAL;
+  return conv_wgrad((cudaStream_t)stream, (const bf16 *)x, (const bf16 *)dz, part, dw, B, H, W, Cin,
+                    Cout) == cudaSuccess ? MDF_OK : MDF_ECUDA;
+}
+
+mdf_status mdf_nn_conv_dgrad(const void *dz, const void *w, void *wt, void *dx, int B, int H, int W,
+                             int Cin, int Cout, void *stream) {
+  if (!dz || !w || !wt || !dx || Cin % 8 || Cout % 8) return MDF_EINVAL;
+  return conv_dgrad((cudaStream_t)stream, (const bf16 *)dz, (const bf16 *)w, (bf16 *)wt, (bf16 *)dx, B,
+                    H, W, Cin, Cout) == cudaSuccess ? MDF_OK : MDF_ECUDA;
+}
+
+const char *mdf_ws_last_error(mdf_ws_t w) { return w ? w->err.c_str() : g_ws_error.c_str(); }
+
+}  // extern "C"

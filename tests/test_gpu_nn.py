@@ -1,0 +1,119 @@
+"""Tensor-core convolution kernels and the warm-start U-Net against the FP64
+network oracle.  Inputs are rounded to BF16 first, so the kernels and the
+oracle see the same numbers; the kernels accumulate in FP32 (bound 1e-5
+relative for FP32 outputs, 2^-8 for BF16 outputs)."""
+import numpy as np
+import pytest
+
+from oracle import nn as onn
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2108_08591_gb300 import _build
+    _build.build()
+
+
+def _bf16(shape, seed, scale=1.0):
+    import torch
+    r = synth.SplitMix64(seed)
+    a = np.array([r.uniform() - 0.5 for _ in range(int(np.prod(shape)))], dtype=np.float32).reshape(shape)
+    t = torch.from_numpy(a * scale).to(torch.bfloat16)
+    return t.cuda(), t.float().numpy().astype(np.float64)
+
+
+def _rel(ref, got):
+    return float(np.linalg.norm((ref - got).ravel()) / np.linalg.norm(ref.ravel()))
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 10, 7, 16, 40), (1, 8, 8, 96, 32), (3, 5, 9, 8, 16),
+                                            (2, 16, 16, 32, 136)])
+def test_conv_forward(B, H, W, Cin, Cout):
+    import torch
+    from paper_2108_08591_gb300 import conv3x3_bf16
+    x, xn = _bf16((B, H, W, Cin), 1)
+    w, wn = _bf16((Cout, 3, 3, Cin), 2)
+    bias = torch.linspace(-0.2, 0.3, Cout, device="cuda", dtype=torch.float32)
+    ref = onn.conv3x3(xn, wn, bias.cpu().numpy().astype(np.float64))
+    got = conv3x3_bf16(x, w, bias).cpu().numpy()
+    assert _rel(ref, got) < 1e-5
+    got = conv3x3_bf16(x, w, bias, relu=True, out_fp32=False).float().cpu().numpy()
+    r = onn.relu(ref)
+    assert np.all(np.abs(got - r) <= 2.0 ** -8 * np.abs(r) + 1e-6)
+
+
+@pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 10, 7, 16, 40), (1, 8, 8, 96, 32), (2, 16, 16, 32, 64)])
+def test_conv_backward(B, H, W, Cin, Cout):
+    from paper_2108_08591_gb300 import conv3x3_bf16_backward
+    x, xn = _bf16((B, H, W, Cin), 3)
+    w, wn = _bf16((Cout, 3, 3, Cin), 4)
+    dz, dzn = _bf16((B, H, W, Cout), 5)
+    dx_ref, dw_ref, _ = onn.conv3x3_backward(xn, wn, dzn)
+    dx, dw = conv3x3_bf16_backward(x, w, dz)
+    assert _rel(dw_ref, dw.cpu().numpy()) < 1e-5
+    got = dx.float().cpu().numpy()
+    assert np.all(np.abs(got - dx_ref) <= 2.0 ** -8 * np.abs(dx_ref) + 1e-5)
+
+
+def _oracle_params(flat, cin, channels, cout):
+    params, off = {}, 0
+    for name, ci, co, _ in onn.unet_layers(cin, channels, cout):
+        nw = co * 9 * ci
+        w = flat[off:off + nw].reshape(co, 3, 3, ci).astype(np.float64)
+        b = flat[off + nw:off + nw + co].astype(np.float64)
+        params[name] = (w, b)
+        off += nw + co
+    assert off == flat.size
+    return params
+
+
+def test_unet_gradients_match_oracle():
+    """One training step (lr = 0) of a small U-Net: loss and every parameter
+    gradient against the FP64 chain rule of the oracle.  The GPU rounds
+    activations and gradients to BF16 between layers: bound 3e-2."""
+    import torch
+    from paper_2108_08591_gb300 import WarmStartNet
+    channels, cin, cout, B, H = (16, 32, 48), 16, 16, 2, 16
+    net = WarmStartNet(H, H, channels, cin=cin, cout=cout, cout_used=cout, max_batch=B, seed=7)
+    xb, xn = _bf16((B, H, H, cin), 11)
+    t = torch.from_numpy(np.sin(np.arange(B * H * H * cout) * 0.37).reshape(B, H, H, cout)
+                         .astype(np.float32)).cuda()
+    loss = net.train_step(xb.float().contiguous(), t, lr=0.0)
+    p, g = net.get_params(grads=True)
+    params = _oracle_params(p, cin, channels, cout)
+    lref, gref, _ = onn.unet_grads(params, xn, t.cpu().numpy().astype(np.float64), channels)
+    assert loss == pytest.approx(lref, rel=1e-2)
+    got = _oracle_params(g, cin, channels, cout)
+    for name in params:
+        assert _rel(gref[name][0], got[name][0]) < 3e-2, name
+        assert _rel(gref[name][1], got[name][1]) < 3e-2, name
+    net.close()
+
+
+def test_training_reduces_the_loss():
+    import torch
+    from paper_2108_08591_gb300 import WarmStartNet
+    H, B = 32, 4
+    net = WarmStartNet(H, H, (16, 32, 64), cin=16, cout=16, cout_used=3, max_batch=B, seed=3)
+    yy, xx = np.meshgrid(np.linspace(0, 1, H), np.linspace(0, 1, H), indexing="ij")
+    x = np.zeros((B, H, H, 16), np.float32)
+    t = np.zeros((B, H, H, 3), np.float32)
+    for b in range(B):
+        a = 0.5 + b / B
+        x[b, :, :, 0], x[b, :, :, 1], x[b, :, :, 2] = a, xx, yy
+        t[b, :, :, 0] = a * np.sin(np.pi * xx) * np.sin(np.pi * yy)
+        t[b, :, :, 1] = a * xx * yy
+        t[b, :, :, 2] = -a * yy * (1 - yy)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    first = net.train_step(xd, td, lr=2e-3)
+    for _ in range(300):
+        last = net.train_step(xd, td, lr=2e-3, want_loss=False)
+    last = net.train_step(xd, td, lr=2e-3)
+    assert last < 0.05 * first, (first, last)
+    net.close()
