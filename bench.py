@@ -417,6 +417,85 @@ def run_mdf(args):
     return 0
 
 
+def run_cavities(args):
+    """Batched lid-driven cavities (64 seeded boxes, sides from {65, 129, 257,
+    513}, Re ~ U[100, 3200], lid 0.1, D2Q5 x 3 FP32): plain-step throughput of
+    the persistent kernel, then every cavity to its residual tolerance."""
+    import collections
+    import numpy as np
+    import torch
+    import synth
+    from paper_2108_08591_gb300 import CavityBatch, _build
+    _build.build()
+    draw = synth.cavity_batch(64, seed=2108)
+    sides = [s for s, _ in draw]
+    Res = [r for _, r in draw]
+    nodes = np.array(sides, dtype=np.int64) ** 2
+    stream = torch.cuda.Stream()
+    b = CavityBatch(sides, Res, lid_speed=0.1, stream=stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b.step(args.warmup * 100)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(args.steps * 100)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / (args.steps * 100)
+    mlups = nodes.sum() / (ms / 1e3) / 1e6
+    peak, kind = _peaks()
+    b.init()
+    t0 = time.perf_counter()
+    steps, status, res = b.run(tol=1e-8, max_steps=args.max_steps, check_every=100)
+    run_s = time.perf_counter() - t0
+    names = {0: "converged", 4: "diverged", 6: "not_converged"}
+    line = {
+        "metric": METRIC, "workload": "cavities", "value": mlups, "unit": "MLUPS",
+        "ms_per_step": ms, "nodes": int(nodes.sum()), "cavities": len(sides),
+        "roofline": {"bound": "hbm", "achieved": mlups * 120 / 1e3, "peak": peak, "unit": "GB/s",
+                     "frac": mlups * 120 / 1e3 / peak, "peak_source": f"{kind} hbm_gbs",
+                     "kernel": "k_batch_chunk<D2Q5> (persistent, cooperative)"},
+        "to_steady": {"tol": 1e-8, "max_steps": args.max_steps, "seconds": run_s,
+                      "aggregate_mlups": float((steps * nodes).sum()) / run_s / 1e6,
+                      "status": {names[k]: v for k, v in collections.Counter(status.tolist()).items()}},
+        "per_cavity": [[int(sides[c]), round(Res[c], 1), int(steps[c]), int(status[c])]
+                       for c in np.argsort(sides, kind="stable")],
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
+def run_conv(args):
+    """Throughput of the network's tensor-core convolution kernels."""
+    import torch
+    from paper_2108_08591_gb300 import _build, conv3x3_bf16, conv3x3_bf16_backward
+    _build.build()
+    rows = []
+    for (B, H, Cin, Cout) in [(8, 256, 32, 32), (8, 128, 64, 64), (8, 64, 128, 128), (8, 32, 256, 256),
+                              (8, 256, 96, 32), (8, 64, 384, 128)]:
+        g = torch.Generator(device="cuda").manual_seed(1)
+        x = torch.randn(B, H, H, Cin, device="cuda", generator=g).to(torch.bfloat16)
+        w = (0.05 * torch.randn(Cout, 3, 3, Cin, device="cuda", generator=g)).to(torch.bfloat16)
+        dz = torch.randn(B, H, H, Cout, device="cuda", generator=g).to(torch.bfloat16)
+        flops = 2.0 * B * H * H * Cout * 9 * Cin
+        for name, fn, mult in (("fwd", lambda: conv3x3_bf16(x, w), 1),
+                               ("bwd", lambda: conv3x3_bf16_backward(x, w, dz), 2)):
+            for _ in range(max(3, args.warmup)):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(args.steps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            rows.append({"B": B, "H": H, "Cin": Cin, "Cout": Cout, "op": name, "ms": ms,
+                         "tflops": mult * flops / ms / 1e9})
+    print(json.dumps({"workload": "conv", "unit": "TFLOP/s", "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -426,8 +505,12 @@ def main():
     ap.add_argument("--storage", choices=("f32", "f16", "bf16", "f16eq", "bf16eq"), default="f32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
-    ap.add_argument("--workload", choices=("tg2d", "tg3d"), default="tg2d",
-                    help="tg2d: the 4096^2 D2Q5 x 3 line (default); tg3d: 512^3 D3Q7 x 4")
+    ap.add_argument("--workload", choices=("tg2d", "tg3d", "cavities", "conv", "warmstart"),
+                    default="tg2d",
+                    help="tg2d: the 4096^2 D2Q5 x 3 line (default); tg3d: 512^3 D3Q7 x 4; "
+                         "cavities: 64 batched cavities; conv: network kernels; warmstart: "
+                         "learned warm start vs cold start at 256^2")
+    ap.add_argument("--max-steps", type=int, default=2_000_000)
     ap.add_argument("--grid", type=int, default=4096,
                     help="lattice side (default 4096; smaller sides are profiling cases)")
     args = ap.parse_args()
@@ -450,6 +533,14 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "cavities":
+        return run_cavities(args)
+    if args.workload == "conv":
+        return run_conv(args)
+    if args.workload == "warmstart":
+        from paper_2108_08591_gb300 import _build, warmstart
+        _build.build()
+        return warmstart.main([])
     return run_mdf(args)
 
 
