@@ -66,6 +66,23 @@ def _config(n_gpus: int, storage: str, d: int = 2):
             "l2": f"inputs larger than L2 (2 x {pop_gb:.2f} GB populations), no flush"}
 
 
+def aggregate(local_updates: float, local_ms: float, dist=None, device="cpu"):
+    """Whole-job throughput of replicas: every rank's timed region is reduced
+    to the maximum (the job takes as long as its slowest rank) and the node
+    updates of all ranks are summed.  Returns (MLUPS, max ms, world)."""
+    world = 1
+    t_max, total = float(local_ms), float(local_updates)
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        u = torch.tensor([float(local_updates)], dtype=torch.float64, device=device)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        t_max, total = float(t.item()), float(u.item())
+    return total / (t_max / 1e3) / 1e6, t_max, world
+
+
 def _kernel_sha() -> str:
     h = hashlib.sha256()
     for p in KERNEL_SOURCES:
@@ -329,12 +346,7 @@ def run_mdf(args):
     clocks = sampler.summary()
 
     updates_local = args.steps * EPI_EVERY * N
-    t_max = elapsed_ms
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = updates_local * world / (t_max / 1e3) / 1e6
+    value, t_max, _ = aggregate(updates_local, elapsed_ms, dist, device="cuda")
 
     # end to end through the C-ABI with host buffers: every step copies the
     # step's inputs (P, u) from pinned host memory, runs the updates with the
@@ -354,11 +366,7 @@ def run_mdf(args):
         lat.fields_host(("P", "u"), out={"P": outP, "u": outu})
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = e2e_steps * EPI_EVERY * N * world / e2e_s / 1e6
+    e2e_value, _, _ = aggregate(e2e_steps * EPI_EVERY * N, e2e_s * 1e3, dist, device="cuda")
     lat.close()
     del fields
     torch.cuda.empty_cache()
