@@ -476,11 +476,12 @@ def run_cavities(args):
 def run_conv(args):
     """Throughput of the network's tensor-core convolution kernels."""
     import torch
-    from paper_2108_08591_gb300 import _build, conv3x3_bf16, conv3x3_bf16_backward
+    from paper_2108_08591_gb300 import _build, conv3x3_bf16, conv3x3_bf16_backward, set_conv_kernel
     _build.build()
     rows = []
-    for (B, H, Cin, Cout) in [(8, 256, 32, 32), (8, 128, 64, 64), (8, 64, 128, 128), (8, 32, 256, 256),
-                              (8, 256, 96, 32), (8, 64, 384, 128)]:
+    for kern, (B, H, Cin, Cout) in [(k, c) for k in ("tcgen05", "mma.sync") for c in [(8, 256, 32, 32), (8, 128, 64, 64), (8, 64, 128, 128), (8, 32, 256, 256),
+                              (8, 256, 96, 32), (8, 64, 384, 128)]]:
+        set_conv_kernel(kern)
         g = torch.Generator(device="cuda").manual_seed(1)
         x = torch.randn(B, H, H, Cin, device="cuda", generator=g).to(torch.bfloat16)
         w = (0.05 * torch.randn(Cout, 3, 3, Cin, device="cuda", generator=g)).to(torch.bfloat16)
@@ -498,8 +499,9 @@ def run_conv(args):
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / args.steps
-            rows.append({"B": B, "H": H, "Cin": Cin, "Cout": Cout, "op": name, "ms": ms,
-                         "tflops": mult * flops / ms / 1e9})
+            rows.append({"kernel": kern, "B": B, "H": H, "Cin": Cin, "Cout": Cout, "op": name,
+                         "ms": ms, "tflops": mult * flops / ms / 1e9})
+    set_conv_kernel("tcgen05")
     print(json.dumps({"workload": "conv", "unit": "TFLOP/s", "rows": rows}), flush=True)
     return 0
 

@@ -360,6 +360,12 @@ mdf_status mdf_nn_conv_wgrad(const void *x, const void *dz, float *dw, float *pa
                              int W, int Cin, int Cout, void *stream);
 mdf_status mdf_nn_conv_dgrad(const void *dz, const void *w, void *wt, void *dx, int B, int H, int W,
                              int Cin, int Cout, void *stream);
+/* Forward/dgrad convolution kernel, process-wide: which = 1 the tcgen05 kernel
+ * (TMEM accumulator, the default), 0 the mma.sync kernel. */
+mdf_status mdf_nn_set_conv_kernel(int which);
+/* Read and clear the tcgen05 kernel's time-out flag (1 when a bounded
+ * mbarrier wait gave up) of the current device; synchronises the device. */
+mdf_status mdf_nn_conv_error(int *flag);
 
 #ifdef __cplusplus
 }

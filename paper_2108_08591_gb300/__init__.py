@@ -372,6 +372,18 @@ class WarmStartNet:
         return float(loss[0]) if want_loss else None
 
 
+def set_conv_kernel(which: str):
+    """Forward/dgrad convolution kernel: 'tcgen05' (default) or 'mma.sync'."""
+    _lib.check(_lib.load().mdf_nn_set_conv_kernel({"mma.sync": 0, "tcgen05": 1}[which]))
+
+
+def conv_timeout_flag() -> int:
+    """Read and clear the tcgen05 kernel's time-out flag (synchronises)."""
+    f = np.zeros(1, dtype=np.int32)
+    _lib.check(_lib.load().mdf_nn_conv_error(f.ctypes.data))
+    return int(f[0])
+
+
 def conv3x3_bf16(x, w, bias=None, relu=False, out_fp32=True):
     """The library's tensor-core convolution on CUDA tensors (bf16 x, w)."""
     import torch

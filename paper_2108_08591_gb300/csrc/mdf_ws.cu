@@ -21,8 +21,12 @@
 #include <string>
 #include <vector>
 
+#include <map>
+#include <mutex>
+
 #include "mdf.h"
 #include "mdf_nn.cuh"
+#include "mdf_nn_tc.cuh"
 
 using namespace mdfnn;
 
@@ -97,11 +101,51 @@ mdf_status wfail(mdf_ws_t w, mdf_status st, const char *fmt, ...) {
       return wfail((w), MDF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
   } while (0)
 
+// Forward-convolution kernel in use: 1 = tcgen05/TMEM (default), 0 = mma.sync.
+int g_conv_kernel = 1;
+std::mutex g_tc_mu;
+std::map<int, int *> g_tc_err;  // per-device error flag of the tcgen05 kernel
+
+int *tc_error_flag() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lock(g_tc_mu);
+  int *&p = g_tc_err[dev];
+  if (!p) {
+    if (cudaMalloc(&p, sizeof(int)) != cudaSuccess) { p = nullptr; return nullptr; }
+    cudaMemset(p, 0, sizeof(int));
+  }
+  return p;
+}
+
+template <int BN>
+cudaError_t launch_tc(cudaStream_t s, const ConvArgs &a, long long M, int *err) {
+  static bool configured = false;
+  const size_t smem = tc_smem_bytes<BN>();
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((a.Cout + BN - 1) / BN));
+  k_conv_fwd_tc<BN><<<grid, 128, smem, s>>>(a, err);
+  return cudaGetLastError();
+}
+
 cudaError_t conv_fwd(cudaStream_t s, const bf16 *x, const bf16 *w, const float *bias, bf16 *y,
                      float *yf, int B, int H, int W, int Cin, int Cout, int ldy, int yoff,
                      int relu) {
   ConvArgs a{x, w, bias, y, yf, B, H, W, Cin, Cout, ldy, yoff, relu};
   const long long M = (long long)B * H * W;
+  if (g_conv_kernel == 1) {
+    int *err = tc_error_flag();
+    if (!err) return cudaErrorMemoryAllocation;
+    if (Cout <= 16) return launch_tc<16>(s, a, M, err);
+    if (Cout <= 32) return launch_tc<32>(s, a, M, err);
+    if (Cout <= 64) return launch_tc<64>(s, a, M, err);
+    return launch_tc<128>(s, a, M, err);
+  }
   dim3 grid((unsigned)((M + CBM - 1) / CBM), (unsigned)((Cout + CBN - 1) / CBN));
   k_conv_fwd<<<grid, 128, 0, s>>>(a);
   return cudaGetLastError();
@@ -477,6 +521,25 @@ mdf_status mdf_nn_conv_dgrad(const void *dz, const void *w, void *wt, void *dx, 
   if (!dz || !w || !wt || !dx || Cin % 8 || Cout % 8) return MDF_EINVAL;
   return conv_dgrad((cudaStream_t)stream, (const bf16 *)dz, (const bf16 *)w, (bf16 *)wt, (bf16 *)dx, B,
                     H, W, Cin, Cout) == cudaSuccess ? MDF_OK : MDF_ECUDA;
+}
+
+// Select the forward-convolution kernel (1 tcgen05, 0 mma.sync), process-wide.
+mdf_status mdf_nn_set_conv_kernel(int which) {
+  if (which != 0 && which != 1) return MDF_EINVAL;
+  g_conv_kernel = which;
+  return MDF_OK;
+}
+
+// Read and clear the tcgen05 kernel's time-out flag of the current device
+// (synchronises the device).  *flag = 1 when a bounded wait gave up.
+mdf_status mdf_nn_conv_error(int *flag) {
+  if (!flag) return MDF_EINVAL;
+  int *p = tc_error_flag();
+  if (!p) return MDF_ENOMEM;
+  if (cudaDeviceSynchronize() != cudaSuccess) return MDF_ECUDA;
+  if (cudaMemcpy(flag, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return MDF_ECUDA;
+  if (cudaMemset(p, 0, sizeof(int)) != cudaSuccess) return MDF_ECUDA;
+  return MDF_OK;
 }
 
 const char *mdf_ws_last_error(mdf_ws_t w) { return w ? w->err.c_str() : g_ws_error.c_str(); }

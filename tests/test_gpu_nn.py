@@ -32,9 +32,18 @@ def _rel(ref, got):
     return float(np.linalg.norm((ref - got).ravel()) / np.linalg.norm(ref.ravel()))
 
 
+@pytest.fixture(params=["tcgen05", "mma.sync"])
+def kernel(request):
+    from paper_2108_08591_gb300 import conv_timeout_flag, set_conv_kernel
+    set_conv_kernel(request.param)
+    yield request.param
+    assert conv_timeout_flag() == 0
+    set_conv_kernel("tcgen05")
+
+
 @pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 10, 7, 16, 40), (1, 8, 8, 96, 32), (3, 5, 9, 8, 16),
-                                            (2, 16, 16, 32, 136)])
-def test_conv_forward(B, H, W, Cin, Cout):
+                                            (2, 16, 16, 32, 136), (1, 20, 13, 64, 256)])
+def test_conv_forward(kernel, B, H, W, Cin, Cout):
     import torch
     from paper_2108_08591_gb300 import conv3x3_bf16
     x, xn = _bf16((B, H, W, Cin), 1)
@@ -49,7 +58,7 @@ def test_conv_forward(B, H, W, Cin, Cout):
 
 
 @pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 10, 7, 16, 40), (1, 8, 8, 96, 32), (2, 16, 16, 32, 64)])
-def test_conv_backward(B, H, W, Cin, Cout):
+def test_conv_backward(kernel, B, H, W, Cin, Cout):
     from paper_2108_08591_gb300 import conv3x3_bf16_backward
     x, xn = _bf16((B, H, W, Cin), 3)
     w, wn = _bf16((Cout, 3, 3, Cin), 4)
