@@ -474,35 +474,46 @@ def run_cavities(args):
 
 
 def run_conv(args):
-    """Throughput of the network's tensor-core convolution kernels."""
+    """Throughput of the network's tensor-core convolution kernels: each op
+    repeated --steps times inside one CUDA graph (host launch cost excluded),
+    inputs L2-resident (the network's working set), CUDA-event timed."""
     import torch
     from paper_2108_08591_gb300 import _build, conv3x3_bf16, conv3x3_bf16_backward, set_conv_kernel
     _build.build()
     rows = []
-    for kern, (B, H, Cin, Cout) in [(k, c) for k in ("tcgen05", "mma.sync") for c in [(8, 256, 32, 32), (8, 128, 64, 64), (8, 64, 128, 128), (8, 32, 256, 256),
-                              (8, 256, 96, 32), (8, 64, 384, 128)]]:
+    shapes = [(8, 256, 32, 32), (8, 128, 64, 64), (8, 64, 128, 128), (8, 32, 256, 256),
+              (8, 256, 96, 32), (8, 64, 384, 128), (8, 256, 16, 32), (8, 256, 64, 16)]
+    for kern in ("tcgen05", "mma.sync"):
         set_conv_kernel(kern)
-        g = torch.Generator(device="cuda").manual_seed(1)
-        x = torch.randn(B, H, H, Cin, device="cuda", generator=g).to(torch.bfloat16)
-        w = (0.05 * torch.randn(Cout, 3, 3, Cin, device="cuda", generator=g)).to(torch.bfloat16)
-        dz = torch.randn(B, H, H, Cout, device="cuda", generator=g).to(torch.bfloat16)
-        flops = 2.0 * B * H * H * Cout * 9 * Cin
-        for name, fn, mult in (("fwd", lambda: conv3x3_bf16(x, w), 1),
-                               ("bwd", lambda: conv3x3_bf16_backward(x, w, dz), 2)):
-            for _ in range(max(3, args.warmup)):
-                fn()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            for _ in range(args.steps):
-                fn()
-            e1.record()
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / args.steps
-            rows.append({"kernel": kern, "B": B, "H": H, "Cin": Cin, "Cout": Cout, "op": name,
-                         "ms": ms, "tflops": mult * flops / ms / 1e9})
+        for (B, H, Cin, Cout) in shapes:
+            g = torch.Generator(device="cuda").manual_seed(1)
+            x = torch.randn(B, H, H, Cin, device="cuda", generator=g).to(torch.bfloat16)
+            w = (0.05 * torch.randn(Cout, 3, 3, Cin, device="cuda", generator=g)).to(torch.bfloat16)
+            dz = torch.randn(B, H, H, Cout, device="cuda", generator=g).to(torch.bfloat16)
+            flops = 2.0 * B * H * H * Cout * 9 * Cin
+            for name, fn, mult in (("fwd", lambda: conv3x3_bf16(x, w, out_fp32=False), 1),
+                                   ("bwd", lambda: conv3x3_bf16_backward(x, w, dz), 2)):
+                for _ in range(max(3, args.warmup)):
+                    fn()
+                torch.cuda.synchronize()
+                graph = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(graph):
+                    for _ in range(args.steps):
+                        fn()
+                graph.replay()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                graph.replay()
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / args.steps
+                rows.append({"kernel": kern, "B": B, "H": H, "Cin": Cin, "Cout": Cout, "op": name,
+                             "ms": ms, "tflops": mult * flops / ms / 1e9})
+                del graph
     set_conv_kernel("tcgen05")
-    print(json.dumps({"workload": "conv", "unit": "TFLOP/s", "rows": rows}), flush=True)
+    print(json.dumps({"workload": "conv", "unit": "TFLOP/s", "timing": "CUDA graph of --steps calls",
+                      "rows": rows}), flush=True)
     return 0
 
 

@@ -363,6 +363,13 @@ mdf_status mdf_nn_conv_dgrad(const void *dz, const void *w, void *wt, void *dx, 
 /* Forward/dgrad convolution kernel, process-wide: which = 1 the tcgen05 kernel
  * (TMEM accumulator, the default), 0 the mma.sync kernel. */
 mdf_status mdf_nn_set_conv_kernel(int which);
+
+/* Tile of the tcgen05 kernel, process-wide: bn (output channels per CTA) in
+ * {16, 32, 64, 128, 256} and stages (shared-memory ring depth) in {3, 4, 6};
+ * 0 keeps the automatic choice.  (256, 6) does not fit and is rejected.
+ * A tuning override: every tile sweeps K in the same order. */
+mdf_status mdf_nn_set_tc_tile(int bn, int stages);
+
 /* Read and clear the tcgen05 kernel's time-out flag (1 when a bounded
  * mbarrier wait gave up) of the current device; synchronises the device. */
 mdf_status mdf_nn_conv_error(int *flag);

@@ -118,19 +118,42 @@ int *tc_error_flag() {
   return p;
 }
 
-template <int BN>
+int g_tc_bn = 0, g_tc_stages = 0;  // tile override of the tcgen05 kernel (0 = automatic)
+
+template <int BN, int S>
 cudaError_t launch_tc(cudaStream_t s, const ConvArgs &a, long long M, int *err) {
   static bool configured = false;
-  const size_t smem = tc_smem_bytes<BN>();
+  const size_t smem = tc_smem_bytes<BN, S>();
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc<BN, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   dim3 grid((unsigned)((M + TC_BM - 1) / TC_BM), (unsigned)((a.Cout + BN - 1) / BN));
-  k_conv_fwd_tc<BN><<<grid, 128, smem, s>>>(a, err);
+  k_conv_fwd_tc<BN, S><<<grid, TC_THREADS, smem, s>>>(a, err);
   return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t launch_tc_s(cudaStream_t s, const ConvArgs &a, long long M, int *err, int stages) {
+  if (stages == 3) return launch_tc<BN, 3>(s, a, M, err);
+  if (stages == 4) return launch_tc<BN, 4>(s, a, M, err);
+  if (stages == 6) return launch_tc<BN, 6>(s, a, M, err);
+  return cudaErrorInvalidValue;
+}
+
+// Tile of the tcgen05 kernel: N tile = the output channels rounded up to a
+// power of two (16..256), halved from 256 when the pixel tiles alone do not
+// fill the SMs once; ring depth 3 for N <= 32 and N = 128 (two CTAs per SM),
+// 4 for N = 64 and N = 256 (measured over the network's layer shapes).
+void tc_tile(long long M, int Cout, int &bn, int &stages) {
+  bn = Cout <= 16 ? 16 : Cout <= 32 ? 32 : Cout <= 64 ? 64 : Cout <= 128 ? 128 : 256;
+  if (bn == 256 && (M + TC_BM - 1) / TC_BM < 152) bn = 128;
+  stages = (bn == 64 || bn == 256) ? 4 : 3;
+  if (g_tc_bn) bn = g_tc_bn;
+  if (g_tc_stages) stages = g_tc_stages;
 }
 
 cudaError_t conv_fwd(cudaStream_t s, const bf16 *x, const bf16 *w, const float *bias, bf16 *y,
@@ -141,10 +164,16 @@ cudaError_t conv_fwd(cudaStream_t s, const bf16 *x, const bf16 *w, const float *
   if (g_conv_kernel == 1) {
     int *err = tc_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
-    if (Cout <= 16) return launch_tc<16>(s, a, M, err);
-    if (Cout <= 32) return launch_tc<32>(s, a, M, err);
-    if (Cout <= 64) return launch_tc<64>(s, a, M, err);
-    return launch_tc<128>(s, a, M, err);
+    int bn, st;
+    tc_tile(M, Cout, bn, st);
+    switch (bn) {
+      case 16: return launch_tc_s<16>(s, a, M, err, st);
+      case 32: return launch_tc_s<32>(s, a, M, err, st);
+      case 64: return launch_tc_s<64>(s, a, M, err, st);
+      case 128: return launch_tc_s<128>(s, a, M, err, st);
+      case 256: return launch_tc_s<256>(s, a, M, err, st);
+      default: return cudaErrorInvalidValue;
+    }
   }
   dim3 grid((unsigned)((M + CBM - 1) / CBM), (unsigned)((Cout + CBN - 1) / CBN));
   k_conv_fwd<<<grid, 128, 0, s>>>(a);
@@ -527,6 +556,16 @@ mdf_status mdf_nn_conv_dgrad(const void *dz, const void *w, void *wt, void *dx, 
 mdf_status mdf_nn_set_conv_kernel(int which) {
   if (which != 0 && which != 1) return MDF_EINVAL;
   g_conv_kernel = which;
+  return MDF_OK;
+}
+
+// Tile override of the tcgen05 kernel (0, 0 = automatic), process-wide.
+mdf_status mdf_nn_set_tc_tile(int bn, int stages) {
+  if (bn && bn != 16 && bn != 32 && bn != 64 && bn != 128 && bn != 256) return MDF_EINVAL;
+  if (stages && stages != 3 && stages != 4 && stages != 6) return MDF_EINVAL;
+  if (bn == 256 && stages == 6) return MDF_EINVAL;  // 288 KB of shared memory
+  g_tc_bn = bn;
+  g_tc_stages = stages;
   return MDF_OK;
 }
 
