@@ -309,7 +309,8 @@ def run_mdf(args):
     d = len(shape)
     N = int(np.prod(shape))
     stream = torch.cuda.current_stream()
-    lat = Lattice(shape, s1=s1, storage=args.storage, stream=stream)
+    lat = Lattice(shape, s1=s1, storage=args.storage, stream=stream, vx=args.vx or 0,
+                  block=args.block or 0)
     lat.init(P, u)
     info = lat.info
     fields = lat.alloc_fields(("P", "u", "G", "div", "S", "sigma", "omega"))
@@ -524,6 +525,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("mdf", "reference"), default="mdf")
     ap.add_argument("--storage", choices=("f32", "f16", "bf16", "f16eq", "bf16eq"), default="f32")
+    ap.add_argument("--vx", type=int, default=None,
+                    help="x-nodes per thread of the step kernel (default: the library's choice)")
+    ap.add_argument("--block", type=int, default=None, help="threads per block of the step kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--workload", choices=("tg2d", "tg3d", "cavities", "conv", "warmstart"),

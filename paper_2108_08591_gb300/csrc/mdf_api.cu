@@ -44,13 +44,18 @@ bool eq_storage(int st) { return st == MDF_F16EQ || st == MDF_BF16EQ; }
 //   3D: one node per thread, 256 threads (FP32 6.94 TB/s, FP16 4.40 TB/s):
 //       with 28 populations per node the vector kernel's register pressure
 //       costs more than its saved instructions.
+//   Equilibrium-shifted 16-bit: 2 nodes per thread (one FP32 pair), 64
+//       threads in 2D (5.43 TB/s) and 128 in 3D (5.39 TB/s).
 // mdf_autotune() measures the candidates for a given handle instead.
 int default_vx(int d, int storage) {
+  if (eq_storage(storage)) return 2;
   if (d == 3) return 1;
-  if (storage == MDF_F16EQ || storage == MDF_BF16EQ) return 2;
   return storage == MDF_F64 ? 2 : 4;
 }
-int default_block(int d, int) { return d == 3 ? 256 : 128; }
+int default_block(int d, int storage) {
+  if (eq_storage(storage)) return d == 3 ? 128 : 64;
+  return d == 3 ? 256 : 128;
+}
 
 }  // namespace
 

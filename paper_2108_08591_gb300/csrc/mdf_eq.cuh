@@ -88,10 +88,195 @@ __device__ __forceinline__ void source_moments(int i, int j, const float (&Mo)[L
 // Moment slots: u_1..u_d, P', then rho' (only stored when with_rho).
 __device__ __forceinline__ int moment_slots(int D, int with_rho) { return D + 1 + with_rho; }
 
+// ---------------------------------------------------------------------------
+// Update kernel.  Arithmetic is carried in "scaled" units G = SCALE * g and
+// per lane group: one float (VX = 1) or an FP32 pair (VX >= 2) handled by
+// the f32x2 instructions, whose lanes round exactly like the scalar ones, so
+// every VX gives the same bits.  Every operation is an explicit add / mul /
+// fma, independent of compiler contraction.
+//
+// Pull (decode): G_i(y) = raw_i(x) + SCALE w_i e_i(M(x)), x = y - c_i, with
+// g^eq_i = w_i e_i (Eq. 2-4, rest-shifted): for a velocity set alpha and a
+// moving direction c_i = sg e_b, e = u_alpha (1 + sg u_b / c_s^2) +
+// [alpha = b] sg P' / c_s^2; for the continuity set e = rho' + sg u_b (1 +
+// rho') / c_s^2; for the rest direction e = u_alpha (rho').
+//
+// Collide (Eq. 3-21) and encode in one: the stored part is
+//   s = SCALE (f* - f^eq(M)) = M^-1 (I - S) (m - m^eq) + SCALE w F,
+// since f - f^eq = M^-1 (m - m^eq) and the conserved moment m_0 equals its
+// equilibrium.  With M's orthogonal rows, M^-1 = M^T diag(1 / |row k|^2),
+// so each stored value is a short signed sum of the moment deviations E_k =
+// m_k - m_k^eq scaled by (1 - s_k) / |row k|^2.
+// ---------------------------------------------------------------------------
+template <int VX> struct Lanes {
+  using T = float2;
+  static constexpr int N = VX / 2, W = 2;
+};
+template <> struct Lanes<1> {
+  using T = float;
+  static constexpr int N = 1, W = 1;
+};
+
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+#define MDF_F32X2_BINARY(name, op)                                                              \
+  __device__ __forceinline__ float2 name(float2 a, float2 b) {                                  \
+    float2 r;                                                                                   \
+    asm("{\n .reg .b64 a, b, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n " op           \
+        " d, a, b;\n mov.b64 {%0, %1}, d;\n}\n"                                                 \
+        : "=f"(r.x), "=f"(r.y)                                                                  \
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));                                              \
+    return r;                                                                                   \
+  }
+MDF_F32X2_BINARY(vadd, "add.rn.f32x2")
+MDF_F32X2_BINARY(vsub, "sub.rn.f32x2")
+MDF_F32X2_BINARY(vmul, "mul.rn.f32x2")
+#undef MDF_F32X2_BINARY
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n .reg .b64 a, b, c, d;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n"
+      " mov.b64 c, {%6, %7};\n fma.rn.f32x2 d, a, b, c;\n mov.b64 {%0, %1}, d;\n}\n"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+
+template <class T> __device__ __forceinline__ T splat(float c);
+template <> __device__ __forceinline__ float splat<float>(float c) { return c; }
+template <> __device__ __forceinline__ float2 splat<float2>(float c) { return make_float2(c, c); }
+__device__ __forceinline__ void to_lanes(float &t, const float *v) { t = v[0]; }
+__device__ __forceinline__ void to_lanes(float2 &t, const float *v) { t = make_float2(v[0], v[1]); }
+__device__ __forceinline__ void from_lanes(float *v, float t) { v[0] = t; }
+__device__ __forceinline__ void from_lanes(float *v, float2 t) { v[0] = t.x; v[1] = t.y; }
+
+// Moving direction i of lattice L: axis b and sign sg (sg = 0: rest).
+template <class L> __host__ __device__ constexpr int dir_axis(int i) {
+  return L::c(i, 0) != 0 ? 0 : L::c(i, 1) != 0 ? 1 : 2;
+}
+template <class L> __host__ __device__ constexpr int dir_sign(int i) {
+  return L::c(i, 0) + L::c(i, 1) + (L::D == 3 ? L::c(i, 2) : 0);
+}
+
+// e_i of set alpha from source moments (u, P', rho') (see above).
+template <class L, class T>
+__device__ __forceinline__ T eq_inner(int alpha, int i, const T (&u)[L::D], T P, T r) {
+  constexpr float ics2 = float(1.0 / L::CS2);
+  if (i == 0) return alpha == 0 ? r : u[alpha - 1];
+  const int b = dir_axis<L>(i);
+  const float sc = dir_sign<L>(i) > 0 ? ics2 : -ics2;
+  if (alpha == 0) return vfma(vmul(u[b], splat<T>(sc)), vadd(r, splat<T>(1.f)), r);
+  const T t = vfma(u[b], splat<T>(sc), splat<T>(1.f));
+  if (alpha - 1 == b) return vfma(u[b], t, vmul(P, splat<T>(sc)));
+  return vmul(u[alpha - 1], t);
+}
+
+// Axis-b direction pair of lattice L: c = +e_b and c = -e_b.
+template <class L> __host__ __device__ constexpr int dir_pos(int b) { return L::Q == 5 ? 1 + b : 1 + 2 * b; }
+template <class L> __host__ __device__ constexpr int dir_neg(int b) { return L::Q == 5 ? 3 + b : 2 + 2 * b; }
+
+// Relax-and-encode of one set: g (scaled pulled populations) -> stored s.
+// Ef: first-moment deviations m_b - m_b^eq (scaled); m0: scaled zeroth
+// moment; Fw, Fw0: scaled source w_i F for i > 0 and i = 0.  k: the
+// (1 - s_k)/|row k|^2 factors.
+template <class L, class T>
+__device__ __forceinline__ void relax_encode(T (&g)[L::Q], const T (&Ef)[L::D], T m0, T Fw, T Fw0,
+                                             const float (&k)[6]) {
+  if constexpr (L::Q == 5) {
+    // D2Q5 rows: m1 = g1 - g3, m2 = g2 - g4, m3 = g1 + g3 - g2 - g4,
+    // m4 = g1 + g2 + g3 + g4 - 4 g0; |row|^2 = 2, 2, 4, 20; m4eq = -2/3 m0.
+    const T p13 = vadd(g[1], g[3]), p24 = vadd(g[2], g[4]);
+    const T E1 = Ef[0], E2 = Ef[1];
+    const T E3 = vsub(p13, p24);
+    const T E4 = vfma(splat<T>(2.f / 3.f), m0, vfma(splat<T>(-4.f), g[0], vadd(p13, p24)));
+    // k = {(1-s1)/2, (1-s2)/4, (1-s2)/20, -4 (1-s2)/20}
+    const T t = vfma(splat<T>(k[2]), E4, Fw);
+    const T pp = vfma(splat<T>(k[1]), E3, t), nn = vfma(splat<T>(-k[1]), E3, t);
+    g[0] = vfma(splat<T>(k[3]), E4, Fw0);
+    g[1] = vfma(splat<T>(k[0]), E1, pp);
+    g[3] = vfma(splat<T>(-k[0]), E1, pp);
+    g[2] = vfma(splat<T>(k[0]), E2, nn);
+    g[4] = vfma(splat<T>(-k[0]), E2, nn);
+  } else {
+    // D3Q7 rows: m1..3 first moments, m4 = sum_{i>0} g - 6 g0,
+    // m5 = 2 sx - sy - sz, m6 = sy - sz; |row|^2 = 2, 42, 12, 4;
+    // m4eq = -3/4 m0, m5eq = m6eq = 0.
+    const T sx = vadd(g[1], g[2]), sy = vadd(g[3], g[4]), sz = vadd(g[5], g[6]);
+    const T syz = vadd(sy, sz);
+    const T E1 = Ef[0], E2 = Ef[1], E3 = Ef[2];
+    const T E4 = vfma(splat<T>(0.75f), m0, vfma(splat<T>(-6.f), g[0], vadd(sx, syz)));
+    const T E5 = vsub(vadd(sx, sx), syz);
+    const T E6 = vsub(sy, sz);
+    // k = {(1-s1)/2, (1-s2)/42, (1-s2)/6, -(1-s2)/12, (1-s2)/4, -6 (1-s2)/42}
+    const T t = vfma(splat<T>(k[1]), E4, Fw);
+    const T A = vfma(splat<T>(k[2]), E5, t), B = vfma(splat<T>(k[3]), E5, t);
+    const T B3 = vfma(splat<T>(k[4]), E6, B), B5 = vfma(splat<T>(-k[4]), E6, B);
+    g[0] = vfma(splat<T>(k[5]), E4, Fw0);
+    g[1] = vfma(splat<T>(k[0]), E1, A);
+    g[2] = vfma(splat<T>(-k[0]), E1, A);
+    g[3] = vfma(splat<T>(k[0]), E2, B3);
+    g[4] = vfma(splat<T>(-k[0]), E2, B3);
+    g[5] = vfma(splat<T>(k[0]), E3, B5);
+    g[6] = vfma(splat<T>(-k[0]), E3, B5);
+  }
+}
+
+// VX consecutive 16-bit values in one load (2, 4 or 8 bytes), with the
+// element bits, the pairs as FP32 lanes and the words the x-neighbours need.
+template <class TS> __device__ __forceinline__ float bits_to_float(unsigned b);
+template <> __device__ __forceinline__ float bits_to_float<__half>(unsigned b) {
+  return __half2float(__ushort_as_half((unsigned short)b));
+}
+template <> __device__ __forceinline__ float bits_to_float<__nv_bfloat16>(unsigned b) {
+  return __uint_as_float(b << 16);
+}
+template <class TS> __device__ __forceinline__ unsigned ldg_bits16(const TS *p) {
+  return __ldg(reinterpret_cast<const unsigned short *>(p));
+}
+template <class TS> __device__ __forceinline__ float2 word_to_f2(unsigned w);
+template <> __device__ __forceinline__ float2 word_to_f2<__half>(unsigned w) {
+  return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+}
+template <> __device__ __forceinline__ float2 word_to_f2<__nv_bfloat16>(unsigned w) {
+  return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+template <class TS, int VX> struct Packed16;
+template <class TS> struct Packed16<TS, 1> {
+  using W = unsigned short;
+  static __device__ __forceinline__ W load(const TS *p) { return __ldg(reinterpret_cast<const W *>(p)); }
+  static __device__ __forceinline__ unsigned bits(W w, int) { return w; }
+  static __device__ __forceinline__ unsigned last_word(W w) { return w; }
+  static __device__ __forceinline__ unsigned first_word(W w) { return w; }
+  static __device__ __forceinline__ float lanes(W w, int) { return bits_to_float<TS>(w); }
+};
+template <class TS> struct Packed16<TS, 2> {
+  using W = unsigned;
+  static __device__ __forceinline__ W load(const TS *p) { return __ldg(reinterpret_cast<const W *>(p)); }
+  static __device__ __forceinline__ unsigned bits(W w, int j) { return j ? w >> 16 : w & 0xffffu; }
+  static __device__ __forceinline__ unsigned last_word(W w) { return w; }
+  static __device__ __forceinline__ unsigned first_word(W w) { return w; }
+  static __device__ __forceinline__ float2 lanes(W w, int) { return word_to_f2<TS>(w); }
+};
+template <class TS> struct Packed16<TS, 4> {
+  using W = uint2;
+  static __device__ __forceinline__ W load(const TS *p) { return __ldg(reinterpret_cast<const W *>(p)); }
+  static __device__ __forceinline__ unsigned bits(W w, int j) {
+    const unsigned v = j < 2 ? w.x : w.y;
+    return (j & 1) ? v >> 16 : v & 0xffffu;
+  }
+  static __device__ __forceinline__ unsigned last_word(W w) { return w.y; }
+  static __device__ __forceinline__ unsigned first_word(W w) { return w.x; }
+  static __device__ __forceinline__ float2 lanes(W w, int q) { return word_to_f2<TS>(q ? w.y : w.x); }
+};
+
 template <class L, class TS, int VX, int MODE, bool WALLS>
 __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
-  constexpr int D = L::D, Q = L::Q;
-  const float scale = EqScale<TS>::s, inv = EqScale<TS>::inv;
+  constexpr int D = L::D, Q = L::Q, KM = D + 2;
+  using T = typename Lanes<VX>::T;
+  constexpr int NP = Lanes<VX>::N, LW = Lanes<VX>::W;
+  constexpr float SC = EqScale<TS>::s, INV = EqScale<TS>::inv;
   const int lane = threadIdx.x & 31;
   int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
   const bool active = x0 < A.nx;
@@ -109,14 +294,13 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
   const int K = moment_slots(D, A.with_rho);
   const TS *__restrict__ fin = static_cast<const TS *>(A.fin);
   const float *__restrict__ min = static_cast<const float *>(A.min);
+  const int a1 = A.with_rho;
 
   uint8_t m[VX];
   if (WALLS) {
 #pragma unroll
     for (int j = 0; j < VX; ++j) m[j] = A.mask[row0 + x0 + j];
   }
-  // moments of this row's nodes, the y/z neighbour rows and the two x ends
-  constexpr int KM = D + 2;
   float Mo[KM][VX], Mym[KM][VX], Myp[KM][VX], Mzm[KM][VX], Mzp[KM][VX], Mxl[KM], Mxr[KM];
   load_moments<KM, VX>(A, K, row0 + x0, Mo);
   load_moments<KM, VX>(A, K, row_ym + x0, Mym);
@@ -139,116 +323,255 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
     Mxr[k] = r;
   }
 
-  float g[D][Q][VX], h[Q][VX];
-  const int a1 = A.with_rho;
+  // ---- pull: every population word is loaded before any is decoded, so
+  // all of a thread's reads are in flight together
+  using PW = typename Packed16<TS, VX>::W;
+  PW wv[D + 1][Q];
+  unsigned edge[D + 1][2];  // per set: x - 1 value of the +x pull, x + VX value of the -x pull
 #pragma unroll
   for (int s = 0; s <= D; ++s) {
     const int alpha = s == D ? 0 : s + 1;  // velocity sets first, alpha = 0 last
     if (alpha == 0 && !A.with_rho) break;
-    const TS *base = fin + (long long)(alpha == 0 ? 0 : a1 + alpha - 1) * Q * A.plane;
-    float(&v)[Q][VX] = s == D ? h : g[s < D ? s : 0];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const TS *p = base + (long long)i * A.plane;
-      float raw[VX];
-      if (L::c(i, 0) == 1) {
-        float own[VX];
-        VecIO<TS, VX>::load(p + row0 + x0, own);
-        float pv = __shfl_up_sync(0xffffffffu, own[VX - 1], 1);
-        if (ledge) pv = Codec<TS>::load(p + row0 + xl);
-        raw[0] = pv;
-#pragma unroll
-        for (int j = 1; j < VX; ++j) raw[j] = own[j - 1];
-      } else if (L::c(i, 0) == -1) {
-        float own[VX];
-        VecIO<TS, VX>::load(p + row0 + x0, own);
-        float nv = __shfl_down_sync(0xffffffffu, own[0], 1);
-        if (redge) nv = Codec<TS>::load(p + row0 + xr);
-#pragma unroll
-        for (int j = 0; j < VX - 1; ++j) raw[j] = own[j + 1];
-        raw[VX - 1] = nv;
-      } else {
-        const int r = L::c(i, 1) == 1 ? row_ym : L::c(i, 1) == -1 ? row_yp
-                    : L::c(i, 2) == 1 ? row_zm : L::c(i, 2) == -1 ? row_zp : row0;
-        VecIO<TS, VX>::load(p + r + x0, raw);
-      }
-#pragma unroll
-      for (int j = 0; j < VX; ++j) {
-        float Ms[D + 2];
-        source_moments<L, VX>(i, j, Mo, Mym, Myp, Mzm, Mzp, Mxl, Mxr, Ms);
-        v[i][j] = raw[j] * inv + geq_m<L>(alpha, i, Ms);
-      }
+      const TS *p = fin + ((long long)(alpha == 0 ? 0 : a1 + alpha - 1) * Q + i) * A.plane;
+      const int r = L::c(i, 1) == 1 ? row_ym : L::c(i, 1) == -1 ? row_yp
+                  : L::c(i, 2) == 1 ? row_zm : L::c(i, 2) == -1 ? row_zp : row0;
+      wv[s][i] = Packed16<TS, VX>::load(p + r + x0);
+      if (L::c(i, 0) == 1) edge[s][0] = ledge ? ldg_bits16(p + row0 + xl) : 0u;
+      if (L::c(i, 0) == -1) edge[s][1] = redge ? ldg_bits16(p + row0 + xr) : 0u;
     }
-    if (WALLS) {  // anti-halfway bounce-back from the node's own opposite population
+  }
+  // ---- decode, direction by direction (source terms shared by the sets)
+  T G[D + 1][Q][NP];  // [velocity sets 0..D-1, continuity set D][i][lane group]
 #pragma unroll
-      for (int i = 1; i < Q; ++i)
+  for (int i = 0; i < Q; ++i) {
+    T su[NP][D], sP[NP], sr[NP];
 #pragma unroll
-        for (int j = 0; j < VX; ++j)
-          if ((m[j] >> L::opp(i)) & 1) {
-            float Mn[D + 2];
+    for (int p = 0; p < NP; ++p) {
+      float e[KM][LW];
 #pragma unroll
-            for (int k = 0; k < D + 2; ++k) Mn[k] = Mo[k][j];
-            const float own = Codec<TS>::load(base + (long long)L::opp(i) * A.plane + row0 + x0 + j);
-            float w = -(own * inv + geq_m<L>(alpha, L::opp(i), Mn));
-            if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u))
-              w += float(2.0 * L::w(i) * A.lid_u[alpha - 1]);
-            v[i][j] = w;
+      for (int q = 0; q < LW; ++q) {
+        float Ms[KM];
+        source_moments<L, VX>(i, LW * p + q, Mo, Mym, Myp, Mzm, Mzp, Mxl, Mxr, Ms);
+#pragma unroll
+        for (int k = 0; k < KM; ++k) e[k][q] = Ms[k];
+      }
+#pragma unroll
+      for (int b = 0; b < D; ++b) to_lanes(su[p][b], e[b]);
+      to_lanes(sP[p], e[D]);
+      to_lanes(sr[p], e[D + 1]);
+    }
+    const float sw = float(SC * L::w(i));
+#pragma unroll
+    for (int s = 0; s <= D; ++s) {
+      const int alpha = s == D ? 0 : s + 1;
+      if (alpha == 0 && !A.with_rho) break;
+      const PW w = wv[s][i];
+      T rv[NP];
+      if (L::c(i, 0) == 1) {  // raw[0] from the lane to the left, raw[j] = own[j - 1]
+        unsigned nb = __shfl_up_sync(0xffffffffu, Packed16<TS, VX>::last_word(w), 1);
+        nb = ledge ? edge[s][0] : (VX == 1 ? nb : nb >> 16);
+        float raw[VX];
+        raw[0] = bits_to_float<TS>(nb);
+#pragma unroll
+        for (int j = 1; j < VX; ++j) raw[j] = bits_to_float<TS>(Packed16<TS, VX>::bits(w, j - 1));
+#pragma unroll
+        for (int q = 0; q < NP; ++q) to_lanes(rv[q], raw + LW * q);
+      } else if (L::c(i, 0) == -1) {  // raw[j] = own[j + 1], raw[VX - 1] from the right
+        unsigned nb = __shfl_down_sync(0xffffffffu, Packed16<TS, VX>::first_word(w), 1);
+        nb = redge ? edge[s][1] : (nb & 0xffffu);
+        float raw[VX];
+#pragma unroll
+        for (int j = 0; j < VX - 1; ++j) raw[j] = bits_to_float<TS>(Packed16<TS, VX>::bits(w, j + 1));
+        raw[VX - 1] = bits_to_float<TS>(nb);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) to_lanes(rv[q], raw + LW * q);
+      } else {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) rv[q] = Packed16<TS, VX>::lanes(w, q);
+      }
+#pragma unroll
+      for (int q = 0; q < NP; ++q)
+        G[s][i][q] = vfma(eq_inner<L, T>(alpha, i, su[q], sP[q], sr[q]), splat<T>(sw), rv[q]);
+    }
+  }
+  if (WALLS) {  // anti-halfway bounce-back from the node's own opposite population
+#pragma unroll
+    for (int s = 0; s <= D; ++s) {
+      const int alpha = s == D ? 0 : s + 1;
+      if (alpha == 0 && !A.with_rho) break;
+      const TS *base = fin + (long long)(alpha == 0 ? 0 : a1 + alpha - 1) * Q * A.plane;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int o = L::opp(i);
+        const float swo = float(SC * L::w(o));
+        const float lid = alpha >= 1 ? float(SC * 2.0 * L::w(i) * A.lid_u[alpha - 1]) : 0.f;
+#pragma unroll
+        for (int j = 0; j < VX; ++j) {
+          if ((m[j] >> o) & 1) {
+            float un[D];
+#pragma unroll
+            for (int b = 0; b < D; ++b) un[b] = Mo[b][j];
+            const float own = Codec<TS>::load(base + (long long)o * A.plane + row0 + x0 + j);
+            float w = -vfma(eq_inner<L, float>(alpha, o, un, Mo[D][j], Mo[D + 1][j]), swo, own);
+            if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u)) w = vadd(w, lid);
+            float v[LW];
+            from_lanes(v, G[s][i][j / LW]);
+            v[j % LW] = w;
+            to_lanes(G[s][i][j / LW], v);
           }
+        }
+      }
     }
   }
 
   const long long N = (long long)A.nx * A.ny * A.nz;
   const long long n0 = ((long long)z * A.ny + y) * A.nx + x0;
-  float F[D][VX];
+  if (MODE != MODE_STEP && active) {  // derived fields of the pulled state (FP32, unscaled)
+#pragma unroll
+    for (int j = 0; j < VX; ++j) {
+      float gn[D][Q], hn[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        float v[LW];
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          from_lanes(v, G[a][i][j / LW]);
+          gn[a][i] = vmul(v[j % LW], INV);
+        }
+        from_lanes(v, G[D][i][j / LW]);
+        hn[i] = A.with_rho ? vmul(v[j % LW], INV) : 0.f;
+      }
+      write_fields<L, float>(A, n0 + j, N, gn, hn);
+    }
+  }
+  if (MODE == MODE_FIELDS || !active) return;
+
+  // ---- collide + encode
+  const float s1 = float(A.s1), s2 = float(A.s2);
+  float kf[6];
+  if constexpr (Q == 5) {
+    kf[0] = (1.f - s1) * 0.5f;
+    kf[1] = (1.f - s2) * 0.25f;
+    kf[2] = (1.f - s2) * 0.05f;
+    kf[3] = (1.f - s2) * -0.2f;
+    kf[4] = kf[5] = 0.f;
+  } else {
+    kf[0] = (1.f - s1) * 0.5f;
+    kf[1] = (1.f - s2) * float(1.0 / 42.0);
+    kf[2] = (1.f - s2) * float(1.0 / 6.0);
+    kf[3] = (1.f - s2) * float(-1.0 / 12.0);
+    kf[4] = (1.f - s2) * 0.25f;
+    kf[5] = (1.f - s2) * float(-1.0 / 7.0);
+  }
+  float Fr[D][VX];
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     if (A.force) {
-      VecIO<float, VX>::load(static_cast<const float *>(A.force) + a * A.plane + row0 + x0, F[a]);
+      VecIO<float, VX>::load(static_cast<const float *>(A.force) + a * A.plane + row0 + x0, Fr[a]);
     } else {
 #pragma unroll
-      for (int j = 0; j < VX; ++j) F[a][j] = 0.f;
+      for (int j = 0; j < VX; ++j) Fr[a][j] = 0.f;
     }
   }
-  const float s1 = float(A.s1), s2 = float(A.s2);
-  float Mnew[D + 2][VX];
+  T Mn[KM][NP];
 #pragma unroll
-  for (int j = 0; j < VX; ++j) {
-    float gn[D][Q], hn[Q], Fn[D], M[D + 2];
+  for (int q = 0; q < NP; ++q) {
+    // Every product that meets a sum is one fma (nothing is left for the
+    // compiler to contract, so scalar and pair lanes give the same bits).
+    T us[D], u[D], un[D], dif[D + 1][D], tr = splat<T>(0.f), usqS = splat<T>(0.f);
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int a = 0; a < D; ++a) {
+      T sm = G[a][0][q];
 #pragma unroll
-      for (int a = 0; a < D; ++a) gn[a][i] = g[a][i][j];
-      hn[i] = h[i][j];
-    }
-    if (MODE != MODE_STEP && active) write_fields<L, float>(A, n0 + j, N, gn, hn);
-    if (MODE == MODE_FIELDS) continue;
-#pragma unroll
-    for (int a = 0; a < D; ++a) Fn[a] = F[a][j];
-    collide_node<L, float>(gn, hn, A.with_rho != 0, Fn, s1, s2, M);
-    // store the non-equilibrium part against the moments just used
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-#pragma unroll
-      for (int a = 0; a < D; ++a) g[a][i][j] = (gn[a][i] - geq_m<L>(a + 1, i, M)) * scale;
-      h[i][j] = (hn[i] - geq_m<L>(0, i, M)) * scale;
+      for (int i = 1; i < Q; ++i) sm = vadd(sm, G[a][i][q]);
+      us[a] = sm;
+      u[a] = SC == 1.f ? sm : vmul(sm, splat<T>(INV));
+      un[a] = vsub(splat<T>(0.f), u[a]);
     }
 #pragma unroll
-    for (int k = 0; k < D + 2; ++k) Mnew[k][j] = M[k];
+    for (int a = 0; a <= D; ++a) {
+      if (a == D && !A.with_rho) break;
+#pragma unroll
+      for (int b = 0; b < D; ++b) dif[a][b] = vsub(G[a][dir_pos<L>(b)][q], G[a][dir_neg<L>(b)][q]);
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) {  // sum_i c_{i,a} G_{i,a} and SCALE |u|^2
+      tr = vadd(tr, dif[a][a]);
+      usqS = vfma(us[a], u[a], usqS);
+    }
+    // Eq. 3-15 (scaled): SCALE P' = (SCALE tr - SCALE |u|^2) / d
+    const T PS = vmul(vsub(tr, usqS), splat<T>(float(1.0 / D)));
+    const T P = SC == 1.f ? PS : vmul(PS, splat<T>(INV));
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      // m_b - m_b^eq with m_b^eq = SCALE (u_a u_b + [a = b] P') (Eq. 3-7a)
+      T Ef[D];
+#pragma unroll
+      for (int b = 0; b < D; ++b)
+        Ef[b] = a == b ? vsub(dif[a][b], vfma(us[a], u[b], PS)) : vfma(us[a], un[b], dif[a][b]);
+      T Fs;
+      float fl[LW];
+#pragma unroll
+      for (int e = 0; e < LW; ++e) fl[e] = Fr[a][LW * q + e];
+      to_lanes(Fs, fl);
+      Fs = vmul(Fs, splat<T>(SC));
+      const T Fw = vmul(Fs, splat<T>(float(L::w(1)))), Fw0 = vmul(Fs, splat<T>(float(L::w(0))));
+      T gq[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) gq[i] = G[a][i][q];
+      relax_encode<L, T>(gq, Ef, us[a], Fw, Fw0, kf);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) G[a][i][q] = gq[i];
+    }
+    T rr = splat<T>(0.f);
+    if (A.with_rho) {
+      T sm = G[D][0][q];
+#pragma unroll
+      for (int i = 1; i < Q; ++i) sm = vadd(sm, G[D][i][q]);
+      rr = SC == 1.f ? sm : vmul(sm, splat<T>(INV));
+      const T rs = vadd(sm, splat<T>(SC));  // SCALE (1 + rho'): m_b^eq = rs u_b
+      T Ef[D];
+#pragma unroll
+      for (int b = 0; b < D; ++b) Ef[b] = vfma(rs, un[b], dif[D][b]);
+      T gq[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) gq[i] = G[D][i][q];
+      relax_encode<L, T>(gq, Ef, sm, splat<T>(0.f), splat<T>(0.f), kf);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) G[D][i][q] = gq[i];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) Mn[a][q] = u[a];
+    Mn[D][q] = P;
+    Mn[D + 1][q] = rr;
   }
-  if (MODE == MODE_FIELDS || !active) return;
+
   TS *__restrict__ fout = static_cast<TS *>(A.fout);
   float *__restrict__ mout = static_cast<float *>(A.mout);
 #pragma unroll
-  for (int a = 0; a < D; ++a)
+  for (int s = 0; s <= D; ++s) {
+    const int alpha = s == D ? 0 : s + 1;
+    if (alpha == 0 && !A.with_rho) break;
+    TS *base = fout + (long long)(alpha == 0 ? 0 : a1 + alpha - 1) * Q * A.plane + row0 + x0;
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-      VecIO<TS, VX>::store(fout + ((long long)(a1 + a) * Q + i) * A.plane + row0 + x0, g[a][i]);
-  if (A.with_rho)
+    for (int i = 0; i < Q; ++i) {
+      float v[VX];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) VecIO<TS, VX>::store(fout + (long long)i * A.plane + row0 + x0, h[i]);
+      for (int q = 0; q < NP; ++q) from_lanes(v + LW * q, G[s][i][q]);
+      VecIO<TS, VX>::store(base + (long long)i * A.plane, v);
+    }
+  }
 #pragma unroll
-  for (int k = 0; k < D + 2; ++k)
-    if (k < K) VecIO<float, VX>::store(mout + (long long)k * A.plane + row0 + x0, Mnew[k]);
+  for (int k = 0; k < KM; ++k) {
+    if (k < K) {
+      float v[VX];
+#pragma unroll
+      for (int q = 0; q < NP; ++q) from_lanes(v + LW * q, Mn[k][q]);
+      VecIO<float, VX>::store(mout + (long long)k * A.plane + row0 + x0, v);
+    }
+  }
 }
 
 // Initial state f = f^eq(P, u) in pull form for this codec: moments
