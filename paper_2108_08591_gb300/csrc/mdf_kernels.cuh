@@ -19,6 +19,7 @@
 
 #include "mdf_internal.h"
 #include "mdf_lattice.cuh"
+#include "mdf_f64.cuh"
 
 namespace mdf {
 
@@ -76,7 +77,8 @@ __device__ __forceinline__ void pull_set(const DevArgs &A, const TS *__restrict_
 // so J (~u^2) and u u + P' carry absolute rounding ~1e-7 |J| while the
 // first moment of f^ne they differ by is ~1e-3..1e-1 |J| at the workloads'
 // sizes; the FP32 storage rounding of g dominates the error.  (GB300's FP64
-// throughput is too low for FP64 arithmetic here to stay HBM-bound.)
+// throughput is too low for FP64 arithmetic here to stay HBM-bound; the
+// widening to FP64 is built on the integer pipe, leaving two FP64 adds.)
 template <class L, class TC>
 __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long long N,
                                              const TC (&gv)[L::D][L::Q], const TC (&h)[L::Q]) {
@@ -103,15 +105,15 @@ __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long
 #pragma unroll
   for (int a = 0; a < D; ++a) { tr += J[a][a]; usq += u[a] * u[a]; }
   const TC Pp = (tr - usq) * TC(1.0 / D);  // Eq. 3-15, P' = P - P0, R = 0
-  if (A.P) A.P[n] = 1.0 + (double)Pp;
+  if (A.P) A.P[n] = 1.0 + widen_f32(Pp);
   if (A.u)
 #pragma unroll
-    for (int a = 0; a < D; ++a) A.u[a * N + n] = (double)u[a];
+    for (int a = 0; a < D; ++a) A.u[a * N + n] = widen_f32(u[a]);
   if (A.rho && A.with_rho) {
     TC s = TC(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) s += h[i];
-    A.rho[n] = 1.0 + (double)s;
+    A.rho[n] = 1.0 + widen_f32(s);
   }
   if (!(A.G || A.div || A.S || A.sigma || A.omega)) return;
   // first moment of f^ne: sum_i c_{i,b} (f - f^eq)_{i,a} = J - u_a u_b - P' delta_ab
@@ -125,12 +127,12 @@ __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
-      for (int b = 0; b < D; ++b) A.G[(a * D + b) * N + n] = (double)(pref * mne[a][b]);
+      for (int b = 0; b < D; ++b) A.G[(a * D + b) * N + n] = widen_f32(pref * mne[a][b]);
   if (A.div) {
     TC s = TC(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) s += mne[a][a];
-    A.div[n] = (double)(pref * s);  // Eq. 3-16a
+    A.div[n] = widen_f32(pref * s);  // Eq. 3-16a
   }
   if (A.S || A.sigma) {
     int k = 0;
@@ -141,17 +143,17 @@ __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long
 #pragma unroll
       for (int b = a; b < D; ++b, ++k) {
         const TC sym = mne[a][b] + mne[b][a];
-        if (A.S) A.S[k * N + n] = (double)(half_pref * sym);  // Eq. 3-17
-        if (A.sigma) A.sigma[k * N + n] = (double)(sig * sym);
+        if (A.S) A.S[k * N + n] = widen_f32(half_pref * sym);  // Eq. 3-17
+        if (A.sigma) A.sigma[k * N + n] = widen_f32(sig * sym);
       }
   }
   if (A.omega) {  // Eq. 3-18, 3-19: omega = curl u
     if (D == 2) {
-      A.omega[n] = (double)(pref * (mne[1][0] - mne[0][1]));
+      A.omega[n] = widen_f32(pref * (mne[1][0] - mne[0][1]));
     } else {
-      A.omega[n] = (double)(pref * (mne[2][1] - mne[1][2]));
-      A.omega[N + n] = (double)(pref * (mne[0][2] - mne[2][0]));
-      A.omega[2 * N + n] = (double)(pref * (mne[1][0] - mne[0][1]));
+      A.omega[n] = widen_f32(pref * (mne[2][1] - mne[1][2]));
+      A.omega[N + n] = widen_f32(pref * (mne[0][2] - mne[2][0]));
+      A.omega[2 * N + n] = widen_f32(pref * (mne[1][0] - mne[0][1]));
     }
   }
 }
