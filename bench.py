@@ -443,13 +443,22 @@ def run_cavities(args):
     stream = torch.cuda.Stream()
     b = CavityBatch(sides, Res, lid_speed=0.1, stream=stream)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    b.step(args.warmup * 100)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    b.step(args.steps * 100)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / (args.steps * 100)
+
+    def timed():
+        b.step(args.warmup * 100)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        b.step(args.steps * 100)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / (args.steps * 100)
+
+    sched_default = b.schedule()
+    ms_default = timed()
+    t0 = time.perf_counter()
+    sched = b.autotune(reps=20)  # untimed: chooses the persistent kernel's launch shape
+    tune_s = time.perf_counter() - t0
+    ms = timed()
     mlups = nodes.sum() / (ms / 1e3) / 1e6
     peak, kind = _peaks()
     b.init()
@@ -462,7 +471,10 @@ def run_cavities(args):
         "ms_per_step": ms, "nodes": int(nodes.sum()), "cavities": len(sides),
         "roofline": {"bound": "hbm", "achieved": mlups * 120 / 1e3, "peak": peak, "unit": "GB/s",
                      "frac": mlups * 120 / 1e3 / peak, "peak_source": f"{kind} hbm_gbs",
-                     "kernel": "k_batch_chunk<D2Q5> (persistent, cooperative)"},
+                     "kernel": f"k_batch_chunk<D2Q5,{sched['threads']},{sched['sched']}> "
+                               "(persistent, cooperative)"},
+        "schedule": {"tuned": sched, "default": sched_default, "autotune_s": tune_s,
+                     "default_mlups": float(nodes.sum() / (ms_default / 1e3) / 1e6)},
         "to_steady": {"tol": 1e-8, "max_steps": args.max_steps, "seconds": run_s,
                       "aggregate_mlups": float((steps * nodes).sum()) / run_s / 1e6,
                       "status": {names[k]: v for k, v in collections.Counter(status.tolist()).items()}},

@@ -305,6 +305,25 @@ mdf_status mdf_batch_info(mdf_batch_t b, long long *nodes, int *tiles, int *grid
  * state is then undefined until the next mdf_batch_init. */
 mdf_status mdf_batch_set_timeout(mdf_batch_t b, long long cycles);
 
+/* mdf_batch_set_schedule -- launch shape of the persistent step kernel:
+ * `threads` per block in {32, 64, 128} (each thread updates 128 / threads
+ * nodes of a 128-node tile, `threads` apart), `grid` co-resident blocks (0:
+ * the most that fit, MDF_EINVAL above that) and `sched` 0 (live tiles dealt
+ * round-robin to the blocks) or 1 (one contiguous run of tiles per block).
+ * Every schedule computes the same bits; only the speed differs. */
+mdf_status mdf_batch_set_schedule(mdf_batch_t b, int threads, int grid, int sched);
+
+/* mdf_batch_get_schedule -- the launch shape in use (any pointer may be NULL). */
+mdf_status mdf_batch_get_schedule(mdf_batch_t b, int *threads, int *grid, int *sched);
+
+/* mdf_batch_autotune -- time `reps` (rounded up to even; < 2: 20) steps of
+ * every schedule candidate (threads 128 / 64 / 32, both tile orders, grids
+ * of 1, 2, 3, 4, 6, 8, 12, 16 blocks per SM up to the co-resident limit) on
+ * the current state with all cavities live, keep the fastest and restore
+ * the state (bit for bit; step counts and statuses are not touched).
+ * Needs one extra population pool of device memory while it runs. */
+mdf_status mdf_batch_autotune(mdf_batch_t b, int reps, int *threads, int *grid, int *sched);
+
 /* mdf_batch_last_error -- message of the last failure (NULL: last create). */
 const char *mdf_batch_last_error(mdf_batch_t b);
 

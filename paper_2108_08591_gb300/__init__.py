@@ -290,6 +290,24 @@ class CavityBatch:
         """Grid-barrier spin limit in SM clock cycles (default ~2 s)."""
         self._check(self._lib.mdf_batch_set_timeout(self._h, int(cycles)))
 
+    def set_schedule(self, threads: int = 128, grid: int = 0, sched: int = 0):
+        """Launch shape of the persistent step kernel (see mdf_batch_set_schedule)."""
+        self._check(self._lib.mdf_batch_set_schedule(self._h, int(threads), int(grid), int(sched)))
+
+    def schedule(self) -> Dict[str, int]:
+        v = np.zeros(3, np.int32)
+        self._check(self._lib.mdf_batch_get_schedule(self._h, v[0:].ctypes.data, v[1:].ctypes.data,
+                                                     v[2:].ctypes.data))
+        return {"threads": int(v[0]), "grid": int(v[1]), "sched": int(v[2])}
+
+    def autotune(self, reps: int = 20) -> Dict[str, int]:
+        """Time every schedule on the current state, keep the fastest, restore
+        the state; returns the chosen {threads, grid, sched}."""
+        v = np.zeros(3, np.int32)
+        self._check(self._lib.mdf_batch_autotune(self._h, int(reps), v[0:].ctypes.data, v[1:].ctypes.data,
+                                                 v[2:].ctypes.data))
+        return {"threads": int(v[0]), "grid": int(v[1]), "sched": int(v[2])}
+
     def fields_host(self, cavity: int, names: Iterable[str] = ("P", "u")) -> Dict[str, np.ndarray]:
         N = int(self.sides[cavity]) ** self.d
         shapes = field_shapes(self.d, N)

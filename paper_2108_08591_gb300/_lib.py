@@ -86,6 +86,10 @@ SIGNATURES = {
     "mdf_batch_fields": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(Fields)]),
     "mdf_batch_info": (ctypes.c_int, [H, DP, DP, DP]),
     "mdf_batch_set_timeout": (ctypes.c_int, [H, ctypes.c_longlong]),
+    "mdf_batch_set_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "mdf_batch_get_schedule": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "mdf_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p]),
     "mdf_batch_last_error": (ctypes.c_char_p, [H]),
     "mdf_ws_create": (ctypes.c_int, [ctypes.POINTER(H), ctypes.c_int, ctypes.c_int, ctypes.c_int, DP,
                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,

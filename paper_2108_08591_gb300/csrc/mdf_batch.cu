@@ -32,13 +32,14 @@ namespace mdf {
 constexpr int kTile = 128;  // nodes per tile = threads per block
 
 struct CavParam {
-  int N;            // nodes per side
-  int tile0;        // first tile of this cavity
-  int ntiles;       // tiles of this cavity
+  int N;                   // nodes per side
+  int tile0;               // first tile of this cavity
+  int ntiles;              // tiles of this cavity
   int pad;
-  long long base;   // first pool node of this cavity
+  long long base;          // first pool node of this cavity
   float s1, s2;
   double s1d;
+  unsigned long long mN;   // ceil(2^64 / N): floor(k / N) = mulhi(k, mN) for k < 2^32
 };
 
 enum CavStatus { CAV_RUNNING = 0, CAV_CONVERGED = 1, CAV_DIVERGED = 2, CAV_MAXSTEPS = 3 };
@@ -115,11 +116,22 @@ __device__ __forceinline__ uint8_t box_mask(const int (&p)[3], int N) {
   return m;
 }
 
+// (x, y[, z]) of local node k = x + N (y + N z).  Division by N is a
+// 64-bit multiply-high by mN = ceil(2^64 / N): with mN N = 2^64 + r, 0 <= r
+// < N, the product k mN / 2^64 exceeds k / N by k r / (N 2^64) < 1 / N for
+// every k < 2^32, so its floor is floor(k / N) exactly.
 template <class L>
-__device__ __forceinline__ void node_pos(int k, int N, int (&p)[3]) {
-  p[0] = k % N;
-  p[1] = (k / N) % N;
-  p[2] = L::D == 3 ? k / (N * N) : 0;
+__device__ __forceinline__ void node_pos(int k, const CavParam &C, int (&p)[3]) {
+  const unsigned q1 = (unsigned)__umul64hi((unsigned long long)(unsigned)k, C.mN);
+  p[0] = k - (int)q1 * C.N;
+  if (L::D == 3) {
+    const unsigned q2 = (unsigned)__umul64hi((unsigned long long)q1, C.mN);
+    p[1] = (int)q1 - (int)q2 * C.N;
+    p[2] = (int)q2;
+  } else {
+    p[1] = (int)q1;
+    p[2] = 0;
+  }
 }
 
 template <class L>
@@ -134,7 +146,7 @@ __device__ __forceinline__ void batch_pull(const BatchArgs &B, const float *fin,
                                            long long &idx) {
   constexpr int D = L::D, Q = L::Q;
   int p[3];
-  node_pos<L>(k, C.N, p);
+  node_pos<L>(k, C, p);
   idx = C.base + k;
   const uint8_t m = box_mask<L>(p, C.N);
   long long src[Q];
@@ -150,37 +162,59 @@ __device__ __forceinline__ void batch_pull(const BatchArgs &B, const float *fin,
   if (B.with_rho) pull_set_p<L, float, true>(fin, B.tot, 0, idx, src, m, B.lid_u, h);
 }
 
+// One update of local node k of cavity C: pull from fin, collide, store to
+// fout; with save, also store the velocity it pulled (for the residual).
+template <class L>
+__device__ __forceinline__ void batch_update_node(const BatchArgs &B, const float *fin, float *fout,
+                                                  const CavParam &C, int k, bool save) {
+  constexpr int D = L::D, Q = L::Q;
+  float g[D][Q], h[Q], F[D] = {}, M[D + 2];
+  long long idx;
+  batch_pull<L>(B, fin, C, k, g, h, idx);
+  collide_node<L, float>(g, h, B.with_rho != 0, F, C.s1, C.s2, M);
+  if (save)
+#pragma unroll
+    for (int a = 0; a < D; ++a) B.usave[a * B.tot + idx] = M[a];
+  const long long setstride = (long long)Q * B.tot;
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+      __stcs(fout + (long long)(B.with_rho + a) * setstride + (long long)i * B.tot + idx, g[a][i]);
+  if (B.with_rho)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) __stcs(fout + (long long)i * B.tot + idx, h[i]);
+}
+
 // `steps` updates of every running cavity; buffer `cur` holds the current
 // state.  With save_first, the first update stores the velocity it pulled
 // (u at the start of the period) for the residual pass.
-template <class L>
-__global__ void __launch_bounds__(kTile) k_batch_chunk(BatchArgs B, int cur, int steps, int save_first) {
-  constexpr int D = L::D, Q = L::Q;
+//
+// Schedule (chosen by mdf_batch_autotune): T threads per block, each thread
+// updating kTile / T nodes of a tile, T apart (so every access of a warp
+// stays on consecutive nodes); blocks take live tiles round-robin (SCHED 0)
+// or one contiguous run of the live list each (SCHED 1).  Every schedule
+// does the same arithmetic per node, so all give the same bits.
+template <class L, int T, int SCHED>
+__global__ void __launch_bounds__(T) k_batch_chunk(BatchArgs B, int cur, int steps, int save_first) {
+  constexpr int PER = kTile / T;
   const int nl = *B.n_live;
+  const int t0 = SCHED == 0 ? (int)blockIdx.x : (int)((long long)nl * blockIdx.x / gridDim.x);
+  const int t1 = SCHED == 0 ? nl : (int)((long long)nl * (blockIdx.x + 1) / gridDim.x);
+  const int dt = SCHED == 0 ? (int)gridDim.x : 1;
   for (int s = 0; s < steps; ++s) {
     const float *fin = B.f[(cur + s) & 1];
     float *fout = B.f[(cur + s + 1) & 1];
-    for (int t = blockIdx.x; t < nl; t += gridDim.x) {
+    const bool save = save_first && s == 0;
+    for (int t = t0; t < t1; t += dt) {
       const int tile = B.live[t];
       const CavParam C = B.cav[B.tile_cav[tile]];
-      const int k = (tile - C.tile0) * kTile + threadIdx.x;
-      if (k >= node_count<L>(C.N)) continue;
-      float g[D][Q], h[Q], F[D] = {}, M[D + 2];
-      long long idx;
-      batch_pull<L>(B, fin, C, k, g, h, idx);
-      collide_node<L, float>(g, h, B.with_rho != 0, F, C.s1, C.s2, M);
-      if (save_first && s == 0)
+      const long long count = node_count<L>(C.N);
 #pragma unroll
-        for (int a = 0; a < D; ++a) B.usave[a * B.tot + idx] = M[a];
-      const long long setstride = (long long)Q * B.tot;
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int i = 0; i < Q; ++i)
-          __stcs(fout + (long long)(B.with_rho + a) * setstride + (long long)i * B.tot + idx, g[a][i]);
-      if (B.with_rho)
-#pragma unroll
-        for (int i = 0; i < Q; ++i) __stcs(fout + (long long)i * B.tot + idx, h[i]);
+      for (int r = 0; r < PER; ++r) {
+        const int k = (tile - C.tile0) * kTile + r * T + (int)threadIdx.x;
+        if (k < count) batch_update_node<L>(B, fin, fout, C, k, save);
+      }
     }
     if (s + 1 < steps && !grid_barrier(B)) return;
   }
@@ -281,7 +315,7 @@ __global__ void __launch_bounds__(kTile) k_batch_init(BatchArgs B, int cur, int 
   const long long NN = node_count<L>(C.N);
   if (n >= NN) return;
   int p[3];
-  node_pos<L>((int)n, C.N, p);
+  node_pos<L>((int)n, C, p);
   const uint8_t m = box_mask<L>(p, C.N);
   DevArgs A;  // only the fields geq() reads
   A.Pin = P;
@@ -332,7 +366,9 @@ struct mdf_batch_s {
   std::vector<CavParam> cav;
   BatchArgs B{};
   int cur = 0;
-  int grid = 0;  // blocks of the persistent kernel
+  int grid = 0;      // blocks of the persistent kernel
+  int threads = 128; // threads per block (kTile / threads nodes per thread)
+  int sched = 0;     // 0: tiles round-robin over blocks, 1: contiguous runs
   int *host_live = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_period = 0, graph_cur = 0;
@@ -363,18 +399,91 @@ mdf_status bfail(mdf_batch_t b, mdf_status st, const char *fmt, ...) {
       return bfail((b), MDF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));     \
   } while (0)
 
-template <class L>
-cudaError_t launch_chunk(mdf_batch_t b, int steps, int save_first) {
+template <class L, int T, int S>
+cudaError_t launch_chunk_t(mdf_batch_t b, int steps, int save_first) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(b->grid);
-  cfg.blockDim = dim3(kTile);
+  cfg.blockDim = dim3(T);
   cfg.stream = b->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_batch_chunk<L>, b->B, b->cur, steps, save_first);
+  return cudaLaunchKernelEx(&cfg, k_batch_chunk<L, T, S>, b->B, b->cur, steps, save_first);
+}
+
+template <class L>
+cudaError_t launch_chunk(mdf_batch_t b, int steps, int save_first) {
+  const int key = b->threads * 2 + b->sched;
+  switch (key) {
+    case 256: return launch_chunk_t<L, 128, 0>(b, steps, save_first);
+    case 257: return launch_chunk_t<L, 128, 1>(b, steps, save_first);
+    case 128: return launch_chunk_t<L, 64, 0>(b, steps, save_first);
+    case 129: return launch_chunk_t<L, 64, 1>(b, steps, save_first);
+    case 64: return launch_chunk_t<L, 32, 0>(b, steps, save_first);
+    case 65: return launch_chunk_t<L, 32, 1>(b, steps, save_first);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Co-resident blocks per SM of the step kernel with this schedule.
+template <class L, int T, int S>
+cudaError_t occupancy_t(int *per) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_batch_chunk<L, T, S>, T, 0);
+}
+cudaError_t occupancy(int d, int threads, int sched, int *per) {
+  const int key = threads * 2 + sched;
+  if (d == 2) {
+    switch (key) {
+      case 256: return occupancy_t<D2Q5, 128, 0>(per);
+      case 257: return occupancy_t<D2Q5, 128, 1>(per);
+      case 128: return occupancy_t<D2Q5, 64, 0>(per);
+      case 129: return occupancy_t<D2Q5, 64, 1>(per);
+      case 64: return occupancy_t<D2Q5, 32, 0>(per);
+      case 65: return occupancy_t<D2Q5, 32, 1>(per);
+    }
+  } else {
+    switch (key) {
+      case 256: return occupancy_t<D3Q7, 128, 0>(per);
+      case 257: return occupancy_t<D3Q7, 128, 1>(per);
+      case 128: return occupancy_t<D3Q7, 64, 0>(per);
+      case 129: return occupancy_t<D3Q7, 64, 1>(per);
+      case 64: return occupancy_t<D3Q7, 32, 0>(per);
+      case 65: return occupancy_t<D3Q7, 32, 1>(per);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
+// Largest persistent grid for a schedule: co-resident blocks on every SM,
+// at most one block per work unit (tile).
+cudaError_t max_grid(mdf_batch_t b, int threads, int sched, int *grid) {
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = occupancy(b->d, threads, sched, &per);
+  if (e == cudaSuccess) *grid = std::max(1, std::min(sms * per, b->ntiles));
+  return e;
+}
+
+void drop_graph(mdf_batch_t b) {
+  if (b->graph) {
+    cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+  }
+}
+
+// All tiles live (plain stepping and tuning) and a cleared barrier.
+mdf_status all_live(mdf_batch_t b) {
+  std::vector<int> live(b->ntiles);
+  for (int t = 0; t < b->ntiles; ++t) live[t] = t;
+  BCU(b, cudaMemcpyAsync(b->B.live, live.data(), sizeof(int) * b->ntiles, cudaMemcpyHostToDevice, b->stream));
+  BCU(b, cudaMemcpyAsync(b->B.n_live, &b->ntiles, sizeof(int), cudaMemcpyHostToDevice, b->stream));
+  BCU(b, cudaMemsetAsync(b->B.err, 0, sizeof(int), b->stream));
+  BCU(b, cudaMemsetAsync(b->B.bar, 0, sizeof(unsigned int) * 2, b->stream));
+  BCU(b, cudaStreamSynchronize(b->stream));  // `live` leaves scope
+  return MDF_OK;
 }
 
 template <class L>
@@ -437,6 +546,7 @@ mdf_status mdf_batch_create(mdf_batch_t *out, int d, int n, const int *side, con
     C.s1 = (float)s1;
     C.s2 = (float)s2;
     C.s1d = s1;
+    C.mN = ~0ull / (unsigned long long)side[c] + 1ull;  // ceil(2^64 / N)
     b->cav.push_back(C);
     tile0 += C.ntiles;
     base += (long long)C.ntiles * kTile;
@@ -480,15 +590,7 @@ mdf_status mdf_batch_create(mdf_batch_t *out, int d, int n, const int *side, con
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((void *)B.tile_cav, tile_cav.data(), sizeof(int) * b->ntiles,
                         cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) {
-    int dev = 0, sms = 0, per = 0;
-    e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-      e = d == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_chunk<D2Q5>, kTile, 0)
-                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_chunk<D3Q7>, kTile, 0);
-    b->grid = std::max(1, std::min(sms * per, b->ntiles));
-  }
+  if (e == cudaSuccess) e = max_grid(b, b->threads, b->sched, &b->grid);
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -628,13 +730,8 @@ mdf_status mdf_batch_run(mdf_batch_t b, double tol, long long max_steps, int che
 mdf_status mdf_batch_step(mdf_batch_t b, long long n) {
   if (!b) return MDF_EINVAL;
   if (n < 0) return bfail(b, MDF_EINVAL, "n < 0");
-  // all tiles live for plain stepping
-  std::vector<int> live(b->ntiles);
-  for (int t = 0; t < b->ntiles; ++t) live[t] = t;
-  BCU(b, cudaMemcpyAsync(b->B.live, live.data(), sizeof(int) * b->ntiles, cudaMemcpyHostToDevice, b->stream));
-  BCU(b, cudaMemcpyAsync(b->B.n_live, &b->ntiles, sizeof(int), cudaMemcpyHostToDevice, b->stream));
-  BCU(b, cudaMemsetAsync(b->B.err, 0, sizeof(int), b->stream));
-  BCU(b, cudaMemsetAsync(b->B.bar, 0, sizeof(unsigned int) * 2, b->stream));
+  mdf_status st = all_live(b);
+  if (st != MDF_OK) return st;
   const int chunk = 1 << 20;
   while (n > 0) {
     const int s = (int)std::min<long long>(n, chunk);
@@ -705,10 +802,118 @@ mdf_status mdf_batch_set_timeout(mdf_batch_t b, long long cycles) {
   if (!b) return MDF_EINVAL;
   if (cycles < 0) return bfail(b, MDF_EINVAL, "timeout must be >= 0 cycles");
   b->B.timeout = cycles;
-  if (b->graph) {  // the captured kernels hold the old value
-    cudaGraphExecDestroy(b->graph);
-    b->graph = nullptr;
+  drop_graph(b);  // the captured kernels hold the old value
+  return MDF_OK;
+}
+
+mdf_status mdf_batch_set_schedule(mdf_batch_t b, int threads, int grid, int sched) {
+  if (!b) return MDF_EINVAL;
+  if (threads != 32 && threads != 64 && threads != 128)
+    return bfail(b, MDF_EINVAL, "threads per block must be 32, 64 or 128 (got %d)", threads);
+  if (sched != 0 && sched != 1) return bfail(b, MDF_EINVAL, "schedule must be 0 or 1 (got %d)", sched);
+  int gmax = 0;
+  BCU(b, max_grid(b, threads, sched, &gmax));
+  if (grid < 0 || grid > gmax)
+    return bfail(b, MDF_EINVAL, "grid %d outside 0 .. %d (co-resident blocks)", grid, gmax);
+  b->threads = threads;
+  b->sched = sched;
+  b->grid = grid ? grid : gmax;
+  drop_graph(b);  // the captured launch holds the old shape
+  return MDF_OK;
+}
+
+mdf_status mdf_batch_get_schedule(mdf_batch_t b, int *threads, int *grid, int *sched) {
+  if (!b) return MDF_EINVAL;
+  if (threads) *threads = b->threads;
+  if (grid) *grid = b->grid;
+  if (sched) *sched = b->sched;
+  return MDF_OK;
+}
+
+mdf_status mdf_batch_autotune(mdf_batch_t b, int reps, int *threads_out, int *grid_out, int *sched_out) {
+  if (!b) return MDF_EINVAL;
+  if (reps < 2) reps = 20;
+  reps += reps & 1;  // an even chunk ends in the current buffer
+  const int nsets = b->d + b->with_rho, Q = b->d == 2 ? 5 : 7;
+  const size_t popb = sizeof(float) * (size_t)nsets * Q * (size_t)b->tot;
+  float *save = nullptr;
+  BCU(b, cudaMallocAsync(&save, popb, b->stream));
+  BCU(b, cudaMemcpyAsync(save, b->B.f[b->cur], popb, cudaMemcpyDeviceToDevice, b->stream));
+  mdf_status st = all_live(b);
+  int dev = 0, sms = 1;
+  if (st == MDF_OK && (cudaGetDevice(&dev) != cudaSuccess ||
+                       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess))
+    st = bfail(b, MDF_ECUDA, "autotune: device query failed");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (st == MDF_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+    st = bfail(b, MDF_ECUDA, "autotune: event creation failed");
+  const int old_threads = b->threads, old_sched = b->sched, old_grid = b->grid;
+  int best_threads = old_threads, best_sched = old_sched, best_grid = old_grid;
+  float best = 1e30f;
+  const int threads_c[3] = {128, 64, 32};
+  const int mult_c[8] = {1, 2, 3, 4, 6, 8, 12, 16};
+  bool warmed = false;
+  for (int ti = 0; ti < 3 && st == MDF_OK; ++ti)
+    for (int sc = 0; sc < 2 && st == MDF_OK; ++sc) {
+      int gmax = 0;
+      if (max_grid(b, threads_c[ti], sc, &gmax) != cudaSuccess) {
+        st = bfail(b, MDF_ECUDA, "autotune: occupancy query failed");
+        break;
+      }
+      int last = 0;
+      for (int mi = 0; mi < 8 && st == MDF_OK; ++mi) {
+        const int g = std::min(gmax, mult_c[mi] * sms);
+        if (g == last) continue;
+        last = g;
+        b->threads = threads_c[ti];
+        b->sched = sc;
+        b->grid = g;
+        cudaError_t e = cudaMemsetAsync(b->B.bar, 0, sizeof(unsigned int) * 2, b->stream);
+        if (e == cudaSuccess && !warmed) {
+          e = b->d == 2 ? launch_chunk<D2Q5>(b, 2, 0) : launch_chunk<D3Q7>(b, 2, 0);
+          warmed = true;
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = b->d == 2 ? launch_chunk<D2Q5>(b, reps, 0) : launch_chunk<D3Q7>(b, reps, 0);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        int err = 0;
+        if (e == cudaSuccess) e = cudaMemcpy(&err, b->B.err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+          st = bfail(b, MDF_ECUDA, "autotune: %s", cudaGetErrorString(e));
+        } else if (err) {
+          st = bfail(b, MDF_ETIMEOUT, "autotune: grid barrier timed out");
+        } else if (ms < best) {
+          best = ms;
+          best_threads = b->threads;
+          best_sched = b->sched;
+          best_grid = b->grid;
+        }
+      }
+    }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  // the tuning steps advanced the state: put it back
+  cudaError_t e = cudaMemcpyAsync(b->B.f[b->cur], save, popb, cudaMemcpyDeviceToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaFreeAsync(save, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess && st == MDF_OK) st = bfail(b, MDF_ECUDA, "autotune restore: %s", cudaGetErrorString(e));
+  if (st == MDF_OK) {
+    b->threads = best_threads;
+    b->sched = best_sched;
+    b->grid = best_grid;
+  } else {
+    b->threads = old_threads;
+    b->sched = old_sched;
+    b->grid = old_grid;
   }
+  drop_graph(b);
+  if (st != MDF_OK) return st;
+  if (threads_out) *threads_out = best_threads;
+  if (grid_out) *grid_out = best_grid;
+  if (sched_out) *sched_out = best_sched;
   return MDF_OK;
 }
 

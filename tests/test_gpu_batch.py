@@ -130,3 +130,67 @@ def test_barrier_timeout_is_reported_not_hung():
     b.step(20)  # usable again
     assert np.isfinite(b.fields_host(0, ("u",))["u"]).all()
     b.close()
+
+
+@pytest.mark.parametrize("d,sides,Res", [(2, [17, 65, 40], [100.0, 400.0, 1000.0]),
+                                         (3, [10, 13], [50.0, 200.0])])
+def test_every_schedule_gives_the_same_bits(d, sides, Res):
+    """Threads per block 128 / 64 / 32 (1, 2, 4 nodes per thread), both tile
+    orders, a one-block and the largest grid: the same arithmetic per node,
+    so the same bits after 40 updates (several barriers per chunk)."""
+    from paper_2108_08591_gb300 import CavityBatch
+    names = ("P", "u", "G")
+    ref = None
+    for threads in (128, 64, 32):
+        for sched in (0, 1):
+            for grid in (1, 0):
+                b = CavityBatch(sides, Res, lid_speed=U, d=d)
+                b.set_schedule(threads, grid, sched)
+                got = b.schedule()
+                assert got["threads"] == threads and got["sched"] == sched
+                assert got["grid"] >= 1 and (grid == 0 or got["grid"] == grid)
+                b.step(40)
+                out = [b.fields_host(c, names) for c in range(len(sides))]
+                b.close()
+                if ref is None:
+                    ref = out
+                    continue
+                for c in range(len(sides)):
+                    for k in names:
+                        assert np.array_equal(ref[c][k], out[c][k]), (threads, sched, grid, c, k)
+
+
+def test_autotune_keeps_the_state_and_the_bits():
+    from paper_2108_08591_gb300 import CavityBatch
+    sides, Res = [33, 48, 65], [200.0, 500.0, 800.0]
+    a = CavityBatch(sides, Res, lid_speed=U)
+    b = CavityBatch(sides, Res, lid_speed=U)
+    for x in (a, b):
+        x.step(30)
+    before = [b.fields_host(c, ("P", "u")) for c in range(3)]
+    best = b.autotune(reps=6)
+    assert best == b.schedule()
+    assert best["threads"] in (32, 64, 128) and best["sched"] in (0, 1) and best["grid"] >= 1
+    after = [b.fields_host(c, ("P", "u")) for c in range(3)]
+    for c in range(3):
+        for k in ("P", "u"):
+            assert np.array_equal(before[c][k], after[c][k]), (c, k)
+    a.step(50)
+    b.step(50)
+    for c in range(3):
+        fa, fb = a.fields_host(c, ("u",)), b.fields_host(c, ("u",))
+        assert np.array_equal(fa["u"], fb["u"]), c
+    steps, status, _ = b.run(tol=1e-5, max_steps=4000, check_every=100)
+    assert (steps > 0).all()
+    a.close()
+    b.close()
+
+
+def test_schedule_rejects_bad_arguments():
+    from paper_2108_08591_gb300 import CavityBatch
+    from paper_2108_08591_gb300._lib import MdfError
+    b = CavityBatch([17], [100.0], lid_speed=U)
+    for args in ((96, 0, 0), (128, 0, 2), (128, -1, 0), (128, 10 ** 7, 0)):
+        with pytest.raises(MdfError, match="EINVAL"):
+            b.set_schedule(*args)
+    b.close()
