@@ -171,9 +171,10 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
 
 
-def cpu_oracle_sample(steps: int = 2, warmup: int = 1):
+def cpu_oracle_sample(steps: int = 40, warmup: int = 1):
     """Time the FP64 CPU oracle, as it stands, on the benchmark workload:
-    the full 4096^2 lattice, `steps` timed updates after `warmup`."""
+    the full 4096^2 lattice, `steps` timed updates after `warmup` (about 16 s
+    of work on 16 host cores)."""
     import oracle
     import synth
     P, u = synth.tg_plus_modes(N_GRID, U0=0.01, seed=2108)
