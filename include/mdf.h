@@ -278,6 +278,16 @@ void mdf_batch_destroy(mdf_batch_t b);
  * u[d][N^d] FP64 in `where` memory, or the rest state when P = u = NULL. */
 mdf_status mdf_batch_init(mdf_batch_t b, int cavity, const double *P, const double *u, int where);
 
+/* mdf_batch_seed -- as mdf_batch_init; with neq = 1 (P and u required) the
+ * velocity sets also get the first-order non-equilibrium part of the seed,
+ * f^ne_i = -(w_i / s1) [(c_i . grad) u_alpha - c_{i,alpha} div u / d] (the
+ * Chapman-Enskog term whose first moment Eq. 3-16 maps back to grad u, made
+ * traceless so that Eq. 3-15 still returns P), with grad u by central
+ * differences of u and ghost values 2 u_wall - u beyond the walls.  The
+ * initial state then has the seed's u and P, and its Eq. 3-16 gradient is
+ * the traceless part of that finite-difference gradient. */
+mdf_status mdf_batch_seed(mdf_batch_t b, int cavity, const double *P, const double *u, int where, int neq);
+
 /* mdf_batch_run -- advance every cavity until its residual
  * r = ||u^n - u^{n-R}||_2 / (R ||u^n||_2), the mean per-step relative change
  * of u over the check period R = check_every (even), computed in FP64, drops

@@ -265,11 +265,13 @@ class CavityBatch:
         except Exception:
             pass
 
-    def init(self, cavity: int = -1, P=None, u=None):
-        """Rest state (P = u = None) or f = f^eq(P, u) for one cavity."""
+    def init(self, cavity: int = -1, P=None, u=None, neq: bool = False):
+        """Rest state (P = u = None) or f = f^eq(P, u) for one cavity; with
+        neq, plus the non-equilibrium part of the seed's velocity gradient
+        (see mdf_batch_seed)."""
         dev = P is not None and _is_device(P)
-        self._check(self._lib.mdf_batch_init(self._h, int(cavity), _ptr(P), _ptr(u),
-                                             DEVICE if dev else HOST))
+        self._check(self._lib.mdf_batch_seed(self._h, int(cavity), _ptr(P), _ptr(u),
+                                             DEVICE if dev else HOST, int(bool(neq))))
 
     def run(self, tol: float = 1e-8, max_steps: int = 2_000_000, check_every: int = 100):
         """Run to steady state; returns (steps, status, residual) arrays.

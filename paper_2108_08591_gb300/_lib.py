@@ -81,6 +81,8 @@ SIGNATURES = {
                                         ctypes.c_double, ctypes.POINTER(Opts)]),
     "mdf_batch_destroy": (None, [H]),
     "mdf_batch_init": (ctypes.c_int, [H, ctypes.c_int, DP, DP, ctypes.c_int]),
+    "mdf_batch_seed": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                      ctypes.c_int]),
     "mdf_batch_run": (ctypes.c_int, [H, ctypes.c_double, ctypes.c_longlong, ctypes.c_int, DP, DP, DP]),
     "mdf_batch_step": (ctypes.c_int, [H, ctypes.c_longlong]),
     "mdf_batch_fields": (ctypes.c_int, [H, ctypes.c_int, ctypes.POINTER(Fields)]),

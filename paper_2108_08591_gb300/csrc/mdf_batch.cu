@@ -305,10 +305,54 @@ __global__ void k_batch_compact(BatchArgs B) {
   }
 }
 
-// Initial state of one cavity: f = f^eq(P, u) in pull form (see k_init).
+// Central difference of the seed velocity u_alpha along axis b at node p of
+// a closed box of side N; beyond a wall the velocity is mirrored about the
+// wall value (ghost = 2 u_wall - u), the wall lying half a cell outside the
+// boundary node.  The lid moves the + face of the last axis.
+template <class L>
+__device__ double seed_grad(const double *u, long long NN, int N, const int (&p)[3], int alpha, int b,
+                            const double (&lid)[3]) {
+  const double *ua = u + (long long)(alpha - 1) * NN;
+  auto at = [&](const int (&q)[3]) {
+    return ua[((long long)q[2] * N + q[1]) * N + q[0]];
+  };
+  const double u0 = at(p);
+  int q[3] = {p[0], p[1], p[2]};
+  q[b] = p[b] + 1;
+  const double wall_hi = b == L::D - 1 ? lid[alpha - 1] : 0.0;
+  const double up = q[b] < N ? at(q) : 2.0 * wall_hi - u0;
+  q[b] = p[b] - 1;
+  const double dn = q[b] >= 0 ? at(q) : -u0;
+  return 0.5 * (up - dn);
+}
+
+// First-order non-equilibrium part of the velocity set alpha along c_i at
+// node p: the Chapman-Enskog term f^ne_i = -(w_i / s1) (c_i . grad) u_alpha,
+// whose first moment -(c_s^2 / s1) grad u_alpha Eq. 3-16 inverts, with the
+// trace removed, f^ne_i += (w_i / s1) c_{i,alpha} div u / d: Eq. 3-15 reads
+// the trace of the first moments as pressure, so the traceless part keeps
+// the seeded P, and the gradient differs only where the seed is not
+// solenoidal.
+template <class L>
+__device__ double seed_fne(const double *u, long long NN, int N, const int (&p)[3], int alpha, int i,
+                           double s1, const double (&lid)[3]) {
+  if (alpha == 0 || i == 0) return 0.0;
+  const int b = L::c(i, 0) != 0 ? 0 : L::c(i, 1) != 0 ? 1 : 2;
+  const int sg = L::c(i, b);
+  double g = seed_grad<L>(u, NN, N, p, alpha, b, lid);
+  if (alpha - 1 == b) {
+    double div = 0.0;
+    for (int a = 0; a < L::D; ++a) div += seed_grad<L>(u, NN, N, p, a + 1, a, lid);
+    g -= div / L::D;
+  }
+  return -(L::w(i) / s1) * sg * g;
+}
+
+// Initial state of one cavity in pull form (see k_init): f = f^eq(P, u),
+// plus, with neq, the non-equilibrium part of the seed's velocity gradient.
 template <class L>
 __global__ void __launch_bounds__(kTile) k_batch_init(BatchArgs B, int cur, int c, const double *P,
-                                                     const double *u) {
+                                                     const double *u, int neq) {
   constexpr int D = L::D, Q = L::Q;
   const CavParam C = B.cav[c];
   const long long n = (long long)blockIdx.x * kTile + threadIdx.x;
@@ -329,11 +373,16 @@ __global__ void __launch_bounds__(kTile) k_batch_init(BatchArgs B, int cur, int 
       float v;
       if (i != 0 && ((m >> i) & 1)) {
         v = -geq<L, float>(A, NN, n, alpha, L::opp(i));
+        if (neq) v -= (float)seed_fne<L>(u, NN, C.N, p, alpha, L::opp(i), C.s1d, B.lid_u);
         if (alpha >= 1 && i == L::UP && (m & 0x80u)) v += float(2.0 * L::w(i) * B.lid_u[alpha - 1]);
       } else {
         const long long t = n + L::c(i, 0) + (long long)L::c(i, 1) * C.N +
                             (D == 3 ? (long long)L::c(i, 2) * C.N * C.N : 0);
         v = geq<L, float>(A, NN, t, alpha, i);
+        if (neq) {
+          const int pt[3] = {p[0] + L::c(i, 0), p[1] + L::c(i, 1), p[2] + (D == 3 ? L::c(i, 2) : 0)};
+          v += (float)seed_fne<L>(u, NN, C.N, pt, alpha, i, C.s1d, B.lid_u);
+        }
       }
       f[((long long)a * Q + i) * B.tot + C.base + n] = v;
     }
@@ -616,7 +665,12 @@ void mdf_batch_destroy(mdf_batch_t b) {
 }
 
 mdf_status mdf_batch_init(mdf_batch_t b, int cavity, const double *P, const double *u, int where) {
+  return mdf_batch_seed(b, cavity, P, u, where, 0);
+}
+
+mdf_status mdf_batch_seed(mdf_batch_t b, int cavity, const double *P, const double *u, int where, int neq) {
   if (!b) return MDF_EINVAL;
+  if (neq && !(P && u)) return bfail(b, MDF_EINVAL, "the non-equilibrium seed needs P and u");
   if (cavity < -1 || cavity >= b->ncav) return bfail(b, MDF_EINVAL, "cavity %d out of range", cavity);
   const int lo = cavity < 0 ? 0 : cavity, hi = cavity < 0 ? b->ncav : cavity + 1;
   if ((P || u) && cavity < 0) return bfail(b, MDF_EINVAL, "fields need a single cavity");
@@ -638,8 +692,9 @@ mdf_status mdf_batch_init(mdf_batch_t b, int cavity, const double *P, const doub
       BCU(b, cudaStreamSynchronize(b->stream));
     }
     const unsigned blocks = (unsigned)((nn + kTile - 1) / kTile);
-    if (b->d == 2) k_batch_init<D2Q5><<<blocks, kTile, 0, b->stream>>>(b->B, b->cur, c, dP, du);
-    else k_batch_init<D3Q7><<<blocks, kTile, 0, b->stream>>>(b->B, b->cur, c, dP, du);
+    const int ne = (neq && P && u) ? 1 : 0;
+    if (b->d == 2) k_batch_init<D2Q5><<<blocks, kTile, 0, b->stream>>>(b->B, b->cur, c, dP, du, ne);
+    else k_batch_init<D3Q7><<<blocks, kTile, 0, b->stream>>>(b->B, b->cur, c, dP, du, ne);
     BCU(b, cudaGetLastError());
     BCU(b, cudaFreeAsync(dP, b->stream));
     BCU(b, cudaFreeAsync(du, b->stream));

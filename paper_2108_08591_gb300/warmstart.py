@@ -60,9 +60,10 @@ def draw_cases(n: int, seed: int, re_range: Tuple[float, float]) -> List[float]:
 
 
 def solve(N: int, Res: Sequence[float], U: float, tol: float, max_steps: int, check_every: int,
-          seeds=None, stream=None):
+          seeds=None, stream=None, neq: bool = False):
     """Run cavities of side N to the residual `tol`; `seeds` (optional) is a
-    list of (P, u) host arrays for a warm start.  Returns (batch, steps,
+    list of (P, u) host arrays for a warm start, seeded as f^eq(P, u), plus
+    the non-equilibrium part of grad u with `neq`.  Returns (batch, steps,
     status, residual, seconds) with the solve timed by CUDA events."""
     import torch
     if stream is None:
@@ -70,7 +71,7 @@ def solve(N: int, Res: Sequence[float], U: float, tol: float, max_steps: int, ch
     b = CavityBatch([N] * len(Res), list(Res), lid_speed=U, stream=stream)
     if seeds is not None:
         for c, (P, u) in enumerate(seeds):
-            b.init(c, P, u)
+            b.init(c, P, u, neq=neq)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -157,7 +158,11 @@ def study(side: int, n_train: int, n_test: int, U: float, re_range, tol: float, 
     infer_s = time.perf_counter() - t_inf
     bc, st_c, stat_c, _, cold_s = solve(side, re_test, U, tol, max_steps, check_every)
     bw, st_w, stat_w, _, warm_s = solve(side, re_test, U, tol, max_steps, check_every, seeds=seeds)
+    bn, st_n, stat_n, _, warm_ne_s = solve(side, re_test, U, tol, max_steps, check_every, seeds=seeds,
+                                           neq=True)
+    bn.close()
     both = [c for c in range(n_test) if stat_c[c] == 0 and stat_w[c] == 0]
+    all3 = [c for c in both if stat_n[c] == 0]
     err_final, err_pred = [], []
     for c in both:
         fc = bc.fields_host(c, ("P", "u"))
@@ -176,6 +181,8 @@ def study(side: int, n_train: int, n_test: int, U: float, re_range, tol: float, 
         "cold_steps_mean": float(np.mean([st_c[c] for c in both])) if both else None,
         "warm_steps_mean": float(np.mean([st_w[c] for c in both])) if both else None,
         "cold_s": cold_s, "warm_s": warm_s + infer_s, "infer_s": infer_s,
+        "warm_neq_steps_mean": float(np.mean([st_n[c] for c in all3])) if all3 else None,
+        "warm_neq_s": warm_ne_s + infer_s, "n_test_converged_neq": len(all3),
         "speedup_time": cold_s / (warm_s + infer_s),
         "speedup_steps": (float(np.mean([st_c[c] for c in both])) / float(np.mean([st_w[c] for c in both])))
         if both else None,

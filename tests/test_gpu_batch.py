@@ -194,3 +194,46 @@ def test_schedule_rejects_bad_arguments():
         with pytest.raises(MdfError, match="EINVAL"):
             b.set_schedule(*args)
     b.close()
+
+
+def _fd_grad(u, N, d, lid):
+    """grad u by central differences, ghost 2 u_wall - u beyond the walls
+    (lid on the + face of the last axis): G[a][b] = d u_a / d x_b."""
+    G = np.zeros((d, d) + (N,) * d)
+    for a in range(d):
+        ua = u[a].reshape((N,) * d)  # [z][y][x] / [y][x]
+        for b in range(d):
+            ax = d - 1 - b  # numpy axis of lattice axis b
+            lo_wall = 0.0
+            hi_wall = lid[a] if b == d - 1 else 0.0
+            first = np.take(ua, [0], axis=ax)
+            last = np.take(ua, [N - 1], axis=ax)
+            ext = np.concatenate([2 * lo_wall - first, ua, 2 * hi_wall - last], axis=ax)
+            G[a, b] = 0.5 * (np.take(ext, np.arange(2, N + 2), axis=ax) - np.take(ext, np.arange(0, N), axis=ax))
+    return G.reshape(d, d, -1)
+
+
+@pytest.mark.parametrize("d,sides,Res", [(2, [24, 33], [150.0, 600.0]), (3, [12], [80.0])])
+def test_nonequilibrium_seed_returns_the_seed_gradient(d, sides, Res):
+    """With the f^ne seed, Eq. 3-16 on the initial state gives the traceless
+    part of the seed's finite-difference gradient, Eq. 2-7 the seed velocity
+    and Eq. 3-15 the seed pressure; without it the gradient is zero."""
+    from paper_2108_08591_gb300 import CavityBatch
+    lid = (U, 0.0, 0.0)
+    b = CavityBatch(sides, Res, lid_speed=U, d=d)
+    for c, N in enumerate(sides):
+        P, u = synth.smooth_fields((N,) * d, seed=40 + c)
+        G = _fd_grad(u, N, d, lid)
+        div = sum(G[a, a] for a in range(d))
+        for a in range(d):
+            G[a, a] -= div / d
+        b.init(c, P, u, neq=True)
+        got = b.fields_host(c, ("P", "u", "G"))
+        scale = np.abs(G).max()
+        assert np.abs(got["G"] - G).max() < 2e-4 * scale, np.abs(got["G"] - G).max() / scale
+        assert np.abs(got["u"] - u).max() < 1e-6 * np.abs(u).max()
+        assert np.abs(got["P"] - P).max() < 1e-3 * np.abs(P - 1).max()
+        b.init(c, P, u)
+        g0 = b.fields_host(c, ("G",))["G"]
+        assert np.abs(g0).max() < 1e-5 * scale
+    b.close()

@@ -25,3 +25,4 @@ def test_warm_start_reduces_steps_to_steady():
     assert r["warm_steps_mean"] < 0.7 * r["cold_steps_mean"], r
     assert r["final_warm_vs_cold_u_max"] < 1e-4, r
     assert r["pred_err_u_mean"] < 0.2, r
+    assert r["n_test_converged_neq"] == 8 and r["warm_neq_steps_mean"] < 0.7 * r["cold_steps_mean"], r
