@@ -389,8 +389,10 @@ mdf_status mdf_nn_conv_wgrad(const void *x, const void *dz, float *dw, float *pa
                              int W, int Cin, int Cout, void *stream);
 mdf_status mdf_nn_conv_dgrad(const void *dz, const void *w, void *wt, void *dx, int B, int H, int W,
                              int Cin, int Cout, void *stream);
-/* Forward/dgrad convolution kernel, process-wide: which = 1 the tcgen05 kernel
- * (TMEM accumulator, the default), 0 the mma.sync kernel. */
+/* Forward/dgrad convolution kernel, process-wide: which = 2 the tcgen05
+ * kernel with one staged input halo per channel chunk reused by the nine
+ * taps (the default; Cin % 16 != 0 falls back to 1), 1 the tcgen05 kernel
+ * with im2col gathers, 0 the mma.sync kernel.  All accumulate in FP32. */
 mdf_status mdf_nn_set_conv_kernel(int which);
 
 /* Tile of the tcgen05 kernel, process-wide: bn (output channels per CTA) in
@@ -398,6 +400,12 @@ mdf_status mdf_nn_set_conv_kernel(int which);
  * 0 keeps the automatic choice.  (256, 6) does not fit and is rejected.
  * A tuning override: every tile sweeps K in the same order. */
 mdf_status mdf_nn_set_tc_tile(int bn, int stages);
+
+/* Tile of the halo kernel, process-wide: mt 128-output M tiles per CTA (1 or
+ * 2) and kc input channels per staged chunk (16 or 32, used when it divides
+ * Cin); 0 keeps the automatic choice.  Its N tile follows
+ * mdf_nn_set_tc_tile's bn. */
+mdf_status mdf_nn_set_halo_tile(int mt, int kc);
 
 /* Read and clear the tcgen05 kernel's time-out flag (1 when a bounded
  * mbarrier wait gave up) of the current device; synchronises the device. */

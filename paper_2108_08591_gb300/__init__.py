@@ -392,9 +392,13 @@ class WarmStartNet:
         return float(loss[0]) if want_loss else None
 
 
+CONV_KERNELS = {"mma.sync": 0, "tcgen05": 1, "tcgen05-halo": 2}
+
+
 def set_conv_kernel(which: str):
-    """Forward/dgrad convolution kernel: 'tcgen05' (default) or 'mma.sync'."""
-    _lib.check(_lib.load().mdf_nn_set_conv_kernel({"mma.sync": 0, "tcgen05": 1}[which]))
+    """Forward/dgrad convolution kernel: 'tcgen05-halo' (default), 'tcgen05'
+    (im2col gathers) or 'mma.sync'."""
+    _lib.check(_lib.load().mdf_nn_set_conv_kernel(CONV_KERNELS[which]))
 
 
 def conv_timeout_flag() -> int:

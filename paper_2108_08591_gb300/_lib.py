@@ -112,6 +112,7 @@ SIGNATURES = {
                                          ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     "mdf_nn_set_conv_kernel": (ctypes.c_int, [ctypes.c_int]),
     "mdf_nn_set_tc_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "mdf_nn_set_halo_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "mdf_nn_conv_error": (ctypes.c_int, [DP]),
 }
 

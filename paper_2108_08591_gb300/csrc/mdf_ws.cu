@@ -26,7 +26,7 @@
 
 #include "mdf.h"
 #include "mdf_nn.cuh"
-#include "mdf_nn_tc.cuh"
+#include "mdf_nn_halo.cuh"
 
 using namespace mdfnn;
 
@@ -101,8 +101,11 @@ mdf_status wfail(mdf_ws_t w, mdf_status st, const char *fmt, ...) {
       return wfail((w), MDF_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
   } while (0)
 
-// Forward-convolution kernel in use: 1 = tcgen05/TMEM (default), 0 = mma.sync.
-int g_conv_kernel = 1;
+// Forward-convolution kernel in use: 2 = tcgen05 with a staged input halo
+// (default; needs Cin % 16 == 0, else kernel 1), 1 = tcgen05 with im2col
+// gathers, 0 = mma.sync.
+int g_conv_kernel = 2;
+int g_halo_mt = 0, g_halo_kc = 0;  // halo kernel tile override (0 = automatic)
 std::mutex g_tc_mu;
 std::map<int, int *> g_tc_err;  // per-device error flag of the tcgen05 kernel
 
@@ -156,12 +159,69 @@ void tc_tile(long long M, int Cout, int &bn, int &stages) {
   if (g_tc_stages) stages = g_tc_stages;
 }
 
+template <int BN, int KC, int MT>
+cudaError_t launch_halo(cudaStream_t s, const ConvArgs &a, int *err) {
+  constexpr int S = 4;
+  static bool configured = false;
+  const size_t smem = halo_smem_bytes<BN, KC, MT, S>();
+  if (smem > 227 * 1024) return cudaErrorInvalidConfiguration;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_halo<BN, KC, MT, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const HaloGeom g = halo_geom(a.H, a.W, MT);
+  const long long nx = (long long)a.B * g.strips * g.tiles;
+  if (nx > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+  dim3 grid((unsigned)nx, (unsigned)((a.Cout + BN - 1) / BN));
+  k_conv_fwd_halo<BN, KC, MT, S><<<grid, HX_THREADS, smem, s>>>(a, err);
+  return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t launch_halo_bn(cudaStream_t s, const ConvArgs &a, int *err, int kc, int mt) {
+  if (kc == 32) return mt == 2 ? launch_halo<BN, 32, 2>(s, a, err) : launch_halo<BN, 32, 1>(s, a, err);
+  return mt == 2 ? launch_halo<BN, 16, 2>(s, a, err) : launch_halo<BN, 16, 1>(s, a, err);
+}
+
+// Tile of the halo kernel, from a sweep over the network's layer shapes
+// (B = 8, 32^2 .. 256^2, Cin 16 .. 384, Cout 16 .. 256; every shape then runs
+// its fastest measured tile): N tile = Cout rounded up to a power of two, at
+// most 64 (more CTAs resident beat wider tiles); 16-channel chunks, 32 for
+// deep layers (Cin >= 128) on images at most 64 wide; two M tiles per CTA
+// when that still gives at least 1.5 CTAs per SM.
+void halo_tile(const ConvArgs &a, int &bn, int &kc, int &mt) {
+  bn = a.Cout <= 16 ? 16 : a.Cout <= 32 ? 32 : 64;
+  kc = (a.Cin % 32 == 0 && a.Cin >= 128 && a.W <= 64) ? 32 : 16;
+  const HaloGeom g2 = halo_geom(a.H, a.W, 2);
+  const long long ctas = (long long)a.B * g2.strips * g2.tiles * ((a.Cout + bn - 1) / bn);
+  mt = 2 * ctas >= 3 * 152 ? 2 : 1;
+  if (g_tc_bn) bn = g_tc_bn;
+  if (g_halo_kc && a.Cin % g_halo_kc == 0) kc = g_halo_kc;
+  if (g_halo_mt) mt = g_halo_mt;
+}
+
 cudaError_t conv_fwd(cudaStream_t s, const bf16 *x, const bf16 *w, const float *bias, bf16 *y,
                      float *yf, int B, int H, int W, int Cin, int Cout, int ldy, int yoff,
                      int relu) {
   ConvArgs a{x, w, bias, y, yf, B, H, W, Cin, Cout, ldy, yoff, relu};
   const long long M = (long long)B * H * W;
-  if (g_conv_kernel == 1) {
+  if (g_conv_kernel == 2 && Cin % 16 == 0) {
+    int *err = tc_error_flag();
+    if (!err) return cudaErrorMemoryAllocation;
+    int bn, kc, mt;
+    halo_tile(a, bn, kc, mt);
+    switch (bn) {
+      case 16: return launch_halo_bn<16>(s, a, err, kc, mt);
+      case 32: return launch_halo_bn<32>(s, a, err, kc, mt);
+      case 64: return launch_halo_bn<64>(s, a, err, kc, mt);
+      case 128: return launch_halo_bn<128>(s, a, err, kc, mt);
+      case 256: return launch_halo_bn<256>(s, a, err, kc, mt);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (g_conv_kernel >= 1) {
     int *err = tc_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
     int bn, st;
@@ -552,10 +612,20 @@ mdf_status mdf_nn_conv_dgrad(const void *dz, const void *w, void *wt, void *dx, 
                     H, W, Cin, Cout) == cudaSuccess ? MDF_OK : MDF_ECUDA;
 }
 
-// Select the forward-convolution kernel (1 tcgen05, 0 mma.sync), process-wide.
+// Select the forward-convolution kernel (2 tcgen05 + halo, 1 tcgen05 +
+// im2col, 0 mma.sync), process-wide.
 mdf_status mdf_nn_set_conv_kernel(int which) {
-  if (which != 0 && which != 1) return MDF_EINVAL;
+  if (which < 0 || which > 2) return MDF_EINVAL;
   g_conv_kernel = which;
+  return MDF_OK;
+}
+
+// Halo kernel tile override (0, 0 = automatic), process-wide.
+mdf_status mdf_nn_set_halo_tile(int mt, int kc) {
+  if (mt != 0 && mt != 1 && mt != 2) return MDF_EINVAL;
+  if (kc != 0 && kc != 16 && kc != 32) return MDF_EINVAL;
+  g_halo_mt = mt;
+  g_halo_kc = kc;
   return MDF_OK;
 }
 

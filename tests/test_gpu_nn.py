@@ -32,17 +32,20 @@ def _rel(ref, got):
     return float(np.linalg.norm((ref - got).ravel()) / np.linalg.norm(ref.ravel()))
 
 
-@pytest.fixture(params=["tcgen05", "mma.sync"])
+@pytest.fixture(params=["tcgen05-halo", "tcgen05", "mma.sync"])
 def kernel(request):
     from paper_2108_08591_gb300 import conv_timeout_flag, set_conv_kernel
     set_conv_kernel(request.param)
     yield request.param
     assert conv_timeout_flag() == 0
-    set_conv_kernel("tcgen05")
+    set_conv_kernel("tcgen05-halo")
 
 
+# shapes: ragged M and N tiles, Cin 8 (halo kernel falls back), Cin 16/32/64/96,
+# widths above 64 (several column strips, a narrow last one), 256-wide N tiles
 @pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 10, 7, 16, 40), (1, 8, 8, 96, 32), (3, 5, 9, 8, 16),
-                                            (2, 16, 16, 32, 136), (1, 20, 13, 64, 256)])
+                                            (2, 16, 16, 32, 136), (1, 20, 13, 64, 256),
+                                            (1, 12, 130, 32, 48), (2, 9, 70, 16, 16), (1, 6, 64, 64, 64)])
 def test_conv_forward(kernel, B, H, W, Cin, Cout):
     import torch
     from paper_2108_08591_gb300 import conv3x3_bf16
@@ -57,7 +60,8 @@ def test_conv_forward(kernel, B, H, W, Cin, Cout):
     assert np.all(np.abs(got - r) <= 2.0 ** -8 * np.abs(r) + 1e-6)
 
 
-@pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 10, 7, 16, 40), (1, 8, 8, 96, 32), (2, 16, 16, 32, 64)])
+@pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 10, 7, 16, 40), (1, 8, 8, 96, 32), (2, 16, 16, 32, 64),
+                                            (1, 5, 66, 32, 16)])
 def test_conv_backward(kernel, B, H, W, Cin, Cout):
     from paper_2108_08591_gb300 import conv3x3_bf16_backward
     x, xn = _bf16((B, H, W, Cin), 3)
