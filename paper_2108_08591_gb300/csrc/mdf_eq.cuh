@@ -582,8 +582,8 @@ template <class L>
 __device__ __forceinline__ void init_moments(const DevArgs &A, long long N, long long n,
                                              float (&M)[L::D + 2]) {
 #pragma unroll
-  for (int b = 0; b < L::D; ++b) M[b] = float(A.uin[b * N + n]);
-  M[L::D] = float(A.Pin[n] - 1.0);
+  for (int b = 0; b < L::D; ++b) M[b] = narrow_f64(A.uin[b * N + n]);
+  M[L::D] = narrow_f64(A.Pin[n] - 1.0);
   M[L::D + 1] = 0.f;
 }
 

@@ -486,29 +486,45 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_vec(const DevArgs A) {
     for (int i = 0; i < Q; ++i) VecIO<TS, VX>::store(fout + (long long)i * A.plane + row0 + x0, h[i]);
 }
 
-// Shifted equilibrium g^eq_i of set alpha at dense node n (Eq. 2-4 minus
-// the rest state): alpha >= 1: w_i [u_a + (c_i.u u_a + c_{i,a} P')/c_s^2];
-// alpha = 0 (ubar_0 = rho0 = 1): w_i c_i.u / c_s^2.  P' = P - 1 is formed in
-// FP64 (P ~ 1), the rest in the compute type TC.
+// Seed (u, P' = P - 1) of node n in the compute type TC: P' is formed in
+// FP64 (P ~ 1), then both are rounded to TC (narrow_to: integer pipe).
 template <class L, class TC>
-__device__ __forceinline__ TC geq(const DevArgs &A, long long N, long long n, int alpha, int i) {
+__device__ __forceinline__ void seed_at(const DevArgs &A, long long N, long long n, TC (&u)[L::D],
+                                        TC &Pp) {
+#pragma unroll
+  for (int b = 0; b < L::D; ++b) u[b] = narrow_to<TC>(A.uin[b * N + n]);
+  Pp = narrow_to<TC>(A.Pin[n] - 1.0);
+}
+
+// Shifted equilibrium g^eq_i of set alpha (Eq. 2-4 minus the rest state)
+// from a node's (u, P'): alpha >= 1: w_i [u_a + (c_i.u u_a + c_{i,a} P') /
+// c_s^2]; alpha = 0 (ubar_0 = rho0 = 1): w_i c_i.u / c_s^2.
+template <class L, class TC>
+__device__ __forceinline__ TC geq_v(int alpha, int i, const TC (&u)[L::D], TC Pp) {
   TC cu = TC(0);
 #pragma unroll
   for (int b = 0; b < L::D; ++b) {
-    if (L::c(i, b) > 0) cu += TC(A.uin[b * N + n]);
-    if (L::c(i, b) < 0) cu -= TC(A.uin[b * N + n]);
+    if (L::c(i, b) > 0) cu += u[b];
+    if (L::c(i, b) < 0) cu -= u[b];
   }
   const TC wi = TC(L::w(i)), ics2 = TC(1.0 / L::CS2);
   if (alpha == 0) return wi * cu * ics2;
-  const TC ua = TC(A.uin[(alpha - 1) * N + n]);
-  const TC Pp = TC(A.Pin[n] - 1.0);
+  const TC ua = u[alpha - 1];
   const TC cP = L::c(i, alpha - 1) > 0 ? Pp : (L::c(i, alpha - 1) < 0 ? -Pp : TC(0));
   return wi * (ua + (cu * ua + cP) * ics2);
 }
 
+template <class L, class TC>
+__device__ __forceinline__ TC geq(const DevArgs &A, long long N, long long n, int alpha, int i) {
+  TC u[L::D], Pp;
+  seed_at<L, TC>(A, N, n, u, Pp);
+  return geq_v<L, TC>(alpha, i, u, Pp);
+}
+
 // Initial state f = f^eq(P, u) written in pull form: the value stored at x
 // for direction i is the one the first update pulls into x + c_i, and for a
-// wall link the one whose bounce-back returns f^eq_opp(i)(x).
+// wall link the one whose bounce-back returns f^eq_opp(i)(x).  Each of the
+// Q source nodes' seed is rounded once and shared by the sets.
 template <class L, class TS, bool WALLS>
 __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
   using TC = typename ComputeOf<TS>::T;
@@ -520,6 +536,18 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
   const long long N = (long long)A.nx * A.ny * A.nz;
   const long long n = ((long long)z * A.ny + y) * A.nx + x;
   const uint8_t m = WALLS ? A.mask[idx] : uint8_t(0);
+  TC tu[Q][D], tP[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    long long t = n;
+    if (!(WALLS && i != 0 && ((m >> i) & 1))) {
+      const int tx = wrap(x + L::c(i, 0), A.nx);
+      const int ty = wrap(y + L::c(i, 1), A.ny);
+      const int tz = D == 3 ? wrap(z + L::c(i, 2), A.nz) : z;
+      t = ((long long)tz * A.ny + ty) * A.nx + tx;
+    }
+    seed_at<L, TC>(A, N, t, tu[i], tP[i]);
+  }
   TS *fout = static_cast<TS *>(A.fout);
   const int nsets = D + A.with_rho;
   for (int a = 0; a < nsets; ++a) {
@@ -528,13 +556,10 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
     for (int i = 0; i < Q; ++i) {
       TC v;
       if (WALLS && i != 0 && ((m >> i) & 1)) {
-        v = -geq<L, TC>(A, N, n, alpha, L::opp(i));
+        v = -geq_v<L, TC>(alpha, L::opp(i), tu[i], tP[i]);
         if (alpha >= 1 && i == L::UP && (m & 0x80u)) v += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
       } else {
-        const int tx = wrap(x + L::c(i, 0), A.nx);
-        const int ty = wrap(y + L::c(i, 1), A.ny);
-        const int tz = D == 3 ? wrap(z + L::c(i, 2), A.nz) : z;
-        v = geq<L, TC>(A, N, ((long long)tz * A.ny + ty) * A.nx + tx, alpha, i);
+        v = geq_v<L, TC>(alpha, i, tu[i], tP[i]);
       }
       Codec<TS>::store(fout + ((long long)a * Q + i) * A.plane + idx, v);
     }
