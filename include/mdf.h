@@ -319,15 +319,18 @@ mdf_status mdf_batch_set_timeout(mdf_batch_t b, long long cycles);
  * `threads` per block in {32, 64, 128} (each thread updates 128 / threads
  * nodes of a 128-node tile, `threads` apart), `grid` co-resident blocks (0:
  * the most that fit, MDF_EINVAL above that) and `sched` 0 (live tiles dealt
- * round-robin to the blocks) or 1 (one contiguous run of tiles per block).
- * Every schedule computes the same bits; only the speed differs. */
+ * round-robin to the blocks, a grid barrier between steps), 1 (one
+ * contiguous run of tiles per block, grid barrier) or 2 (round-robin, no
+ * grid barrier: a tile starts a step once the tiles within one neighbour
+ * stride of it have finished the previous one).  Every schedule computes
+ * the same bits; only the speed differs. */
 mdf_status mdf_batch_set_schedule(mdf_batch_t b, int threads, int grid, int sched);
 
 /* mdf_batch_get_schedule -- the launch shape in use (any pointer may be NULL). */
 mdf_status mdf_batch_get_schedule(mdf_batch_t b, int *threads, int *grid, int *sched);
 
 /* mdf_batch_autotune -- time `reps` (rounded up to even; < 2: 20) steps of
- * every schedule candidate (threads 128 / 64 / 32, both tile orders, grids
+ * every schedule candidate (threads 128 / 64 / 32, schedules 0 / 1 / 2, grids
  * of 1, 2, 3, 4, 6, 8, 12, 16 blocks per SM up to the co-resident limit) on
  * the current state with all cavities live, keep the fastest and restore
  * the state (bit for bit; step counts and statuses are not touched).

@@ -60,8 +60,9 @@ struct BatchArgs {
   long long *steps;         // [ncav]
   double *res;              // [ncav]
   unsigned int *bar;        // [0] arrivals, [1] generation
-  int *err;                 // MDF_ETIMEOUT on a barrier time-out
+  int *err;                 // MDF_ETIMEOUT on a barrier or neighbour-wait time-out
   long long timeout;        // barrier spin limit in clock cycles
+  int *prog;                // [ntiles] steps completed in the current launch (schedule 2)
 };
 
 // Bounded grid-wide barrier for a cooperative launch: the last block to
@@ -162,6 +163,56 @@ __device__ __forceinline__ void batch_pull(const BatchArgs &B, const float *fin,
   if (B.with_rho) pull_set_p<L, float, true>(fin, B.tot, 0, idx, src, m, B.lid_u, h);
 }
 
+__device__ __forceinline__ int ld_acquire(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Schedule 2 (no grid barrier): before step s of tile `tile`, wait until
+// every tile of the same cavity within one neighbour stride (N nodes in 2D,
+// N^2 in 3D) has completed s steps.  Those are the tiles the pulls read, and
+// the same tiles read this tile's step s - 1 values, which step s
+// overwrites.  The block's threads watch the tile counters in parallel;
+// each wait is bounded and a time-out raises MDF_ETIMEOUT.  The least
+// advanced block waits only on tiles of lower steps, which are complete,
+// so some block always progresses.
+template <class L>
+__device__ bool wait_neighbours(const BatchArgs &B, const CavParam &C, int tile, int s,
+                                long long count) {
+  const long long S = L::D == 3 ? (long long)C.N * C.N : (long long)C.N;
+  const long long k0 = (long long)(tile - C.tile0) * kTile;
+  const long long lo = k0 - S > 0 ? k0 - S : 0;
+  const long long hi = k0 + kTile - 1 + S < count - 1 ? k0 + kTile - 1 + S : count - 1;
+  const int tlo = C.tile0 + (int)(lo / kTile), thi = C.tile0 + (int)(hi / kTile);
+  bool ok = true;
+  volatile int *err = B.err;
+  for (int j = tlo + (int)threadIdx.x; j <= thi && ok; j += blockDim.x) {
+    const long long t0 = clock64();
+    while (ld_acquire(B.prog + j) < s) {
+      if (*err) { ok = false; break; }
+      if (clock64() - t0 > B.timeout) {
+        atomicCAS(B.err, 0, (int)MDF_ETIMEOUT);
+        ok = false;
+        break;
+      }
+      __nanosleep(32);
+    }
+  }
+  __threadfence();
+  return __syncthreads_and(ok) != 0;
+}
+
+// Schedule 2: publish that tile `tile` has completed `done` steps, after
+// every thread's stores of it.
+__device__ __forceinline__ void publish_tile(const BatchArgs &B, int tile, int done) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;\n" ::"l"(B.prog + tile), "r"(done) : "memory");
+  }
+}
+
 // One update of local node k of cavity C: pull from fin, collide, store to
 // fout; with save, also store the velocity it pulled (for the residual).
 template <class L>
@@ -193,15 +244,17 @@ __device__ __forceinline__ void batch_update_node(const BatchArgs &B, const floa
 // Schedule (chosen by mdf_batch_autotune): T threads per block, each thread
 // updating kTile / T nodes of a tile, T apart (so every access of a warp
 // stays on consecutive nodes); blocks take live tiles round-robin (SCHED 0)
-// or one contiguous run of the live list each (SCHED 1).  Every schedule
-// does the same arithmetic per node, so all give the same bits.
+// or one contiguous run of the live list each (SCHED 1), with a grid
+// barrier between steps, or round-robin with per-tile step counters and
+// neighbour waits instead of the barrier (SCHED 2).  Every schedule does the
+// same arithmetic per node, so all give the same bits.
 template <class L, int T, int SCHED>
 __global__ void __launch_bounds__(T) k_batch_chunk(BatchArgs B, int cur, int steps, int save_first) {
   constexpr int PER = kTile / T;
   const int nl = *B.n_live;
-  const int t0 = SCHED == 0 ? (int)blockIdx.x : (int)((long long)nl * blockIdx.x / gridDim.x);
-  const int t1 = SCHED == 0 ? nl : (int)((long long)nl * (blockIdx.x + 1) / gridDim.x);
-  const int dt = SCHED == 0 ? (int)gridDim.x : 1;
+  const int t0 = SCHED != 1 ? (int)blockIdx.x : (int)((long long)nl * blockIdx.x / gridDim.x);
+  const int t1 = SCHED != 1 ? nl : (int)((long long)nl * (blockIdx.x + 1) / gridDim.x);
+  const int dt = SCHED != 1 ? (int)gridDim.x : 1;
   for (int s = 0; s < steps; ++s) {
     const float *fin = B.f[(cur + s) & 1];
     float *fout = B.f[(cur + s + 1) & 1];
@@ -210,13 +263,15 @@ __global__ void __launch_bounds__(T) k_batch_chunk(BatchArgs B, int cur, int ste
       const int tile = B.live[t];
       const CavParam C = B.cav[B.tile_cav[tile]];
       const long long count = node_count<L>(C.N);
+      if (SCHED == 2 && !wait_neighbours<L>(B, C, tile, s, count)) return;
 #pragma unroll
       for (int r = 0; r < PER; ++r) {
         const int k = (tile - C.tile0) * kTile + r * T + (int)threadIdx.x;
         if (k < count) batch_update_node<L>(B, fin, fout, C, k, save);
       }
+      if (SCHED == 2) publish_tile(B, tile, s + 1);
     }
-    if (s + 1 < steps && !grid_barrier(B)) return;
+    if (SCHED != 2 && s + 1 < steps && !grid_barrier(B)) return;
   }
 }
 
@@ -462,47 +517,50 @@ cudaError_t launch_chunk_t(mdf_batch_t b, int steps, int save_first) {
   return cudaLaunchKernelEx(&cfg, k_batch_chunk<L, T, S>, b->B, b->cur, steps, save_first);
 }
 
+template <class L, int T>
+cudaError_t launch_chunk_s(mdf_batch_t b, int steps, int save_first) {
+  switch (b->sched) {
+    case 0: return launch_chunk_t<L, T, 0>(b, steps, save_first);
+    case 1: return launch_chunk_t<L, T, 1>(b, steps, save_first);
+    case 2: {  // step counters start at zero for every launch
+      cudaError_t e = cudaMemsetAsync(b->B.prog, 0, sizeof(int) * (size_t)b->ntiles, b->stream);
+      return e != cudaSuccess ? e : launch_chunk_t<L, T, 2>(b, steps, save_first);
+    }
+  }
+  return cudaErrorInvalidValue;
+}
+
 template <class L>
 cudaError_t launch_chunk(mdf_batch_t b, int steps, int save_first) {
-  const int key = b->threads * 2 + b->sched;
-  switch (key) {
-    case 256: return launch_chunk_t<L, 128, 0>(b, steps, save_first);
-    case 257: return launch_chunk_t<L, 128, 1>(b, steps, save_first);
-    case 128: return launch_chunk_t<L, 64, 0>(b, steps, save_first);
-    case 129: return launch_chunk_t<L, 64, 1>(b, steps, save_first);
-    case 64: return launch_chunk_t<L, 32, 0>(b, steps, save_first);
-    case 65: return launch_chunk_t<L, 32, 1>(b, steps, save_first);
+  switch (b->threads) {
+    case 128: return launch_chunk_s<L, 128>(b, steps, save_first);
+    case 64: return launch_chunk_s<L, 64>(b, steps, save_first);
+    case 32: return launch_chunk_s<L, 32>(b, steps, save_first);
   }
   return cudaErrorInvalidValue;
 }
 
 // Co-resident blocks per SM of the step kernel with this schedule.
-template <class L, int T, int S>
-cudaError_t occupancy_t(int *per) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_batch_chunk<L, T, S>, T, 0);
-}
-cudaError_t occupancy(int d, int threads, int sched, int *per) {
-  const int key = threads * 2 + sched;
-  if (d == 2) {
-    switch (key) {
-      case 256: return occupancy_t<D2Q5, 128, 0>(per);
-      case 257: return occupancy_t<D2Q5, 128, 1>(per);
-      case 128: return occupancy_t<D2Q5, 64, 0>(per);
-      case 129: return occupancy_t<D2Q5, 64, 1>(per);
-      case 64: return occupancy_t<D2Q5, 32, 0>(per);
-      case 65: return occupancy_t<D2Q5, 32, 1>(per);
-    }
-  } else {
-    switch (key) {
-      case 256: return occupancy_t<D3Q7, 128, 0>(per);
-      case 257: return occupancy_t<D3Q7, 128, 1>(per);
-      case 128: return occupancy_t<D3Q7, 64, 0>(per);
-      case 129: return occupancy_t<D3Q7, 64, 1>(per);
-      case 64: return occupancy_t<D3Q7, 32, 0>(per);
-      case 65: return occupancy_t<D3Q7, 32, 1>(per);
-    }
+template <class L, int T>
+cudaError_t occupancy_t(int sched, int *per) {
+  switch (sched) {
+    case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_batch_chunk<L, T, 0>, T, 0);
+    case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_batch_chunk<L, T, 1>, T, 0);
+    case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_batch_chunk<L, T, 2>, T, 0);
   }
   return cudaErrorInvalidValue;
+}
+template <class L>
+cudaError_t occupancy_l(int threads, int sched, int *per) {
+  switch (threads) {
+    case 128: return occupancy_t<L, 128>(sched, per);
+    case 64: return occupancy_t<L, 64>(sched, per);
+    case 32: return occupancy_t<L, 32>(sched, per);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t occupancy(int d, int threads, int sched, int *per) {
+  return d == 2 ? occupancy_l<D2Q5>(threads, sched, per) : occupancy_l<D3Q7>(threads, sched, per);
 }
 
 // Largest persistent grid for a schedule: co-resident blocks on every SM,
@@ -623,6 +681,7 @@ mdf_status mdf_batch_create(mdf_batch_t *out, int d, int n, const int *side, con
   if (e == cudaSuccess) e = cudaMalloc(&B.usave, sizeof(float) * d * (size_t)b->tot);
   if (e == cudaSuccess) e = cudaMalloc(&B.part, sizeof(double) * 2 * b->ntiles);
   if (e == cudaSuccess) e = cudaMalloc(&B.badtile, sizeof(int) * b->ntiles);
+  if (e == cudaSuccess) e = cudaMalloc(&B.prog, sizeof(int) * b->ntiles);
   if (e == cudaSuccess) e = cudaMalloc(&B.status, sizeof(int) * n);
   if (e == cudaSuccess) e = cudaMalloc(&B.steps, sizeof(long long) * n);
   if (e == cudaSuccess) e = cudaMalloc(&B.res, sizeof(double) * n);
@@ -660,6 +719,7 @@ void mdf_batch_destroy(mdf_batch_t b) {
   cudaFree(B.f[0]); cudaFree(B.f[1]); cudaFree((void *)B.cav); cudaFree((void *)B.tile_cav);
   cudaFree(B.live); cudaFree(B.n_live); cudaFree(B.usave); cudaFree(B.part); cudaFree(B.badtile);
   cudaFree(B.status); cudaFree(B.steps); cudaFree(B.res); cudaFree(B.bar); cudaFree(B.err);
+  cudaFree(B.prog);
   cudaFreeHost(b->host_live);
   delete b;
 }
@@ -865,7 +925,7 @@ mdf_status mdf_batch_set_schedule(mdf_batch_t b, int threads, int grid, int sche
   if (!b) return MDF_EINVAL;
   if (threads != 32 && threads != 64 && threads != 128)
     return bfail(b, MDF_EINVAL, "threads per block must be 32, 64 or 128 (got %d)", threads);
-  if (sched != 0 && sched != 1) return bfail(b, MDF_EINVAL, "schedule must be 0 or 1 (got %d)", sched);
+  if (sched < 0 || sched > 2) return bfail(b, MDF_EINVAL, "schedule must be 0, 1 or 2 (got %d)", sched);
   int gmax = 0;
   BCU(b, max_grid(b, threads, sched, &gmax));
   if (grid < 0 || grid > gmax)
@@ -909,7 +969,7 @@ mdf_status mdf_batch_autotune(mdf_batch_t b, int reps, int *threads_out, int *gr
   const int mult_c[8] = {1, 2, 3, 4, 6, 8, 12, 16};
   bool warmed = false;
   for (int ti = 0; ti < 3 && st == MDF_OK; ++ti)
-    for (int sc = 0; sc < 2 && st == MDF_OK; ++sc) {
+    for (int sc = 0; sc < 3 && st == MDF_OK; ++sc) {
       int gmax = 0;
       if (max_grid(b, threads_c[ti], sc, &gmax) != cudaSuccess) {
         st = bfail(b, MDF_ECUDA, "autotune: occupancy query failed");
