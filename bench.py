@@ -437,9 +437,13 @@ def run_cavities(args):
     import synth
     from paper_2108_08591_gb300 import CavityBatch, _build
     _build.build()
-    draw = synth.cavity_batch(64, seed=2108)
-    sides = [s for s, _ in draw]
-    Res = [r for _, r in draw]
+    if args.cavity_side:  # a uniform batch (profiling case), Re spread over [400, 1150]
+        sides = [args.cavity_side] * args.cavity_count
+        Res = [400.0 + 750.0 * k / max(1, args.cavity_count - 1) for k in range(args.cavity_count)]
+    else:
+        draw = synth.cavity_batch(64, seed=2108)
+        sides = [s for s, _ in draw]
+        Res = [r for _, r in draw]
     nodes = np.array(sides, dtype=np.int64) ** 2
     stream = torch.cuda.Stream()
     b = CavityBatch(sides, Res, lid_speed=0.1, stream=stream)
@@ -464,7 +468,10 @@ def run_cavities(args):
     peak, kind = _peaks()
     b.init()
     t0 = time.perf_counter()
-    steps, status, res = b.run(tol=1e-8, max_steps=args.max_steps, check_every=100)
+    if args.max_steps > 0:
+        steps, status, res = b.run(tol=1e-8, max_steps=args.max_steps, check_every=100)
+    else:  # throughput only
+        steps, status, res = np.zeros(len(sides), np.int64), np.full(len(sides), 6, np.int32), np.zeros(len(sides))
     run_s = time.perf_counter() - t0
     names = {0: "converged", 4: "diverged", 6: "not_converged"}
     line = {
@@ -477,7 +484,7 @@ def run_cavities(args):
         "schedule": {"tuned": sched, "default": sched_default, "autotune_s": tune_s,
                      "default_mlups": float(nodes.sum() / (ms_default / 1e3) / 1e6)},
         "to_steady": {"tol": 1e-8, "max_steps": args.max_steps, "seconds": run_s,
-                      "aggregate_mlups": float((steps * nodes).sum()) / run_s / 1e6,
+                      "aggregate_mlups": float((steps * nodes).sum()) / run_s / 1e6 if run_s > 0 else None,
                       "status": {names[k]: v for k, v in collections.Counter(status.tolist()).items()}},
         "per_cavity": [[int(sides[c]), round(Res[c], 1), int(steps[c]), int(status[c])]
                        for c in np.argsort(sides, kind="stable")],
@@ -548,7 +555,11 @@ def main():
                     help="tg2d: the 4096^2 D2Q5 x 3 line (default); tg3d: 512^3 D3Q7 x 4; "
                          "cavities: 64 batched cavities; conv: network kernels; warmstart: "
                          "learned warm start vs cold start at 256^2")
-    ap.add_argument("--max-steps", type=int, default=2_000_000)
+    ap.add_argument("--max-steps", type=int, default=2_000_000,
+                    help="cavities: step cap of the run to steady state (0 skips it)")
+    ap.add_argument("--cavity-side", type=int, default=0,
+                    help="cavities workload: a uniform batch of this side instead of the 64 seeded boxes")
+    ap.add_argument("--cavity-count", type=int, default=16, help="cavities in the uniform batch")
     ap.add_argument("--grid", type=int, default=4096,
                     help="lattice side (default 4096; smaller sides are profiling cases)")
     args = ap.parse_args()
