@@ -499,13 +499,15 @@ def run_conv(args):
     repeated --steps times inside one CUDA graph (host launch cost excluded),
     inputs L2-resident (the network's working set), CUDA-event timed."""
     import torch
-    from paper_2108_08591_gb300 import _build, conv3x3_bf16, conv3x3_bf16_backward, set_conv_kernel
+    from paper_2108_08591_gb300 import (_build, conv3x3_bf16, conv3x3_bf16_backward, set_conv_kernel,
+                                        set_wgrad_kernel)
     _build.build()
     rows = []
     shapes = [(8, 256, 32, 32), (8, 128, 64, 64), (8, 64, 128, 128), (8, 32, 256, 256),
               (8, 256, 96, 32), (8, 64, 384, 128), (8, 256, 16, 32), (8, 256, 64, 16)]
     for kern in ("tcgen05-halo", "tcgen05", "mma.sync"):
         set_conv_kernel(kern)
+        set_wgrad_kernel("mma.sync")  # the default weight gradient (the faster here)
         for (B, H, Cin, Cout) in shapes:
             g = torch.Generator(device="cuda").manual_seed(1)
             x = torch.randn(B, H, H, Cin, device="cuda", generator=g).to(torch.bfloat16)

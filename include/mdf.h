@@ -410,6 +410,17 @@ mdf_status mdf_nn_set_tc_tile(int bn, int stages);
  * mdf_nn_set_tc_tile's bn. */
 mdf_status mdf_nn_set_halo_tile(int mt, int kc);
 
+/* Weight-gradient kernel, process-wide: which = 0 the mma.sync split-K
+ * kernel (the default), 1 the tcgen05 kernel (nine TMEM accumulators, one
+ * staged x halo per pixel chunk; Cin % 16 != 0 falls back to 0).  Both
+ * accumulate in FP32; the tcgen05 one is the slower on this GPU. */
+mdf_status mdf_nn_set_wgrad_kernel(int which);
+
+/* Input-channel tile of the tcgen05 weight-gradient kernel, process-wide:
+ * 16 or 32 (used when it divides into Cin's 16-channel steps), 0 keeps the
+ * automatic choice. */
+mdf_status mdf_nn_set_wgrad_tile(int bn);
+
 /* Read and clear the tcgen05 kernel's time-out flag (1 when a bounded
  * mbarrier wait gave up) of the current device; synchronises the device. */
 mdf_status mdf_nn_conv_error(int *flag);

@@ -401,6 +401,11 @@ def set_conv_kernel(which: str):
     _lib.check(_lib.load().mdf_nn_set_conv_kernel(CONV_KERNELS[which]))
 
 
+def set_wgrad_kernel(which: str):
+    """Weight-gradient kernel: 'mma.sync' (default) or 'tcgen05'."""
+    _lib.check(_lib.load().mdf_nn_set_wgrad_kernel({"mma.sync": 0, "tcgen05": 1}[which]))
+
+
 def conv_timeout_flag() -> int:
     """Read and clear the tcgen05 kernel's time-out flag (synchronises)."""
     f = np.zeros(1, dtype=np.int32)

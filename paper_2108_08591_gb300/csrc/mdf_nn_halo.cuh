@@ -269,16 +269,17 @@ __global__ void __launch_bounds__(HX_THREADS) k_conv_fwd_halo(ConvArgs a, int *e
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n");
-      const uint32_t hb = smem_u32(sH + (c & 1) * HALO_BYTES), wb = smem_u32(sW + (j % S) * W_BYTES);
+      // descriptors of the slots, advanced through their start-address field
+      // (address / 16; shared memory stays below 256 KB, so no carry)
+      const uint64_t hd = umma_smem_desc(smem_u32(sH + (c & 1) * HALO_BYTES), hlbo, hsbo);
+      const uint64_t wd = umma_smem_desc(smem_u32(sW + (j % S) * W_BYTES), wlbo, wsbo);
+      const uint64_t tap = (uint64_t)(kh * g.P + kw);  // rows of 16 B
 #pragma unroll
       for (int ks = 0; ks < KC / 16; ++ks) {
-        const uint64_t bdesc = umma_smem_desc(wb + ks * 256, wlbo, wsbo);
 #pragma unroll
-        for (int mt = 0; mt < MT; ++mt) {
-          const uint32_t arow = (uint32_t)(mt * 128 + kh * g.P + kw);
-          tc_mma(tmem + (uint32_t)(mt * BN), umma_smem_desc(hb + 2 * ks * hlbo + arow * 16, hlbo, hsbo),
-                 bdesc, idesc, (j > 0 || ks > 0) ? 1u : 0u);
-        }
+        for (int mt = 0; mt < MT; ++mt)
+          tc_mma(tmem + (uint32_t)(mt * BN), hd + (uint64_t)(2 * ks * RMAX + mt * 128) + tap,
+                 wd + (uint64_t)(ks * 16), idesc, (j > 0 || ks > 0) ? 1u : 0u);
       }
       tc_commit(&wempty[j % S]);
       if (t == 8) tc_commit(&hempty[c & 1]);

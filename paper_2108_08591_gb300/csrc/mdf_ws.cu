@@ -26,7 +26,7 @@
 
 #include "mdf.h"
 #include "mdf_nn.cuh"
-#include "mdf_nn_halo.cuh"
+#include "mdf_nn_wgrad_tc.cuh"
 
 using namespace mdfnn;
 
@@ -106,6 +106,13 @@ mdf_status wfail(mdf_ws_t w, mdf_status st, const char *fmt, ...) {
 // gathers, 0 = mma.sync.
 int g_conv_kernel = 2;
 int g_halo_mt = 0, g_halo_kc = 0;  // halo kernel tile override (0 = automatic)
+// Weight-gradient kernel: 0 = mma.sync split-K (default), 1 = tcgen05 with
+// nine TMEM accumulators (needs Cin % 16 == 0, else 0).  The tcgen05 one
+// measured 1.7-3.6x slower on the network's layers: with all nine taps in
+// TMEM only one or two CTAs fit per SM, too few to hide the loads of its
+// small per-chunk MMA batches.
+int g_wgrad_kernel = 0;
+int g_wgrad_bn = 0;  // tcgen05 weight-gradient channel tile override (0 = automatic)
 std::mutex g_tc_mu;
 std::map<int, int *> g_tc_err;  // per-device error flag of the tcgen05 kernel
 
@@ -242,11 +249,44 @@ cudaError_t conv_fwd(cudaStream_t s, const bf16 *x, const bf16 *w, const float *
 
 int pix_per_split(long long M) { return M >= 8192 ? 2048 : 256; }
 
+template <int BN, int S>
+cudaError_t launch_wgrad_tc(cudaStream_t s, const WgradTcArgs &a, int *err) {
+  static bool configured = false;
+  const size_t smem = wgrad_tc_smem_bytes<BN, S>();
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_tc<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  dim3 grid((unsigned)((a.Cin + BN - 1) / BN), (unsigned)((a.Cout + 127) / 128), (unsigned)a.splits);
+  k_conv_wgrad_tc<BN, S><<<grid, HX_THREADS, smem, s>>>(a, err);
+  return cudaGetLastError();
+}
+
 cudaError_t conv_wgrad(cudaStream_t s, const bf16 *x, const bf16 *dz, float *part, float *dw,
                        int B, int H, int W, int Cin, int Cout) {
   const long long M = (long long)B * H * W;
   const int pps = pix_per_split(M);
   const int splits = (int)((M + pps - 1) / pps);
+  if (g_wgrad_kernel == 1 && Cin % 16 == 0) {
+    int *err = tc_error_flag();
+    if (!err) return cudaErrorMemoryAllocation;
+    // split the pixel chunks for about two CTAs per SM, within the partial
+    // buffer sized for the mma.sync kernel's splits
+    const HaloGeom g = halo_geom(H, W, 1);
+    const long long nq = (long long)B * g.strips * ((H * g.P + WG_KP - 1) / WG_KP);
+    const int bn = g_wgrad_bn ? g_wgrad_bn : (Cin % 32 == 0 ? 32 : 16);
+    const long long tiles = (long long)((Cin + bn - 1) / bn) * ((Cout + 127) / 128);
+    long long sp = (2 * 152 + tiles - 1) / tiles;
+    sp = std::min<long long>(std::min<long long>(sp, splits), nq);
+    WgradTcArgs a{x, dz, part, B, H, W, Cin, Cout, (int)std::max<long long>(1, sp)};
+    cudaError_t e = bn == 32 ? launch_wgrad_tc<32, 3>(s, a, err) : launch_wgrad_tc<16, 3>(s, a, err);
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)Cout * 9 * Cin;
+    k_sum_splits<<<grid1(n), 256, 0, s>>>(part, a.splits, n, dw, 0);
+    return cudaGetLastError();
+  }
   const int K = 9 * Cin;
   WgradArgs a{x, dz, part, B, H, W, Cin, Cout, pps};
   dim3 grid((unsigned)((K + 63) / 64), (unsigned)((Cout + 63) / 64), (unsigned)splits);
@@ -617,6 +657,20 @@ mdf_status mdf_nn_conv_dgrad(const void *dz, const void *w, void *wt, void *dx, 
 mdf_status mdf_nn_set_conv_kernel(int which) {
   if (which < 0 || which > 2) return MDF_EINVAL;
   g_conv_kernel = which;
+  return MDF_OK;
+}
+
+// Weight-gradient kernel (1 tcgen05, 0 mma.sync), process-wide.
+mdf_status mdf_nn_set_wgrad_kernel(int which) {
+  if (which != 0 && which != 1) return MDF_EINVAL;
+  g_wgrad_kernel = which;
+  return MDF_OK;
+}
+
+// tcgen05 weight-gradient channel tile override (0 = automatic), process-wide.
+mdf_status mdf_nn_set_wgrad_tile(int bn) {
+  if (bn != 0 && bn != 16 && bn != 32) return MDF_EINVAL;
+  g_wgrad_bn = bn;
   return MDF_OK;
 }
 

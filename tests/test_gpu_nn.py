@@ -60,9 +60,21 @@ def test_conv_forward(kernel, B, H, W, Cin, Cout):
     assert np.all(np.abs(got - r) <= 2.0 ** -8 * np.abs(r) + 1e-6)
 
 
+@pytest.fixture(params=["tcgen05", "mma.sync"])
+def wgrad_kernel(request):
+    from paper_2108_08591_gb300 import conv_timeout_flag, set_wgrad_kernel
+    set_wgrad_kernel(request.param)
+    yield request.param
+    assert conv_timeout_flag() == 0
+    set_wgrad_kernel("mma.sync")
+
+
+# shapes: ragged channel tiles, Cin 8 (tcgen05 wgrad falls back), several
+# column strips, more than 128 output channels (two M tiles)
 @pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 10, 7, 16, 40), (1, 8, 8, 96, 32), (2, 16, 16, 32, 64),
-                                            (1, 5, 66, 32, 16)])
-def test_conv_backward(kernel, B, H, W, Cin, Cout):
+                                            (1, 5, 66, 32, 16), (3, 5, 9, 8, 16), (1, 12, 130, 32, 48),
+                                            (2, 9, 9, 64, 136)])
+def test_conv_backward(kernel, wgrad_kernel, B, H, W, Cin, Cout):
     from paper_2108_08591_gb300 import conv3x3_bf16_backward
     x, xn = _bf16((B, H, W, Cin), 3)
     w, wn = _bf16((Cout, 3, 3, Cin), 4)
