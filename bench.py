@@ -171,7 +171,7 @@ class ClockSampler:
                 "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
 
 
-def cpu_oracle_sample(steps: int = 40, warmup: int = 1):
+def cpu_oracle_sample(steps: int = 40, warmup: int = 1, single_thread: bool = True):
     """Time the FP64 CPU oracle, as it stands, on the benchmark workload:
     the full 4096^2 lattice, `steps` timed updates after `warmup` (about 16 s
     of work on 16 host cores)."""
@@ -185,11 +185,24 @@ def cpu_oracle_sample(steps: int = 40, warmup: int = 1):
     t0 = time.perf_counter()
     oracle.run(pb, f, steps)
     dt = time.perf_counter() - t0
-    return {"value": N_GRID * N_GRID * steps / dt / 1e6, "unit": "MLUPS",
-            "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"{steps} FP64 oracle updates of the full 4096^2 D2Q5x3 lattice "
-                      f"after {warmup} warm-up, OpenMP threads = {oracle.threads()}",
-            "seconds": dt}
+    out = {"value": N_GRID * N_GRID * steps / dt / 1e6, "unit": "MLUPS",
+           "cores": oracle.threads(), "kind": "oracle",
+           "sample": f"{steps} FP64 oracle updates of the full {N_GRID}^2 D2Q5x3 lattice "
+                     f"after {warmup} warm-up, OpenMP threads = {oracle.threads()}",
+           "seconds": dt}
+    if single_thread and oracle.threads() > 1:
+        # the same oracle on one host thread (a fresh process: OpenMP reads
+        # its thread count at start-up), one full-lattice update
+        code = ("import json, bench; "
+                "print(json.dumps(bench.cpu_oracle_sample(steps=1, warmup=0, single_thread=False)))")
+        r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                           env=dict(os.environ, OMP_NUM_THREADS="1"), timeout=600)
+        lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+        if r.returncode == 0 and lines:
+            one = json.loads(lines[-1])
+            out["single_thread"] = {"value": one["value"], "unit": "MLUPS", "cores": one["cores"],
+                                    "sample": one["sample"]}
+    return out
 
 
 def run_reference(args):
