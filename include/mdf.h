@@ -315,7 +315,12 @@ mdf_status mdf_batch_info(mdf_batch_t b, long long *nodes, int *tiles, int *grid
  * state is then undefined until the next mdf_batch_init. */
 mdf_status mdf_batch_set_timeout(mdf_batch_t b, long long cycles);
 
-/* mdf_batch_set_schedule -- launch shape of the persistent step kernel:
+/* Scheduling of the batch's persistent kernel (mdf_batch_set_schedule,
+ * mdf_batch_get_schedule, mdf_batch_autotune) is a GPU launch control with
+ * no counterpart in the paper: it changes how the updates of Eq. 3-21 are
+ * distributed over the GPU, never their arithmetic.
+ *
+ * mdf_batch_set_schedule -- launch shape of the persistent step kernel:
  * `threads` per block in {32, 64, 128} (each thread updates 128 / threads
  * nodes of a 128-node tile, `threads` apart), `grid` co-resident blocks (0:
  * the most that fit, MDF_EINVAL above that) and `sched` 0 (live tiles dealt
