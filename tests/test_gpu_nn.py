@@ -155,3 +155,42 @@ def test_training_reduces_the_loss():
     last = net.train_step(xd, td, lr=2e-3)
     assert last < 0.05 * first, (first, last)
     net.close()
+
+
+def test_every_tcgen05_tile_matches_oracle():
+    """Every instantiated tile of the two tcgen05 forward kernels, chosen
+    through the tuning overrides: halo kernel N tile 16..256 x 1 or 2 M tiles
+    x 16- or 32-channel chunks, im2col kernel N tile 16..256 x 3, 4 or 6
+    stages (256 x 6 does not fit and is rejected).  A ragged shape with two
+    column strips; FP32 output against the FP64 oracle."""
+    import torch
+    from paper_2108_08591_gb300 import _lib, conv3x3_bf16, conv_timeout_flag, set_conv_kernel
+    lib = _lib.load()
+    B, H, W, Cin, Cout = 2, 11, 70, 32, 40
+    x, xn = _bf16((B, H, W, Cin), 21)
+    w, wn = _bf16((Cout, 3, 3, Cin), 22)
+    ref = onn.conv3x3(xn, wn, np.zeros(Cout))
+    try:
+        set_conv_kernel("tcgen05-halo")
+        for bn in (16, 32, 64, 128, 256):
+            for mt in (1, 2):
+                for kc in (16, 32):
+                    assert lib.mdf_nn_set_tc_tile(bn, 0) == 0 and lib.mdf_nn_set_halo_tile(mt, kc) == 0
+                    got = conv3x3_bf16(x, w).cpu().numpy()
+                    assert _rel(ref, got) < 1e-5, ("halo", bn, mt, kc, _rel(ref, got))
+        lib.mdf_nn_set_halo_tile(0, 0)
+        set_conv_kernel("tcgen05")
+        for bn in (16, 32, 64, 128, 256):
+            for st in (3, 4, 6):
+                rc = lib.mdf_nn_set_tc_tile(bn, st)
+                if bn == 256 and st == 6:
+                    assert rc != 0
+                    continue
+                assert rc == 0
+                got = conv3x3_bf16(x, w).cpu().numpy()
+                assert _rel(ref, got) < 1e-5, ("im2col", bn, st, _rel(ref, got))
+        assert conv_timeout_flag() == 0
+    finally:
+        lib.mdf_nn_set_tc_tile(0, 0)
+        lib.mdf_nn_set_halo_tile(0, 0)
+        set_conv_kernel("tcgen05-halo")
