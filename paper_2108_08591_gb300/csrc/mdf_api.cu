@@ -40,20 +40,23 @@ bool eq_storage(int st) { return st == MDF_F16EQ || st == MDF_BF16EQ; }
 // Launch shape defaults of the update kernel, per lattice and storage, from
 // a sweep on GB300 (4096^2 D2Q5 x 3 and 512^3 D3Q7 x 4; CUDA-event timing):
 //   2D: vector kernel, 4 nodes per thread, 128 threads (FP32 6.91 TB/s,
-//       FP16 5.62 TB/s, BF16 5.35 TB/s); FP64 2 nodes per thread.
-//   3D: one node per thread, 256 threads (FP32 6.94 TB/s, FP16 4.40 TB/s):
-//       with 28 populations per node the vector kernel's register pressure
-//       costs more than its saved instructions.
+//       FP16 6.80 TB/s, BF16 6.64 TB/s); FP64 2 nodes per thread.
+//   3D: FP32 one node per thread, 256 threads (6.94 TB/s): with 28
+//       populations per node the vector kernel's register pressure costs
+//       more than its saved instructions; rest-shifted 16-bit 8 nodes per
+//       thread, 64 threads (FP16 4.99, BF16 5.27 TB/s; the 16-bit vector
+//       kernel loads every word of its nodes before converting any).
 //   Equilibrium-shifted 16-bit: 2 nodes per thread (one FP32 pair), 64
 //       threads in 2D (5.43 TB/s) and 128 in 3D (5.39 TB/s).
 // mdf_autotune() measures the candidates for a given handle instead.
 int default_vx(int d, int storage) {
   if (eq_storage(storage)) return 2;
-  if (d == 3) return 1;
+  if (d == 3) return (storage == MDF_F16 || storage == MDF_BF16) ? 8 : 1;
   return storage == MDF_F64 ? 2 : 4;
 }
 int default_block(int d, int storage) {
   if (eq_storage(storage)) return d == 3 ? 128 : 64;
+  if (d == 3 && (storage == MDF_F16 || storage == MDF_BF16)) return 64;
   return d == 3 ? 256 : 128;
 }
 

@@ -20,6 +20,7 @@
 #include "mdf_internal.h"
 #include "mdf_lattice.cuh"
 #include "mdf_f64.cuh"
+#include "mdf_pack16.cuh"
 
 namespace mdf {
 
@@ -358,6 +359,26 @@ struct VecRows {
   bool ledge, redge;                         // x - 1 / x + VX not held by a neighbour lane
 };
 
+// Anti-halfway bounce-back on the wall links of VX nodes of one set (see
+// pull_set): the pulled value is minus the node's own opposite population,
+// plus the lid term on the lid.
+template <class L, class TS, int VX>
+__device__ __forceinline__ void bounce_back_vec(const DevArgs &A, const TS *__restrict__ base, int alpha,
+                                                const VecRows &R, const uint8_t (&m)[VX],
+                                                typename ComputeOf<TS>::T (&v)[L::Q][VX]) {
+  using TC = typename ComputeOf<TS>::T;
+#pragma unroll
+  for (int i = 1; i < L::Q; ++i)
+#pragma unroll
+    for (int j = 0; j < VX; ++j)
+      if ((m[j] >> L::opp(i)) & 1) {
+        TC w = -TC(Codec<TS>::load(base + (long long)L::opp(i) * A.plane + R.row0 + R.x0 + j));
+        if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u))
+          w += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+        v[i][j] = w;
+      }
+}
+
 // Pull VX consecutive nodes of one set (carrying alpha) into v[i][j].
 template <class L, class TS, int VX, bool WALLS>
 __device__ __forceinline__ void pull_set_vec(const DevArgs &A, const TS *__restrict__ base,
@@ -390,17 +411,69 @@ __device__ __forceinline__ void pull_set_vec(const DevArgs &A, const TS *__restr
       VecIO<TS, VX>::load(p + r + R.x0, v[i]);
     }
   }
-  if (WALLS) {  // anti-halfway bounce-back on wall links (see pull_set)
+  if (WALLS) bounce_back_vec<L, TS, VX>(A, base, alpha, R, m, v);
+}
+
+// 16-bit storage, all sets: every population word of the VX nodes is loaded
+// before any is converted, so all of a thread's reads are in flight
+// together; then the x-shifted pulls take their end values from the
+// neighbouring lanes (or, at a warp or row edge, the scalar loads issued
+// with the words), and the wall links bounce back.  Same values as
+// pull_set_vec.
+template <class L, class TS, int VX, bool WALLS>
+__device__ __forceinline__ void pull_all_vec16(const DevArgs &A, const TS *__restrict__ fin,
+                                               const VecRows &R, const uint8_t (&m)[VX],
+                                               float (&g)[L::D][L::Q][VX], float (&h)[L::Q][VX]) {
+  constexpr int D = L::D, Q = L::Q;
+  using PK = Packed16<TS, VX>;
+  typename PK::W wv[D + 1][Q];
+  unsigned edge[D + 1][2];
+  const int a1 = A.with_rho;
 #pragma unroll
-    for (int i = 1; i < Q; ++i)
+  for (int s = 0; s <= D; ++s) {  // velocity sets first, the continuity set last
+    if (s == D && !A.with_rho) break;
+    const TS *base = fin + (long long)(s < D ? a1 + s : 0) * Q * A.plane;
 #pragma unroll
-      for (int j = 0; j < VX; ++j)
-        if ((m[j] >> L::opp(i)) & 1) {
-          TC w = -TC(Codec<TS>::load(base + (long long)L::opp(i) * A.plane + R.row0 + R.x0 + j));
-          if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u))
-            w += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
-          v[i][j] = w;
+    for (int i = 0; i < Q; ++i) {
+      const TS *p = base + (long long)i * A.plane;
+      const int r = L::c(i, 1) == 1 ? R.row_ym : L::c(i, 1) == -1 ? R.row_yp
+                  : L::c(i, 2) == 1 ? R.row_zm : L::c(i, 2) == -1 ? R.row_zp : R.row0;
+      wv[s][i] = PK::load(p + r + R.x0);
+      if (L::c(i, 0) == 1) edge[s][0] = R.ledge ? ldg_bits16(p + R.row0 + R.xl) : 0u;
+      if (L::c(i, 0) == -1) edge[s][1] = R.redge ? ldg_bits16(p + R.row0 + R.xr) : 0u;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s <= D; ++s) {
+    if (s == D && !A.with_rho) break;
+    float(&v)[Q][VX] = s < D ? g[s < D ? s : 0] : h;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const typename PK::W w = wv[s][i];
+      if (L::c(i, 0) == 1) {  // from x - 1: v[0] from the lane to the left
+        unsigned nb = __shfl_up_sync(0xffffffffu, PK::last_word(w), 1);
+        nb = R.ledge ? edge[s][0] : (VX == 1 ? nb : nb >> 16);
+        v[i][0] = bits_to_float<TS>(nb);
+#pragma unroll
+        for (int j = 1; j < VX; ++j) v[i][j] = bits_to_float<TS>(PK::bits(w, j - 1));
+      } else if (L::c(i, 0) == -1) {  // from x + 1: v[VX - 1] from the lane to the right
+        unsigned nb = __shfl_down_sync(0xffffffffu, PK::first_word(w), 1);
+        nb = R.redge ? edge[s][1] : (nb & 0xffffu);
+#pragma unroll
+        for (int j = 0; j < VX - 1; ++j) v[i][j] = bits_to_float<TS>(PK::bits(w, j + 1));
+        v[i][VX - 1] = bits_to_float<TS>(nb);
+      } else {
+#pragma unroll
+        for (int q = 0; q < VX / 2; ++q) {
+          const float2 f = PK::lanes(w, q);
+          v[i][2 * q] = f.x;
+          v[i][2 * q + 1] = f.y;
         }
+      }
+    }
+    if (WALLS)
+      bounce_back_vec<L, TS, VX>(A, fin + (long long)(s < D ? a1 + s : 0) * Q * A.plane, s < D ? s + 1 : 0,
+                                 R, m, v);
   }
 }
 
@@ -433,11 +506,15 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_vec(const DevArgs A) {
 
   const VecRows rows{row0, row_ym, row_yp, row_zm, row_zp, x0, xl, xr, ledge, redge};
   TC g[D][Q][VX], h[Q][VX];
+  if constexpr (sizeof(TS) == 2) {
+    pull_all_vec16<L, TS, VX, WALLS>(A, fin, rows, m, g, h);
+  } else {
 #pragma unroll
-  for (int al = 1; al <= D; ++al)
-    pull_set_vec<L, TS, VX, WALLS>(A, fin + (long long)(a1 + al - 1) * Q * A.plane, al, rows, m,
-                                   g[al - 1]);
-  if (A.with_rho) pull_set_vec<L, TS, VX, WALLS>(A, fin, 0, rows, m, h);
+    for (int al = 1; al <= D; ++al)
+      pull_set_vec<L, TS, VX, WALLS>(A, fin + (long long)(a1 + al - 1) * Q * A.plane, al, rows, m,
+                                     g[al - 1]);
+    if (A.with_rho) pull_set_vec<L, TS, VX, WALLS>(A, fin, 0, rows, m, h);
+  }
 
   const long long N = (long long)A.nx * A.ny * A.nz;
   const long long n0 = ((long long)z * A.ny + y) * A.nx + x0;
