@@ -44,6 +44,7 @@ class _Problem(ctypes.Structure):
         ("lid_u", ctypes.c_double * 3), ("dx", ctypes.c_double), ("dt", ctypes.c_double),
         ("s0", ctypes.c_double), ("s1", ctypes.c_double), ("s2", ctypes.c_double),
         ("rho0", ctypes.c_double), ("force", ctypes.POINTER(ctypes.c_double)),
+        ("scheme", ctypes.c_int),
     ]
 
 
@@ -105,6 +106,7 @@ class Problem:
     dt: float = 1.0
     rho0: float = 1.0
     force: Optional[np.ndarray] = None  # [d][N] body force at nodes
+    scheme: int = 0  # forcing: 0 = Eq. 3-21, 2 = Scheme II (Eq. 2-3c, 2-7a; state is fbar)
     _c: _Problem = field(default=None, repr=False)
 
     @property
@@ -143,6 +145,7 @@ class Problem:
             pb.force = _dptr(self.force)
         else:
             pb.force = None
+        pb.scheme = int(self.scheme)
         self._c = pb
         return pb
 

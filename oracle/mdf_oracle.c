@@ -20,6 +20,11 @@
  *     and then streams f* to x + c_i dt (periodic wrap or anti-halfway
  *     bounce-back at walls, Sec. 4);
  *   - the derived fields follow Eq. 3-16 .. 3-19.
+ * With scheme = 2 the forcing is Scheme II of Sec. 3.2 instead: the state
+ * is fbar = f - dt F / 2, advanced by Eq. 2-3c
+ *   fbar* = fbar - Lambda (fbar - f^eq) + dt (I - Lambda / 2) F,
+ * with ubar_alpha = sum_i fbar + dt Fbar_alpha / 2 (Eq. 2-7a) and P from
+ * Eq. 3-15 taken over fbar.
  * Everything is in physical units: c = dx/dt and the lattice speeds scale
  * with c, so the paper's experiments can be run as printed.  Lattice units
  * are the special case dx = dt = 1.
@@ -35,6 +40,9 @@
  *     with ubar_wall = rho0 for alpha = 0 and the wall velocity component
  *     for alpha >= 1 (the moving lid on the + face of the last axis).
  *   - For alpha = 0, ubar_0 in Eq. 2-4 is taken from Eq. 2-7 (sum of f_0).
+ *   - Scheme II: initialisation by the equilibrium means f = f^eq(P, u), so
+ *     the stored state is fbar = f^eq - dt F / 2 with the force at t = 0;
+ *     the derived fields take f^ne = f - f^eq with f = fbar + dt F / 2.
  *
  * Population layout: f[a][i][node], node = x + nx*(y + ny*z); set index a
  * maps to alpha = a when the continuity set is carried (with_rho = 1) and to
@@ -180,7 +188,24 @@ static int check(const orc_problem *pb)
         if (pb->n[b] < 1) return -1;
     if (pb->d == 2 && pb->n[2] != 1) return -1;
     if (!(pb->dx > 0.0) || !(pb->dt > 0.0)) return -1;
+    if (pb->scheme != 0 && pb->scheme != 2) return -1;
     return 0;
+}
+
+/* Fbar_alpha at a node (alpha >= 1; zero without a force or for alpha = 0). */
+static double force_at(const orc_problem *pb, int alpha, long node, long N)
+{
+    if (alpha < 1 || !pb->force) return 0.0;
+    return pb->force[(long)(alpha - 1) * N + node];
+}
+
+/* dt F_{i,alpha} / 2 = dt w_i Fbar_alpha / 2: the change of variable of
+ * Scheme II (fbar = f - dt F / 2); zero for the Eq. 3-21 forcing. */
+static double half_source(const orc_problem *pb, const double *w, int i, int alpha,
+                          long node, long N)
+{
+    if (pb->scheme != 2) return 0.0;
+    return 0.5 * pb->dt * w[i] * force_at(pb, alpha, node, N);
 }
 
 static int opposite(const double *cv, int q, int i)
@@ -216,7 +241,9 @@ static void equilibrium(int q, int d, int alpha, const double *cv, const double 
     }
 }
 
-/* Eq. 2-7 and Eq. 3-15 at one node: ubar_a for every set, u, P. */
+/* Eq. 2-7 and Eq. 3-15 at one node: ubar_a for every set, u, P.  Under
+ * Scheme II f holds fbar: ubar_a = sum_i fbar + dt Fbar_a / 2 (Eq. 2-7a) and
+ * the first moments in P are those of fbar. */
 static void macroscopic(const orc_problem *pb, const double *cv, const double *f,
                         long node, long N, double *ubar, double *u, double *P)
 {
@@ -225,6 +252,7 @@ static void macroscopic(const orc_problem *pb, const double *cv, const double *f
     for (a = 0; a < ns; ++a) {
         double s = 0.0;
         for (i = 0; i < q; ++i) s += f[((long)a * q + i) * N + node];
+        if (pb->scheme == 2) s += 0.5 * pb->dt * force_at(pb, alpha_of(pb, a), node, N);
         ubar[a] = s;
     }
     for (b = 0; b < d; ++b) {
@@ -260,7 +288,9 @@ int orc_init(const orc_problem *pb, const double *P, const double *u, double *f)
             int alpha = alpha_of(pb, a);
             double ubar = alpha == 0 ? pb->rho0 : un[alpha - 1];
             equilibrium(pb->q, pb->d, alpha, cv, w, cs2, ubar, un, P[n], feq);
-            for (i = 0; i < pb->q; ++i) f[((long)a * pb->q + i) * N + n] = feq[i];
+            /* Scheme II stores fbar = f - dt F / 2 */
+            for (i = 0; i < pb->q; ++i)
+                f[((long)a * pb->q + i) * N + n] = feq[i] - half_source(pb, w, i, alpha, n, N);
         }
     }
     return 0;
@@ -312,7 +342,7 @@ int orc_mask(const orc_problem *pb, unsigned char *mask)
 }
 
 /* ---------------------------------------------------------------------- */
-/* One time step of Eq. 3-21 followed by streaming.                       */
+/* One time step of Eq. 3-21 (Eq. 2-3c under Scheme II) and streaming.   */
 /* f holds f(x, t) (post-stream); fnew receives f(x, t + dt).             */
 /* ---------------------------------------------------------------------- */
 int orc_step(const orc_problem *pb, const double *Lam, const double *f, double *fnew)
@@ -341,14 +371,18 @@ int orc_step(const orc_problem *pb, const double *Lam, const double *f, double *
         for (a = 0; a < ns; ++a) {
             int alpha = alpha_of(pb, a);
             const double *fa = f + (long)a * q * N;
-            double Fbar = 0.0;
             /* Eq. 2-6: F_i = w_i Fbar_alpha; Fbar_0 = R = 0 */
-            if (alpha >= 1 && pb->force) Fbar = pb->force[(long)(alpha - 1) * N + n];
+            const double Fbar = force_at(pb, alpha, n, N);
             equilibrium(q, d, alpha, cv, w, cs2, ubar[a], u, P, feq); /* Eq. 2-4 */
-            for (i = 0; i < q; ++i) {                                  /* Eq. 3-21 */
-                double coll = 0.0;
+            for (i = 0; i < q; ++i) {
+                double coll = 0.0, src = 0.0;
                 for (k = 0; k < q; ++k) coll += Lam[i * q + k] * (fa[k * N + n] - feq[k]);
-                fstar[i] = fa[i * N + n] - coll + pb->dt * w[i] * Fbar;
+                if (pb->scheme == 2) /* Eq. 2-3c: dt (delta_ik - Lambda_ik / 2) F_k */
+                    for (k = 0; k < q; ++k)
+                        src += ((k == i ? 1.0 : 0.0) - 0.5 * Lam[i * q + k]) * w[k] * Fbar;
+                else                 /* Eq. 3-21: dt F_i */
+                    src = w[i] * Fbar;
+                fstar[i] = fa[i * N + n] - coll + pb->dt * src;
             }
             /* streaming to x + c_i dt, periodic or anti-halfway bounce-back */
             for (i = 0; i < q; ++i) {
@@ -449,8 +483,11 @@ int orc_derived(const orc_problem *pb, const double *f, double *G, double *div,
             equilibrium(q, d, a + 1, cv, w, cs2, ubar[set], u, P, feq);
             for (b = 0; b < d; ++b) {
                 double s = 0.0;
-                for (i = 0; i < q; ++i)
-                    s += cv[3 * i + b] * (f[((long)set * q + i) * N + n] - feq[i]);
+                for (i = 0; i < q; ++i) {
+                    /* f = fbar + dt F / 2 under Scheme II */
+                    double fi = f[((long)set * q + i) * N + n] + half_source(pb, w, i, a + 1, n, N);
+                    s += cv[3 * i + b] * (fi - feq[i]);
+                }
                 mne[a][b] = s;
             }
         }
@@ -490,7 +527,8 @@ int orc_derived(const orc_problem *pb, const double *f, double *G, double *div,
     return 0;
 }
 
-/* Sum over all nodes of ubar_a (Eq. 2-7) for every carried set. */
+/* Sum over all nodes of ubar_a (Eq. 2-7; Eq. 2-7a under Scheme II) for
+ * every carried set. */
 int orc_sums(const orc_problem *pb, const double *f, double *sums)
 {
     long N, n;
@@ -500,8 +538,10 @@ int orc_sums(const orc_problem *pb, const double *f, double *sums)
     ns = nsets(pb);
     for (a = 0; a < ns; ++a) {
         double s = 0.0;
-        for (n = 0; n < N; ++n)
+        for (n = 0; n < N; ++n) {
             for (i = 0; i < pb->q; ++i) s += f[((long)a * pb->q + i) * N + n];
+            if (pb->scheme == 2) s += 0.5 * pb->dt * force_at(pb, alpha_of(pb, a), n, N);
+        }
         sums[a] = s;
     }
     return 0;

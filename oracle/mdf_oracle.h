@@ -23,6 +23,7 @@ typedef struct {
     double s0, s1, s2; /* relaxation rates of S_d (Eq. 4-3) */
     double rho0;       /* constant density, ubar_0 */
     const double *force; /* nullable [d][N] body force at the nodes */
+    int scheme;        /* forcing: 0 = Eq. 3-21, 2 = Scheme II (Eq. 2-3c, 2-7a) */
 } orc_problem;
 
 int orc_lattice(int d, int q, double c, double *cv, double *w, double *cs2);

@@ -331,11 +331,11 @@ def test_poiseuille_matches_paper():
     assert np.abs(D["div"]).max() < 1e-12
 
 
-def _four_roll_mill(N, s1, U0=1e-4, nu=0.01, T=800.0):
+def _four_roll_mill(N, s1, U0=1e-4, nu=0.01, T=800.0, scheme=0):
     dx = 2 * math.pi / N
     dt = (1 / s1 - 0.5) * dx * dx / (3 * nu)
     F = synth.four_roll_mill_force(N, U0, nu, dx)
-    pb = O.Problem(d=2, n=(N, N), s1=s1, dx=dx, dt=dt, force=F, with_rho=False)
+    pb = O.Problem(d=2, n=(N, N), s1=s1, dx=dx, dt=dt, force=F, with_rho=False, scheme=scheme)
     f = O.init(pb, *synth.rest_state(N * N, 2))
     O.run(pb, f, int(T / dt))
     _, un, _ = O.macro(pb, f)
@@ -437,3 +437,144 @@ def test_mask_geometry_brute_force():
                 want |= ((z == n3[2] - 1) << 5) | ((z == 0) << 6)
                 want |= (z == n3[2] - 1) << 7
                 assert m[z, y, x] == want
+
+
+# --------------------------------------------------------------------------
+# Scheme II forcing (Eq. 2-3c, 2-7a)
+# --------------------------------------------------------------------------
+def _half_source(pb, F, w):
+    """dt F_{i,alpha} / 2 = dt w_i Fbar_alpha / 2 laid out like the populations."""
+    h = np.zeros((pb.nsets, pb.q, pb.N))
+    off = 1 if pb.with_rho else 0
+    for a in range(pb.d):
+        h[off + a] = 0.5 * pb.dt * w[:, None] * F[a][None, :]
+    return h
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_scheme2_is_eq_2_3a_with_implicit_force_derivative(d):
+    """Scheme II comes from Eq. 2-3a with D_i F replaced by the implicit
+    difference (F(x + c_i dt, t + dt) - F(x, t)) / dt and the variable
+    fbar = f - dt F / 2.  Undo the change of variable and check Eq. 2-3a
+    itself.  Let G be one step of Eq. 3-21 (pinned above) applied to
+    f = fbar + dt F / 2.  Then, at y = x + c_i dt, Eq. 2-3a with a steady,
+    non-uniform force reads
+        f_i(y, t + dt) = G_i(y) + (dt / 2) (F_i(y) - F_i(y - c_i dt)).
+    The check is in physical units (dx, dt != 1) and keeps the alpha = 0 set."""
+    if d == 2:
+        n = (9, 7)
+        P, u = _seeded_fields_2d(*n, 5)
+    else:
+        n = (5, 4, 6)
+        P, u = _seeded_fields_3d(n, 5)
+    dx, dt = 0.5, 0.2
+    rng = synth.SplitMix64(77)
+    X = synth.grid_coords(n)
+    F = np.stack([0.03 * np.sin(2 * math.pi * X[a] / n[a] + 6 * rng.uniform())
+                  + 0.02 * np.cos(2 * math.pi * X[(a + 1) % d] / n[(a + 1) % d] + 6 * rng.uniform())
+                  for a in range(d)])
+    pb2 = O.Problem(d=d, n=n, s1=1.3, s2=0.9, s0=1.1, dx=dx, dt=dt, force=F, scheme=2)
+    pb0 = O.Problem(d=d, n=n, s1=1.3, s2=0.9, s0=1.1, dx=dx, dt=dt, force=F, scheme=0)
+    cint, w, _ = O.lattice(d, pb2.q, 1.0)
+    fb = O.run(pb2, O.init(pb2, P, u), 3)  # a non-equilibrium fbar
+    fb1 = O.run(pb2, fb.copy(), 1)
+    h = _half_source(pb2, F, w)
+    G = O.run(pb0, fb + h, 1)
+    shape = (n[2], n[1], n[0]) if d == 3 else (n[1], n[0])
+    want = G.copy()
+    off = 1
+    for a in range(d):
+        Fa = F[a].reshape(shape)
+        for i in range(pb2.q):
+            shift = tuple(int(cint[i, b]) for b in reversed(range(d)))  # array axes: z, y, x
+            Fprev = np.roll(Fa, shift, axis=tuple(range(d))).ravel()    # F(y - c_i dt)
+            want[off + a, i] -= 0.5 * dt * w[i] * Fprev
+    # fbar(t + dt) + dt F(y) / 2 = G + (dt / 2)(F(y) - F(y - c_i dt))
+    assert np.abs(fb1 - want).max() < 1e-15
+    assert np.abs(fb1 - G).max() > 1e-4  # the two forcings differ at O(dt F)
+
+
+def test_scheme2_time_dependent_uniform_force_is_trapezoidal():
+    """A uniform force on a periodic box keeps every node equal, so the zeroth
+    moment of Eq. 2-3c gains dt Fbar per step and Eq. 2-7a reads
+    ubar(t_n) = u0 + dt [F^0/2 + F^1 + ... + F^(n-1) + F^n/2]: the
+    trapezoidal rule, exact for a force linear in time, given the equilibrium
+    start f = f^eq (fbar = f^eq - dt F^0 / 2).  Eq. 3-21 gives the left
+    Riemann sum instead."""
+    n, dt = (4, 3), 0.5
+    u0 = np.array([0.01, -0.02])
+    a, b = np.array([2e-3, -1e-3]), np.array([3e-4, 5e-4])
+    N = n[0] * n[1]
+    P = np.ones(N)
+    u = np.repeat(u0[:, None], N, axis=1)
+    out = {}
+    for scheme in (0, 2):
+        pb = O.Problem(d=2, n=n, s1=1.5, dt=dt, dx=1.0, scheme=scheme,
+                       force=np.repeat((a)[:, None], N, axis=1))
+        f = O.init(pb, P, u)
+        errs = []
+        for k in range(1, 21):
+            t = k * dt
+            pb.force = np.repeat((a + b * (t - dt))[:, None], N, axis=1)
+            O.run(pb, f, 1)
+            pb.force = np.repeat((a + b * t)[:, None], N, axis=1)
+            _, un, _ = O.macro(pb, f)
+            exact = u0 + a * t + 0.5 * b * t * t
+            errs.append(np.abs(un - exact[:, None]).max())
+        out[scheme] = max(errs)
+    assert out[2] < 1e-15
+    assert out[0] > 1e-4
+
+
+def test_scheme2_poiseuille_is_exact():
+    """Sec. 4.1 Poiseuille flow under Scheme II, with the anti-halfway
+    bounce-back acting on the evolved variable fbar.  In the bulk the steady
+    state of Eq. 2-3c solves the same second-order difference equation as
+    Eq. 3-21 (a uniform force has no implicit difference), which a parabola
+    satisfies exactly.  At a wall, Scheme II's bounce-back of fbar =
+    f - dt F / 2 is Eq. 3-21's bounce-back plus dt w_i Fbar: the force term
+    the Eq. 3-21 wall rule misses, and the source of the O(dx^2) error
+    the paper prints for it (E(u1) = 5.9427e-4 at this size).  So
+    the steady profile is the parabola itself, up to the convergence of
+    the run, and so are du1/dy and S_xy."""
+    g = _gold("paper_numbers.json")["poiseuille"]
+    N, nu, F1, s1 = g["N"], g["nu"], g["F1"], g["s1"]
+    dx = 1.0 / N
+    dt = (1 / s1 - 0.5) * dx * dx / (3 * nu)
+    F = np.zeros((2, N * N))
+    F[0] = F1
+    out = {}
+    for scheme in (0, 2):
+        pb = O.Problem(d=2, n=(N, N), s1=s1, wall=(0, 1, 0), dx=dx, dt=dt, force=F, scheme=scheme)
+        f = O.init(pb, *synth.rest_state(N * N, 2))
+        O.run(pb, f, 22000)
+        _, un, _ = O.macro(pb, f)
+        out[scheme] = (un, O.derived(pb, f))
+    y = (np.arange(N) + 0.5) * dx
+    ua = np.repeat(F1 / (2 * nu) * (y - y * y), N)
+    gy = np.repeat(F1 / (2 * nu) * (1 - 2 * y), N)
+    un, D = out[2]
+    assert O.rel_l2(ua, un[0]) < 1e-8
+    assert np.abs(un[1]).max() < 1e-13
+    assert O.rel_l2(gy, D["G"][0, 1]) < 1e-8
+    assert O.rel_l2(gy / 2, D["S"][1]) < 1e-8
+    assert np.abs(D["div"]).max() < 1e-12
+    # the same run under Eq. 3-21 keeps the printed wall error
+    assert O.rel_l2(ua, out[0][0][0]) == pytest.approx(g["E_u1"], rel=2e-3)
+    # and the wall rule is the only difference: the two profiles differ by
+    # a constant, the slip velocity of the Eq. 3-21 wall rule
+    du = (out[0][0][0] - un[0]).reshape(N, N)[:, 0]
+    assert np.allclose(du, du[0], rtol=0, atol=1e-9 * np.abs(ua).max())
+
+
+def test_scheme2_four_roll_mill_second_order():
+    """Scheme II on the four-roll mill of Sec. 4.2 (a steady, non-uniform
+    force): u, S and omega converge at second order to the closed-form
+    solution, with errors of the size Table 1 prints for Eq. 3-21."""
+    e = [_four_roll_mill(N, 1.2, scheme=2) for N in (16, 32, 64)]
+    ref = _four_roll_mill(64, 1.2)
+    for key in ("E_u1", "E_Sxx", "E_omega"):
+        for lo, hi in zip(e[:-1], e[1:]):
+            assert 3.6 < lo[key] / hi[key] < 4.4, (key, lo[key], hi[key])
+        assert 0.25 < e[-1][key] / ref[key] < 4.0, (key, e[-1][key], ref[key])
+    assert e[-1]["E_u1"] != ref["E_u1"]
