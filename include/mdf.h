@@ -154,6 +154,29 @@ mdf_status mdf_init(mdf_t h, const double *P, const double *u, int where);
  */
 mdf_status mdf_set_force(mdf_t h, const double *F, int where);
 
+/*
+ * mdf_set_forcing -- forcing scheme of the update (Sec. 3.2):
+ *   MDF_FORCING_EQ321   (default) Eq. 3-21: f* = f - Lambda (f - f^eq) + dt F;
+ *   MDF_FORCING_SCHEME2 Scheme II, Eq. 2-3c and Eq. 2-7a: the state is
+ *     fbar = f - dt F/2, fbar* = fbar - Lambda (fbar - f^eq) + dt (I - Lambda/2) F,
+ *     ubar_alpha = sum_i fbar_{i,alpha} + dt Fbar_alpha / 2, and P from
+ *     Eq. 3-15 over fbar.
+ * Under Scheme II:
+ *   - the anti-halfway bounce-back acts on fbar;
+ *   - mdf_init stores fbar = f^eq(P, u) - dt F/2 with the force set at
+ *     that time, so call mdf_set_force first;
+ *   - the fields, sums and residual read ubar from Eq. 2-7a;
+ *   - the f^ne of Eq. 3-16 is that of f = fbar + dt F/2, which has the same
+ *     first moment.
+ * Without a force the two schemes are the same update.  A change does not
+ * convert the state; checkpoints record the scheme, and mdf_load requires a
+ * match.  Errors: MDF_EINVAL for an unknown scheme.
+ */
+#define MDF_FORCING_EQ321 0
+#define MDF_FORCING_SCHEME2 2
+mdf_status mdf_set_forcing(mdf_t h, int scheme);
+mdf_status mdf_get_forcing(mdf_t h, int *scheme);
+
 /* mdf_step -- advance n >= 0 time steps of Eq. 3-21 with streaming. */
 mdf_status mdf_step(mdf_t h, long long n);
 

@@ -137,6 +137,20 @@ class Lattice:
             return
         self._check(self._lib.mdf_set_force(self._h, _ptr(F), DEVICE if _is_device(F) else HOST))
 
+    FORCING = {"eq3-21": 0, "scheme2": 2}
+
+    def set_forcing(self, scheme: str):
+        """'eq3-21' (default, Eq. 3-21) or 'scheme2' (Scheme II, Eq. 2-3c and
+        2-7a: the state is fbar = f - dt F/2).  Set it, and the force, before
+        init: the Scheme II initial state is f^eq - dt F/2."""
+        self._check(self._lib.mdf_set_forcing(self._h, self.FORCING[scheme]))
+
+    @property
+    def forcing(self) -> str:
+        v = ctypes.c_int()
+        self._check(self._lib.mdf_get_forcing(self._h, ctypes.byref(v)))
+        return {k: n for n, k in self.FORCING.items()}[v.value]
+
     def step(self, n: int = 1):
         self._check(self._lib.mdf_step(self._h, int(n)))
 

@@ -61,6 +61,8 @@ SIGNATURES = {
     "mdf_destroy": (None, [H]),
     "mdf_init": (ctypes.c_int, [H, DP, DP, ctypes.c_int]),
     "mdf_set_force": (ctypes.c_int, [H, DP, ctypes.c_int]),
+    "mdf_set_forcing": (ctypes.c_int, [H, ctypes.c_int]),
+    "mdf_get_forcing": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_int)]),
     "mdf_step": (ctypes.c_int, [H, ctypes.c_longlong]),
     "mdf_step_fields": (ctypes.c_int, [H, ctypes.c_longlong, ctypes.POINTER(Fields)]),
     "mdf_fields": (ctypes.c_int, [H, ctypes.POINTER(Fields)]),

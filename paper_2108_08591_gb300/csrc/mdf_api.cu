@@ -74,6 +74,7 @@ struct mdf_s {
   void *cur = nullptr, *nxt = nullptr;  // population buffers
   uint8_t *mask = nullptr;
   void *force = nullptr;  // FP32, or FP64 with FP64 storage
+  int forcing = MDF_FORCING_EQ321;  // forcing scheme of the update
   double *stage = nullptr;  // staging for host inputs/outputs
   size_t stage_bytes = 0;
   double *uprev = nullptr;  // residual memory [d][N]
@@ -119,6 +120,7 @@ DevArgs base_args(const mdf_t h) {
   a.fout = h->nxt;
   a.mask = h->walls ? h->mask : nullptr;
   a.force = h->force;
+  a.scheme2 = (h->forcing == MDF_FORCING_SCHEME2 && h->force) ? 1 : 0;
   a.nx = h->nx; a.ny = h->ny; a.nz = h->nz; a.px = h->px;
   a.plane = h->plane;
   a.with_rho = h->with_rho;
@@ -239,6 +241,7 @@ uint64_t fnv1a(const unsigned char *p, size_t n, uint64_t hsh = 1469598103934665
 struct CkptHeader {
   char magic[8];
   int32_t version, d, q, nsets, storage, nx, ny, nz, px, wall[3], lid;
+  int32_t forcing;  // the state is fbar under Scheme II: part of its meaning
   double s0, s1, s2, lid_u[3];
   int64_t step, payload;
   uint64_t checksum;
@@ -413,6 +416,24 @@ mdf_status mdf_set_force(mdf_t h, const double *F, int where) {
   return MDF_OK;
 }
 
+mdf_status mdf_set_forcing(mdf_t h, int scheme) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (scheme != MDF_FORCING_EQ321 && scheme != MDF_FORCING_SCHEME2)
+    return fail(h, MDF_EINVAL, "set_forcing: unknown scheme %d", scheme);
+  if (scheme == h->forcing) return MDF_OK;
+  CU(h, cudaStreamSynchronize(h->stream));
+  drop_graphs(h);  // captured launches hold the old scheme
+  h->forcing = scheme;
+  return MDF_OK;
+}
+
+mdf_status mdf_get_forcing(mdf_t h, int *scheme) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!scheme) return fail(h, MDF_EINVAL, "get_forcing: null output");
+  *scheme = h->forcing;
+  return MDF_OK;
+}
+
 mdf_status mdf_step(mdf_t h, long long n) {
   if (check_handle(h)) return MDF_EINVAL;
   if (n < 0) return fail(h, MDF_EINVAL, "step: n < 0");
@@ -545,6 +566,7 @@ static void fill_header(const mdf_t h, CkptHeader &hd) {
   hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz; hd.px = h->px;
   for (int b = 0; b < 3; ++b) { hd.wall[b] = h->bc.wall[b]; hd.lid_u[b] = h->bc.lid_u[b]; }
   hd.lid = h->bc.lid;
+  hd.forcing = h->forcing;
   hd.s0 = h->s0; hd.s1 = h->s1; hd.s2 = h->s2;
   hd.step = h->step;
   hd.payload = (int64_t)(h->pop_bytes() + h->mom_bytes());

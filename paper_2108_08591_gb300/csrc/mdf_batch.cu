@@ -455,7 +455,8 @@ __global__ void __launch_bounds__(kTile) k_batch_fields(BatchArgs B, int cur, in
   float g[D][Q], h[Q];
   long long idx;
   batch_pull<L>(B, B.f[cur], C, (int)n, g, h, idx);
-  write_fields<L, float>(A, n, NN, g, h);
+  const float F0[D] = {};  // cavities carry no body force
+  write_fields<L, float>(A, n, NN, g, h, F0);
 }
 
 }  // namespace mdf

@@ -380,10 +380,22 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
 
   const long long N = (long long)A.nx * A.ny * A.nz;
   const long long n0 = ((long long)z * A.ny + y) * A.nx + x0;
+  float Fr[D][VX];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (A.force) {
+      VecIO<float, VX>::load(static_cast<const float *>(A.force) + a * A.plane + row0 + x0, Fr[a]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < VX; ++j) Fr[a][j] = 0.f;
+    }
+  }
   if (MODE != MODE_STEP && active) {  // derived fields of the pulled state (FP32, unscaled)
 #pragma unroll
     for (int j = 0; j < VX; ++j) {
-      float gn[D][Q], hn[Q];
+      float gn[D][Q], hn[Q], Fn[D];
+#pragma unroll
+      for (int a = 0; a < D; ++a) Fn[a] = Fr[a][j];
 #pragma unroll
       for (int i = 0; i < Q; ++i) {
         float v[LW];
@@ -395,7 +407,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
         from_lanes(v, G[D][i][j / LW]);
         hn[i] = A.with_rho ? vmul(v[j % LW], INV) : 0.f;
       }
-      write_fields<L, float>(A, n0 + j, N, gn, hn);
+      write_fields<L, float>(A, n0 + j, N, gn, hn, Fn);
     }
   }
   if (MODE == MODE_FIELDS || !active) return;
@@ -417,29 +429,31 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
     kf[4] = (1.f - s2) * 0.25f;
     kf[5] = (1.f - s2) * float(-1.0 / 7.0);
   }
-  float Fr[D][VX];
-#pragma unroll
-  for (int a = 0; a < D; ++a) {
-    if (A.force) {
-      VecIO<float, VX>::load(static_cast<const float *>(A.force) + a * A.plane + row0 + x0, Fr[a]);
-    } else {
-#pragma unroll
-      for (int j = 0; j < VX; ++j) Fr[a][j] = 0.f;
-    }
-  }
+  // Scheme II (Eq. 2-3c): G holds SCALE fbar; ubar = sum fbar + Fbar/2
+  // (Eq. 2-7a) builds the equilibrium first moments and the stored moments,
+  // m4 relaxes towards k sum fbar, and the stored deviation from
+  // g^eq(ubar) carries w_i Fbar / 2 (the zeroth and m4 parts of the
+  // (I - S/2) source less the Fbar/2 in g^eq; the s0 and s2 terms cancel).
+  const float fw_scale = A.scheme2 ? 0.5f : 1.f;
   T Mn[KM][NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) {
     // Every product that meets a sum is one fma (nothing is left for the
     // compiler to contract, so scalar and pair lanes give the same bits).
-    T us[D], u[D], un[D], dif[D + 1][D], tr = splat<T>(0.f), usqS = splat<T>(0.f);
+    T us[D], ub[D], u[D], un[D], Fs[D], dif[D + 1][D], tr = splat<T>(0.f), usqS = splat<T>(0.f);
 #pragma unroll
     for (int a = 0; a < D; ++a) {
+      float fl[LW];
+#pragma unroll
+      for (int e = 0; e < LW; ++e) fl[e] = Fr[a][LW * q + e];
+      to_lanes(Fs[a], fl);
+      Fs[a] = vmul(Fs[a], splat<T>(SC));
       T sm = G[a][0][q];
 #pragma unroll
       for (int i = 1; i < Q; ++i) sm = vadd(sm, G[a][i][q]);
       us[a] = sm;
-      u[a] = SC == 1.f ? sm : vmul(sm, splat<T>(INV));
+      ub[a] = A.scheme2 ? vfma(Fs[a], splat<T>(0.5f), sm) : sm;
+      u[a] = SC == 1.f ? ub[a] : vmul(ub[a], splat<T>(INV));
       un[a] = vsub(splat<T>(0.f), u[a]);
     }
 #pragma unroll
@@ -451,7 +465,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
 #pragma unroll
     for (int a = 0; a < D; ++a) {  // sum_i c_{i,a} G_{i,a} and SCALE |u|^2
       tr = vadd(tr, dif[a][a]);
-      usqS = vfma(us[a], u[a], usqS);
+      usqS = vfma(ub[a], u[a], usqS);
     }
     // Eq. 3-15 (scaled): SCALE P' = (SCALE tr - SCALE |u|^2) / d
     const T PS = vmul(vsub(tr, usqS), splat<T>(float(1.0 / D)));
@@ -462,14 +476,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
       T Ef[D];
 #pragma unroll
       for (int b = 0; b < D; ++b)
-        Ef[b] = a == b ? vsub(dif[a][b], vfma(us[a], u[b], PS)) : vfma(us[a], un[b], dif[a][b]);
-      T Fs;
-      float fl[LW];
-#pragma unroll
-      for (int e = 0; e < LW; ++e) fl[e] = Fr[a][LW * q + e];
-      to_lanes(Fs, fl);
-      Fs = vmul(Fs, splat<T>(SC));
-      const T Fw = vmul(Fs, splat<T>(float(L::w(1)))), Fw0 = vmul(Fs, splat<T>(float(L::w(0))));
+        Ef[b] = a == b ? vsub(dif[a][b], vfma(ub[a], u[b], PS)) : vfma(ub[a], un[b], dif[a][b]);
+      const T Fw = vmul(Fs[a], splat<T>(fw_scale * float(L::w(1))));
+      const T Fw0 = vmul(Fs[a], splat<T>(fw_scale * float(L::w(0))));
       T gq[Q];
 #pragma unroll
       for (int i = 0; i < Q; ++i) gq[i] = G[a][i][q];
@@ -529,7 +538,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
 // Initial state f = f^eq(P, u) in pull form for this codec: moments
 // M0 = (u, P - 1, 0) at every node, and s_i(x) such that the first pull
 // rebuilds g^eq_i(M0(x + c_i)) at x + c_i (or, on a wall link, the value
-// whose bounce-back returns g^eq_opp(M0(x)) at x).
+// whose bounce-back returns g^eq_opp(M0(x)) at x).  Under Scheme II the
+// rebuilt value is fbar = f^eq - w_i Fbar / 2 (its ubar is still u).
 template <class L>
 __device__ __forceinline__ void init_moments(const DevArgs &A, long long N, long long n,
                                              float (&M)[L::D + 2]) {
@@ -561,9 +571,12 @@ __global__ void __launch_bounds__(kMaxBlock) k_init_eq(const DevArgs A) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       float target;
+      const bool half = A.scheme2 && alpha >= 1;
+      const float *Fa = half ? static_cast<const float *>(A.force) + (alpha - 1) * A.plane : nullptr;
       if (WALLS && i != 0 && ((m >> i) & 1)) {
         target = -geq_m<L>(alpha, L::opp(i), M0);
         if (alpha >= 1 && i == L::UP && (m & 0x80u)) target += float(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+        if (half) target += float(0.5 * L::w(i)) * __ldg(Fa + idx);  // negated by the bounce-back
       } else {
         const int tx = wrap(x + L::c(i, 0), A.nx);
         const int ty = wrap(y + L::c(i, 1), A.ny);
@@ -571,6 +584,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_init_eq(const DevArgs A) {
         float Mt[D + 2];
         init_moments<L>(A, N, ((long long)tz * A.ny + ty) * A.nx + tx, Mt);
         target = geq_m<L>(alpha, i, Mt);
+        if (half) target -= float(0.5 * L::w(i)) * __ldg(Fa + ((long long)tz * A.ny + ty) * A.px + tx);
       }
       Codec<TS>::store(fout + ((long long)a * Q + i) * A.plane + idx,
                        (target - geq_m<L>(alpha, i, M0)) * EqScale<TS>::s);
@@ -636,6 +650,9 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_eq(const DevArgs A) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) s += (double)g[a][i];
       if (alpha == 0) s += 1.0;
+      if (A.scheme2 && alpha >= 1)  // Eq. 2-7a
+        s += 0.5 * (double)__ldg(static_cast<const float *>(A.force) + (alpha - 1) * A.plane +
+                                 ((long long)z * A.ny + y) * A.px + x);
       bad |= !isfinite(s);
       if (KIND == RED_SUMS) {
         acc[a] += s;

@@ -82,7 +82,8 @@ __device__ __forceinline__ void pull_set(const DevArgs &A, const TS *__restrict_
 // widening to FP64 is built on the integer pipe, leaving two FP64 adds.)
 template <class L, class TC>
 __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long long N,
-                                             const TC (&gv)[L::D][L::Q], const TC (&h)[L::Q]) {
+                                             const TC (&gv)[L::D][L::Q], const TC (&h)[L::Q],
+                                             const TC (&F)[L::D]) {
   constexpr int D = L::D, Q = L::Q;
   TC u[D], J[D][D];
 #pragma unroll
@@ -90,7 +91,7 @@ __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long
     TC s = TC(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) s += gv[a][i];
-    u[a] = s;
+    u[a] = A.scheme2 ? s + TC(0.5) * F[a] : s;  // Eq. 2-7a under Scheme II
 #pragma unroll
     for (int b = 0; b < D; ++b) {
       TC t = TC(0);
@@ -118,6 +119,7 @@ __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long
   }
   if (!(A.G || A.div || A.S || A.sigma || A.omega)) return;
   // first moment of f^ne: sum_i c_{i,b} (f - f^eq)_{i,a} = J - u_a u_b - P' delta_ab
+  // (under Scheme II f = fbar + F/2, whose first moment is fbar's)
   TC mne[D][D];
 #pragma unroll
   for (int a = 0; a < D; ++a)
@@ -162,7 +164,19 @@ __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long
 // Eq. 2-7, 3-15, 2-4 (moments of Eq. 3-7a) and 3-21 at one node, in place
 // on its pulled populations: g (the d velocity sets) and h (the alpha = 0
 // set) become the post-collision populations.  F: Fbar_alpha, alpha = 1..d.
-template <class L, class TC>
+//
+// S2 (Scheme II): g holds fbar = f - F/2 and the update is Eq. 2-3c with ubar from
+// Eq. 2-7a.  In moment space (M has orthogonal rows, m = M fbar, F_m = M F):
+//   row 0:    m0 - s0 (m0 - ubar) + (1 - s0/2) Fbar = m0 + Fbar, as
+//             m0 - ubar = -Fbar/2, so s0 drops out;
+//   rows b:   m_b - s1 (m_b - ubar_a ubar_b - P' delta_ab), F_m = 0;
+//   m4 row:   with k = sum_i w_i M4_i, m4eq = k ubar = k (m0 + Fbar/2), and
+//             the s2 (Fbar/2) terms cancel: k (m0 + Fbar) + (1 - s2)(m4 - k m0);
+//   other rows carry no equilibrium or force part.
+// So Scheme II is the Eq. 3-21 relaxation below with the equilibrium first
+// moments built from ubar (m4 relaxes towards k m0 there already) and the
+// same w_i Fbar source.
+template <class L, class TC, bool S2 = false>
 __device__ __forceinline__ void collide_node(TC (&g)[L::D][L::Q], TC (&h)[L::Q], bool with_rho,
                                              const TC (&F)[L::D], TC s1, TC s2,
                                              TC (&M)[L::D + 2]) {
@@ -179,7 +193,8 @@ __device__ __forceinline__ void collide_node(TC (&g)[L::D][L::Q], TC (&h)[L::Q],
       if (L::c(i, a) > 0) t += g[a][i];
       if (L::c(i, a) < 0) t -= g[a][i];
     }
-    u[a] = s;
+    if constexpr (S2) u[a] = s + TC(0.5) * F[a];  // Eq. 2-7a
+    else u[a] = s;
     tr += t;
   }
 #pragma unroll
@@ -231,19 +246,20 @@ __global__ void __launch_bounds__(kMaxBlock) k_update(const DevArgs A) {
   for (int al = 1; al <= D; ++al) pull_set<L, TS, WALLS>(A, fin, a1 + al - 1, al, idx, src, m, g[al - 1]);
   if (A.with_rho) pull_set<L, TS, WALLS>(A, fin, 0, 0, idx, src, m, h);
 
-  if (MODE != MODE_STEP) {
-    const long long N = (long long)A.nx * A.ny * A.nz;
-    const long long n = ((long long)z * A.ny + y) * A.nx + x;
-    write_fields<L, TC>(A, n, N, g, h);
-    if (MODE == MODE_FIELDS) return;
-  }
-
   TC F[D];
 #pragma unroll
   for (int a = 0; a < D; ++a)
     F[a] = A.force ? __ldg(static_cast<const TC *>(A.force) + a * A.plane + idx) : TC(0);
+  if (MODE != MODE_STEP) {
+    const long long N = (long long)A.nx * A.ny * A.nz;
+    const long long n = ((long long)z * A.ny + y) * A.nx + x;
+    write_fields<L, TC>(A, n, N, g, h, F);
+    if (MODE == MODE_FIELDS) return;
+  }
+
   TC M[D + 2];
-  collide_node<L, TC>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M);
+  if (A.scheme2) collide_node<L, TC, true>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M);
+  else collide_node<L, TC, false>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M);
 
   TS *__restrict__ fout = static_cast<TS *>(A.fout);
 #pragma unroll
@@ -477,7 +493,7 @@ __device__ __forceinline__ void pull_all_vec16(const DevArgs &A, const TS *__res
   }
 }
 
-template <class L, class TS, int VX, int MODE, bool WALLS>
+template <class L, class TS, int VX, int MODE, bool WALLS, bool S2>
 __global__ void __launch_bounds__(kMaxBlock) k_update_vec(const DevArgs A) {
   using TC = typename ComputeOf<TS>::T;
   constexpr int D = L::D, Q = L::Q;
@@ -538,12 +554,12 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_vec(const DevArgs A) {
       for (int a = 0; a < D; ++a) gn[a][i] = g[a][i][j];
       hn[i] = h[i][j];
     }
-    if (MODE != MODE_STEP && active) write_fields<L, TC>(A, n0 + j, N, gn, hn);
-    if (MODE == MODE_FIELDS) continue;
 #pragma unroll
     for (int a = 0; a < D; ++a) Fn[a] = F[a][j];
+    if (MODE != MODE_STEP && active) write_fields<L, TC>(A, n0 + j, N, gn, hn, Fn);
+    if (MODE == MODE_FIELDS) continue;
     TC M[D + 2];
-    collide_node<L, TC>(gn, hn, A.with_rho != 0, Fn, s1, s2, M);
+    collide_node<L, TC, S2>(gn, hn, A.with_rho != 0, Fn, s1, s2, M);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
 #pragma unroll
@@ -601,7 +617,9 @@ __device__ __forceinline__ TC geq(const DevArgs &A, long long N, long long n, in
 // Initial state f = f^eq(P, u) written in pull form: the value stored at x
 // for direction i is the one the first update pulls into x + c_i, and for a
 // wall link the one whose bounce-back returns f^eq_opp(i)(x).  Each of the
-// Q source nodes' seed is rounded once and shared by the sets.
+// Q source nodes' seed is rounded once and shared by the sets.  Under
+// Scheme II the state is fbar = f^eq - w_i Fbar_alpha / 2 with the force at
+// the node the value arrives at.
 template <class L, class TS, bool WALLS>
 __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
   using TC = typename ComputeOf<TS>::T;
@@ -614,14 +632,17 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
   const long long n = ((long long)z * A.ny + y) * A.nx + x;
   const uint8_t m = WALLS ? A.mask[idx] : uint8_t(0);
   TC tu[Q][D], tP[Q];
+  long long tidx[Q];  // padded index of the node each value arrives at
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     long long t = n;
+    tidx[i] = idx;
     if (!(WALLS && i != 0 && ((m >> i) & 1))) {
       const int tx = wrap(x + L::c(i, 0), A.nx);
       const int ty = wrap(y + L::c(i, 1), A.ny);
       const int tz = D == 3 ? wrap(z + L::c(i, 2), A.nz) : z;
       t = ((long long)tz * A.ny + ty) * A.nx + tx;
+      tidx[i] = ((long long)tz * A.ny + ty) * A.px + tx;
     }
     seed_at<L, TC>(A, N, t, tu[i], tP[i]);
   }
@@ -632,11 +653,17 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       TC v;
-      if (WALLS && i != 0 && ((m >> i) & 1)) {
+      const bool wall = WALLS && i != 0 && ((m >> i) & 1);
+      if (wall) {
         v = -geq_v<L, TC>(alpha, L::opp(i), tu[i], tP[i]);
         if (alpha >= 1 && i == L::UP && (m & 0x80u)) v += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
       } else {
         v = geq_v<L, TC>(alpha, i, tu[i], tP[i]);
+      }
+      if (A.scheme2 && alpha >= 1) {  // the bounce-back negates the shift
+        const TC Fh = TC(0.5 * L::w(i)) * __ldg(static_cast<const TC *>(A.force) +
+                                                (alpha - 1) * A.plane + (wall ? idx : tidx[i]));
+        v = wall ? v + Fh : v - Fh;
       }
       Codec<TS>::store(fout + ((long long)a * Q + i) * A.plane + idx, v);
     }
@@ -695,6 +722,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const DevArgs A) {
 #pragma unroll
       for (int i = 0; i < Q; ++i) s += (double)g[i];
       if (alpha == 0) s += 1.0;  // the rest shift of the alpha = 0 set sums to rho0
+      if (A.scheme2 && alpha >= 1)  // Eq. 2-7a
+        s += 0.5 * (double)__ldg(static_cast<const TC *>(A.force) + (alpha - 1) * A.plane + idx);
       bad |= !isfinite(s);
       if (KIND == RED_SUMS) {
         acc[a] += s;
@@ -771,8 +800,15 @@ cudaError_t update_vec(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
   const int bx = a.block;
   const int threads = a.nx / VX;
   const dim3 grid((unsigned)((threads + bx - 1) / bx), (unsigned)a.ny, (unsigned)a.nz), block(bx);
-  if (walls) k_update_vec<L, TS, VX, MODE_STEP, true><<<grid, block, 0, s>>>(a);
-  else k_update_vec<L, TS, VX, MODE_STEP, false><<<grid, block, 0, s>>>(a);
+  // Scheme II is a separate build: its ubar needs the force before the
+  // moments, which costs the Eq. 3-21 kernel registers when decided at run time
+  if (a.scheme2) {
+    if (walls) k_update_vec<L, TS, VX, MODE_STEP, true, true><<<grid, block, 0, s>>>(a);
+    else k_update_vec<L, TS, VX, MODE_STEP, false, true><<<grid, block, 0, s>>>(a);
+  } else {
+    if (walls) k_update_vec<L, TS, VX, MODE_STEP, true, false><<<grid, block, 0, s>>>(a);
+    else k_update_vec<L, TS, VX, MODE_STEP, false, false><<<grid, block, 0, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -97,6 +97,72 @@ def test_four_roll_mill_table1(storage):
         assert _rel(om, out["omega"][0]) == pytest.approx(g["E_omega"][j], rel=tol)
 
 
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_scheme2_poiseuille_is_exact(storage):
+    """Sec. 4.1's Poiseuille flow under Scheme II (Eq. 2-3c, 2-7a): the
+    bounce-back of fbar carries the force term Eq. 3-21's wall rule misses,
+    and the steady profile is the parabola itself (the FP64 oracle reaches
+    it to 1e-9 in these 22000 steps), where Eq. 3-21 leaves the printed
+    E(u1) = 5.9427e-4.  FP32 storage: the biased rounding of the force
+    increments (see the Eq. 3-21 test) leaves ~1e-5."""
+    from paper_2108_08591_gb300 import Lattice
+    g = _gold("poiseuille")
+    N, nu, F1, s1 = g["N"], g["nu"], g["F1"], g["s1"]
+    dx = 1.0 / N
+    dt = (1 / s1 - 0.5) * dx * dx / (3 * nu)
+    lat = Lattice((N, N), s1=s1, wall=(0, 1), storage=storage)
+    F = np.zeros((2, N * N))
+    F[0] = F1 * dt * dt / dx
+    lat.set_forcing("scheme2")
+    lat.set_force(F)
+    lat.init(*synth.rest_state(N * N, 2))
+    lat.step(22000)
+    out = lat.fields_host(("u", "G", "S"))
+    lat.close()
+    y = (np.arange(N) + 0.5) * dx
+    ua = np.repeat(F1 / (2 * nu) * (y - y * y), N) * dt / dx
+    gy = np.repeat(F1 / (2 * nu) * (1 - 2 * y), N) * dt
+    bound = 1e-8 if storage == "f64" else 1e-4
+    assert _rel(ua, out["u"][0]) < bound
+    floor = 1e-8 if storage == "f64" else 3e-2
+    assert _rel(gy, out["G"][0, 1]) < floor
+    assert _rel(gy / 2, out["S"][1]) < floor
+
+
+def test_scheme2_four_roll_mill_matches_oracle():
+    """The four-roll mill of Sec. 4.2 at 64^2, s1 = 1.2, under Scheme II:
+    the errors against the closed form equal the FP64 oracle's (which halves
+    Eq. 3-21's velocity error) within 0.1 %."""
+    import oracle as O
+    from paper_2108_08591_gb300 import Lattice
+    g = _gold("four_roll_mill_table1")
+    N, U0, nu, s1 = g["N"], g["U0"], g["nu"], 1.2
+    dx = 2 * math.pi / N
+    dt = (1 / s1 - 0.5) * dx * dx / (3 * nu)
+    F = synth.four_roll_mill_force(N, U0, nu, dx)
+    steps = int(800.0 / dt)
+    pb = O.Problem(d=2, n=(N, N), s1=s1, dx=dx, dt=dt, force=F, with_rho=False, scheme=2)
+    f = O.run(pb, O.init(pb, *synth.rest_state(N * N, 2)), steps)
+    _, un, _ = O.macro(pb, f)
+    D = O.derived(pb, f)
+    lat = Lattice((N, N), s1=s1, storage="f64", with_rho=False)
+    lat.set_forcing("scheme2")
+    lat.set_force(F * dt * dt / dx)
+    lat.init(*synth.rest_state(N * N, 2))
+    lat.step(steps)
+    out = lat.fields_host(("u", "S", "omega"))
+    lat.close()
+    X, Y = synth.grid_coords((N, N))
+    X, Y = X * dx, Y * dx
+    u1 = U0 * np.sin(X) * np.cos(Y)
+    Sxx = U0 * np.cos(X) * np.cos(Y)
+    om = 2 * U0 * np.sin(X) * np.sin(Y)
+    assert _rel(u1 * dt / dx, out["u"][0]) == pytest.approx(_rel(u1, un[0]), rel=1e-3)
+    assert _rel(Sxx * dt, out["S"][0]) == pytest.approx(_rel(Sxx, D["S"][0]), rel=1e-3)
+    assert _rel(om * dt, out["omega"][0]) == pytest.approx(_rel(om, D["omega"][0]), rel=1e-3)
+    assert _rel(u1, un[0]) < 0.6 * g["E_u1"][1]
+
+
 def _streamfunction(u, N):
     """psi(x, y) = integral of u from the bottom wall (midpoint rule on the
     node centres (j + 1/2)/N); psi = 0 on the walls."""

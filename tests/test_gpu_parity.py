@@ -174,6 +174,91 @@ def test_mixed_walls_and_force():
 
 
 # --------------------------------------------------------------------------
+# Scheme II forcing (Eq. 2-3c, 2-7a)
+# --------------------------------------------------------------------------
+def _scheme2_force(shape, amp):
+    X = synth.grid_coords(shape)
+    d = len(shape)
+    return np.stack([amp * (1.0 + 0.7 * np.cos(2 * np.pi * X[(a + 1) % d] / shape[(a + 1) % d])
+                            + 0.4 * np.sin(2 * np.pi * X[a] / shape[a]))
+                     for a in range(d)])
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16", "f16eq", "bf16eq"])
+@pytest.mark.parametrize("case", ["2d_walls_lid", "3d_walls"])
+def test_scheme2_matches_oracle(storage, case):
+    """Scheme II with a non-uniform force: walls and a lid in 2D (ragged
+    67 x 45), walls on two axes in 3D, a non-rest start.  Fields, rho and
+    the Eq. 2-7a sums against the oracle.  The same run under Eq. 3-21 is
+    farther from the Scheme II oracle than the tolerance (the test tells
+    the schemes apart)."""
+    if case == "2d_walls_lid":
+        shape, steps, s1 = (67, 45), 300, 1.3
+        kw = dict(wall=(1, 1, 0), lid=True, lid_u=(0.02, 0.0, 0.0))
+        amp = 2e-5
+    else:
+        shape, steps, s1 = (36, 19, 17), 80, 1.5
+        kw = dict(wall=(1, 0, 1), lid=False)
+        amp = 1e-5
+    P, u = synth.smooth_fields(shape, seed=41, amp=0.01)
+    F = _scheme2_force(shape, amp)
+    ref = run_oracle(shape, P, u, steps, s1, force=F, scheme=2, **kw)
+    got = run_gpu(shape, P, u, steps, s1, storage=storage, force=F, forcing="scheme2", **kw)
+    assert np.array_equal(got["mask"], ref["mask"])
+    e = errors(ref, got)
+    tu, tp, tg = _tol(storage)
+    assert e["u"] < tu and e["P"] < tp, e
+    assert e["G"] < tg and e["S"] < tg and e["omega"] < tg, e
+    if storage in ("f64", "f32"):
+        other = run_oracle(shape, P, u, steps, s1, force=F, scheme=0, **kw)
+        assert rel(ref["u"], other["u"]) > 20 * tu
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16eq"])
+def test_scheme2_init_sums_and_residual(storage):
+    """The Scheme II initial state is fbar = f^eq - F/2, so ubar (Eq. 2-7a)
+    reads back the input u; sums of ubar and the residual follow the oracle."""
+    from paper_2108_08591_gb300 import Lattice
+    shape, s1 = (48, 40), 1.4
+    P, u = synth.smooth_fields(shape, seed=5, amp=0.01)
+    F = _scheme2_force(shape, 3e-5)
+    lat = Lattice(shape, s1=s1, storage=storage)
+    try:
+        lat.set_forcing("scheme2")
+        assert lat.forcing == "scheme2"
+        lat.set_force(F)
+        lat.init(P, u)
+        tu = _tol(storage)[0]
+        assert rel(u, lat.fields_host(("u",))["u"]) < tu
+        lat.step(25)
+        pb = O.Problem(d=2, n=shape, s1=s1, force=F, scheme=2)
+        f = O.run(pb, O.init(pb, P, u), 25)
+        want = O.sums(pb, f)
+        got = lat.sums()
+        tol_sum = {"f64": 1e-12, "f32": 1e-6, "f16eq": 1e-5}[storage] * pb.N
+        assert np.abs(got - want).max() < tol_sum, (got, want)
+        assert lat.residual() == np.inf
+        lat.step(1)
+        f1 = O.run(pb, f.copy(), 1)
+        u0 = O.macro(pb, f)[1]
+        u1 = O.macro(pb, f1)[1]
+        r_ref = np.linalg.norm(u1 - u0) / np.linalg.norm(u1)
+        assert lat.residual() == pytest.approx(r_ref, rel=1e-6 if storage == "f64" else 2e-2)
+    finally:
+        lat.close()
+
+
+def test_scheme2_without_force_is_eq_3_21():
+    """Without a force the two schemes are one update: same bits."""
+    shape = (64, 33)
+    P, u = synth.smooth_fields(shape, seed=9)
+    a = run_gpu(shape, P, u, 40, 1.3, storage="f32", forcing="scheme2")
+    b = run_gpu(shape, P, u, 40, 1.3, storage="f32")
+    for k in ("P", "u", "G"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+# --------------------------------------------------------------------------
 # Fused epilogue, reductions, checkpoints, edges
 # --------------------------------------------------------------------------
 def test_fused_fields_equal_separate_pass():
