@@ -69,6 +69,7 @@ def lib():
             "orc_collision_matrix": [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, dp],
             "orc_init": [P, dp, dp, dp],
+            "orc_init_neq": [P, dp, dp, dp, dp],
             "orc_mask": [P, ctypes.POINTER(ctypes.c_ubyte)],
             "orc_step": [P, dp, dp, dp],
             "orc_run": [P, ctypes.c_long, dp],
@@ -176,12 +177,19 @@ def collision_matrix(d: int, q: int, c: float, s0: float, s1: float, s2: float):
     return L.reshape(q, q)
 
 
-def init(pb: Problem, P: np.ndarray, u: np.ndarray) -> np.ndarray:
-    """f = f^eq(P, u) for every set; returns populations [nsets][q][N]."""
+def init(pb: Problem, P: np.ndarray, u: np.ndarray, G: Optional[np.ndarray] = None) -> np.ndarray:
+    """f = f^eq(P, u) for every set, plus the first-order non-equilibrium part
+    of the velocity gradient G [d][d][N] (G[a][b] = du_a/dx_b) when given;
+    returns populations [nsets][q][N]."""
     P = np.ascontiguousarray(P, dtype=np.float64).reshape(pb.N)
     u = np.ascontiguousarray(u, dtype=np.float64).reshape(pb.d, pb.N)
     f = np.zeros((pb.nsets, pb.q, pb.N))
-    _check(lib().orc_init(ctypes.byref(pb.c_struct()), _dptr(P), _dptr(u), _dptr(f)), "init")
+    if G is None:
+        _check(lib().orc_init(ctypes.byref(pb.c_struct()), _dptr(P), _dptr(u), _dptr(f)), "init")
+    else:
+        G = np.ascontiguousarray(G, dtype=np.float64).reshape(pb.d, pb.d, pb.N)
+        _check(lib().orc_init_neq(ctypes.byref(pb.c_struct()), _dptr(P), _dptr(u), _dptr(G),
+                                  _dptr(f)), "init")
     return f
 
 

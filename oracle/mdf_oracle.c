@@ -268,9 +268,41 @@ static void macroscopic(const orc_problem *pb, const double *cv, const double *f
 
 /* ---------------------------------------------------------------------- */
 /* Initialisation: f = f^eq(P, u) (Sec. 4, "initialization ... by their    */
-/* equilibrium distribution functions").                                  */
+/* equilibrium distribution functions"), optionally plus the first-order  */
+/* non-equilibrium part of a given velocity gradient.                     */
 /* ---------------------------------------------------------------------- */
-int orc_init(const orc_problem *pb, const double *P, const double *u, double *f)
+
+/* First-order non-equilibrium part of set alpha >= 1 for the velocity
+ * gradient G[a][b] = d u_a / d x_b at one node.  The first moment of
+ * f^ne relaxes with s1 (Eq. 4-3), and D_i f^eq_{i,alpha} carries
+ * w_i (c_i . grad) ubar_alpha at first order, which has first moments only,
+ * so Lambda^-1 acts on it as 1/s1:
+ *   f^ne_{i,alpha} = -(dt / s1) w_i sum_b c_{i,b} (G[alpha-1][b] - delta tr(G) / d).
+ * Its first moment is -(c_s^2 dt / s1) times the traceless gradient: the
+ * inverse of Eq. 3-16.  The trace is removed because Eq. 3-15 reads the
+ * trace of the first moments as pressure; the seeded P is kept.  The
+ * alpha = 0 set gets none (its first-order part is O(u grad u)). */
+static void neq_part(const orc_problem *pb, const double *cv, const double *w, int alpha,
+                     const double *G, long node, long N, double *fne)
+{
+    int d = pb->d, i, b;
+    double tr = 0.0;
+    for (i = 0; i < pb->q; ++i) fne[i] = 0.0;
+    if (alpha < 1 || !G) return;
+    for (b = 0; b < d; ++b) tr += G[((long)b * d + b) * N + node];
+    for (i = 0; i < pb->q; ++i) {
+        double s = 0.0;
+        for (b = 0; b < d; ++b) {
+            double g = G[((long)(alpha - 1) * d + b) * N + node];
+            if (b == alpha - 1) g -= tr / d;
+            s += cv[3 * i + b] * g;
+        }
+        fne[i] = -(pb->dt / pb->s1) * w[i] * s;
+    }
+}
+
+int orc_init_neq(const orc_problem *pb, const double *P, const double *u, const double *G,
+                 double *f)
 {
     double cv[QMAX * 3], w[QMAX], cs2, c;
     long N, n;
@@ -281,19 +313,26 @@ int orc_init(const orc_problem *pb, const double *P, const double *u, double *f)
     N = nnodes(pb);
     ns = nsets(pb);
     for (n = 0; n < N; ++n) {
-        double un[3], feq[QMAX];
+        double un[3], feq[QMAX], fne[QMAX];
         int b, i;
         for (b = 0; b < pb->d; ++b) un[b] = u[(long)b * N + n];
         for (a = 0; a < ns; ++a) {
             int alpha = alpha_of(pb, a);
             double ubar = alpha == 0 ? pb->rho0 : un[alpha - 1];
             equilibrium(pb->q, pb->d, alpha, cv, w, cs2, ubar, un, P[n], feq);
+            neq_part(pb, cv, w, alpha, G, n, N, fne);
             /* Scheme II stores fbar = f - dt F / 2 */
             for (i = 0; i < pb->q; ++i)
-                f[((long)a * pb->q + i) * N + n] = feq[i] - half_source(pb, w, i, alpha, n, N);
+                f[((long)a * pb->q + i) * N + n] =
+                    feq[i] + fne[i] - half_source(pb, w, i, alpha, n, N);
         }
     }
     return 0;
+}
+
+int orc_init(const orc_problem *pb, const double *P, const double *u, double *f)
+{
+    return orc_init_neq(pb, P, u, NULL, f);
 }
 
 /* ---------------------------------------------------------------------- */

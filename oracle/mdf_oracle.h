@@ -32,6 +32,8 @@ int orc_moment_basis(int d, int q, double c, double s0, double s1, double s2,
 int orc_collision_matrix(int d, int q, double c, double s0, double s1, double s2,
                          double *Lam);
 int orc_init(const orc_problem *pb, const double *P, const double *u, double *f);
+int orc_init_neq(const orc_problem *pb, const double *P, const double *u, const double *G,
+                 double *f);
 int orc_mask(const orc_problem *pb, unsigned char *mask);
 int orc_step(const orc_problem *pb, const double *Lam, const double *f, double *fnew);
 int orc_run(const orc_problem *pb, long nsteps, double *f);
