@@ -147,6 +147,20 @@ void mdf_destroy(mdf_t h);
 mdf_status mdf_init(mdf_t h, const double *P, const double *u, int where);
 
 /*
+ * mdf_init_neq -- as mdf_init, plus the first-order non-equilibrium part of
+ * a given velocity gradient, so that the start has no initial layer:
+ *   f^ne_{i,alpha} = -(dt / s1) w_i c_i . (G_alpha - (tr G / d) e_alpha)
+ * for alpha = 1..d, and none for alpha = 0.  This is the inverse of
+ * Eq. 3-16: the fields of the new state give back the traceless part of G.
+ * The trace is dropped because Eq. 3-15 would read it as pressure, so P is
+ * kept.
+ *   G[a][b][N] = du_a / dx_b (lattice units): FP64 in `where` memory, laid
+ *     out like mdf_fields_t.G.  Same ownership rules as P and u.
+ * Errors: MDF_EINVAL for a null G, plus those of mdf_init.
+ */
+mdf_status mdf_init_neq(mdf_t h, const double *P, const double *u, const double *G, int where);
+
+/*
  * mdf_set_force -- body force Fbar_alpha(x) of Eq. 2-6 (F_i = w_i Fbar_alpha),
  * added as dt w_i Fbar_alpha in Eq. 3-21.  F[d][N] FP64 in `where` memory,
  * stored on the device in the compute precision (FP32; FP64 for MDF_F64

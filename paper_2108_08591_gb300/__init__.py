@@ -121,14 +121,20 @@ class Lattice:
         return inf
 
     # ------------------------------------------------------------------
-    def init(self, P, u):
-        """f = f^eq(P, u); P [N], u [d][N] FP64, numpy (host) or CUDA tensors."""
+    def init(self, P, u, G=None):
+        """f = f^eq(P, u); P [N], u [d][N] FP64, numpy (host) or CUDA tensors.
+        With G [d][d][N] (G[a][b] = du_a/dx_b) the state also carries the
+        first-order non-equilibrium part of that gradient (mdf_init_neq)."""
         dev = _is_device(P)
-        if dev != _is_device(u):
-            raise ValueError("P and u must both be on the host or both on the device")
+        if dev != _is_device(u) or (G is not None and dev != _is_device(G)):
+            raise ValueError("P, u (and G) must all be on the host or all on the device")
         if dev:
-            self._keep = [P, u]
-        self._check(self._lib.mdf_init(self._h, _ptr(P), _ptr(u), DEVICE if dev else HOST))
+            self._keep = [P, u, G]
+        where = DEVICE if dev else HOST
+        if G is None:
+            self._check(self._lib.mdf_init(self._h, _ptr(P), _ptr(u), where))
+        else:
+            self._check(self._lib.mdf_init_neq(self._h, _ptr(P), _ptr(u), _ptr(G), where))
 
     def set_force(self, F):
         """Body force Fbar [d][N] (Eq. 2-6); None removes it."""

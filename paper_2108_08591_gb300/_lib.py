@@ -60,6 +60,7 @@ SIGNATURES = {
                                   ctypes.POINTER(Rates), ctypes.POINTER(BC), ctypes.POINTER(Opts)]),
     "mdf_destroy": (None, [H]),
     "mdf_init": (ctypes.c_int, [H, DP, DP, ctypes.c_int]),
+    "mdf_init_neq": (ctypes.c_int, [H, DP, DP, DP, ctypes.c_int]),
     "mdf_set_force": (ctypes.c_int, [H, DP, ctypes.c_int]),
     "mdf_set_forcing": (ctypes.c_int, [H, ctypes.c_int]),
     "mdf_get_forcing": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_int)]),

@@ -357,21 +357,27 @@ void mdf_destroy(mdf_t h) {
   delete h;
 }
 
-mdf_status mdf_init(mdf_t h, const double *P, const double *u, int where) {
+static mdf_status init_state(mdf_t h, const double *P, const double *u, const double *G, int where) {
   if (check_handle(h)) return MDF_EINVAL;
   if (!P || !u) return fail(h, MDF_EINVAL, "init: null P or u");
   const size_t nb = sizeof(double) * (size_t)h->N;
+  const int dd = h->d * h->d;
   DevArgs a = base_args(h);
   if (where == MDF_HOST) {
-    mdf_status st = ensure_stage(h, nb * (1 + h->d));
+    mdf_status st = ensure_stage(h, nb * (1 + h->d + (G ? dd : 0)));
     if (st != MDF_OK) return st;
     CU(h, cudaMemcpyAsync(h->stage, P, nb, cudaMemcpyHostToDevice, h->stream));
     CU(h, cudaMemcpyAsync(h->stage + h->N, u, nb * h->d, cudaMemcpyHostToDevice, h->stream));
     a.Pin = h->stage;
     a.uin = h->stage + h->N;
+    if (G) {
+      CU(h, cudaMemcpyAsync(h->stage + (1 + h->d) * h->N, G, nb * dd, cudaMemcpyHostToDevice, h->stream));
+      a.Gin = h->stage + (1 + h->d) * h->N;
+    }
   } else if (where == MDF_DEVICE) {
     a.Pin = P;
     a.uin = u;
+    a.Gin = G;
   } else {
     return fail(h, MDF_EINVAL, "init: bad `where` %d", where);
   }
@@ -383,6 +389,16 @@ mdf_status mdf_init(mdf_t h, const double *P, const double *u, int where) {
   h->step = 0;
   h->have_prev = false;
   return MDF_OK;
+}
+
+mdf_status mdf_init(mdf_t h, const double *P, const double *u, int where) {
+  return init_state(h, P, u, nullptr, where);
+}
+
+mdf_status mdf_init_neq(mdf_t h, const double *P, const double *u, const double *G, int where) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!G) return fail(h, MDF_EINVAL, "init_neq: null G");
+  return init_state(h, P, u, G, where);
 }
 
 mdf_status mdf_set_force(mdf_t h, const double *F, int where) {

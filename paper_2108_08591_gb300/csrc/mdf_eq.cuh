@@ -538,8 +538,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
 // Initial state f = f^eq(P, u) in pull form for this codec: moments
 // M0 = (u, P - 1, 0) at every node, and s_i(x) such that the first pull
 // rebuilds g^eq_i(M0(x + c_i)) at x + c_i (or, on a wall link, the value
-// whose bounce-back returns g^eq_opp(M0(x)) at x).  Under Scheme II the
-// rebuilt value is fbar = f^eq - w_i Fbar / 2 (its ubar is still u).
+// whose bounce-back returns g^eq_opp(M0(x)) at x).  A seed gradient adds
+// f^ne (fne_at); under Scheme II the rebuilt value is fbar = f - w_i Fbar / 2
+// (its ubar is still u).
 template <class L>
 __device__ __forceinline__ void init_moments(const DevArgs &A, long long N, long long n,
                                              float (&M)[L::D + 2]) {
@@ -575,15 +576,18 @@ __global__ void __launch_bounds__(kMaxBlock) k_init_eq(const DevArgs A) {
       const float *Fa = half ? static_cast<const float *>(A.force) + (alpha - 1) * A.plane : nullptr;
       if (WALLS && i != 0 && ((m >> i) & 1)) {
         target = -geq_m<L>(alpha, L::opp(i), M0);
+        if (A.Gin) target -= narrow_f64(fne_at<L>(A, N, n, alpha, L::opp(i)));
         if (alpha >= 1 && i == L::UP && (m & 0x80u)) target += float(2.0 * L::w(i) * A.lid_u[alpha - 1]);
         if (half) target += float(0.5 * L::w(i)) * __ldg(Fa + idx);  // negated by the bounce-back
       } else {
         const int tx = wrap(x + L::c(i, 0), A.nx);
         const int ty = wrap(y + L::c(i, 1), A.ny);
         const int tz = D == 3 ? wrap(z + L::c(i, 2), A.nz) : z;
+        const long long tn = ((long long)tz * A.ny + ty) * A.nx + tx;
         float Mt[D + 2];
-        init_moments<L>(A, N, ((long long)tz * A.ny + ty) * A.nx + tx, Mt);
+        init_moments<L>(A, N, tn, Mt);
         target = geq_m<L>(alpha, i, Mt);
+        if (A.Gin) target += narrow_f64(fne_at<L>(A, N, tn, alpha, i));
         if (half) target -= float(0.5 * L::w(i)) * __ldg(Fa + ((long long)tz * A.ny + ty) * A.px + tx);
       }
       Codec<TS>::store(fout + ((long long)a * Q + i) * A.plane + idx,

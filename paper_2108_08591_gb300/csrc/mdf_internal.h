@@ -25,8 +25,8 @@ struct DevArgs {
   double lid_u[3];               // lid velocity
   // derived-field outputs (dense [N] layout), each nullable
   double *P, *u, *rho, *G, *div, *S, *sigma, *omega;
-  // init inputs (dense FP64 on the device)
-  const double *Pin, *uin;
+  // init inputs (dense FP64 on the device); Gin [d][d][N] nullable
+  const double *Pin, *uin, *Gin;
   // reductions
   double *partials;              // [blocks][k] block partial sums
   double *uprev;                 // [d][N] previous velocity (residual)

@@ -607,6 +607,28 @@ __device__ __forceinline__ TC geq_v(int alpha, int i, const TC (&u)[L::D], TC Pp
   return wi * (ua + (cu * ua + cP) * ics2);
 }
 
+// First-order non-equilibrium part of set alpha along c_i at node n from
+// the seed gradient Gin[a][b] = du_a/dx_b: -(w_i / s1) c_i . (G_alpha -
+// tr G / d e_alpha), the inverse of Eq. 3-16 (its first moment is
+// -(c_s^2 / s1) times the traceless gradient; the trace would read as
+// pressure in Eq. 3-15).  Zero without a gradient, for alpha = 0 and for
+// the rest direction.
+template <class L>
+__device__ __forceinline__ double fne_at(const DevArgs &A, long long N, long long n, int alpha, int i) {
+  constexpr int D = L::D;
+  if (!A.Gin || alpha == 0 || i == 0) return 0.0;
+  const int b = L::c(i, 0) != 0 ? 0 : L::c(i, 1) != 0 ? 1 : 2;
+  const int sg = L::c(i, b);
+  double g = A.Gin[((long long)(alpha - 1) * D + b) * N + n];
+  if (alpha - 1 == b) {
+    double tr = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) tr += A.Gin[((long long)a * D + a) * N + n];
+    g -= tr / D;
+  }
+  return -(L::w(i) / A.s1) * sg * g;
+}
+
 template <class L, class TC>
 __device__ __forceinline__ TC geq(const DevArgs &A, long long N, long long n, int alpha, int i) {
   TC u[L::D], Pp;
@@ -617,9 +639,9 @@ __device__ __forceinline__ TC geq(const DevArgs &A, long long N, long long n, in
 // Initial state f = f^eq(P, u) written in pull form: the value stored at x
 // for direction i is the one the first update pulls into x + c_i, and for a
 // wall link the one whose bounce-back returns f^eq_opp(i)(x).  Each of the
-// Q source nodes' seed is rounded once and shared by the sets.  Under
-// Scheme II the state is fbar = f^eq - w_i Fbar_alpha / 2 with the force at
-// the node the value arrives at.
+// Q source nodes' seed is rounded once and shared by the sets.  With a seed
+// gradient the state is f^eq + f^ne (fne_at), and under Scheme II it is
+// fbar = f - w_i Fbar_alpha / 2, both at the node the value arrives at.
 template <class L, class TS, bool WALLS>
 __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
   using TC = typename ComputeOf<TS>::T;
@@ -632,7 +654,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
   const long long n = ((long long)z * A.ny + y) * A.nx + x;
   const uint8_t m = WALLS ? A.mask[idx] : uint8_t(0);
   TC tu[Q][D], tP[Q];
-  long long tidx[Q];  // padded index of the node each value arrives at
+  long long tidx[Q], tn[Q];  // padded and dense index of the node each value arrives at
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     long long t = n;
@@ -644,6 +666,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
       t = ((long long)tz * A.ny + ty) * A.nx + tx;
       tidx[i] = ((long long)tz * A.ny + ty) * A.px + tx;
     }
+    tn[i] = t;
     seed_at<L, TC>(A, N, t, tu[i], tP[i]);
   }
   TS *fout = static_cast<TS *>(A.fout);
@@ -656,9 +679,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
       const bool wall = WALLS && i != 0 && ((m >> i) & 1);
       if (wall) {
         v = -geq_v<L, TC>(alpha, L::opp(i), tu[i], tP[i]);
+        if (A.Gin) v -= narrow_to<TC>(fne_at<L>(A, N, n, alpha, L::opp(i)));
         if (alpha >= 1 && i == L::UP && (m & 0x80u)) v += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
       } else {
         v = geq_v<L, TC>(alpha, i, tu[i], tP[i]);
+        if (A.Gin) v += narrow_to<TC>(fne_at<L>(A, N, tn[i], alpha, i));
       }
       if (A.scheme2 && alpha >= 1) {  // the bounce-back negates the shift
         const TC Fh = TC(0.5 * L::w(i)) * __ldg(static_cast<const TC *>(A.force) +

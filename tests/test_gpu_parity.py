@@ -259,6 +259,78 @@ def test_scheme2_without_force_is_eq_3_21():
 
 
 # --------------------------------------------------------------------------
+# Non-equilibrium seeding (mdf_init_neq)
+# --------------------------------------------------------------------------
+def _seed_gradient(shape, seed, amp=1e-3):
+    """A smooth, non-solenoidal gradient field [d][d][N] (its trace is
+    dropped by the seed, which the comparison with the oracle covers)."""
+    d = len(shape)
+    X = synth.grid_coords(shape)
+    rng = synth.SplitMix64(seed)
+    G = np.zeros((d, d, int(np.prod(shape))))
+    for a in range(d):
+        for b in range(d):
+            ph = 6 * rng.uniform()
+            G[a, b] = amp * np.sin(2 * np.pi * X[(a + b) % d] / shape[(a + b) % d] + ph).ravel()
+    return G
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "f16eq", "bf16eq"])
+@pytest.mark.parametrize("case", ["2d_walls_lid", "3d_periodic", "2d_scheme2"])
+@pytest.mark.parametrize("steps", [0, 40])
+def test_neq_seed_matches_oracle(storage, case, steps):
+    """f^eq + f^ne(G) at the start (steps = 0: the fields read back the
+    traceless G) and after 40 updates, against the oracle."""
+    kw = {}
+    if case == "3d_periodic":
+        shape, s1 = (24, 18, 14), 1.4
+    else:
+        shape, s1 = (45, 37), 1.3
+        kw = dict(wall=(1, 1, 0), lid=True, lid_u=(0.02, 0.0, 0.0))
+    P, u = synth.smooth_fields(shape, seed=17, amp=0.01)
+    G = _seed_gradient(shape, 3)
+    okw, gkw = dict(kw), dict(kw)
+    if case == "2d_scheme2":
+        F = _scheme2_force(shape, 2e-5)
+        okw.update(force=F, scheme=2)
+        gkw.update(force=F, forcing="scheme2")
+    ref = run_oracle(shape, P, u, steps, s1, G=G, **okw)
+    got = run_gpu(shape, P, u, steps, s1, storage=storage, G=G, **gkw)
+    e = errors(ref, got)
+    tu, tp, tg = _tol(storage)
+    assert e["u"] < tu and e["P"] < tp, e
+    assert e["G"] < tg and e["S"] < tg and e["omega"] < tg, e
+    if steps == 0 and storage in ("f64", "f32"):
+        d = len(shape)
+        tr = np.einsum("aan->n", G)
+        want = G - np.eye(d)[:, :, None] * tr[None, None, :] / d
+        assert rel(want, got["G"]) < (1e-12 if storage == "f64" else 1e-4)
+
+
+def test_neq_seed_removes_the_initial_layer_on_the_gpu():
+    """2D Taylor-Green from its exact gradient (FP32 storage): the Eq. 3-16
+    gradient after one update is within 1e-2 of the closed form, against
+    ~0.2 from the equilibrium start."""
+    from paper_2108_08591_gb300 import Lattice
+    n, U0, s1 = 64, 0.01, 1.2
+    nu = (1 / s1 - 0.5) / 3
+    k = 2 * np.pi / n
+    P, u = synth.taylor_green_2d(n, U0)
+    X, Y = synth.grid_coords((n, n))
+    cc, ss = (np.cos(k * X) * np.cos(k * Y)).ravel(), (np.sin(k * X) * np.sin(k * Y)).ravel()
+    G0 = U0 * k * np.stack([np.stack([cc, -ss]), np.stack([ss, -cc])])
+    err = {}
+    for name, G in (("eq", None), ("neq", G0)):
+        lat = Lattice((n, n), s1=s1)
+        lat.init(P, u, G)
+        lat.step(1)
+        g01 = lat.fields_host(("G",))["G"][0, 1]
+        lat.close()
+        err[name] = rel(G0[0, 1] * np.exp(-2 * nu * k * k), g01)
+    assert err["neq"] < 1e-2 and err["eq"] > 0.1, err
+
+
+# --------------------------------------------------------------------------
 # Fused epilogue, reductions, checkpoints, edges
 # --------------------------------------------------------------------------
 def test_fused_fields_equal_separate_pass():
