@@ -108,11 +108,12 @@ class Problem:
     rho0: float = 1.0
     force: Optional[np.ndarray] = None  # [d][N] body force at nodes
     scheme: int = 0  # forcing: 0 = Eq. 3-21, 2 = Scheme II (Eq. 2-3c, 2-7a; state is fbar)
+    nq: int = 0  # directions: 0 = D2Q5 / D3Q7; 4 = D2Q4, 6 = D3Q6 (no rest direction)
     _c: _Problem = field(default=None, repr=False)
 
     @property
     def q(self) -> int:
-        return 5 if self.d == 2 else 7
+        return self.nq if self.nq else (5 if self.d == 2 else 7)
 
     @property
     def N(self) -> int:

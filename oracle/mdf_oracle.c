@@ -8,7 +8,8 @@
  * the CUDA library.
  *
  * It is written to be read against the paper, not to be fast:
- *   - the lattices are the paper's tables (D2Q5 and D3Q7, Sec. 2.2);
+ *   - the lattices are the paper's tables (D2Q5 and D3Q7, Sec. 2.2; also
+ *     D2Q4 and D3Q6, which have no rest direction);
  *   - the collision matrix is assembled densely as Lambda = M^-1 S M
  *     (Eq. 4-1) with M^-1 obtained by Gauss-Jordan elimination, not by any
  *     orthogonality shortcut;
@@ -60,12 +61,35 @@
 #define QMAX 7
 
 /* ---------------------------------------------------------------------- */
-/* Lattices, Sec. 2.2: D2Q5 (c_s^2 = c^2/3) and D3Q7 (c_s^2 = c^2/4).     */
+/* Lattices, Sec. 2.2: D2Q5 (c_s^2 = c^2/3), D3Q7 (c_s^2 = c^2/4), and    */
+/* the lattices without a rest direction, D2Q4 (c_s^2 = c^2/2) and D3Q6   */
+/* (c_s^2 = c^2/3), in the paper's direction order.                       */
 /* ---------------------------------------------------------------------- */
 int orc_lattice(int d, int q, double c, double *cv, double *w, double *cs2)
 {
     int i, b;
     for (i = 0; i < QMAX * 3; ++i) cv[i] = 0.0;
+    if (d == 2 && q == 4) {
+        /* c_1..c_4 = (1,0), (0,1), (-1,0), (0,-1) times c (index 0..3 here) */
+        static const int e[4][2] = {{1, 0}, {0, 1}, {-1, 0}, {0, -1}};
+        for (i = 0; i < 4; ++i) {
+            for (b = 0; b < 2; ++b) cv[3 * i + b] = e[i][b] * c;
+            w[i] = 0.25;
+        }
+        *cs2 = c * c / 2.0;
+        return 0;
+    }
+    if (d == 3 && q == 6) {
+        /* c_1..c_6 = +-x, +-y, +-z times c (index 0..5 here) */
+        static const int e[6][3] = {{1, 0, 0}, {-1, 0, 0}, {0, 1, 0},
+                                    {0, -1, 0}, {0, 0, 1}, {0, 0, -1}};
+        for (i = 0; i < 6; ++i) {
+            for (b = 0; b < 3; ++b) cv[3 * i + b] = e[i][b] * c;
+            w[i] = 1.0 / 6.0;
+        }
+        *cs2 = c * c / 3.0;
+        return 0;
+    }
     if (d == 2 && q == 5) {
         /* c_0..c_4 = (0,0), (1,0), (0,1), (-1,0), (0,-1) times c */
         static const int e[5][2] = {{0, 0}, {1, 0}, {0, 1}, {-1, 0}, {0, -1}};
@@ -122,13 +146,42 @@ static int invert(int n, const double *A, double *Ainv)
 }
 
 /* Transformation matrix M (q x q, row-major) and relaxation diagonal S.
- * D2Q5: Eq. 4-2 and Eq. 4-3.  D3Q7: the orthogonal analogue read above. */
+ * D2Q5: Eq. 4-2 and Eq. 4-3.  D3Q7: the orthogonal analogue read above.
+ * D2Q4 and D3Q6 (no M printed): the conserved row, the d first moments and
+ * the traceless second moments of the same analogue (|c|^2 = c^2 is the
+ * conserved row there), relaxed with s0, s1 and s2:
+ *   D2Q4: 1, c_x, c_y, c_x^2 - c_y^2;
+ *   D3Q6: 1, c_x, c_y, c_z, 2 c_x^2 - c_y^2 - c_z^2, c_y^2 - c_z^2. */
 int orc_moment_basis(int d, int q, double c, double s0, double s1, double s2,
                      double *M, double *S)
 {
     double cv[QMAX * 3], w[QMAX], cs2;
     int i;
     if (orc_lattice(d, q, c, cv, w, &cs2)) return -1;
+    if (q == 4) {
+        for (i = 0; i < 4; ++i) {
+            double cx = cv[3 * i], cy = cv[3 * i + 1];
+            M[0 * 4 + i] = 1.0;
+            M[1 * 4 + i] = cx;
+            M[2 * 4 + i] = cy;
+            M[3 * 4 + i] = cx * cx - cy * cy;
+        }
+        S[0] = s0; S[1] = s1; S[2] = s1; S[3] = s2;
+        return 0;
+    }
+    if (q == 6) {
+        for (i = 0; i < 6; ++i) {
+            double cx = cv[3 * i], cy = cv[3 * i + 1], cz = cv[3 * i + 2];
+            M[0 * 6 + i] = 1.0;
+            M[1 * 6 + i] = cx;
+            M[2 * 6 + i] = cy;
+            M[3 * 6 + i] = cz;
+            M[4 * 6 + i] = 2.0 * cx * cx - cy * cy - cz * cz;
+            M[5 * 6 + i] = cy * cy - cz * cz;
+        }
+        S[0] = s0; S[1] = s1; S[2] = s1; S[3] = s1; S[4] = s2; S[5] = s2;
+        return 0;
+    }
     if (d == 2) {
         for (i = 0; i < 5; ++i) {
             double cx = cv[3 * i], cy = cv[3 * i + 1];
@@ -183,7 +236,8 @@ static int alpha_of(const orc_problem *pb, int a) { return pb->with_rho ? a : a 
 static int check(const orc_problem *pb)
 {
     int b;
-    if (!((pb->d == 2 && pb->q == 5) || (pb->d == 3 && pb->q == 7))) return -1;
+    if (!((pb->d == 2 && (pb->q == 5 || pb->q == 4)) || (pb->d == 3 && (pb->q == 7 || pb->q == 6))))
+        return -1;
     for (b = 0; b < 3; ++b)
         if (pb->n[b] < 1) return -1;
     if (pb->d == 2 && pb->n[2] != 1) return -1;
