@@ -56,11 +56,12 @@ def _dist():
     return rank, world, local
 
 
-def _config(n_gpus: int, storage: str, d: int = 2):
+def _config(n_gpus: int, storage: str, d: int = 2, q: int = 0):
     grid = [N_GRID] * d
-    pop_gb = N_GRID ** d * (5 * 3 if d == 2 else 7 * 4) * {"f32": 4, "f16": 2, "bf16": 2,
-                                                           "f16eq": 2, "bf16eq": 2}.get(storage, 8) / 1e9
-    return {"workload": WORKLOAD, "grid": grid, "lattice": "D2Q5" if d == 2 else "D3Q7",
+    q = q or (5 if d == 2 else 7)
+    pop_gb = N_GRID ** d * q * (d + 1) * {"f32": 4, "f16": 2, "bf16": 2,
+                                          "f16eq": 2, "bf16eq": 2}.get(storage, 8) / 1e9
+    return {"workload": WORKLOAD, "grid": grid, "lattice": f"D{d}Q{q}",
             "sets": d + 1, "storage": storage, "steps_per_bench_step": EPI_EVERY,
             "global_batch": n_gpus, "parallelism": f"replicas x{n_gpus}",
             "l2": f"inputs larger than L2 (2 x {pop_gb:.2f} GB populations), no flush"}
@@ -240,19 +241,25 @@ def run_reference(args):
     return 0
 
 
+def _cs2(d: int, q: int) -> float:
+    """c_s^2 of the lattice (Sec. 2.2), lattice units."""
+    return {(2, 5): 1 / 3, (2, 4): 1 / 2, (3, 7): 1 / 4, (3, 6): 1 / 3}[(d, q or (5 if d == 2 else 7))]
+
+
 def _workload(args):
-    """(shape, s1, P, u) of the benchmark workload, FP64 host arrays."""
+    """(shape, s1, P, u) of the benchmark workload, FP64 host arrays.  The
+    viscosity is the workload's; s1 follows from the lattice's c_s^2."""
     import synth
     if args.workload == "tg2d":
         P, u = synth.tg_plus_modes(N_GRID, U0=0.01, seed=2108)
-        return (N_GRID, N_GRID), S1, P, u
+        return (N_GRID, N_GRID), 1.0 / (NU / _cs2(2, args.q) + 0.5), P, u
     k = 2 * math.pi / N_GRID
     nu = TG3D_U0 / (k * TG3D_RE)
     P, u = synth.taylor_green_3d(N_GRID, U0=TG3D_U0)
-    return (N_GRID,) * 3, 1.0 / (4 * nu + 0.5), P, u
+    return (N_GRID,) * 3, 1.0 / (nu / _cs2(3, args.q) + 0.5), P, u
 
 
-def sampled_oracle_error(shape, s1, P, u, storage, steps, samples=8, seed=77):
+def sampled_oracle_error(shape, s1, P, u, storage, steps, samples=8, seed=77, q=0):
     """FP64 oracle error of the GPU fields at full size, on sampled nodes.
 
     After `steps` updates a node depends only on nodes within that many
@@ -264,7 +271,7 @@ def sampled_oracle_error(shape, s1, P, u, storage, steps, samples=8, seed=77):
     import synth
     from paper_2108_08591_gb300 import Lattice
     d = len(shape)
-    lat = Lattice(shape, s1=s1, storage=storage)
+    lat = Lattice(shape, s1=s1, storage=storage, q=q)
     lat.init(P, u)
     fl = lat.alloc_fields(("P",))
     lat.step_fields(steps, fl)
@@ -285,7 +292,7 @@ def sampled_oracle_error(shape, s1, P, u, storage, steps, samples=8, seed=77):
             sel = ((axes[2][:, None, None] * n + axes[1][None, :, None]) * n
                    + axes[0][None, None, :]).ravel()
             g = (c[2] * n + c[1]) * n + c[0]
-        pb = oracle.Problem(d=d, n=(W,) * d, s1=s1)
+        pb = oracle.Problem(d=d, n=(W,) * d, s1=s1, nq=q)
         f = oracle.init(pb, P[sel], u[:, sel])
         oracle.run(pb, f, steps)
         Pr, ur, _ = oracle.macro(pb, f)
@@ -324,7 +331,7 @@ def run_mdf(args):
     N = int(np.prod(shape))
     stream = torch.cuda.current_stream()
     lat = Lattice(shape, s1=s1, storage=args.storage, stream=stream, vx=args.vx or 0,
-                  block=args.block or 0)
+                  block=args.block or 0, q=args.q)
     lat.init(P, u)
     info = lat.info
     fields = lat.alloc_fields(("P", "u", "G", "div", "S", "sigma", "omega"))
@@ -395,15 +402,16 @@ def run_mdf(args):
     bytes_per_launch = info.bytes_per_update * N
     achieved = bytes_per_launch / (plain_ms / 1e3) / 1e9
     sha = _kernel_sha()
+    default_lattice = args.q in (0, 5 if d == 2 else 7)
     traffic = _traffic(sha) if (args.workload == "tg2d" and N_GRID == 4096
-                                and args.storage == "f32") else None
+                                and args.storage == "f32" and default_lattice) else None
     oerr = None
     if not args.no_oracle_check:
-        oerr = sampled_oracle_error(shape, s1, P, u, args.storage, steps=64 if d == 2 else 16)
+        oerr = sampled_oracle_error(shape, s1, P, u, args.storage, steps=64 if d == 2 else 16, q=args.q)
     cpu = None
-    if world == 1 and not args.no_cpu_baseline and args.workload == "tg2d":
+    if world == 1 and not args.no_cpu_baseline and args.workload == "tg2d" and default_lattice:
         cpu = cpu_oracle_sample()
-    kname = {2: "D2Q5", 3: "D3Q7"}[d]
+    kname = f"D{d}Q{info.q}"
     tname = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16", "f16eq": "__half",
              "bf16eq": "__nv_bfloat16"}[args.storage]
     if args.storage.endswith("eq"):
@@ -419,7 +427,7 @@ def run_mdf(args):
         "dtype": {"f32": "f32", "f16": "f16 storage / f32", "bf16": "bf16 storage / f32",
                   "f16eq": "f16 equilibrium-shifted storage + f32 moments / f32",
                   "bf16eq": "bf16 equilibrium-shifted storage + f32 moments / f32"}[args.storage],
-        "data": "synthetic", "config": _config(world, args.storage, d),
+        "data": "synthetic", "config": _config(world, args.storage, d, args.q),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
@@ -575,6 +583,9 @@ def main():
     ap.add_argument("--cavity-side", type=int, default=0,
                     help="cavities workload: a uniform batch of this side instead of the 64 seeded boxes")
     ap.add_argument("--cavity-count", type=int, default=16, help="cavities in the uniform batch")
+    ap.add_argument("--q", type=int, default=0, choices=(0, 4, 5, 6, 7),
+                    help="directions per set: 0 = D2Q5 / D3Q7 (default); 4 = D2Q4, 6 = D3Q6 "
+                         "(no rest direction, rest-shifted storage only)")
     ap.add_argument("--grid", type=int, default=4096,
                     help="lattice side (default 4096; smaller sides are profiling cases)")
     args = ap.parse_args()
@@ -588,6 +599,9 @@ def main():
         WORKLOAD = WORKLOAD.replace(f"{N_GRID}x{N_GRID}", f"{args.grid}x{args.grid}").replace(
             f"{N_GRID}^3", f"{args.grid}^3")
         N_GRID = args.grid
+    if args.q in (4, 6):
+        WORKLOAD = WORKLOAD.replace("D2Q5", "D2Q4").replace("D3Q7", "D3Q6") + (
+            ", same viscosity (s1 from the lattice's c_s^2)")
     if args.impl == "mdf" and args.storage != "f32":
         name = {"f16": "FP16 rest-shifted", "bf16": "BF16 rest-shifted",
                 "f16eq": "FP16 equilibrium-shifted (+FP32 moments)",

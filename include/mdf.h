@@ -86,6 +86,9 @@ typedef struct {
                                 back to 1. */
     int block;               /* threads per block of the update kernel: 0 = tuned
                                 default, else a multiple of 32 in [32, 256] */
+    int q;                   /* directions per set: 0 = D2Q5 / D3Q7 (default), 4 = D2Q4,
+                                6 = D3Q6 (Sec. 2.2: no rest direction, fewer bytes
+                                per node; the rest-shifted storage types only) */
 } mdf_opts;
 
 /* Derived-field outputs, each a caller-owned array of doubles or NULL.
@@ -123,7 +126,9 @@ typedef struct {
  * mdf_create -- allocate a lattice of d+1 (or d) distribution sets.
  *   g: grid (nx, ny >= 2; nz = 1 for d = 2, nz >= 2 for d = 3);
  *   d: 2 (D2Q5, Sec. 2.2) or 3 (D3Q7, Sec. 2.2, MRT basis read analogously
- *      to Eq. 4-2);  r: relaxation rates, each in (0, 2);
+ *      to Eq. 4-2); o->q = 4 or 6 selects D2Q4 or D3Q6 (Sec. 2.2), with the
+ *      conserved, first-moment and traceless second-moment rows as basis;
+ *   r: relaxation rates, each in (0, 2);
  *   bc: periodic axes or anti-halfway bounce-back walls (Sec. 4), optional
  *      moving lid;  o: storage, sets and stream.
  * The library allocates and owns the population buffers (two of

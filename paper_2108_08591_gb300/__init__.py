@@ -53,15 +53,16 @@ class Lattice:
     shape: (nx, ny) or (nx, ny, nz).  s1 sets the viscosity
     nu = (1/s1 - 1/2) c_s^2 (Eq. 3-13a); s2 < 0 picks the paper's rule.
     wall: per-axis halfway walls (anti-halfway bounce-back), lid: the + face
-    of the last axis moves with lid_u.  storage: 'f32', 'f16', 'bf16', 'f64'.
-    vx / block: x-nodes per thread and threads per block of the update
-    kernel (0: the library's tuned default).
+    of the last axis moves with lid_u.  storage: 'f32', 'f16', 'bf16', 'f64',
+    'f16eq', 'bf16eq'.  vx / block: x-nodes per thread and threads per block
+    of the update kernel (0: the library's tuned default).  q: 0 for
+    D2Q5 / D3Q7, 4 for D2Q4, 6 for D3Q6 (rest-shifted storage types only).
     """
 
     def __init__(self, shape: Sequence[int], s1: float, s2: float = -1.0, s0: float = 1.0,
                  wall: Sequence[int] = (0, 0, 0), lid: bool = False,
                  lid_u: Sequence[float] = (0.0, 0.0, 0.0), storage: str = "f32",
-                 with_rho: bool = True, stream=None, vx: int = 0, block: int = 0):
+                 with_rho: bool = True, stream=None, vx: int = 0, block: int = 0, q: int = 0):
         import torch
 
         self._lib = _lib.load()
@@ -84,7 +85,8 @@ class Lattice:
         bc.lid = int(bool(lid))
         lu = list(lid_u) + [0.0] * (3 - len(lid_u))
         bc.lid_u[:] = [float(v) for v in lu[:3]]
-        o = _lib.Opts(STORAGE[storage], int(bool(with_rho)), ctypes.c_void_p(sptr), int(vx), int(block))
+        o = _lib.Opts(STORAGE[storage], int(bool(with_rho)), ctypes.c_void_p(sptr), int(vx), int(block),
+                      int(q))
         h = ctypes.c_void_p()
         _lib.check(self._lib.mdf_create(ctypes.byref(h), ctypes.byref(g), self.d,
                                         ctypes.byref(r), ctypes.byref(bc), ctypes.byref(o)))

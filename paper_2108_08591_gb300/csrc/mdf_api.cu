@@ -138,13 +138,11 @@ DevArgs base_args(const mdf_t h) {
 }
 
 cudaError_t launch_update(const mdf_t h, int mode, const DevArgs &a) {
-  return h->d == 2 ? launch_update_d2q5(h->storage, mode, h->walls, a, h->stream)
-                   : launch_update_d3q7(h->storage, mode, h->walls, a, h->stream);
+  return lattice_launch(h->d, h->q)->update(h->storage, mode, h->walls, a, h->stream);
 }
 
 cudaError_t launch_reduce(const mdf_t h, int kind, const DevArgs &a) {
-  return h->d == 2 ? launch_reduce_d2q5(h->storage, h->walls, kind, a, h->stream)
-                   : launch_reduce_d3q7(h->storage, h->walls, kind, a, h->stream);
+  return lattice_launch(h->d, h->q)->reduce(h->storage, h->walls, kind, a, h->stream);
 }
 
 void drop_graphs(mdf_t h) {
@@ -272,11 +270,16 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
   if (o) opts = *o;
   if (storage_bytes(opts.storage) == 0)
     return fail(nullptr, MDF_EUNSUPPORTED, "unknown storage %d", opts.storage);
+  const int q = opts.q ? opts.q : (d == 2 ? 5 : 7);
+  if (!lattice_launch(d, q))
+    return fail(nullptr, MDF_EUNSUPPORTED, "no D%dQ%d lattice (D2Q5, D2Q4, D3Q7, D3Q6)", d, q);
+  if (q != 5 && q != 7 && eq_storage(opts.storage))
+    return fail(nullptr, MDF_EUNSUPPORTED, "equilibrium-shifted storage needs D2Q5 or D3Q7");
 
   mdf_t h = new (std::nothrow) mdf_s;
   if (!h) return fail(nullptr, MDF_ENOMEM, "host allocation");
   h->d = d;
-  h->q = d == 2 ? 5 : 7;
+  h->q = q;
   h->with_rho = opts.with_rho ? 1 : 0;
   h->nsets = d + h->with_rho;
   h->storage = opts.storage;
@@ -328,8 +331,7 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
     e = cudaMemsetAsync(h->mask, 0, (size_t)h->plane, h->stream);
     if (e == cudaSuccess) {
       DevArgs a = base_args(h);
-      e = d == 2 ? launch_mask_d2q5(h->bc.wall, h->bc.lid, a, h->mask, h->stream)
-                 : launch_mask_d3q7(h->bc.wall, h->bc.lid, a, h->mask, h->stream);
+      e = lattice_launch(h->d, h->q)->mask(h->bc.wall, h->bc.lid, a, h->mask, h->stream);
     }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -383,8 +385,7 @@ static mdf_status init_state(mdf_t h, const double *P, const double *u, const do
   }
   a.fout = h->cur;
   a.mout = h->mac[h->cur_index()];
-  CU(h, h->d == 2 ? launch_init_d2q5(h->storage, h->walls, a, h->stream)
-                  : launch_init_d3q7(h->storage, h->walls, a, h->stream));
+  CU(h, lattice_launch(h->d, h->q)->init(h->storage, h->walls, a, h->stream));
   if (where == MDF_HOST) CU(h, cudaStreamSynchronize(h->stream));
   h->step = 0;
   h->have_prev = false;

@@ -1,5 +1,5 @@
 // D3Q7 instantiations of the MDF-LBM kernels (one translation unit per
-// lattice so the two compile in parallel).
+// lattice so that they compile in parallel).
 #include "mdf_kernels.cuh"
 
 namespace mdf {

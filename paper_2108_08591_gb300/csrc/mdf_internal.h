@@ -64,6 +64,40 @@ cudaError_t launch_mask_d2q5(const int wall[3], int lid, const DevArgs &a, uint8
 cudaError_t launch_mask_d3q7(const int wall[3], int lid, const DevArgs &a, uint8_t *mask,
                              cudaStream_t s);
 
+// Lattices without a rest direction (mdf_d2q4.cu, mdf_d3q6.cu): the
+// rest-shifted storage types only.
+cudaError_t launch_update_d2q4(int storage, int mode, bool walls, const DevArgs &a,
+                               cudaStream_t s);
+cudaError_t launch_init_d2q4(int storage, bool walls, const DevArgs &a, cudaStream_t s);
+cudaError_t launch_reduce_d2q4(int storage, bool walls, int kind, const DevArgs &a,
+                               cudaStream_t s);
+cudaError_t launch_mask_d2q4(const int wall[3], int lid, const DevArgs &a, uint8_t *mask,
+                             cudaStream_t s);
+cudaError_t launch_update_d3q6(int storage, int mode, bool walls, const DevArgs &a,
+                               cudaStream_t s);
+cudaError_t launch_init_d3q6(int storage, bool walls, const DevArgs &a, cudaStream_t s);
+cudaError_t launch_reduce_d3q6(int storage, bool walls, int kind, const DevArgs &a,
+                               cudaStream_t s);
+cudaError_t launch_mask_d3q6(const int wall[3], int lid, const DevArgs &a, uint8_t *mask,
+                             cudaStream_t s);
+
+// The four launchers of one lattice.
+struct LatticeLaunch {
+  cudaError_t (*update)(int storage, int mode, bool walls, const DevArgs &a, cudaStream_t s);
+  cudaError_t (*init)(int storage, bool walls, const DevArgs &a, cudaStream_t s);
+  cudaError_t (*reduce)(int storage, bool walls, int kind, const DevArgs &a, cudaStream_t s);
+  cudaError_t (*mask)(const int wall[3], int lid, const DevArgs &a, uint8_t *mask, cudaStream_t s);
+};
+inline const LatticeLaunch *lattice_launch(int d, int q) {
+  static const LatticeLaunch d2q5{launch_update_d2q5, launch_init_d2q5, launch_reduce_d2q5, launch_mask_d2q5};
+  static const LatticeLaunch d3q7{launch_update_d3q7, launch_init_d3q7, launch_reduce_d3q7, launch_mask_d3q7};
+  static const LatticeLaunch d2q4{launch_update_d2q4, launch_init_d2q4, launch_reduce_d2q4, launch_mask_d2q4};
+  static const LatticeLaunch d3q6{launch_update_d3q6, launch_init_d3q6, launch_reduce_d3q6, launch_mask_d3q6};
+  if (d == 2) return q == 5 ? &d2q5 : q == 4 ? &d2q4 : nullptr;
+  if (d == 3) return q == 7 ? &d3q7 : q == 6 ? &d3q6 : nullptr;
+  return nullptr;
+}
+
 // Second reduction pass: sums `nblocks` x `k` partials in a fixed order.
 cudaError_t launch_reduce_final(const DevArgs &a, int nblocks, int k, cudaStream_t s);
 // Dense FP64 [d][N] -> padded [d][plane] in FP32 (f64 = false) or FP64.

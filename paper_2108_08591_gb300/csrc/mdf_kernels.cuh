@@ -49,7 +49,7 @@ __device__ __forceinline__ void pull_set_p(const TS *__restrict__ base, long lon
   using TC = typename ComputeOf<TS>::T;
 #pragma unroll
   for (int i = 0; i < L::Q; ++i) {
-    if (WALLS && i != 0 && ((m >> L::opp(i)) & 1)) {
+    if (WALLS && moving<L>(i) && ((m >> L::opp(i)) & 1)) {
       // anti-halfway bounce-back; in shifted storage the alpha = 0 wall value
       // rho0 and the rest shift cancel, leaving -g*_opp + 2 w_i u_wall(alpha)
       TC v = -TC(Codec<TS>::load(base + (long long)L::opp(i) * stride + idx));
@@ -384,10 +384,10 @@ __device__ __forceinline__ void bounce_back_vec(const DevArgs &A, const TS *__re
                                                 typename ComputeOf<TS>::T (&v)[L::Q][VX]) {
   using TC = typename ComputeOf<TS>::T;
 #pragma unroll
-  for (int i = 1; i < L::Q; ++i)
+  for (int i = 0; i < L::Q; ++i)
 #pragma unroll
     for (int j = 0; j < VX; ++j)
-      if ((m[j] >> L::opp(i)) & 1) {
+      if (moving<L>(i) && ((m[j] >> L::opp(i)) & 1)) {
         TC w = -TC(Codec<TS>::load(base + (long long)L::opp(i) * A.plane + R.row0 + R.x0 + j));
         if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u))
           w += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
@@ -616,7 +616,7 @@ __device__ __forceinline__ TC geq_v(int alpha, int i, const TC (&u)[L::D], TC Pp
 template <class L>
 __device__ __forceinline__ double fne_at(const DevArgs &A, long long N, long long n, int alpha, int i) {
   constexpr int D = L::D;
-  if (!A.Gin || alpha == 0 || i == 0) return 0.0;
+  if (!A.Gin || alpha == 0 || !moving<L>(i)) return 0.0;
   const int b = L::c(i, 0) != 0 ? 0 : L::c(i, 1) != 0 ? 1 : 2;
   const int sg = L::c(i, b);
   double g = A.Gin[((long long)(alpha - 1) * D + b) * N + n];
@@ -659,7 +659,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
   for (int i = 0; i < Q; ++i) {
     long long t = n;
     tidx[i] = idx;
-    if (!(WALLS && i != 0 && ((m >> i) & 1))) {
+    if (!(WALLS && moving<L>(i) && ((m >> i) & 1))) {
       const int tx = wrap(x + L::c(i, 0), A.nx);
       const int ty = wrap(y + L::c(i, 1), A.ny);
       const int tz = D == 3 ? wrap(z + L::c(i, 2), A.nz) : z;
@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       TC v;
-      const bool wall = WALLS && i != 0 && ((m >> i) & 1);
+      const bool wall = WALLS && moving<L>(i) && ((m >> i) & 1);
       if (wall) {
         v = -geq_v<L, TC>(alpha, L::opp(i), tu[i], tP[i]);
         if (A.Gin) v -= narrow_to<TC>(fne_at<L>(A, N, n, alpha, L::opp(i)));
@@ -773,10 +773,10 @@ __global__ void k_mask(const DevArgs A, int wx, int wy, int wz, int lid, uint8_t
   const int pos[3] = {x, y, z}, ext[3] = {A.nx, A.ny, A.nz}, wall[3] = {wx, wy, wz};
   uint8_t m = 0;
 #pragma unroll
-  for (int i = 1; i < L::Q; ++i) {
+  for (int i = 0; i < L::Q; ++i) {
 #pragma unroll
     for (int b = 0; b < L::D; ++b) {
-      const int t = pos[b] + L::c(i, b);
+      const int t = pos[b] + L::c(i, b);  // the rest direction never leaves
       if (wall[b] && (t < 0 || t >= ext[b])) {
         m |= uint8_t(1u << i);
         if (lid && b == L::D - 1 && t >= ext[b]) m |= 0x80u;
@@ -889,11 +889,17 @@ cudaError_t update_eq_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) 
   return update_eq_vx<L, TS, 1>(mode, walls, a, s);
 }
 
+// Lattices without a rest direction have the rest-shifted codecs only (the
+// equilibrium-shifted kernels are written for D2Q5 and D3Q7).
 template <class L>
 cudaError_t update_lattice(int storage, int mode, bool walls, const DevArgs &a, cudaStream_t s) {
   switch (storage) {
-    case ST_F16EQ: return update_eq_t<L, __half>(mode, walls, a, s);
-    case ST_BF16EQ: return update_eq_t<L, __nv_bfloat16>(mode, walls, a, s);
+    case ST_F16EQ:
+      if constexpr (L::REST == 0) return update_eq_t<L, __half>(mode, walls, a, s);
+      return cudaErrorInvalidValue;
+    case ST_BF16EQ:
+      if constexpr (L::REST == 0) return update_eq_t<L, __nv_bfloat16>(mode, walls, a, s);
+      return cudaErrorInvalidValue;
     case ST_F32: return update_t<L, float>(mode, walls, a, s);
     case ST_F16: return update_t<L, __half>(mode, walls, a, s);
     case ST_BF16: return update_t<L, __nv_bfloat16>(mode, walls, a, s);
@@ -919,8 +925,12 @@ cudaError_t init_eq_t(bool walls, const DevArgs &a, cudaStream_t s) {
 template <class L>
 cudaError_t init_lattice(int storage, bool walls, const DevArgs &a, cudaStream_t s) {
   switch (storage) {
-    case ST_F16EQ: return init_eq_t<L, __half>(walls, a, s);
-    case ST_BF16EQ: return init_eq_t<L, __nv_bfloat16>(walls, a, s);
+    case ST_F16EQ:
+      if constexpr (L::REST == 0) return init_eq_t<L, __half>(walls, a, s);
+      return cudaErrorInvalidValue;
+    case ST_BF16EQ:
+      if constexpr (L::REST == 0) return init_eq_t<L, __nv_bfloat16>(walls, a, s);
+      return cudaErrorInvalidValue;
     case ST_F32: return init_t<L, float>(walls, a, s);
     case ST_F16: return init_t<L, __half>(walls, a, s);
     case ST_BF16: return init_t<L, __nv_bfloat16>(walls, a, s);
@@ -958,8 +968,12 @@ cudaError_t reduce_eq_t(bool walls, int kind, const DevArgs &a, cudaStream_t s) 
 template <class L>
 cudaError_t reduce_lattice(int storage, bool walls, int kind, const DevArgs &a, cudaStream_t s) {
   switch (storage) {
-    case ST_F16EQ: return reduce_eq_t<L, __half>(walls, kind, a, s);
-    case ST_BF16EQ: return reduce_eq_t<L, __nv_bfloat16>(walls, kind, a, s);
+    case ST_F16EQ:
+      if constexpr (L::REST == 0) return reduce_eq_t<L, __half>(walls, kind, a, s);
+      return cudaErrorInvalidValue;
+    case ST_BF16EQ:
+      if constexpr (L::REST == 0) return reduce_eq_t<L, __nv_bfloat16>(walls, kind, a, s);
+      return cudaErrorInvalidValue;
     case ST_F32: return reduce_t<L, float>(walls, kind, a, s);
     case ST_F16: return reduce_t<L, __half>(walls, kind, a, s);
     case ST_BF16: return reduce_t<L, __nv_bfloat16>(walls, kind, a, s);

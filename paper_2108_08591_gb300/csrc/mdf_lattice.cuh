@@ -56,6 +56,7 @@ template <> struct Codec<__nv_bfloat16> {
 // ---------------------------------------------------------------------------
 struct D2Q5 {
   static constexpr int D = 2, Q = 5;
+  static constexpr int REST = 0;  // index of the rest direction
   static constexpr double CS2 = 1.0 / 3.0;
   __host__ __device__ static constexpr int c(int i, int b) {
     return b == 0 ? (i == 1 ? 1 : i == 3 ? -1 : 0) : b == 1 ? (i == 2 ? 1 : i == 4 ? -1 : 0) : 0;
@@ -96,6 +97,7 @@ struct D2Q5 {
 // ---------------------------------------------------------------------------
 struct D3Q7 {
   static constexpr int D = 3, Q = 7;
+  static constexpr int REST = 0;
   static constexpr double CS2 = 0.25;
   __host__ __device__ static constexpr int c(int i, int b) {
     return b == 0 ? (i == 1 ? 1 : i == 2 ? -1 : 0)
@@ -131,5 +133,79 @@ struct D3Q7 {
     g[6] = g[6] + h3 - e4 + eo + q6 + Fw;
   }
 };
+
+// ---------------------------------------------------------------------------
+// Lattices without a rest direction (Sec. 2.2), in the paper's order.
+// D2Q4: c_0..c_3 = (1,0),(0,1),(-1,0),(0,-1); w_i = 1/4; c_s^2 = 1/2.
+// The paper prints no M for it; the basis used is the conserved row, the two
+// first moments and the traceless second moment:
+//   m0 = sum g, m1 = g0 - g2, m2 = g1 - g3, m3 = g0 - g1 + g2 - g3,
+// squared norms (4, 2, 2, 4), S_d = diag(s0, s1, s1, s2); m3eq = 0, and
+// w_i F has no m3 part.
+// ---------------------------------------------------------------------------
+struct D2Q4 {
+  static constexpr int D = 2, Q = 4;
+  static constexpr int REST = -1;
+  static constexpr double CS2 = 0.5;
+  __host__ __device__ static constexpr int c(int i, int b) {
+    return b == 0 ? (i == 0 ? 1 : i == 2 ? -1 : 0) : b == 1 ? (i == 1 ? 1 : i == 3 ? -1 : 0) : 0;
+  }
+  __host__ __device__ static constexpr int opp(int i) { return (i + 2) & 3; }
+  __host__ __device__ static constexpr double w(int) { return 0.25; }
+  static constexpr int UP = 1;
+
+  template <class TC>
+  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F) {
+    const TC d1 = s1 * ((g[0] - g[2]) - jeq[0]);
+    const TC d2 = s1 * ((g[1] - g[3]) - jeq[1]);
+    const TC d3 = s2 * ((g[0] + g[2]) - (g[1] + g[3]));
+    const TC h1 = TC(0.5) * d1, h2 = TC(0.5) * d2, q3 = TC(0.25) * d3;
+    const TC Fw = F * TC(0.25);
+    g[0] = g[0] - h1 - q3 + Fw;
+    g[1] = g[1] - h2 + q3 + Fw;
+    g[2] = g[2] + h1 - q3 + Fw;
+    g[3] = g[3] + h2 + q3 + Fw;
+  }
+};
+
+// D3Q6: c_0..c_5 = +-x, +-y, +-z; w_i = 1/6; c_s^2 = 1/3.  Basis: m0, the
+// three first moments, m4 = 2cx^2 - cy^2 - cz^2 and m5 = cy^2 - cz^2,
+// squared norms (6, 2, 2, 2, 12, 4), S_d = diag(s0, s1 x3, s2 x2);
+// m4eq = m5eq = 0, and w_i F has no m4 or m5 part.
+struct D3Q6 {
+  static constexpr int D = 3, Q = 6;
+  static constexpr int REST = -1;
+  static constexpr double CS2 = 1.0 / 3.0;
+  __host__ __device__ static constexpr int c(int i, int b) {
+    return b == 0 ? (i == 0 ? 1 : i == 1 ? -1 : 0)
+         : b == 1 ? (i == 2 ? 1 : i == 3 ? -1 : 0)
+                  : (i == 4 ? 1 : i == 5 ? -1 : 0);
+  }
+  __host__ __device__ static constexpr int opp(int i) { return i ^ 1; }
+  __host__ __device__ static constexpr double w(int) { return 1.0 / 6.0; }
+  static constexpr int UP = 4;
+
+  template <class TC>
+  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F) {
+    const TC sx = g[0] + g[1], sy = g[2] + g[3], sz = g[4] + g[5];
+    const TC d1 = s1 * ((g[0] - g[1]) - jeq[0]);
+    const TC d2 = s1 * ((g[2] - g[3]) - jeq[1]);
+    const TC d3 = s1 * ((g[4] - g[5]) - jeq[2]);
+    const TC d4 = s2 * (TC(2) * sx - sy - sz);
+    const TC d5 = s2 * (sy - sz);
+    const TC h1 = TC(0.5) * d1, h2 = TC(0.5) * d2, h3 = TC(0.5) * d3;
+    const TC ex = d4 * TC(1.0 / 6.0), eo = d4 * TC(1.0 / 12.0), q5 = TC(0.25) * d5;
+    const TC Fw = F * TC(1.0 / 6.0);
+    g[0] = g[0] - h1 - ex + Fw;
+    g[1] = g[1] + h1 - ex + Fw;
+    g[2] = g[2] - h2 + eo - q5 + Fw;
+    g[3] = g[3] + h2 + eo - q5 + Fw;
+    g[4] = g[4] - h3 + eo + q5 + Fw;
+    g[5] = g[5] + h3 + eo + q5 + Fw;
+  }
+};
+
+// True for a direction with a non-zero velocity (every i but the rest one).
+template <class L> __host__ __device__ constexpr bool moving(int i) { return i != L::REST; }
 
 }  // namespace mdf

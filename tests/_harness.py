@@ -11,10 +11,10 @@ FIELDS = ("P", "u", "rho", "G", "div", "S", "sigma", "omega")
 
 def run_gpu(shape, P, u, steps, s1, s2=-1.0, storage="f32", wall=(0, 0, 0), lid=False,
             lid_u=(0.0, 0.0, 0.0), with_rho=True, force=None, names=FIELDS, forcing="eq3-21",
-            G=None):
+            G=None, q=0):
     from paper_2108_08591_gb300 import Lattice
     lat = Lattice(shape, s1=s1, s2=s2, storage=storage, wall=wall, lid=lid, lid_u=lid_u,
-                  with_rho=with_rho)
+                  with_rho=with_rho, q=q)
     try:
         lat.set_forcing(forcing)
         if force is not None:  # before init: the Scheme II initial state depends on it
@@ -30,10 +30,10 @@ def run_gpu(shape, P, u, steps, s1, s2=-1.0, storage="f32", wall=(0, 0, 0), lid=
 
 
 def run_oracle(shape, P, u, steps, s1, s2=None, wall=(0, 0, 0), lid=False,
-               lid_u=(0.0, 0.0, 0.0), with_rho=True, force=None, scheme=0, G=None):
+               lid_u=(0.0, 0.0, 0.0), with_rho=True, force=None, scheme=0, G=None, q=0):
     d = len(shape)
     pb = O.Problem(d=d, n=tuple(shape), s1=s1, s2=s2, wall=wall, lid=lid, lid_u=lid_u,
-                   with_rho=with_rho, force=force, scheme=scheme)
+                   with_rho=with_rho, force=force, scheme=scheme, nq=q)
     f = O.init(pb, P, u, G)
     O.run(pb, f, steps)
     Pn, un, rho = O.macro(pb, f)

@@ -70,3 +70,46 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     assert lib.mdf_step(None, 1) == _lib.EINVAL
     assert lib.mdf_init(None, None, None, 0) == _lib.EINVAL
     lib.mdf_destroy(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors have the header's sizes and field offsets (a C
+    program built with gcc against include/mdf.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_2108_08591_gb300 import _lib
+    if not shutil.which("gcc"):
+        pytest.skip("gcc not found")
+    mirrors = {"mdf_grid": _lib.Grid, "mdf_rates": _lib.Rates, "mdf_bc": _lib.BC,
+               "mdf_opts": _lib.Opts, "mdf_fields_t": _lib.Fields, "mdf_info_t": _lib.Info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "mdf.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("  return 0;\n}")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_lattice_choice_is_checked_without_a_gpu(lib):
+    """q names a lattice of the dimension; equilibrium-shifted storage needs
+    D2Q5 / D3Q7."""
+    from paper_2108_08591_gb300 import _lib
+    h = ctypes.c_void_p()
+    r = _lib.Rates(1.0, 1.2, -1.0)
+    g2, g3 = _lib.Grid(8, 8, 1), _lib.Grid(8, 8, 8)
+    for g, d, q, storage in ((g2, 2, 3, "f32"), (g2, 2, 6, "f32"), (g3, 3, 4, "f32"),
+                             (g2, 2, 4, "f16eq"), (g3, 3, 6, "bf16eq")):
+        o = _lib.Opts(_lib.STORAGE[storage], 1, None, 0, 0, q)
+        assert lib.mdf_create(ctypes.byref(h), ctypes.byref(g), d, ctypes.byref(r), None,
+                              ctypes.byref(o)) == _lib.EUNSUPPORTED, (d, q, storage)

@@ -331,6 +331,87 @@ def test_neq_seed_removes_the_initial_layer_on_the_gpu():
 
 
 # --------------------------------------------------------------------------
+# Lattices without a rest direction (D2Q4, D3Q6)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16", "bf16"])
+@pytest.mark.parametrize("case", ["2d_periodic", "2d_walls_lid_force", "3d_walls", "3d_periodic_force"])
+def test_rest_free_lattice_matches_oracle(storage, case):
+    """D2Q4 / D3Q6 against the oracle: ragged periodic grids, walls and a
+    lid, a non-uniform force, a non-rest start; fields, rho and the mask."""
+    d = 3 if case.startswith("3d") else 2
+    q = 6 if d == 3 else 4
+    kw, F = {}, None
+    if d == 2:
+        shape, steps, s1 = (67, 45), 300, 1.3
+    else:
+        shape, steps, s1 = (36, 19, 17), 80, 1.5
+    if "walls" in case:
+        kw = dict(wall=(1, 1, 0), lid=True, lid_u=(0.02, 0.0, 0.0)) if d == 2 else dict(wall=(1, 0, 1))
+    if "force" in case:
+        F = _scheme2_force(shape, 1e-5)
+    P, u = synth.smooth_fields(shape, seed=23, amp=0.01)
+    ref = run_oracle(shape, P, u, steps, s1, force=F, q=q, **kw)
+    got = run_gpu(shape, P, u, steps, s1, storage=storage, force=F, q=q, **kw)
+    assert np.array_equal(got["mask"], ref["mask"])
+    e = errors(ref, got)
+    tu, tp, tg = _tol(storage)
+    assert e["u"] < tu and e["P"] < tp, e
+    assert e["G"] < tg and e["S"] < tg and e["omega"] < tg, e
+    assert e["rho"] < (1e-10 if storage == "f64" else 1e-2), e
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_rest_free_scheme2_and_neq_seed(storage):
+    """D2Q4 with Scheme II forcing and a non-equilibrium start, with walls."""
+    shape, steps, s1 = (45, 37), 60, 1.3
+    kw = dict(wall=(0, 1, 0))
+    P, u = synth.smooth_fields(shape, seed=29, amp=0.01)
+    F = _scheme2_force(shape, 2e-5)
+    G = _seed_gradient(shape, 7)
+    ref = run_oracle(shape, P, u, steps, s1, force=F, scheme=2, G=G, q=4, **kw)
+    got = run_gpu(shape, P, u, steps, s1, storage=storage, force=F, forcing="scheme2", G=G, q=4, **kw)
+    e = errors(ref, got)
+    tu, tp, tg = _tol(storage)
+    assert e["u"] < tu and e["P"] < tp and e["G"] < tg, e
+
+
+@pytest.mark.parametrize("d,storage,vx", [
+    (2, "f32", 4), (2, "f32", 2), (2, "f16", 8), (2, "bf16", 4), (2, "f64", 2),
+    (3, "f32", 4), (3, "f16", 4), (3, "bf16", 8), (3, "f64", 2),
+])
+@pytest.mark.parametrize("walls", [False, True])
+def test_rest_free_vector_kernel_is_bitwise_the_scalar_kernel(d, storage, vx, walls):
+    from paper_2108_08591_gb300 import Lattice
+    shape = (264, 9) if d == 2 else (264, 5, 4)
+    P, u = synth.smooth_fields(shape, seed=19)
+    kw = {}
+    if walls:
+        kw = dict(wall=(1, 1, 1)[:d] + (0,) * (3 - d), lid=True, lid_u=(0.02, 0.01, 0.0))
+    outs = []
+    for v in (1, vx):
+        lat = Lattice(shape, s1=1.35, storage=storage, vx=v, block=64, q=2 * d, **kw)
+        lat.init(P, u)
+        lat.step(9)
+        outs.append(lat.fields_host(("P", "u", "G", "rho")))
+        lat.close()
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+def test_rest_free_lattice_rejections():
+    """Equilibrium-shifted storage and the batch need D2Q5 / D3Q7; q must
+    name a lattice of the dimension."""
+    from paper_2108_08591_gb300 import CavityBatch, Lattice, MdfError
+    for shape, q, storage in (((64, 32), 4, "f16eq"), ((32, 16, 8), 6, "bf16eq"),
+                              ((32, 16, 8), 4, "f32"), ((64, 32), 6, "f32"), ((64, 32), 3, "f32")):
+        with pytest.raises(MdfError):
+            Lattice(shape, s1=1.2, storage=storage, q=q)
+    lat = Lattice((64, 32), s1=1.2, q=4)
+    assert lat.info.q == 4
+    lat.close()
+
+
+# --------------------------------------------------------------------------
 # Fused epilogue, reductions, checkpoints, edges
 # --------------------------------------------------------------------------
 def test_fused_fields_equal_separate_pass():
