@@ -636,12 +636,13 @@ __device__ __forceinline__ TC geq(const DevArgs &A, long long N, long long n, in
   return geq_v<L, TC>(alpha, i, u, Pp);
 }
 
-// Initial state f = f^eq(P, u) written in pull form: the value stored at x
-// for direction i is the one the first update pulls into x + c_i, and for a
-// wall link the one whose bounce-back returns f^eq_opp(i)(x).  Each of the
-// Q source nodes' seed is rounded once and shared by the sets.  With a seed
-// gradient the state is f^eq + f^ne (fne_at), and under Scheme II it is
-// fbar = f - w_i Fbar_alpha / 2, both at the node the value arrives at.
+// Initial state f = f^eq(P, u) written in pull form, pushed from each node:
+// the population arriving at x along c_i is stored where the first update
+// pulls it from, at x - c_i, or, when that link comes through a wall, in the
+// slot of the opposite direction at x, whose bounce-back returns it.  Every
+// slot is written once, and a node reads only its own seed.  With a seed
+// gradient the population is f^eq + f^ne (fne_at); under Scheme II it is
+// fbar = f - w_i Fbar_alpha / 2.  The seed is rounded once per node.
 template <class L, class TS, bool WALLS>
 __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
   using TC = typename ComputeOf<TS>::T;
@@ -653,44 +654,33 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
   const long long N = (long long)A.nx * A.ny * A.nz;
   const long long n = ((long long)z * A.ny + y) * A.nx + x;
   const uint8_t m = WALLS ? A.mask[idx] : uint8_t(0);
-  TC tu[Q][D], tP[Q];
-  long long tidx[Q], tn[Q];  // padded and dense index of the node each value arrives at
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    long long t = n;
-    tidx[i] = idx;
-    if (!(WALLS && moving<L>(i) && ((m >> i) & 1))) {
-      const int tx = wrap(x + L::c(i, 0), A.nx);
-      const int ty = wrap(y + L::c(i, 1), A.ny);
-      const int tz = D == 3 ? wrap(z + L::c(i, 2), A.nz) : z;
-      t = ((long long)tz * A.ny + ty) * A.nx + tx;
-      tidx[i] = ((long long)tz * A.ny + ty) * A.px + tx;
-    }
-    tn[i] = t;
-    seed_at<L, TC>(A, N, t, tu[i], tP[i]);
-  }
+  TC u[D], Pp;
+  seed_at<L, TC>(A, N, n, u, Pp);
   TS *fout = static_cast<TS *>(A.fout);
   const int nsets = D + A.with_rho;
   for (int a = 0; a < nsets; ++a) {
     const int alpha = a + 1 - A.with_rho;
+    const TC Fa = (A.scheme2 && alpha >= 1)
+                      ? __ldg(static_cast<const TC *>(A.force) + (alpha - 1) * A.plane + idx) : TC(0);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
+      const int o = L::opp(i);
+      const bool wall = WALLS && moving<L>(i) && ((m >> o) & 1);  // arrives through a wall
       TC v;
-      const bool wall = WALLS && moving<L>(i) && ((m >> i) & 1);
-      if (wall) {
-        v = -geq_v<L, TC>(alpha, L::opp(i), tu[i], tP[i]);
-        if (A.Gin) v -= narrow_to<TC>(fne_at<L>(A, N, n, alpha, L::opp(i)));
-        if (alpha >= 1 && i == L::UP && (m & 0x80u)) v += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
-      } else {
-        v = geq_v<L, TC>(alpha, i, tu[i], tP[i]);
-        if (A.Gin) v += narrow_to<TC>(fne_at<L>(A, N, tn[i], alpha, i));
+      long long dst;
+      if (wall) {  // stored in slot o at x, negated by the bounce-back
+        v = -geq_v<L, TC>(alpha, i, u, Pp);
+        if (A.Gin) v -= narrow_to<TC>(fne_at<L>(A, N, n, alpha, i));
+        if (alpha >= 1 && o == L::UP && (m & 0x80u)) v += TC(2.0 * L::w(o) * A.lid_u[alpha - 1]);
+        if (A.scheme2 && alpha >= 1) v = v + TC(0.5 * L::w(o)) * Fa;
+        dst = ((long long)a * Q + o) * A.plane + idx;
+      } else {  // stored in slot i at x - c_i
+        v = geq_v<L, TC>(alpha, i, u, Pp);
+        if (A.Gin) v += narrow_to<TC>(fne_at<L>(A, N, n, alpha, i));
+        if (A.scheme2 && alpha >= 1) v = v - TC(0.5 * L::w(i)) * Fa;
+        dst = ((long long)a * Q + i) * A.plane + pull_src<L>(A, x, y, z, i);
       }
-      if (A.scheme2 && alpha >= 1) {  // the bounce-back negates the shift
-        const TC Fh = TC(0.5 * L::w(i)) * __ldg(static_cast<const TC *>(A.force) +
-                                                (alpha - 1) * A.plane + (wall ? idx : tidx[i]));
-        v = wall ? v + Fh : v - Fh;
-      }
-      Codec<TS>::store(fout + ((long long)a * Q + i) * A.plane + idx, v);
+      Codec<TS>::store(fout + dst, v);
     }
   }
 }
