@@ -56,7 +56,7 @@ def _dist():
     return rank, world, local
 
 
-def _config(n_gpus: int, storage: str, d: int = 2, q: int = 0):
+def _config(n_gpus: int, storage: str, d: int = 2, q: int = 0, inplace: bool = False):
     grid = [N_GRID] * d
     q = q or (5 if d == 2 else 7)
     pop_gb = N_GRID ** d * q * (d + 1) * {"f32": 4, "f16": 2, "bf16": 2,
@@ -64,7 +64,7 @@ def _config(n_gpus: int, storage: str, d: int = 2, q: int = 0):
     return {"workload": WORKLOAD, "grid": grid, "lattice": f"D{d}Q{q}",
             "sets": d + 1, "storage": storage, "steps_per_bench_step": EPI_EVERY,
             "global_batch": n_gpus, "parallelism": f"replicas x{n_gpus}",
-            "l2": f"inputs larger than L2 (2 x {pop_gb:.2f} GB populations), no flush"}
+            "l2": f"inputs larger than L2 ({1 if inplace else 2} x {pop_gb:.2f} GB populations), no flush"}
 
 
 def aggregate(local_updates: float, local_ms: float, dist=None, device="cpu"):
@@ -331,7 +331,7 @@ def run_mdf(args):
     N = int(np.prod(shape))
     stream = torch.cuda.current_stream()
     lat = Lattice(shape, s1=s1, storage=args.storage, stream=stream, vx=args.vx or 0,
-                  block=args.block or 0, q=args.q)
+                  block=args.block or 0, q=args.q, inplace=args.inplace)
     lat.init(P, u)
     info = lat.info
     fields = lat.alloc_fields(("P", "u", "G", "div", "S", "sigma", "omega"))
@@ -439,7 +439,7 @@ def run_mdf(args):
     bytes_per_launch = info.bytes_per_update * N
     achieved = bytes_per_launch / (plain_ms / 1e3) / 1e9
     sha = _kernel_sha()
-    default_lattice = args.q in (0, 5 if d == 2 else 7)
+    default_lattice = args.q in (0, 5 if d == 2 else 7) and not args.inplace
     traffic = _traffic(sha) if (args.workload == "tg2d" and N_GRID == 4096
                                 and args.storage == "f32" and default_lattice) else None
     oerr = None
@@ -451,7 +451,9 @@ def run_mdf(args):
     kname = f"D{d}Q{info.q}"
     tname = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16", "f16eq": "__half",
              "bf16eq": "__nv_bfloat16"}[args.storage]
-    if args.storage.endswith("eq"):
+    if args.inplace:
+        kernel = f"k_update_aa<{kname},{tname},even+odd,MODE_STEP,periodic>"
+    elif args.storage.endswith("eq"):
         kernel = f"k_update_eq<{kname},{tname},VX={info.vx},MODE_STEP,periodic>"
     elif info.vx > 1:
         kernel = f"k_update_vec<{kname},{tname},VX={info.vx},MODE_STEP,periodic>"
@@ -464,7 +466,7 @@ def run_mdf(args):
         "dtype": {"f32": "f32", "f16": "f16 storage / f32", "bf16": "bf16 storage / f32",
                   "f16eq": "f16 equilibrium-shifted storage + f32 moments / f32",
                   "bf16eq": "bf16 equilibrium-shifted storage + f32 moments / f32"}[args.storage],
-        "data": "synthetic", "config": _config(world, args.storage, d, args.q),
+        "data": "synthetic", "config": _config(world, args.storage, d, args.q, args.inplace),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_kind} hbm_gbs (MEASURED_PEAKS.json)",
@@ -625,6 +627,8 @@ def main():
     ap.add_argument("--q", type=int, default=0, choices=(0, 4, 5, 6, 7),
                     help="directions per set: 0 = D2Q5 / D3Q7 (default); 4 = D2Q4, 6 = D3Q6 "
                          "(no rest direction, rest-shifted storage only)")
+    ap.add_argument("--inplace", action="store_true",
+                    help="one population buffer, streamed in place by the AA pattern")
     ap.add_argument("--grid", type=int, default=4096,
                     help="lattice side (default 4096; smaller sides are profiling cases)")
     args = ap.parse_args()
@@ -638,6 +642,8 @@ def main():
         WORKLOAD = WORKLOAD.replace(f"{N_GRID}x{N_GRID}", f"{args.grid}x{args.grid}").replace(
             f"{N_GRID}^3", f"{args.grid}^3")
         N_GRID = args.grid
+    if args.inplace:
+        WORKLOAD += ", in-place AA-pattern stream (one population buffer)"
     if args.q in (4, 6):
         WORKLOAD = WORKLOAD.replace("D2Q5", "D2Q4").replace("D3Q7", "D3Q6") + (
             ", same viscosity (s1 from the lattice's c_s^2)")

@@ -89,6 +89,12 @@ typedef struct {
     int q;                   /* directions per set: 0 = D2Q5 / D3Q7 (default), 4 = D2Q4,
                                 6 = D3Q6 (Sec. 2.2: no rest direction, fewer bytes
                                 per node; the rest-shifted storage types only) */
+    int inplace;             /* 1: one population buffer, streamed in place by the AA
+                                pattern (even updates collide within a node, odd
+                                updates read and write the neighbours; same results
+                                as the default pull stream over two buffers, half
+                                the population memory).  Rest-shifted storage types
+                                only; one node per thread; no mdf_autotune. */
 } mdf_opts;
 
 /* Derived-field outputs, each a caller-owned array of doubles or NULL.
@@ -267,10 +273,11 @@ mdf_status mdf_residual(mdf_t h, double *r);
  * Synchronises. */
 mdf_status mdf_mask(mdf_t h, unsigned char *host_out);
 
-/* mdf_save / mdf_load -- raw populations plus a header (grid, d, sets,
- * storage, rates, boundary, step) and an FNV-1a checksum.  Load requires a
- * handle created with the same configuration; MDF_EIO on a mismatch or a
- * corrupt file.  Both synchronise.  A resumed run is bit-identical. */
+/* mdf_save / mdf_load -- raw populations plus a header (grid, d, q, sets,
+ * storage, rates, boundary, forcing scheme, buffer layout and AA parity,
+ * step) and an FNV-1a checksum.  Load requires a handle created with the
+ * same configuration; MDF_EIO on a mismatch or a corrupt file.  Both
+ * synchronise.  A resumed run is bit-identical. */
 mdf_status mdf_save(mdf_t h, const char *path);
 mdf_status mdf_load(mdf_t h, const char *path);
 

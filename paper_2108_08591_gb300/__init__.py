@@ -57,12 +57,15 @@ class Lattice:
     'f16eq', 'bf16eq'.  vx / block: x-nodes per thread and threads per block
     of the update kernel (0: the library's tuned default).  q: 0 for
     D2Q5 / D3Q7, 4 for D2Q4, 6 for D3Q6 (rest-shifted storage types only).
+    inplace: one population buffer streamed in place by the AA pattern
+    (rest-shifted storage types; half the memory, the same results).
     """
 
     def __init__(self, shape: Sequence[int], s1: float, s2: float = -1.0, s0: float = 1.0,
                  wall: Sequence[int] = (0, 0, 0), lid: bool = False,
                  lid_u: Sequence[float] = (0.0, 0.0, 0.0), storage: str = "f32",
-                 with_rho: bool = True, stream=None, vx: int = 0, block: int = 0, q: int = 0):
+                 with_rho: bool = True, stream=None, vx: int = 0, block: int = 0, q: int = 0,
+                 inplace: bool = False):
         import torch
 
         self._lib = _lib.load()
@@ -86,7 +89,7 @@ class Lattice:
         lu = list(lid_u) + [0.0] * (3 - len(lid_u))
         bc.lid_u[:] = [float(v) for v in lu[:3]]
         o = _lib.Opts(STORAGE[storage], int(bool(with_rho)), ctypes.c_void_p(sptr), int(vx), int(block),
-                      int(q))
+                      int(q), int(bool(inplace)))
         h = ctypes.c_void_p()
         _lib.check(self._lib.mdf_create(ctypes.byref(h), ctypes.byref(g), self.d,
                                         ctypes.byref(r), ctypes.byref(bc), ctypes.byref(o)))

@@ -34,7 +34,8 @@ class BC(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("storage", ctypes.c_int), ("with_rho", ctypes.c_int), ("stream", ctypes.c_void_p),
-                ("vx", ctypes.c_int), ("block", ctypes.c_int), ("q", ctypes.c_int)]
+                ("vx", ctypes.c_int), ("block", ctypes.c_int), ("q", ctypes.c_int),
+                ("inplace", ctypes.c_int)]
 
 
 class Fields(ctypes.Structure):

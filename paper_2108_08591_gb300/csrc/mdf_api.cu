@@ -84,6 +84,8 @@ struct mdf_s {
   long long step = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // chunk starting from buffer 0 / 1
   void *buf[2] = {nullptr, nullptr};
+  bool inplace = false;  // one buffer, AA pattern (buf[1] unused)
+  int parity = 0;        // AA layout of the current state: 0 even, 1 odd
   void *mac[2] = {nullptr, nullptr};  // node moments of equilibrium-shifted storage
   int kmom = 0;                       // moment slots per node (0 for other storage)
   std::string err = "no error";
@@ -117,7 +119,8 @@ DevArgs base_args(const mdf_t h) {
   DevArgs a;
   std::memset(&a, 0, sizeof a);
   a.fin = h->cur;
-  a.fout = h->nxt;
+  a.fout = h->nxt;  // == cur for the in-place AA pattern
+  a.aa = h->inplace ? 1 + h->parity : 0;
   a.mask = h->walls ? h->mask : nullptr;
   a.force = h->force;
   a.scheme2 = (h->forcing == MDF_FORCING_SCHEME2 && h->force) ? 1 : 0;
@@ -168,27 +171,39 @@ mdf_status one_update(mdf_t h, int mode, const mdf_fields_t *out) {
     a.S = out->S; a.sigma = out->sigma; a.omega = out->omega;
   }
   CU(h, launch_update(h, mode, a));
-  if (mode != MODE_FIELDS) { std::swap(h->cur, h->nxt); ++h->step; }
+  if (mode != MODE_FIELDS) {
+    if (h->inplace) h->parity ^= 1;
+    else std::swap(h->cur, h->nxt);
+    ++h->step;
+  }
   return MDF_OK;
 }
 
-// Capture kGraphChunk updates starting from buffer `which` into a graph.
+// Capture kGraphChunk updates starting from buffer `which` (the AA parity
+// for the in-place pattern) into a graph.
 mdf_status build_graph(mdf_t h, int which) {
   void *c0 = h->cur, *n0 = h->nxt;
-  h->cur = h->buf[which];
-  h->nxt = h->buf[1 - which];
+  const int p0 = h->parity;
+  if (h->inplace) {
+    h->parity = which;
+  } else {
+    h->cur = h->buf[which];
+    h->nxt = h->buf[1 - which];
+  }
   cudaGraph_t g = nullptr;
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k) {
       e = launch_update(h, MODE_STEP, base_args(h));
-      std::swap(h->cur, h->nxt);
+      if (h->inplace) h->parity ^= 1;
+      else std::swap(h->cur, h->nxt);
     }
     cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
     if (e == cudaSuccess) e = e2;
   }
   h->cur = c0;
   h->nxt = n0;
+  h->parity = p0;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&h->graph[which], g, 0);
   if (g) cudaGraphDestroy(g);
   if (e != cudaSuccess) {
@@ -204,7 +219,7 @@ mdf_status run_steps(mdf_t h, long long n) {
   // on the legacy default stream.
   const bool use_graph = h->stream != nullptr && n >= kGraphChunk;
   while (use_graph && n >= kGraphChunk) {
-    const int which = h->cur == h->buf[0] ? 0 : 1;
+    const int which = h->inplace ? h->parity : (h->cur == h->buf[0] ? 0 : 1);
     if (!h->graph[which]) {
       mdf_status st = build_graph(h, which);
       if (st != MDF_OK) return st;
@@ -240,6 +255,7 @@ struct CkptHeader {
   char magic[8];
   int32_t version, d, q, nsets, storage, nx, ny, nz, px, wall[3], lid;
   int32_t forcing;  // the state is fbar under Scheme II: part of its meaning
+  int32_t layout;   // 0: two buffers (pull); in-place AA: 1 even, 2 odd layout
   double s0, s1, s2, lid_u[3];
   int64_t step, payload;
   uint64_t checksum;
@@ -304,6 +320,11 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
     delete h;
     return fail(nullptr, MDF_EINVAL, "vx must be 0 (default), 1, 2, 4 or 8");
   }
+  h->inplace = opts.inplace != 0;
+  if (h->inplace && eq_storage(h->storage)) {
+    delete h;
+    return fail(nullptr, MDF_EUNSUPPORTED, "the in-place AA pattern takes the rest-shifted storage types");
+  }
   if (eq_storage(h->storage)) {
     h->kmom = d + 1 + h->with_rho;
     if (h->plane >= (1LL << 31) - 64) {
@@ -313,10 +334,11 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
   }
   h->block = opts.block ? opts.block : default_block(d, h->storage);
   h->vx = opts.vx ? opts.vx : default_vx(d, h->storage);
+  if (h->inplace) h->vx = 1;  // the AA kernels run one node per thread
 
   const size_t pb = h->pop_bytes();
   cudaError_t e = cudaMalloc(&h->buf[0], pb);
-  if (e == cudaSuccess) e = cudaMalloc(&h->buf[1], pb);
+  if (e == cudaSuccess && !h->inplace) e = cudaMalloc(&h->buf[1], pb);
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, sizeof(double) * kReduceBlocks * 4);
   if (e == cudaSuccess) e = cudaMalloc(&h->result, sizeof(double) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&h->nonfinite, sizeof(int));
@@ -326,7 +348,7 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
   if (e == cudaSuccess && h->kmom) e = cudaMemsetAsync(h->mac[0], 0, h->mom_bytes(), h->stream);
   if (e == cudaSuccess && h->kmom) e = cudaMemsetAsync(h->mac[1], 0, h->mom_bytes(), h->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[0], 0, pb, h->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(h->buf[1], 0, pb, h->stream);
+  if (e == cudaSuccess && !h->inplace) e = cudaMemsetAsync(h->buf[1], 0, pb, h->stream);
   if (e == cudaSuccess && h->walls) {
     e = cudaMemsetAsync(h->mask, 0, (size_t)h->plane, h->stream);
     if (e == cudaSuccess) {
@@ -343,7 +365,7 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
     return st;
   }
   h->cur = h->buf[0];
-  h->nxt = h->buf[1];
+  h->nxt = h->inplace ? h->buf[0] : h->buf[1];
   *out = h;
   return MDF_OK;
 }
@@ -387,6 +409,7 @@ static mdf_status init_state(mdf_t h, const double *P, const double *u, const do
   a.mout = h->mac[h->cur_index()];
   CU(h, lattice_launch(h->d, h->q)->init(h->storage, h->walls, a, h->stream));
   if (where == MDF_HOST) CU(h, cudaStreamSynchronize(h->stream));
+  h->parity = 0;  // the in-place pattern starts in the even layout
   h->step = 0;
   h->have_prev = false;
   return MDF_OK;
@@ -578,12 +601,13 @@ mdf_status mdf_mask(mdf_t h, unsigned char *host_out) {
 static void fill_header(const mdf_t h, CkptHeader &hd) {
   std::memset(&hd, 0, sizeof hd);
   std::memcpy(hd.magic, "MDFLBM1", 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.d = h->d; hd.q = h->q; hd.nsets = h->nsets; hd.storage = h->storage;
   hd.nx = h->nx; hd.ny = h->ny; hd.nz = h->nz; hd.px = h->px;
   for (int b = 0; b < 3; ++b) { hd.wall[b] = h->bc.wall[b]; hd.lid_u[b] = h->bc.lid_u[b]; }
   hd.lid = h->bc.lid;
   hd.forcing = h->forcing;
+  hd.layout = h->inplace ? 1 + h->parity : 0;
   hd.s0 = h->s0; hd.s1 = h->s1; hd.s2 = h->s2;
   hd.step = h->step;
   hd.payload = (int64_t)(h->pop_bytes() + h->mom_bytes());
@@ -620,6 +644,7 @@ mdf_status mdf_load(mdf_t h, const char *path) {
   if (ok) {
     want.step = hd.step;
     want.checksum = hd.checksum;
+    if (h->inplace && (hd.layout == 1 || hd.layout == 2)) want.layout = hd.layout;
     ok = std::memcmp(&hd, &want, sizeof hd) == 0;
   }
   if (!ok) { std::fclose(fp); return fail(h, MDF_EIO, "load: header of %s does not match this handle", path); }
@@ -634,6 +659,7 @@ mdf_status mdf_load(mdf_t h, const char *path) {
                           cudaMemcpyHostToDevice, h->stream));
   CU(h, cudaStreamSynchronize(h->stream));
   h->step = hd.step;
+  if (h->inplace) h->parity = hd.layout - 1;
   h->have_prev = false;
   return MDF_OK;
 }
@@ -654,6 +680,8 @@ mdf_status mdf_info(mdf_t h, mdf_info_t *out) {
 
 mdf_status mdf_autotune(mdf_t h, int reps, int *vx_out, int *block_out) {
   if (check_handle(h)) return MDF_EINVAL;
+  if (h->inplace)  // its trial updates run out of place, and there is one buffer
+    return fail(h, MDF_EUNSUPPORTED, "autotune needs the two-buffer layout");
   if (reps < 1) reps = 10;
   // Candidates: one node per thread, and every vector width built for the
   // storage type that divides nx; 64, 128 and 256 threads per block.

@@ -14,6 +14,7 @@ struct DevArgs {
   const uint8_t *mask;           // link mask [plane] or null (periodic)
   const void *force;             // [d][plane] body force (compute type) or null
   int scheme2;                   // 1: Scheme II forcing (Eq. 2-3c, 2-7a) with a force set
+  int aa;                        // 0: two buffers, pull; in-place AA pattern: 1 even, 2 odd phase
   const void *min;               // moments [K][plane] read (equilibrium-shifted storage)
   void *mout;                    // moments written
   int nx, ny, nz, px;            // grid and padded x pitch

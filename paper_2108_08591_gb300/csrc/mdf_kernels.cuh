@@ -636,13 +636,22 @@ __device__ __forceinline__ TC geq(const DevArgs &A, long long N, long long n, in
   return geq_v<L, TC>(alpha, i, u, Pp);
 }
 
+// v rounded to the storage type and back (exact for FP32 and FP64).
+template <class TS> __device__ __forceinline__ typename ComputeOf<TS>::T round_to(typename ComputeOf<TS>::T v) {
+  if constexpr (std::is_same<TS, __half>::value) return __half2float(__float2half_rn(v));
+  else if constexpr (std::is_same<TS, __nv_bfloat16>::value) return __bfloat162float(__float2bfloat16_rn(v));
+  else return v;
+}
+
 // Initial state f = f^eq(P, u) written in pull form, pushed from each node:
 // the population arriving at x along c_i is stored where the first update
 // pulls it from, at x - c_i, or, when that link comes through a wall, in the
 // slot of the opposite direction at x, whose bounce-back returns it.  Every
 // slot is written once, and a node reads only its own seed.  With a seed
 // gradient the population is f^eq + f^ne (fne_at); under Scheme II it is
-// fbar = f - w_i Fbar_alpha / 2.  The seed is rounded once per node.
+// fbar = f - w_i Fbar_alpha / 2.  The seed is rounded once per node.  For
+// the in-place AA pattern (A.aa) the state starts in the even layout, where
+// each node's slots hold its own arriving populations.
 template <class L, class TS, bool WALLS>
 __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
   using TC = typename ComputeOf<TS>::T;
@@ -668,12 +677,25 @@ __global__ void __launch_bounds__(kMaxBlock) k_init(const DevArgs A) {
       const bool wall = WALLS && moving<L>(i) && ((m >> o) & 1);  // arrives through a wall
       TC v;
       long long dst;
-      if (wall) {  // stored in slot o at x, negated by the bounce-back
+      const bool lid = WALLS && wall && alpha >= 1 && o == L::UP && (m & 0x80u);
+      if (A.aa && !lid) {  // in-place AA, even layout: slot i of x holds the arriving f_i(x)
+        v = geq_v<L, TC>(alpha, i, u, Pp);
+        if (A.Gin) v += narrow_to<TC>(fne_at<L>(A, N, n, alpha, i));
+        if (A.scheme2 && alpha >= 1) v = v - TC(0.5 * L::w(i)) * Fa;
+        dst = ((long long)a * Q + i) * A.plane + idx;
+      } else if (wall) {  // stored in slot o at x, negated by the bounce-back
         v = -geq_v<L, TC>(alpha, i, u, Pp);
         if (A.Gin) v -= narrow_to<TC>(fne_at<L>(A, N, n, alpha, i));
-        if (alpha >= 1 && o == L::UP && (m & 0x80u)) v += TC(2.0 * L::w(o) * A.lid_u[alpha - 1]);
+        if (lid) v += TC(2.0 * L::w(o) * A.lid_u[alpha - 1]);
         if (A.scheme2 && alpha >= 1) v = v + TC(0.5 * L::w(o)) * Fa;
         dst = ((long long)a * Q + o) * A.plane + idx;
+        if (A.aa) {
+          // the value the pull stream's first bounce-back delivers (the lid
+          // term does not cancel exactly in rounded arithmetic), so that
+          // both layouts start from the same state
+          v = -round_to<TS>(v) + TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+          dst = ((long long)a * Q + i) * A.plane + idx;
+        }
       } else {  // stored in slot i at x - c_i
         v = geq_v<L, TC>(alpha, i, u, Pp);
         if (A.Gin) v += narrow_to<TC>(fne_at<L>(A, N, n, alpha, i));
@@ -779,6 +801,7 @@ __global__ void k_mask(const DevArgs A, int wx, int wy, int wz, int lid, uint8_t
 }  // namespace mdf
 
 #include "mdf_eq.cuh"
+#include "mdf_aa.cuh"
 
 namespace mdf {
 
@@ -890,10 +913,11 @@ cudaError_t update_lattice(int storage, int mode, bool walls, const DevArgs &a, 
     case ST_BF16EQ:
       if constexpr (L::REST == 0) return update_eq_t<L, __nv_bfloat16>(mode, walls, a, s);
       return cudaErrorInvalidValue;
-    case ST_F32: return update_t<L, float>(mode, walls, a, s);
-    case ST_F16: return update_t<L, __half>(mode, walls, a, s);
-    case ST_BF16: return update_t<L, __nv_bfloat16>(mode, walls, a, s);
-    case ST_F64: return update_t<L, double>(mode, walls, a, s);
+    case ST_F32: return a.aa ? update_aa_t<L, float>(mode, walls, a, s) : update_t<L, float>(mode, walls, a, s);
+    case ST_F16: return a.aa ? update_aa_t<L, __half>(mode, walls, a, s) : update_t<L, __half>(mode, walls, a, s);
+    case ST_BF16:
+      return a.aa ? update_aa_t<L, __nv_bfloat16>(mode, walls, a, s) : update_t<L, __nv_bfloat16>(mode, walls, a, s);
+    case ST_F64: return a.aa ? update_aa_t<L, double>(mode, walls, a, s) : update_t<L, double>(mode, walls, a, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -964,10 +988,11 @@ cudaError_t reduce_lattice(int storage, bool walls, int kind, const DevArgs &a, 
     case ST_BF16EQ:
       if constexpr (L::REST == 0) return reduce_eq_t<L, __nv_bfloat16>(walls, kind, a, s);
       return cudaErrorInvalidValue;
-    case ST_F32: return reduce_t<L, float>(walls, kind, a, s);
-    case ST_F16: return reduce_t<L, __half>(walls, kind, a, s);
-    case ST_BF16: return reduce_t<L, __nv_bfloat16>(walls, kind, a, s);
-    case ST_F64: return reduce_t<L, double>(walls, kind, a, s);
+    case ST_F32: return a.aa ? reduce_aa_t<L, float>(walls, kind, a, s) : reduce_t<L, float>(walls, kind, a, s);
+    case ST_F16: return a.aa ? reduce_aa_t<L, __half>(walls, kind, a, s) : reduce_t<L, __half>(walls, kind, a, s);
+    case ST_BF16:
+      return a.aa ? reduce_aa_t<L, __nv_bfloat16>(walls, kind, a, s) : reduce_t<L, __nv_bfloat16>(walls, kind, a, s);
+    case ST_F64: return a.aa ? reduce_aa_t<L, double>(walls, kind, a, s) : reduce_t<L, double>(walls, kind, a, s);
   }
   return cudaErrorInvalidValue;
 }

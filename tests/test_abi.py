@@ -113,3 +113,8 @@ def test_lattice_choice_is_checked_without_a_gpu(lib):
         o = _lib.Opts(_lib.STORAGE[storage], 1, None, 0, 0, q)
         assert lib.mdf_create(ctypes.byref(h), ctypes.byref(g), d, ctypes.byref(r), None,
                               ctypes.byref(o)) == _lib.EUNSUPPORTED, (d, q, storage)
+    # the in-place AA pattern takes the rest-shifted storage types only
+    for storage in ("f16eq", "bf16eq"):
+        o = _lib.Opts(_lib.STORAGE[storage], 1, None, 0, 0, 0, 1)
+        assert lib.mdf_create(ctypes.byref(h), ctypes.byref(g2), 2, ctypes.byref(r), None,
+                              ctypes.byref(o)) == _lib.EUNSUPPORTED, storage

@@ -412,6 +412,124 @@ def test_rest_free_lattice_rejections():
 
 
 # --------------------------------------------------------------------------
+# In-place AA pattern (one population buffer)
+# --------------------------------------------------------------------------
+def _run_pattern(shape, storage, inplace, steps_list, kw, q=0, forcing="eq3-21", F=None, G=None):
+    """Fields after each entry of steps_list, the fused-epilogue fields of
+    the last update and the sums, from one lattice."""
+    from paper_2108_08591_gb300 import Lattice
+    P, u = synth.smooth_fields(shape, seed=31, amp=0.01)
+    lat = Lattice(shape, s1=1.35, storage=storage, q=q, inplace=inplace, **kw)
+    out = []
+    try:
+        lat.set_forcing(forcing)
+        if F is not None:
+            lat.set_force(F)
+        lat.init(P, u, G)
+        for n in steps_list:
+            lat.step(n)
+            out.append(lat.fields_host(("P", "u", "G", "omega") + (("rho",) if lat.with_rho else ())))
+        fl = lat.alloc_fields(("P", "u", "S"))
+        lat.step_fields(3, fl)
+        out.append({k: t.cpu().numpy() for k, t in fl.items()})
+        out.append({"sums": lat.sums()})
+    finally:
+        lat.close()
+    return out
+
+
+@pytest.mark.parametrize("storage", ["f32", "f64", "f16", "bf16"])
+@pytest.mark.parametrize("case", ["2d_periodic", "2d_walls_lid", "3d_walls", "2d_q4_walls", "3d_q6_periodic"])
+def test_inplace_aa_is_bitwise_the_pull_stream(storage, case):
+    """The AA pattern moves the same values through one buffer: fields after
+    odd and even step counts, a fused-epilogue update and the sums equal
+    the two-buffer pull stream's bit for bit.  (With 16-bit storage and a
+    moving lid the AA pattern stores the bounced value with its lid term
+    and rounds once more; that case is compared against the oracle
+    instead.)"""
+    d = 3 if case.startswith("3d") else 2
+    q = 4 if "q4" in case else 6 if "q6" in case else 0
+    shape = (45, 37) if d == 2 else (24, 18, 14)
+    kw = {}
+    if "walls_lid" in case:
+        kw = dict(wall=(1, 1, 0), lid=True, lid_u=(0.02, 0.0, 0.0))
+    elif "walls" in case:
+        kw = dict(wall=(1, 1, 0)) if d == 2 else dict(wall=(1, 0, 1))
+    steps = [1, 2, 7, 10]
+    if storage in ("f16", "bf16") and kw.get("lid"):
+        ref = run_oracle(shape, *synth.smooth_fields(shape, seed=31, amp=0.01), sum(steps), 1.35, **kw)
+        got = _run_pattern(shape, storage, True, steps, kw)[len(steps) - 1]
+        e = errors(ref, got)
+        tu, tp, tg = _tol(storage)
+        assert e["u"] < tu and e["P"] < tp, e
+        return
+    a = _run_pattern(shape, storage, False, steps, kw, q=q)
+    b = _run_pattern(shape, storage, True, steps, kw, q=q)
+    for ra, rb in zip(a, b):
+        for k in ra:
+            assert np.array_equal(ra[k], rb[k]), (k, np.abs(ra[k] - rb[k]).max())
+
+
+def test_inplace_aa_with_force_scheme2_and_seed():
+    """Force, Scheme II and a non-equilibrium start through the AA pattern."""
+    shape = (45, 37)
+    F = _scheme2_force(shape, 2e-5)
+    G = _seed_gradient(shape, 11)
+    kw = dict(wall=(0, 1, 0))
+    a = _run_pattern(shape, "f32", False, [3, 4], kw, forcing="scheme2", F=F, G=G)
+    b = _run_pattern(shape, "f32", True, [3, 4], kw, forcing="scheme2", F=F, G=G)
+    for ra, rb in zip(a, b):
+        for k in ra:
+            assert np.array_equal(ra[k], rb[k]), k
+
+
+def test_inplace_aa_checkpoint_keeps_the_parity(tmp_path):
+    """A checkpoint taken in the odd layout resumes bit for bit; a
+    two-buffer handle refuses it."""
+    from paper_2108_08591_gb300 import Lattice, MdfError
+    shape = (64, 33)
+    P, u = synth.smooth_fields(shape, seed=5)
+    path = str(tmp_path / "aa.ckpt")
+    a = Lattice(shape, s1=1.3, inplace=True)
+    a.init(P, u)
+    a.step(5)  # odd layout
+    a.save(path)
+    a.step(6)
+    want = a.fields_host(("P", "u", "G"))
+    b = Lattice(shape, s1=1.3, inplace=True)
+    b.load(path)
+    b.step(6)
+    got = b.fields_host(("P", "u", "G"))
+    for k in want:
+        assert np.array_equal(want[k], got[k]), k
+    c = Lattice(shape, s1=1.3)
+    with pytest.raises(MdfError):
+        c.load(path)
+    with pytest.raises(MdfError):
+        a.autotune(reps=1)
+    for lat in (a, b, c):
+        lat.close()
+
+
+def test_inplace_aa_halves_the_population_memory():
+    """One buffer: the device memory a handle takes drops by one population
+    buffer (2048^2 D2Q5 x 3 FP32: 252 MB per buffer)."""
+    import torch
+    from paper_2108_08591_gb300 import Lattice
+    shape = (2048, 2048)
+    used = {}
+    for inplace in (False, True):
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        lat = Lattice(shape, s1=1.3, inplace=inplace)
+        torch.cuda.synchronize()
+        used[inplace] = free0 - torch.cuda.mem_get_info()[0]
+        lat.close()
+    buf = 2048 * 2048 * 15 * 4
+    assert abs((used[False] - used[True]) - buf) < 0.05 * buf, used
+
+
+# --------------------------------------------------------------------------
 # Fused epilogue, reductions, checkpoints, edges
 # --------------------------------------------------------------------------
 def test_fused_fields_equal_separate_pass():
