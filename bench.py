@@ -452,7 +452,8 @@ def run_mdf(args):
     tname = {"f32": "float", "f16": "__half", "bf16": "__nv_bfloat16", "f16eq": "__half",
              "bf16eq": "__nv_bfloat16"}[args.storage]
     if args.inplace:
-        kernel = f"k_update_aa<{kname},{tname},even+odd,MODE_STEP,periodic>"
+        kernel = (f"k_update_aa_vec<{kname},{tname},VX={info.vx},even+odd,periodic>" if info.vx > 1
+                  else f"k_update_aa<{kname},{tname},even+odd,MODE_STEP,periodic>")
     elif args.storage.endswith("eq"):
         kernel = f"k_update_eq<{kname},{tname},VX={info.vx},MODE_STEP,periodic>"
     elif info.vx > 1:

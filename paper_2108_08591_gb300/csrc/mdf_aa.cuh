@@ -24,6 +24,8 @@
 // read-only cache path and no restrict qualifiers: the locations alias).
 #pragma once
 
+#include <type_traits>
+
 namespace mdf {
 
 template <class T> struct CodecRW;
@@ -133,6 +135,247 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_aa(const DevArgs A) {
   if (A.with_rho) aa_write_set<L, TS, ODD, WALLS>(A, f, 0, x, y, z, idx, m, h);
 }
 
+// ---------------------------------------------------------------------------
+// Vector AA update: VX consecutive x-nodes per thread (plain updates).  The
+// even phase touches the thread's own VX nodes only, with one vector access
+// per slot.  The odd phase pulls and pushes along x: a slot's VX values
+// shift by one node, the end value crossing to the neighbouring lane by a
+// warp shuffle; at a warp or row edge that value is loaded or stored with
+// one scalar access by the thread owning the node, so every location is
+// still read and written by one thread only.  A wall link (only the row's
+// end nodes along x; whole rows along y and z) takes the per-node path.
+// ---------------------------------------------------------------------------
+template <class TS, int VX> struct VecRW;  // coherent vector loads (the buffer is written too)
+template <int VX> struct VecRW<float, VX> {
+  static __device__ __forceinline__ void load(const float *p, float (&v)[VX]) {
+    if constexpr (VX == 4) {
+      const float4 t = *reinterpret_cast<const float4 *>(p);
+      v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else {
+      static_assert(VX == 2, "FP32 vectors of 2 or 4");
+      const float2 t = *reinterpret_cast<const float2 *>(p);
+      v[0] = t.x; v[1] = t.y;
+    }
+  }
+};
+template <> struct VecRW<double, 2> {
+  static __device__ __forceinline__ void load(const double *p, double (&v)[2]) {
+    const double2 t = *reinterpret_cast<const double2 *>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+};
+template <class T16, int VX> struct VecRW16 {
+  static_assert(VX == 4 || VX == 8, "16-bit vectors of 4 or 8");
+  using Raw = typename std::conditional<VX == 4, uint2, uint4>::type;
+  static __device__ __forceinline__ void load(const T16 *p, float (&v)[VX]) {
+    const Raw r = *reinterpret_cast<const Raw *>(p);
+    const unsigned *w = reinterpret_cast<const unsigned *>(&r);
+#pragma unroll
+    for (int k = 0; k < VX / 2; ++k) {
+      const float2 f = word_to_f2<T16>(w[k]);
+      v[2 * k] = f.x;
+      v[2 * k + 1] = f.y;
+    }
+  }
+};
+template <int VX> struct VecRW<__half, VX> : VecRW16<__half, VX> {};
+template <int VX> struct VecRW<__nv_bfloat16, VX> : VecRW16<__nv_bfloat16, VX> {};
+
+template <class L, class TS, int VX, bool ODD, bool WALLS>
+__device__ __forceinline__ void aa_read_vec(const DevArgs &A, const TS *base, int alpha, const VecRows &R,
+                                            const uint8_t (&m)[VX],
+                                            typename ComputeOf<TS>::T (&v)[L::Q][VX]) {
+  using TC = typename ComputeOf<TS>::T;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    if (!ODD) {
+      VecRW<TS, VX>::load(base + (long long)i * A.plane + R.row0 + R.x0, v[i]);
+      continue;
+    }
+    const TS *p = base + (long long)L::opp(i) * A.plane;
+    if (L::c(i, 0) == 1) {  // from x - 1
+      TC own[VX];
+      VecRW<TS, VX>::load(p + R.row0 + R.x0, own);
+      TC pv = __shfl_up_sync(0xffffffffu, own[VX - 1], 1);
+      if (R.ledge) pv = CodecRW<TS>::load(p + R.row0 + R.xl);
+      v[i][0] = pv;
+#pragma unroll
+      for (int j = 1; j < VX; ++j) v[i][j] = own[j - 1];
+    } else if (L::c(i, 0) == -1) {  // from x + 1
+      TC own[VX];
+      VecRW<TS, VX>::load(p + R.row0 + R.x0, own);
+      TC nv = __shfl_down_sync(0xffffffffu, own[0], 1);
+      if (R.redge) nv = CodecRW<TS>::load(p + R.row0 + R.xr);
+#pragma unroll
+      for (int j = 0; j < VX - 1; ++j) v[i][j] = own[j + 1];
+      v[i][VX - 1] = nv;
+    } else {
+      const int r = L::c(i, 1) == 1 ? R.row_ym : L::c(i, 1) == -1 ? R.row_yp
+                  : L::c(i, 2) == 1 ? R.row_zm : L::c(i, 2) == -1 ? R.row_zp : R.row0;
+      VecRW<TS, VX>::load(p + r + R.x0, v[i]);
+    }
+  }
+  if (ODD && WALLS) {  // arrived through a wall: minus the node's own leaving value
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+#pragma unroll
+      for (int j = 0; j < VX; ++j)
+        if (moving<L>(i) && ((m[j] >> L::opp(i)) & 1)) {
+          TC w = -TC(CodecRW<TS>::load(base + (long long)i * A.plane + R.row0 + R.x0 + j));
+          if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u)) w += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+          v[i][j] = w;
+        }
+  }
+}
+
+// Every lane runs the shuffles; a lane past the row end (`active` false)
+// stores nothing.
+template <class L, class TS, int VX, bool ODD, bool WALLS>
+__device__ __forceinline__ void aa_write_vec(const DevArgs &A, TS *base, int alpha, const VecRows &R,
+                                             const uint8_t (&m)[VX], bool active,
+                                             const typename ComputeOf<TS>::T (&v)[L::Q][VX]) {
+  using TC = typename ComputeOf<TS>::T;
+#pragma unroll
+  for (int i = 0; i < L::Q; ++i) {
+    if (!ODD) {
+      if (active) VecIO<TS, VX>::store(base + (long long)L::opp(i) * A.plane + R.row0 + R.x0, v[i]);
+      continue;
+    }
+    TS *p = base + (long long)i * A.plane;
+    // nodes whose link along c_i leaves through a wall: bounced into slot opp(i)
+    bool any_wall = false;
+    if (WALLS && moving<L>(i))
+#pragma unroll
+      for (int j = 0; j < VX; ++j) any_wall |= ((m[j] >> i) & 1) != 0;
+    auto bounce = [&](int j) {
+      TC w = -v[i][j];
+      if (alpha >= 1 && i == L::UP && (m[j] & 0x80u)) w += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+      Codec<TS>::store(base + (long long)L::opp(i) * A.plane + R.row0 + R.x0 + j, w);
+    };
+    if (L::c(i, 0) == 1) {  // to x + 1: position x0 + j holds node x0 + j - 1
+      TC out[VX];
+      out[0] = __shfl_up_sync(0xffffffffu, v[i][VX - 1], 1);
+#pragma unroll
+      for (int j = 1; j < VX; ++j) out[j] = v[i][j - 1];
+      if (!active) continue;
+      if (!R.ledge) {
+        VecIO<TS, VX>::store(p + R.row0 + R.x0, out);
+      } else {
+#pragma unroll
+        for (int j = 1; j < VX; ++j) Codec<TS>::store(p + R.row0 + R.x0 + j, out[j]);
+      }
+      if (R.redge) {  // node x0 + VX - 1 feeds the next thread's first position
+        if (any_wall && ((m[VX - 1] >> i) & 1)) bounce(VX - 1);
+        else Codec<TS>::store(p + R.row0 + R.xr, v[i][VX - 1]);
+      }
+    } else if (L::c(i, 0) == -1) {  // to x - 1: position x0 + j holds node x0 + j + 1
+      TC out[VX];
+#pragma unroll
+      for (int j = 0; j < VX - 1; ++j) out[j] = v[i][j + 1];
+      out[VX - 1] = __shfl_down_sync(0xffffffffu, v[i][0], 1);
+      if (!active) continue;
+      if (!R.redge) {
+        VecIO<TS, VX>::store(p + R.row0 + R.x0, out);
+      } else {
+#pragma unroll
+        for (int j = 0; j < VX - 1; ++j) Codec<TS>::store(p + R.row0 + R.x0 + j, out[j]);
+      }
+      if (R.ledge) {  // node x0 feeds the previous thread's last position
+        if (any_wall && ((m[0] >> i) & 1)) bounce(0);
+        else Codec<TS>::store(p + R.row0 + R.xl, v[i][0]);
+      }
+    } else {
+      if (!active) continue;
+      const int r = L::c(i, 1) == 1 ? R.row_yp : L::c(i, 1) == -1 ? R.row_ym
+                  : L::c(i, 2) == 1 ? R.row_zp : L::c(i, 2) == -1 ? R.row_zm : R.row0;
+      if (!any_wall) {
+        VecIO<TS, VX>::store(p + r + R.x0, v[i]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < VX; ++j) {
+          if ((m[j] >> i) & 1) bounce(j);
+          else Codec<TS>::store(p + r + R.x0 + j, v[i][j]);
+        }
+      }
+    }
+  }
+}
+
+template <class L, class TS, int VX, bool ODD, bool WALLS, bool S2>
+__global__ void __launch_bounds__(kMaxBlock) k_update_aa_vec(const DevArgs A) {
+  using TC = typename ComputeOf<TS>::T;
+  constexpr int D = L::D, Q = L::Q;
+  const int lane = threadIdx.x & 31;
+  int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
+  const bool active = x0 < A.nx;
+  if (!active) x0 = A.nx - VX;  // stays in the shuffles, stores nothing
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int row0 = (z * A.ny + y) * A.px;
+  const int row_ym = (z * A.ny + wrap(y - 1, A.ny)) * A.px;
+  const int row_yp = (z * A.ny + wrap(y + 1, A.ny)) * A.px;
+  const int row_zm = D == 3 ? (wrap(z - 1, A.nz) * A.ny + y) * A.px : row0;
+  const int row_zp = D == 3 ? (wrap(z + 1, A.nz) * A.ny + y) * A.px : row0;
+  const bool ledge = lane == 0 || x0 == 0;
+  const bool redge = lane == 31 || x0 + VX >= A.nx;
+  const int xl = x0 == 0 ? A.nx - 1 : x0 - 1;
+  const int xr = x0 + VX >= A.nx ? 0 : x0 + VX;
+  TS *f = static_cast<TS *>(A.fout);  // == A.fin
+  const int a1 = A.with_rho;
+  uint8_t m[VX];
+#pragma unroll
+  for (int j = 0; j < VX; ++j) m[j] = WALLS ? A.mask[row0 + x0 + j] : uint8_t(0);
+
+  const VecRows R{row0, row_ym, row_yp, row_zm, row_zp, x0, xl, xr, ledge, redge};
+  TC g[D][Q][VX], h[Q][VX];
+#pragma unroll
+  for (int al = 1; al <= D; ++al)
+    aa_read_vec<L, TS, VX, ODD, WALLS>(A, f + (long long)(a1 + al - 1) * Q * A.plane, al, R, m, g[al - 1]);
+  if (A.with_rho) {
+    aa_read_vec<L, TS, VX, ODD, WALLS>(A, f, 0, R, m, h);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+      for (int j = 0; j < VX; ++j) h[i][j] = TC(0);
+  }
+
+  TC F[D][VX];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (A.force) {
+      VecIO<TC, VX>::load(static_cast<const TC *>(A.force) + a * A.plane + row0 + x0, F[a]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < VX; ++j) F[a][j] = TC(0);
+    }
+  }
+  const TC s1 = TC(A.s1), s2 = TC(A.s2);
+#pragma unroll
+  for (int j = 0; j < VX; ++j) {
+    TC gn[D][Q], hn[Q], Fn[D];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) gn[a][i] = g[a][i][j];
+      hn[i] = h[i][j];
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a) Fn[a] = F[a][j];
+    TC M[D + 2];
+    collide_node<L, TC, S2>(gn, hn, A.with_rho != 0, Fn, s1, s2, M);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+#pragma unroll
+      for (int a = 0; a < D; ++a) g[a][i][j] = gn[a][i];
+      h[i][j] = hn[i];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a)
+    aa_write_vec<L, TS, VX, ODD, WALLS>(A, f + (long long)(a1 + a) * Q * A.plane, a + 1, R, m, active, g[a]);
+  if (A.with_rho) aa_write_vec<L, TS, VX, ODD, WALLS>(A, f, 0, R, m, active, h);
+}
+
 // FP64 sums and residual over the in-place buffer (see k_reduce).
 template <class L, class TS, bool ODD, bool WALLS, int KIND>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce_aa(const DevArgs A) {
@@ -195,8 +438,44 @@ cudaError_t update_aa_phase(int mode, bool walls, const DevArgs &a, cudaStream_t
   return cudaGetLastError();
 }
 
+template <class L, class TS, int VX, bool ODD>
+cudaError_t update_aa_vec_phase(bool walls, const DevArgs &a, cudaStream_t s) {
+  const int bx = a.block;
+  const int threads = a.nx / VX;
+  const dim3 grid((unsigned)((threads + bx - 1) / bx), (unsigned)a.ny, (unsigned)a.nz), block(bx);
+  if (a.scheme2) {
+    if (walls) k_update_aa_vec<L, TS, VX, ODD, true, true><<<grid, block, 0, s>>>(a);
+    else k_update_aa_vec<L, TS, VX, ODD, false, true><<<grid, block, 0, s>>>(a);
+  } else {
+    if (walls) k_update_aa_vec<L, TS, VX, ODD, true, false><<<grid, block, 0, s>>>(a);
+    else k_update_aa_vec<L, TS, VX, ODD, false, false><<<grid, block, 0, s>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <class L, class TS, int VX>
+cudaError_t update_aa_vec(bool walls, const DevArgs &a, cudaStream_t s) {
+  return a.aa == 2 ? update_aa_vec_phase<L, TS, VX, true>(walls, a, s)
+                   : update_aa_vec_phase<L, TS, VX, false>(walls, a, s);
+}
+
+// Plain updates with a width built for the storage type that divides nx
+// run the vector kernel (FP32 2 or 4, 16-bit 4 or 8, FP64 2); everything
+// else, and every field-writing update, runs one node per thread.
 template <class L, class TS>
 cudaError_t update_aa_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
+  const bool ok = mode == MODE_STEP && a.vx > 1 && a.nx % a.vx == 0 && a.plane < (1LL << 31) - 64;
+  if (ok) {
+    if constexpr (sizeof(TS) == 4) {
+      if (a.vx == 4) return update_aa_vec<L, TS, 4>(walls, a, s);
+      if (a.vx == 2) return update_aa_vec<L, TS, 2>(walls, a, s);
+    } else if constexpr (sizeof(TS) == 2) {
+      if (a.vx == 8) return update_aa_vec<L, TS, 8>(walls, a, s);
+      if (a.vx == 4) return update_aa_vec<L, TS, 4>(walls, a, s);
+    } else {
+      if (a.vx == 2) return update_aa_vec<L, TS, 2>(walls, a, s);
+    }
+  }
   return a.aa == 2 ? update_aa_phase<L, TS, true>(mode, walls, a, s)
                    : update_aa_phase<L, TS, false>(mode, walls, a, s);
 }

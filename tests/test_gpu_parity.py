@@ -414,12 +414,12 @@ def test_rest_free_lattice_rejections():
 # --------------------------------------------------------------------------
 # In-place AA pattern (one population buffer)
 # --------------------------------------------------------------------------
-def _run_pattern(shape, storage, inplace, steps_list, kw, q=0, forcing="eq3-21", F=None, G=None):
+def _run_pattern(shape, storage, inplace, steps_list, kw, q=0, forcing="eq3-21", F=None, G=None, vx=0):
     """Fields after each entry of steps_list, the fused-epilogue fields of
     the last update and the sums, from one lattice."""
     from paper_2108_08591_gb300 import Lattice
     P, u = synth.smooth_fields(shape, seed=31, amp=0.01)
-    lat = Lattice(shape, s1=1.35, storage=storage, q=q, inplace=inplace, **kw)
+    lat = Lattice(shape, s1=1.35, storage=storage, q=q, inplace=inplace, vx=vx, block=64, **kw)
     out = []
     try:
         lat.set_forcing(forcing)
@@ -465,6 +465,26 @@ def test_inplace_aa_is_bitwise_the_pull_stream(storage, case):
         return
     a = _run_pattern(shape, storage, False, steps, kw, q=q)
     b = _run_pattern(shape, storage, True, steps, kw, q=q)
+    for ra, rb in zip(a, b):
+        for k in ra:
+            assert np.array_equal(ra[k], rb[k]), (k, np.abs(ra[k] - rb[k]).max())
+
+
+@pytest.mark.parametrize("d,storage,vx", [
+    (2, "f32", 4), (2, "f32", 2), (2, "f16", 8), (2, "bf16", 4), (2, "f64", 2),
+    (3, "f32", 4), (3, "f16", 8), (3, "bf16", 4), (3, "f64", 2),
+])
+@pytest.mark.parametrize("walls", [False, True])
+def test_inplace_aa_vector_kernel_is_bitwise_the_pull_stream(d, storage, vx, walls):
+    """The vector AA kernel (shuffled x-neighbours, scalar accesses at warp
+    and row edges, per-node wall links) against the one-node-per-thread pull
+    stream: x extents of several warps with a partial last block (264 = 33 x
+    8), odd and even step counts, walls on every axis."""
+    shape = (264, 9) if d == 2 else (264, 5, 4)
+    kw = dict(wall=(1, 1, 1)[:d] + (0,) * (3 - d)) if walls else {}
+    steps = [1, 2, 5, 6]
+    a = _run_pattern(shape, storage, False, steps, kw, vx=1)
+    b = _run_pattern(shape, storage, True, steps, kw, vx=vx)
     for ra, rb in zip(a, b):
         for k in ra:
             assert np.array_equal(ra[k], rb[k]), (k, np.abs(ra[k] - rb[k]).max())
