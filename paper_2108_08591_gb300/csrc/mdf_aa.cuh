@@ -181,50 +181,131 @@ template <class T16, int VX> struct VecRW16 {
 template <int VX> struct VecRW<__half, VX> : VecRW16<__half, VX> {};
 template <int VX> struct VecRW<__nv_bfloat16, VX> : VecRW16<__nv_bfloat16, VX> {};
 
+// Source row of the pull along c_i (the node's own row for x and the rest).
+template <class L>
+__device__ __forceinline__ int source_row(const VecRows &R, int i) {
+  return L::c(i, 1) == 1 ? R.row_ym : L::c(i, 1) == -1 ? R.row_yp
+       : L::c(i, 2) == 1 ? R.row_zm : L::c(i, 2) == -1 ? R.row_zp : R.row0;
+}
+
+// The VX nodes' arriving populations of every set, in the layout of the
+// phase: every load of the thread is issued first (the odd phase's x-shifted
+// values then cross lanes by shuffles), as in the pull kernels.  g: the d
+// velocity sets, h: the continuity set (zero without it).
 template <class L, class TS, int VX, bool ODD, bool WALLS>
-__device__ __forceinline__ void aa_read_vec(const DevArgs &A, const TS *base, int alpha, const VecRows &R,
-                                            const uint8_t (&m)[VX],
-                                            typename ComputeOf<TS>::T (&v)[L::Q][VX]) {
+__device__ __forceinline__ void aa_read_all_vec(const DevArgs &A, const TS *f, const VecRows &R,
+                                                const uint8_t (&m)[VX],
+                                                typename ComputeOf<TS>::T (&g)[L::D][L::Q][VX],
+                                                typename ComputeOf<TS>::T (&h)[L::Q][VX]) {
   using TC = typename ComputeOf<TS>::T;
+  constexpr int D = L::D, Q = L::Q;
+  const int a1 = A.with_rho;
+  auto set_base = [&](int s) { return f + (long long)(s < D ? a1 + s : 0) * Q * A.plane; };
+  if constexpr (sizeof(TS) == 2) {
+    using PK = Packed16<TS, VX>;
+    using W = typename PK::W;
+    W wv[D + 1][Q];
+    unsigned edge[D + 1][2];
 #pragma unroll
-  for (int i = 0; i < L::Q; ++i) {
-    if (!ODD) {
-      VecRW<TS, VX>::load(base + (long long)i * A.plane + R.row0 + R.x0, v[i]);
-      continue;
+    for (int s = 0; s <= D; ++s) {
+      if (s == D && !A.with_rho) break;
+      const TS *base = set_base(s);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const TS *p = base + (long long)(ODD ? L::opp(i) : i) * A.plane;
+        wv[s][i] = *reinterpret_cast<const W *>(p + (ODD ? source_row<L>(R, i) : R.row0) + R.x0);
+        if (ODD && L::c(i, 0) == 1)
+          edge[s][0] = R.ledge ? *reinterpret_cast<const unsigned short *>(p + R.row0 + R.xl) : 0u;
+        if (ODD && L::c(i, 0) == -1)
+          edge[s][1] = R.redge ? *reinterpret_cast<const unsigned short *>(p + R.row0 + R.xr) : 0u;
+      }
     }
-    const TS *p = base + (long long)L::opp(i) * A.plane;
-    if (L::c(i, 0) == 1) {  // from x - 1
-      TC own[VX];
-      VecRW<TS, VX>::load(p + R.row0 + R.x0, own);
-      TC pv = __shfl_up_sync(0xffffffffu, own[VX - 1], 1);
-      if (R.ledge) pv = CodecRW<TS>::load(p + R.row0 + R.xl);
-      v[i][0] = pv;
 #pragma unroll
-      for (int j = 1; j < VX; ++j) v[i][j] = own[j - 1];
-    } else if (L::c(i, 0) == -1) {  // from x + 1
-      TC own[VX];
-      VecRW<TS, VX>::load(p + R.row0 + R.x0, own);
-      TC nv = __shfl_down_sync(0xffffffffu, own[0], 1);
-      if (R.redge) nv = CodecRW<TS>::load(p + R.row0 + R.xr);
+    for (int s = 0; s <= D; ++s) {
+      if (s == D && !A.with_rho) break;
+      float(&v)[Q][VX] = s < D ? g[s < D ? s : 0] : h;
 #pragma unroll
-      for (int j = 0; j < VX - 1; ++j) v[i][j] = own[j + 1];
-      v[i][VX - 1] = nv;
-    } else {
-      const int r = L::c(i, 1) == 1 ? R.row_ym : L::c(i, 1) == -1 ? R.row_yp
-                  : L::c(i, 2) == 1 ? R.row_zm : L::c(i, 2) == -1 ? R.row_zp : R.row0;
-      VecRW<TS, VX>::load(p + r + R.x0, v[i]);
+      for (int i = 0; i < Q; ++i) {
+        const W w = wv[s][i];
+        if (ODD && L::c(i, 0) == 1) {  // from x - 1
+          unsigned nb = __shfl_up_sync(0xffffffffu, PK::last_word(w), 1);
+          nb = R.ledge ? edge[s][0] : (nb >> 16);
+          v[i][0] = bits_to_float<TS>(nb);
+#pragma unroll
+          for (int j = 1; j < VX; ++j) v[i][j] = bits_to_float<TS>(PK::bits(w, j - 1));
+        } else if (ODD && L::c(i, 0) == -1) {  // from x + 1
+          unsigned nb = __shfl_down_sync(0xffffffffu, PK::first_word(w), 1);
+          nb = R.redge ? edge[s][1] : (nb & 0xffffu);
+#pragma unroll
+          for (int j = 0; j < VX - 1; ++j) v[i][j] = bits_to_float<TS>(PK::bits(w, j + 1));
+          v[i][VX - 1] = bits_to_float<TS>(nb);
+        } else {
+#pragma unroll
+          for (int j = 0; j < VX; ++j) v[i][j] = bits_to_float<TS>(PK::bits(w, j));
+        }
+      }
+    }
+  } else {
+    TC edge[D + 1][2];
+#pragma unroll
+    for (int s = 0; s <= D; ++s) {
+      if (s == D && !A.with_rho) break;
+      const TS *base = set_base(s);
+      TC(&v)[Q][VX] = s < D ? g[s < D ? s : 0] : h;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const TS *p = base + (long long)(ODD ? L::opp(i) : i) * A.plane;
+        VecRW<TS, VX>::load(p + (ODD ? source_row<L>(R, i) : R.row0) + R.x0, v[i]);
+        if (ODD && L::c(i, 0) == 1) edge[s][0] = R.ledge ? CodecRW<TS>::load(p + R.row0 + R.xl) : TC(0);
+        if (ODD && L::c(i, 0) == -1) edge[s][1] = R.redge ? CodecRW<TS>::load(p + R.row0 + R.xr) : TC(0);
+      }
+    }
+    if (ODD) {
+#pragma unroll
+      for (int s = 0; s <= D; ++s) {
+        if (s == D && !A.with_rho) break;
+        TC(&v)[Q][VX] = s < D ? g[s < D ? s : 0] : h;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+          if (L::c(i, 0) == 1) {  // from x - 1: shift up by one node
+            TC pv = __shfl_up_sync(0xffffffffu, v[i][VX - 1], 1);
+            if (R.ledge) pv = edge[s][0];
+#pragma unroll
+            for (int j = VX - 1; j > 0; --j) v[i][j] = v[i][j - 1];
+            v[i][0] = pv;
+          } else if (L::c(i, 0) == -1) {  // from x + 1: shift down by one node
+            TC nv = __shfl_down_sync(0xffffffffu, v[i][0], 1);
+            if (R.redge) nv = edge[s][1];
+#pragma unroll
+            for (int j = 0; j < VX - 1; ++j) v[i][j] = v[i][j + 1];
+            v[i][VX - 1] = nv;
+          }
+        }
+      }
     }
   }
+  if (!A.with_rho)
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+      for (int j = 0; j < VX; ++j) h[i][j] = TC(0);
   if (ODD && WALLS) {  // arrived through a wall: minus the node's own leaving value
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i)
+    for (int s = 0; s <= D; ++s) {
+      if (s == D && !A.with_rho) break;
+      const int alpha = s < D ? s + 1 : 0;
+      const TS *base = set_base(s);
+      TC(&v)[Q][VX] = s < D ? g[s < D ? s : 0] : h;
 #pragma unroll
-      for (int j = 0; j < VX; ++j)
-        if (moving<L>(i) && ((m[j] >> L::opp(i)) & 1)) {
-          TC w = -TC(CodecRW<TS>::load(base + (long long)i * A.plane + R.row0 + R.x0 + j));
-          if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u)) w += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
-          v[i][j] = w;
-        }
+      for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int j = 0; j < VX; ++j)
+          if (moving<L>(i) && ((m[j] >> L::opp(i)) & 1)) {
+            TC w = -TC(CodecRW<TS>::load(base + (long long)i * A.plane + R.row0 + R.x0 + j));
+            if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u)) w += TC(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+            v[i][j] = w;
+          }
+    }
   }
 }
 
@@ -327,17 +408,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_aa_vec(const DevArgs A) {
 
   const VecRows R{row0, row_ym, row_yp, row_zm, row_zp, x0, xl, xr, ledge, redge};
   TC g[D][Q][VX], h[Q][VX];
-#pragma unroll
-  for (int al = 1; al <= D; ++al)
-    aa_read_vec<L, TS, VX, ODD, WALLS>(A, f + (long long)(a1 + al - 1) * Q * A.plane, al, R, m, g[al - 1]);
-  if (A.with_rho) {
-    aa_read_vec<L, TS, VX, ODD, WALLS>(A, f, 0, R, m, h);
-  } else {
-#pragma unroll
-    for (int i = 0; i < Q; ++i)
-#pragma unroll
-      for (int j = 0; j < VX; ++j) h[i][j] = TC(0);
-  }
+  aa_read_all_vec<L, TS, VX, ODD, WALLS>(A, f, R, m, g, h);
 
   TC F[D][VX];
 #pragma unroll

@@ -54,12 +54,18 @@ int default_vx(int d, int storage) {
   if (d == 3) return (storage == MDF_F16 || storage == MDF_BF16) ? 8 : 1;
   return storage == MDF_F64 ? 2 : 4;
 }
-// Nodes per thread of the in-place AA kernels (measured at 4096^2 and 512^3,
-// GB300): 2D FP32 2 (55.2 GLUPS against 50.6 with 4), 2D 16-bit 4 (77.0
-// against 59.3 with 8), 3D FP32 1 (28.0 against 26.4 with 2), 3D 16-bit 8.
+// Launch shape of the in-place AA kernels (measured at 4096^2 and 512^3 on
+// GB300): 2D FP32 4 nodes per thread (56.8 GLUPS, 56.3 with 2); 2D 16-bit
+// 4 (92.0, 76.3 with 8); 3D FP32 2 (30.1, 28.1 with 1); 3D 16-bit 4 with
+// 128 threads (39.8, 37.9 with 8 nodes and 64 threads); FP64 2.
 int default_vx_aa(int d, int storage) {
-  if (d == 3) return (storage == MDF_F16 || storage == MDF_BF16) ? 8 : 1;
-  return (storage == MDF_F16 || storage == MDF_BF16) ? 4 : 2;
+  if (storage == MDF_F64) return 2;
+  if (d == 3) return (storage == MDF_F16 || storage == MDF_BF16) ? 4 : 2;
+  return 4;
+}
+int default_block_aa(int d, int storage) {
+  if (d == 3) return (storage == MDF_F16 || storage == MDF_BF16) ? 128 : 256;
+  return 128;
 }
 int default_block(int d, int storage) {
   if (eq_storage(storage)) return d == 3 ? 128 : 64;
@@ -339,7 +345,7 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
       return fail(nullptr, MDF_EUNSUPPORTED, "equilibrium-shifted storage needs < 2^31 padded nodes");
     }
   }
-  h->block = opts.block ? opts.block : default_block(d, h->storage);
+  h->block = opts.block ? opts.block : (h->inplace ? default_block_aa(d, h->storage) : default_block(d, h->storage));
   h->vx = opts.vx ? opts.vx : (h->inplace ? default_vx_aa(d, h->storage) : default_vx(d, h->storage));
 
   const size_t pb = h->pop_bytes();
