@@ -294,6 +294,35 @@ mdf_status mdf_info(mdf_t h, mdf_info_t *out);
  */
 mdf_status mdf_autotune(mdf_t h, int reps, int *vx, int *block);
 
+/*
+ * Slab decomposition (one lattice as k sub-domains on one GPU).
+ *
+ * mdf_slabs_create -- split the grid g along its last axis (y in 2D, z in 3D)
+ * into k equal slabs, each a lattice of its own with one ghost layer on
+ * either side.  After every update, mdf_slabs_step copies device to device,
+ * per face and set, the one layer of post-collision populations that points
+ * across the face (the direction along +axis into the upper neighbour's
+ * lower ghost layer and the one along -axis into the lower neighbour's
+ * upper ghost layer).  This is the exchange that ranks holding neighbouring
+ * slabs would make.  The results equal the undivided lattice's bit for bit.
+ *   - The split axis must be periodic.  The two-buffer rest-shifted storage
+ *     types only.  All slabs use o->stream.
+ *   - Errors: MDF_EINVAL (k does not divide the axis), MDF_EUNSUPPORTED, and
+ *     those of mdf_create.
+ * mdf_slabs_init   -- f = f^eq(P, u) from global host arrays (as mdf_init).
+ * mdf_slabs_step   -- n updates with the exchange after each.
+ * mdf_slabs_fields -- the derived fields of the global lattice, host outputs
+ *                     only (out->where = MDF_HOST); synchronises.
+ */
+typedef struct mdf_slabs_s *mdf_slabs_t;
+mdf_status mdf_slabs_create(mdf_slabs_t *s, const mdf_grid *g, int d, const mdf_rates *r,
+                            const mdf_bc *bc, const mdf_opts *o, int k);
+mdf_status mdf_slabs_init(mdf_slabs_t s, const double *P, const double *u);
+mdf_status mdf_slabs_step(mdf_slabs_t s, long long n);
+mdf_status mdf_slabs_fields(mdf_slabs_t s, const mdf_fields_t *out);
+void mdf_slabs_destroy(mdf_slabs_t s);
+const char *mdf_slabs_last_error(mdf_slabs_t s);
+
 /* mdf_sync -- wait for all work enqueued on h's stream. */
 mdf_status mdf_sync(mdf_t h);
 

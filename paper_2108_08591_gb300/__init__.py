@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib
 from ._lib import DEVICE, HOST, MdfError, STORAGE
 
-__all__ = ["Lattice", "CavityBatch", "MdfError", "FIELD_NAMES", "field_shapes", "s2_rule"]
+__all__ = ["Lattice", "Slabs", "CavityBatch", "MdfError", "FIELD_NAMES", "field_shapes", "s2_rule"]
 
 FIELD_NAMES = ("P", "u", "rho", "G", "div", "S", "sigma", "omega")
 
@@ -248,6 +248,71 @@ class Lattice:
 
     def sync(self):
         self._check(self._lib.mdf_sync(self._h))
+
+
+class Slabs:
+    """One lattice split into k slabs along its last axis, with the per-face
+    exchange of the populations crossing each face after every update
+    (mdf_slabs_*).  Same arguments as Lattice; the split axis is periodic."""
+
+    def __init__(self, shape: Sequence[int], s1: float, k: int, s2: float = -1.0, s0: float = 1.0,
+                 wall: Sequence[int] = (0, 0, 0), storage: str = "f32", with_rho: bool = True,
+                 stream=None, q: int = 0):
+        import torch
+
+        self._lib = _lib.load()
+        self.d = len(shape)
+        nx, ny = int(shape[0]), int(shape[1])
+        nz = int(shape[2]) if self.d == 3 else 1
+        self.shape = tuple(int(v) for v in shape)
+        self.N = nx * ny * nz
+        self.with_rho = bool(with_rho)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        g = _lib.Grid(nx, ny, nz)
+        r = _lib.Rates(s0, s1, s2)
+        bc = _lib.BC()
+        w = list(wall) + [0] * (3 - len(wall))
+        bc.wall[:] = [int(v) for v in w[:3]]
+        o = _lib.Opts(STORAGE[storage], int(self.with_rho), ctypes.c_void_p(sptr), 0, 0, int(q), 0)
+        h = ctypes.c_void_p()
+        _lib.check_slabs(self._lib.mdf_slabs_create(ctypes.byref(h), ctypes.byref(g), self.d, ctypes.byref(r),
+                                                    ctypes.byref(bc), ctypes.byref(o), int(k)))
+        self._h = h
+
+    def _check(self, status: int):
+        _lib.check_slabs(status, self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.mdf_slabs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, P, u):
+        """f = f^eq(P, u) from host FP64 arrays P [N], u [d][N]."""
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        self._check(self._lib.mdf_slabs_init(self._h, _ptr(P), _ptr(u)))
+
+    def step(self, n: int = 1):
+        self._check(self._lib.mdf_slabs_step(self._h, int(n)))
+
+    def fields_host(self, names: Iterable[str] = ("P", "u")) -> Dict[str, np.ndarray]:
+        shapes = field_shapes(self.d, self.N)
+        out = {k: np.empty(shapes[k]) for k in names}
+        f = _lib.Fields()
+        for k, v in out.items():
+            setattr(f, k, _ptr(v))
+        f.where = HOST
+        self._check(self._lib.mdf_slabs_fields(self._h, ctypes.byref(f)))
+        return out
 
 
 class CavityBatch:

@@ -64,6 +64,13 @@ SIGNATURES = {
     "mdf_init_neq": (ctypes.c_int, [H, DP, DP, DP, ctypes.c_int]),
     "mdf_set_force": (ctypes.c_int, [H, DP, ctypes.c_int]),
     "mdf_set_forcing": (ctypes.c_int, [H, ctypes.c_int]),
+    "mdf_slabs_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_void_p, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "mdf_slabs_init": (ctypes.c_int, [H, DP, DP]),
+    "mdf_slabs_step": (ctypes.c_int, [H, ctypes.c_longlong]),
+    "mdf_slabs_fields": (ctypes.c_int, [H, ctypes.c_void_p]),
+    "mdf_slabs_destroy": (None, [H]),
+    "mdf_slabs_last_error": (ctypes.c_char_p, [H]),
     "mdf_get_forcing": (ctypes.c_int, [H, ctypes.POINTER(ctypes.c_int)]),
     "mdf_step": (ctypes.c_int, [H, ctypes.c_longlong]),
     "mdf_step_fields": (ctypes.c_int, [H, ctypes.c_longlong, ctypes.POINTER(Fields)]),
@@ -159,6 +166,12 @@ def check(status: int, handle=None):
 def check_ws(status: int, handle=None):
     if status != OK:
         msg = load().mdf_ws_last_error(handle)
+        raise MdfError(status, msg.decode() if msg else "")
+
+
+def check_slabs(status: int, handle=None):
+    if status != OK:
+        msg = load().mdf_slabs_last_error(handle)
         raise MdfError(status, msg.decode() if msg else "")
 
 

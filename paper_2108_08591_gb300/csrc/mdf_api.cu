@@ -843,3 +843,191 @@ extern "C" mdf_status mdf_fields_host_noalloc(mdf_t h, const mdf_fields_t *out) 
   CU(h, cudaStreamSynchronize(h->stream));
   return MDF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Slab decomposition: one lattice as k sub-domains along its last axis (y in
+// 2D, z in 3D), each a handle of its own with one ghost layer on either side.
+// After every update the only populations that cross a face are exchanged:
+// for each set, the post-collision values of the one direction pointing
+// across it, one layer (a row of x in 2D, an x-y plane in 3D) per face,
+// copied device to device.  The ghost layers are updated with the rest and
+// their results ignored: the next update of a real layer pulls from a ghost
+// layer only the exchanged slot.  The per-node arithmetic is the undivided
+// lattice's, so the two give the same bits.  This is the exchange a
+// multi-GPU run would make between neighbouring ranks; here all sub-domains
+// live on one GPU and share one stream.
+// ---------------------------------------------------------------------------
+struct mdf_slabs_s {
+  int d = 0, k = 0, nloc = 0;  // sub-domains and real layers per sub-domain
+  int nx = 0, ny = 0, nz = 0;  // global grid
+  std::vector<mdf_t> h;
+  cudaStream_t stream = nullptr;
+  long long step = 0;
+  std::string err = "no error";
+};
+
+namespace {
+
+std::string g_slabs_create_error = "no error";
+
+mdf_status sfail(mdf_slabs_t s, mdf_status st, const char *fmt, ...) {
+  char msg[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(msg, sizeof msg, fmt, ap);
+  va_end(ap);
+  if (s) s->err = msg;
+  else g_slabs_create_error = msg;
+  return st;
+}
+
+// Elements of one layer along the last axis, and the address of layer `l`
+// of slot i of set a in buffer `buf` of handle h.
+size_t layer_elems(const mdf_t h) { return h->d == 2 ? (size_t)h->px : (size_t)h->px * h->ny; }
+char *layer_at(const mdf_t h, void *buf, int a, int i, int l) {
+  const size_t el = storage_bytes(h->storage);
+  return static_cast<char *>(buf) +
+         (((size_t)a * h->q + i) * (size_t)h->plane + (size_t)l * layer_elems(h)) * el;
+}
+
+// Direction index of c = sg e_last for lattice (d, q).
+int axis_dir(int d, int q, int sg) {
+  if (d == 2) return q == 5 ? (sg > 0 ? 2 : 4) : (sg > 0 ? 1 : 3);
+  return q == 7 ? (sg > 0 ? 5 : 6) : (sg > 0 ? 4 : 5);
+}
+
+mdf_status exchange(mdf_slabs_t S) {
+  const int k = S->k;
+  const size_t bytes = layer_elems(S->h[0]) * storage_bytes(S->h[0]->storage);
+  const int up = axis_dir(S->d, S->h[0]->q, +1), dn = axis_dir(S->d, S->h[0]->q, -1);
+  for (int s = 0; s < k; ++s) {
+    mdf_t me = S->h[s], lo = S->h[(s + k - 1) % k], hi = S->h[(s + 1) % k];
+    for (int a = 0; a < me->nsets; ++a) {
+      // ghost layer 0 <- the lower neighbour's last real layer, moving up
+      cudaError_t e = cudaMemcpyAsync(layer_at(me, me->cur, a, up, 0), layer_at(lo, lo->cur, a, up, S->nloc),
+                                      bytes, cudaMemcpyDeviceToDevice, S->stream);
+      // ghost layer nloc + 1 <- the upper neighbour's first real layer, moving down
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(layer_at(me, me->cur, a, dn, S->nloc + 1), layer_at(hi, hi->cur, a, dn, 1), bytes,
+                            cudaMemcpyDeviceToDevice, S->stream);
+      if (e != cudaSuccess) return sfail(S, MDF_ECUDA, "slab exchange: %s", cudaGetErrorString(e));
+    }
+  }
+  return MDF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void mdf_slabs_destroy(mdf_slabs_t s) {
+  if (!s) return;
+  for (mdf_t h : s->h) mdf_destroy(h);
+  delete s;
+}
+
+mdf_status mdf_slabs_create(mdf_slabs_t *out, const mdf_grid *g, int d, const mdf_rates *r,
+                            const mdf_bc *bc, const mdf_opts *o, int k) {
+  if (!out) return sfail(nullptr, MDF_EINVAL, "null handle pointer");
+  *out = nullptr;
+  if (!g || !r) return sfail(nullptr, MDF_EINVAL, "null grid or rates");
+  if (d != 2 && d != 3) return sfail(nullptr, MDF_EINVAL, "d must be 2 or 3");
+  const int n = d == 2 ? g->ny : g->nz;
+  if (k < 1 || n % k != 0) return sfail(nullptr, MDF_EINVAL, "%d layers do not split into %d slabs", n, k);
+  if (bc && (bc->wall[d - 1] || bc->lid))
+    return sfail(nullptr, MDF_EUNSUPPORTED, "the split axis must be periodic (no walls or lid on it)");
+  if (o && (o->inplace || o->storage == MDF_F16EQ || o->storage == MDF_BF16EQ))
+    return sfail(nullptr, MDF_EUNSUPPORTED, "slabs take the two-buffer rest-shifted storage types");
+  mdf_slabs_t S = new (std::nothrow) mdf_slabs_s;
+  if (!S) return sfail(nullptr, MDF_ENOMEM, "host allocation");
+  S->d = d; S->k = k; S->nloc = n / k;
+  S->nx = g->nx; S->ny = g->ny; S->nz = g->nz;
+  S->stream = o ? static_cast<cudaStream_t>(o->stream) : nullptr;
+  mdf_grid gl = *g;
+  if (d == 2) gl.ny = S->nloc + 2;
+  else gl.nz = S->nloc + 2;
+  for (int s = 0; s < k; ++s) {
+    mdf_t h = nullptr;
+    const mdf_status st = mdf_create(&h, &gl, d, r, bc, o);
+    if (st != MDF_OK) {
+      sfail(nullptr, st, "slab %d: %s", s, mdf_last_error(nullptr));
+      mdf_slabs_destroy(S);
+      return st;
+    }
+    S->h.push_back(h);
+  }
+  *out = S;
+  return MDF_OK;
+}
+
+mdf_status mdf_slabs_init(mdf_slabs_t S, const double *P, const double *u) {
+  if (!S) return MDF_EINVAL;
+  if (!P || !u) return sfail(S, MDF_EINVAL, "init: null P or u");
+  const long long N = (long long)S->nx * S->ny * S->nz;
+  const long long L = S->d == 2 ? S->nx : (long long)S->nx * S->ny;  // nodes per layer
+  const int n = S->nloc * S->k, nl = S->nloc + 2;
+  std::vector<double> Pl((size_t)(L * nl)), ul((size_t)(L * nl * S->d));
+  for (int s = 0; s < S->k; ++s) {
+    for (int l = 0; l < nl; ++l) {  // local layer l holds global layer s nloc + l - 1 (periodic)
+      const long long gl = ((long long)s * S->nloc + l - 1 + n) % n;
+      std::memcpy(&Pl[(size_t)(l * L)], P + gl * L, sizeof(double) * (size_t)L);
+      for (int b = 0; b < S->d; ++b)
+        std::memcpy(&ul[(size_t)(b * L * nl + l * L)], u + b * N + gl * L, sizeof(double) * (size_t)L);
+    }
+    const mdf_status st = mdf_init(S->h[s], Pl.data(), ul.data(), MDF_HOST);
+    if (st != MDF_OK) return sfail(S, st, "slab %d init: %s", s, mdf_last_error(S->h[s]));
+  }
+  S->step = 0;
+  return MDF_OK;
+}
+
+mdf_status mdf_slabs_step(mdf_slabs_t S, long long n) {
+  if (!S) return MDF_EINVAL;
+  if (n < 0) return sfail(S, MDF_EINVAL, "step: n < 0");
+  for (long long t = 0; t < n; ++t) {
+    for (mdf_t h : S->h) {
+      const mdf_status st = one_update(h, MODE_STEP, nullptr);
+      if (st != MDF_OK) return sfail(S, st, "slab update: %s", h->err.c_str());
+    }
+    const mdf_status st = exchange(S);
+    if (st != MDF_OK) return st;
+    ++S->step;
+  }
+  return MDF_OK;
+}
+
+mdf_status mdf_slabs_fields(mdf_slabs_t S, const mdf_fields_t *out) {
+  if (!S) return MDF_EINVAL;
+  if (!out || out->where != MDF_HOST) return sfail(S, MDF_EINVAL, "fields: host outputs only");
+  const int d = S->d;
+  const long long N = (long long)S->nx * S->ny * S->nz;
+  const long long L = d == 2 ? S->nx : (long long)S->nx * S->ny;
+  const long long Nl = L * (S->nloc + 2);
+  const int nsymm = d == 2 ? 3 : 6;
+  double *const dst[8] = {out->P, out->u, out->rho, out->G, out->div, out->S, out->sigma, out->omega};
+  const int comps[8] = {1, d, 1, d * d, 1, nsymm, nsymm, d == 2 ? 1 : 3};
+  std::vector<double> loc[8];
+  mdf_fields_t lf{};
+  lf.where = MDF_HOST;
+  double **slot[8] = {&lf.P, &lf.u, &lf.rho, &lf.G, &lf.div, &lf.S, &lf.sigma, &lf.omega};
+  for (int f = 0; f < 8; ++f)
+    if (dst[f]) {
+      loc[f].resize((size_t)(comps[f] * Nl));
+      *slot[f] = loc[f].data();
+    }
+  for (int s = 0; s < S->k; ++s) {
+    const mdf_status st = mdf_fields(S->h[s], &lf);
+    if (st != MDF_OK) return sfail(S, st, "slab %d fields: %s", s, mdf_last_error(S->h[s]));
+    for (int f = 0; f < 8; ++f) {
+      if (!dst[f]) continue;
+      for (int c = 0; c < comps[f]; ++c)  // real layers 1 .. nloc
+        std::memcpy(dst[f] + c * N + (long long)s * S->nloc * L, loc[f].data() + c * Nl + L,
+                    sizeof(double) * (size_t)(S->nloc * L));
+    }
+  }
+  return MDF_OK;
+}
+
+const char *mdf_slabs_last_error(mdf_slabs_t S) { return S ? S->err.c_str() : g_slabs_create_error.c_str(); }
+
+}  // extern "C"

@@ -118,3 +118,23 @@ def test_lattice_choice_is_checked_without_a_gpu(lib):
         o = _lib.Opts(_lib.STORAGE[storage], 1, None, 0, 0, 0, 1)
         assert lib.mdf_create(ctypes.byref(h), ctypes.byref(g2), 2, ctypes.byref(r), None,
                               ctypes.byref(o)) == _lib.EUNSUPPORTED, storage
+
+
+def test_slab_split_is_checked_without_a_gpu(lib):
+    """The split axis must divide into k slabs and be periodic; slabs take
+    the two-buffer rest-shifted storage types."""
+    from paper_2108_08591_gb300 import _lib
+    s = ctypes.c_void_p()
+    g = _lib.Grid(16, 12, 1)
+    r = _lib.Rates(1.0, 1.2, -1.0)
+    assert lib.mdf_slabs_create(ctypes.byref(s), ctypes.byref(g), 2, ctypes.byref(r), None, None, 5) == _lib.EINVAL
+    assert lib.mdf_slabs_create(ctypes.byref(s), ctypes.byref(g), 2, ctypes.byref(r), None, None, 0) == _lib.EINVAL
+    bc = _lib.BC()
+    bc.wall[:] = [0, 1, 0]
+    assert lib.mdf_slabs_create(ctypes.byref(s), ctypes.byref(g), 2, ctypes.byref(r), ctypes.byref(bc), None,
+                                3) == _lib.EUNSUPPORTED
+    for storage, inplace in (("f16eq", 0), ("f32", 1)):
+        o = _lib.Opts(_lib.STORAGE[storage], 1, None, 0, 0, 0, inplace)
+        assert lib.mdf_slabs_create(ctypes.byref(s), ctypes.byref(g), 2, ctypes.byref(r), None, ctypes.byref(o),
+                                    3) == _lib.EUNSUPPORTED
+    assert b"periodic" in lib.mdf_slabs_last_error(None) or b"storage" in lib.mdf_slabs_last_error(None)

@@ -550,6 +550,42 @@ def test_inplace_aa_halves_the_population_memory():
 
 
 # --------------------------------------------------------------------------
+# Slab decomposition with the per-face exchange (mdf_slabs_*)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("case,storage,k", [
+    ("2d", "f32", 1), ("2d", "f32", 2), ("2d", "f32", 3), ("2d", "f32", 4), ("2d", "f64", 4),
+    ("2d", "f16", 4), ("2d", "bf16", 2), ("2d_xwalls", "f32", 4), ("2d_q4", "f32", 3),
+    ("3d", "f32", 2), ("3d", "f32", 4), ("3d_q6_xwalls", "f64", 2),
+])
+def test_slabs_are_bitwise_the_undivided_lattice(case, storage, k):
+    """k sub-domains along the last axis, each with ghost layers refilled by
+    the face exchange after every update, give the undivided lattice's bits
+    (the exchange is the whole coupling between slabs)."""
+    from paper_2108_08591_gb300 import Lattice, Slabs
+    d = 3 if case.startswith("3d") else 2
+    q = 4 if "q4" in case else 6 if "q6" in case else 0
+    shape = (40, 48) if d == 2 else (20, 14, 16)
+    wall = (1, 0, 0) if "xwalls" in case else (0, 0, 0)
+    P, u = synth.smooth_fields(shape, seed=37, amp=0.01)
+    names = ("P", "u", "G", "omega", "rho")
+    ref = Lattice(shape, s1=1.3, storage=storage, wall=wall, q=q)
+    ref.init(P, u)
+    sl = Slabs(shape, s1=1.3, k=k, storage=storage, wall=wall, q=q)
+    sl.init(P, u)
+    try:
+        for n in (1, 6, 17):
+            ref.step(n)
+            sl.step(n)
+            a = ref.fields_host(names)
+            b = sl.fields_host(names)
+            for key in names:
+                assert np.array_equal(a[key], b[key]), (n, key, np.abs(a[key] - b[key]).max())
+    finally:
+        ref.close()
+        sl.close()
+
+
+# --------------------------------------------------------------------------
 # Fused epilogue, reductions, checkpoints, edges
 # --------------------------------------------------------------------------
 def test_fused_fields_equal_separate_pass():
