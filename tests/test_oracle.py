@@ -185,7 +185,15 @@ def test_continuity_set_never_feeds_back(d):
 def _amplification(d, q, c_int, w, cs2, s, k, with_rho):
     """A(k) of the scheme linearised about rest (P0 = rho0 = 1, u = 0):
     push-streaming e^{-i k.c_i} after f -> f - Lam (f - E f)."""
-    if d == 2:
+    cc = np.array(c_int, dtype=float)
+    if q == 4:  # conserved, first and traceless second moments
+        M = np.stack([np.ones(q), cc[:, 0], cc[:, 1], cc[:, 0] ** 2 - cc[:, 1] ** 2])
+        S = np.diag([s[0], s[1], s[1], s[2]])
+    elif q == 6:
+        M = np.stack([np.ones(q), cc[:, 0], cc[:, 1], cc[:, 2],
+                      2 * cc[:, 0] ** 2 - cc[:, 1] ** 2 - cc[:, 2] ** 2, cc[:, 1] ** 2 - cc[:, 2] ** 2])
+        S = np.diag([s[0]] + [s[1]] * 3 + [s[2]] * 2)
+    elif d == 2:
         M = np.array(_gold("lattices.json")["D2Q5"]["M"], dtype=float)
         S = np.diag([s[0], s[1], s[1], s[2], s[2]])
     else:
@@ -223,10 +231,10 @@ def _amplification(d, q, c_int, w, cs2, s, k, with_rho):
     return D @ C, E
 
 
-@pytest.mark.parametrize("d,n,m", [(2, (16, 12), (1, 2)), (2, (10, 14), (2, -1)),
-                                   (3, (12, 10, 9), (1, 1, -1))])
-def test_linear_dispersion(d, n, m):
-    q = 5 if d == 2 else 7
+@pytest.mark.parametrize("d,n,m,q", [(2, (16, 12), (1, 2), 5), (2, (10, 14), (2, -1), 5),
+                                     (3, (12, 10, 9), (1, 1, -1), 7), (2, (16, 12), (1, 2), 4),
+                                     (3, (12, 10, 9), (1, 1, -1), 6)])
+def test_linear_dispersion(d, n, m, q):
     s = (1.0, 1.35, 0.8)
     cv, w, cs2 = O.lattice(d, q, 1.0)
     k = [2 * math.pi * m[b] / n[b] for b in range(d)]
@@ -237,7 +245,7 @@ def test_linear_dispersion(d, n, m):
     amp = [0.7, -0.4, 0.5][:d]
     u = np.stack([eps * amp[b] * np.cos(phase) for b in range(d)])
     P = 1.0 + 0.3 * eps * np.cos(phase)
-    pb = O.Problem(d=d, n=n, s1=s[1], s2=s[2], s0=s[0])
+    pb = O.Problem(d=d, n=n, s1=s[1], s2=s[2], s0=s[0], nq=q)
     f = O.init(pb, P, u)
     rest = O.init(pb, *synth.rest_state(pb.N, d))
     # linear initial deviation: E applied to a state carrying (d rho = 0, du, dP)
