@@ -43,15 +43,15 @@ bool eq_storage(int st) { return st == MDF_F16EQ || st == MDF_BF16EQ; }
 //       FP16 6.80 TB/s, BF16 6.64 TB/s); FP64 2 nodes per thread.
 //   3D: FP32 one node per thread, 256 threads (6.94 TB/s): with 28
 //       populations per node the vector kernel's register pressure costs
-//       more than its saved instructions; rest-shifted 16-bit 8 nodes per
-//       thread, 64 threads (FP16 4.99, BF16 5.27 TB/s; the 16-bit vector
-//       kernel loads every word of its nodes before converting any).
+//       more than its saved instructions; rest-shifted 16-bit 4 nodes per
+//       thread, 128 threads, populations kept packed in registers (FP16
+//       5.82 TB/s; 4.35 with the FP32-copy kernel at 8 nodes and 64 threads).
 //   Equilibrium-shifted 16-bit: 2 nodes per thread (one FP32 pair), 64
 //       threads in 2D (5.43 TB/s) and 128 in 3D (5.39 TB/s).
 // mdf_autotune() measures the candidates for a given handle instead.
 int default_vx(int d, int storage) {
   if (eq_storage(storage)) return 2;
-  if (d == 3) return (storage == MDF_F16 || storage == MDF_BF16) ? 8 : 1;
+  if (d == 3) return (storage == MDF_F16 || storage == MDF_BF16) ? 4 : 1;
   return storage == MDF_F64 ? 2 : 4;
 }
 // Launch shape of the in-place AA kernels (measured at 4096^2 and 512^3 on
@@ -69,7 +69,7 @@ int default_block_aa(int d, int storage) {
 }
 int default_block(int d, int storage) {
   if (eq_storage(storage)) return d == 3 ? 128 : 64;
-  if (d == 3 && (storage == MDF_F16 || storage == MDF_BF16)) return 64;
+  if (d == 3 && (storage == MDF_F16 || storage == MDF_BF16)) return 128;
   return d == 3 ? 256 : 128;
 }
 

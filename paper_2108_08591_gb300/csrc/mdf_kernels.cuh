@@ -802,6 +802,7 @@ __global__ void k_mask(const DevArgs A, int wx, int wy, int wz, int lid, uint8_t
 
 #include "mdf_eq.cuh"
 #include "mdf_aa.cuh"
+#include "mdf_vec16p.cuh"
 
 namespace mdf {
 
@@ -840,6 +841,18 @@ cudaError_t update_vec(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
   const dim3 grid((unsigned)((threads + bx - 1) / bx), (unsigned)a.ny, (unsigned)a.nz), block(bx);
   // Scheme II is a separate build: its ubar needs the force before the
   // moments, which costs the Eq. 3-21 kernel registers when decided at run time
+  // 3D 16-bit: populations kept packed in registers (the FP32 copies of
+  // 28 x VX values do not fit; in 2D the FP32 form is the faster one)
+  if constexpr (sizeof(TS) == 2 && L::D == 3) {
+    if (a.scheme2) {
+      if (walls) k_update_vec16p<L, TS, VX, true, true><<<grid, block, 0, s>>>(a);
+      else k_update_vec16p<L, TS, VX, false, true><<<grid, block, 0, s>>>(a);
+    } else {
+      if (walls) k_update_vec16p<L, TS, VX, true, false><<<grid, block, 0, s>>>(a);
+      else k_update_vec16p<L, TS, VX, false, false><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
   if (a.scheme2) {
     if (walls) k_update_vec<L, TS, VX, MODE_STEP, true, true><<<grid, block, 0, s>>>(a);
     else k_update_vec<L, TS, VX, MODE_STEP, false, true><<<grid, block, 0, s>>>(a);
