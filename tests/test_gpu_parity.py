@@ -775,6 +775,75 @@ def test_full_size_4096_sampled_parity():
     assert rel(np.array(ref_w), np.array(got_w)) < 1e-3
 
 
+def _sampled_window_errors(shape, s1, P, u, got, steps, samples, seed):
+    """Relative L2 of u, P - 1 and omega on sampled nodes of a periodic
+    lattice, against the FP64 oracle on (2 steps + 1)^d windows (after
+    `steps` updates a node depends only on nodes within that many links)."""
+    d = len(shape)
+    n = shape[0]
+    rng = synth.SplitMix64(seed)
+    W = 2 * steps + 1
+    offs = np.arange(-steps, steps + 1)
+    ref = {"u": [], "P": [], "omega": []}
+    num = {"u": [], "P": [], "omega": []}
+    for _ in range(samples):
+        c = [rng.randint(0, n - 1) for _ in range(d)]
+        axes = [(c[b] + offs) % n for b in range(d)]
+        if d == 2:
+            sel = (axes[1][:, None] * n + axes[0][None, :]).ravel()
+            g = c[1] * n + c[0]
+        else:
+            sel = ((axes[2][:, None, None] * n + axes[1][None, :, None]) * n + axes[0][None, None, :]).ravel()
+            g = (c[2] * n + c[1]) * n + c[0]
+        pb = O.Problem(d=d, n=(W,) * d, s1=s1)
+        f = O.run(pb, O.init(pb, P[sel], u[:, sel]), steps)
+        Pr, ur, _ = O.macro(pb, f)
+        D = O.derived(pb, f)
+        mid = (W ** d) // 2
+        ref["u"].append(ur[:, mid]); num["u"].append(got["u"][:, g])
+        ref["P"].append(Pr[mid] - 1.0); num["P"].append(got["P"][g] - 1.0)
+        ref["omega"].append(D["omega"][:, mid]); num["omega"].append(got["omega"][:, g])
+    return {k: rel(np.array(ref[k]), np.array(num[k])) for k in ref}
+
+
+@pytest.mark.parametrize("storage,tol", [("f16eq", (2e-3, 2e-3, 1e-2)), ("bf16eq", (2e-3, 1e-2, 5e-2))])
+def test_full_size_4096_equilibrium_shifted_sampled_parity(storage, tol):
+    """The 4096^2 workload with equilibrium-shifted 16-bit storage, in the
+    benchmark's launch configuration (2 nodes per thread, 64 threads), at
+    sampled nodes: u within the 2e-3 bound on 16-bit storage."""
+    from paper_2108_08591_gb300 import Lattice
+    n, steps = 4096, 40
+    P, u = synth.tg_plus_modes(n, U0=0.01, seed=2108)
+    lat = Lattice((n, n), s1=S1_TG, storage=storage)
+    assert (lat.info.vx, lat.info.block) == (2, 64)
+    lat.init(P, u)
+    lat.step(steps)
+    got = {k: v.cpu().numpy() for k, v in lat.fields(("P", "u", "omega")).items()}
+    lat.close()
+    e = _sampled_window_errors((n, n), S1_TG, P, u, got, steps, 8, 91)
+    assert e["u"] < tol[0] and e["P"] < tol[1] and e["omega"] < tol[2], e
+
+
+@pytest.mark.parametrize("storage,tol", [("f32", (1e-5, 1e-4, 1e-3)), ("f16", (2e-3, 2e-2, 0.5))])
+def test_full_size_512_cubed_sampled_parity(storage, tol):
+    """512^3 D3Q7 x 4 3D Taylor-Green (U0 = 0.05, Re = 1600), in the
+    benchmark's launch configuration (FP32: one node per thread; FP16: 4
+    nodes per thread, populations packed in registers), at sampled nodes."""
+    from paper_2108_08591_gb300 import Lattice
+    n, steps = 512, 12
+    k = 2 * np.pi / n
+    nu = 0.05 / (k * 1600.0)
+    s1 = 1.0 / (4 * nu + 0.5)
+    P, u = synth.taylor_green_3d(n, U0=0.05)
+    lat = Lattice((n, n, n), s1=s1, storage=storage)
+    lat.init(P, u)
+    lat.step(steps)
+    got = {k_: v.cpu().numpy() for k_, v in lat.fields(("P", "u", "omega")).items()}
+    lat.close()
+    e = _sampled_window_errors((n, n, n), s1, P, u, got, steps, 6, 93)
+    assert e["u"] < tol[0] and e["P"] < tol[1] and e["omega"] < tol[2], e
+
+
 # --------------------------------------------------------------------------
 # Vector kernel (VX x-nodes per thread) against the one-node-per-thread kernel
 # --------------------------------------------------------------------------
