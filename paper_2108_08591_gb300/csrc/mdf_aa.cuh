@@ -26,6 +26,8 @@
 
 #include <type_traits>
 
+#include "mdf_vec16p.cuh"  // packed 16-bit words (Words, set_bits, f2bits)
+
 namespace mdf {
 
 template <class T> struct CodecRW;
@@ -447,6 +449,194 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_aa_vec(const DevArgs A) {
   if (A.with_rho) aa_write_vec<L, TS, VX, ODD, WALLS>(A, f, 0, R, m, active, h);
 }
 
+// ---------------------------------------------------------------------------
+// 16-bit vector AA update with the populations packed in registers (see
+// k_update_vec16p): words are loaded (and, in the odd phase, realigned along
+// x) first, every node is decoded, collided and encoded back into its
+// element, and the words are stored in the layout the phase leaves.  A
+// population leaving through a wall is bounced in FP32 before it is encoded
+// (as the one-node-per-thread kernel does) and its element is stored in the
+// node's own slot.
+// ---------------------------------------------------------------------------
+template <class TS> __device__ __forceinline__ void st_bits16(TS *p, unsigned b) {
+  *reinterpret_cast<unsigned short *>(p) = (unsigned short)b;
+}
+
+template <class L, class TS, int VX, bool ODD, bool WALLS, bool S2>
+__global__ void __launch_bounds__(kMaxBlock) k_update_aa_vec16p(const DevArgs A) {
+  constexpr int D = L::D, Q = L::Q;
+  using PK = Packed16<TS, VX>;
+  using W = typename Words<VX>::W;
+  const int lane = threadIdx.x & 31;
+  int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * VX;
+  const bool active = x0 < A.nx;
+  if (!active) x0 = A.nx - VX;  // stays in the shuffles, stores nothing
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int row0 = (z * A.ny + y) * A.px;
+  const int row_ym = (z * A.ny + wrap(y - 1, A.ny)) * A.px;
+  const int row_yp = (z * A.ny + wrap(y + 1, A.ny)) * A.px;
+  const int row_zm = D == 3 ? (wrap(z - 1, A.nz) * A.ny + y) * A.px : row0;
+  const int row_zp = D == 3 ? (wrap(z + 1, A.nz) * A.ny + y) * A.px : row0;
+  const bool ledge = lane == 0 || x0 == 0;
+  const bool redge = lane == 31 || x0 + VX >= A.nx;
+  const int xl = x0 == 0 ? A.nx - 1 : x0 - 1;
+  const int xr = x0 + VX >= A.nx ? 0 : x0 + VX;
+  const VecRows R{row0, row_ym, row_yp, row_zm, row_zp, x0, xl, xr, ledge, redge};
+  TS *f = static_cast<TS *>(A.fout);  // == A.fin
+  const int a1 = A.with_rho;
+  uint8_t m[VX];
+#pragma unroll
+  for (int j = 0; j < VX; ++j) m[j] = WALLS ? A.mask[row0 + x0 + j] : uint8_t(0);
+  auto set_base = [&](int s) { return f + (long long)(s < D ? a1 + s : 0) * Q * A.plane; };
+
+  W wv[D + 1][Q];
+  unsigned edge[D + 1][2];
+#pragma unroll
+  for (int s = 0; s <= D; ++s) {
+    if (s == D && !A.with_rho) break;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const TS *p = set_base(s) + (long long)(ODD ? L::opp(i) : i) * A.plane;
+      wv[s][i] = *reinterpret_cast<const W *>(p + (ODD ? source_row<L>(R, i) : row0) + x0);
+      if (ODD && L::c(i, 0) == 1) edge[s][0] = ledge ? *reinterpret_cast<const unsigned short *>(p + row0 + xl) : 0u;
+      if (ODD && L::c(i, 0) == -1) edge[s][1] = redge ? *reinterpret_cast<const unsigned short *>(p + row0 + xr) : 0u;
+    }
+  }
+  if (ODD) {
+#pragma unroll
+    for (int s = 0; s <= D; ++s) {
+      if (s == D && !A.with_rho) break;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        if (L::c(i, 0) == 1) {
+          unsigned nb = __shfl_up_sync(0xffffffffu, PK::last_word(wv[s][i]), 1) >> 16;
+          if (ledge) nb = edge[s][0];
+          wv[s][i] = Words<VX>::up(wv[s][i], nb);
+        } else if (L::c(i, 0) == -1) {
+          unsigned nb = __shfl_down_sync(0xffffffffu, PK::first_word(wv[s][i]), 1) & 0xffffu;
+          if (redge) nb = edge[s][1];
+          wv[s][i] = Words<VX>::down(wv[s][i], nb);
+        }
+      }
+    }
+  }
+
+  float F[D][VX];
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    if (A.force) {
+      VecIO<float, VX>::load(static_cast<const float *>(A.force) + a * A.plane + row0 + x0, F[a]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < VX; ++j) F[a][j] = 0.f;
+    }
+  }
+  const float s1 = float(A.s1), s2 = float(A.s2);
+#pragma unroll
+  for (int j = 0; j < VX; ++j) {
+    float gn[D][Q], hn[Q], Fn[D];
+#pragma unroll
+    for (int s = 0; s <= D; ++s) {
+      if (s == D && !A.with_rho) break;
+      const int alpha = s < D ? s + 1 : 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        float v = bits_to_float<TS>(PK::bits(wv[s][i], j));
+        if (ODD && WALLS && moving<L>(i) && ((m[j] >> L::opp(i)) & 1)) {  // arrived through a wall
+          v = -CodecRW<TS>::load(set_base(s) + (long long)i * A.plane + row0 + x0 + j);
+          if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u)) v += float(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+        }
+        if (s < D) gn[s < D ? s : 0][i] = v;
+        else hn[i] = v;
+      }
+    }
+    if (!A.with_rho)
+#pragma unroll
+      for (int i = 0; i < Q; ++i) hn[i] = 0.f;
+#pragma unroll
+    for (int a = 0; a < D; ++a) Fn[a] = F[a][j];
+    float M[D + 2];
+    collide_node<L, float, S2>(gn, hn, A.with_rho != 0, Fn, s1, s2, M);
+#pragma unroll
+    for (int s = 0; s <= D; ++s) {
+      if (s == D && !A.with_rho) break;
+      const int alpha = s < D ? s + 1 : 0;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        float v = s < D ? gn[s < D ? s : 0][i] : hn[i];
+        if (ODD && WALLS && moving<L>(i) && ((m[j] >> i) & 1)) {  // leaves through a wall: bounced
+          v = -v;
+          if (alpha >= 1 && i == L::UP && (m[j] & 0x80u)) v += float(2.0 * L::w(i) * A.lid_u[alpha - 1]);
+        }
+        set_bits<VX>(wv[s][i], j, f2bits<TS>(v));
+      }
+    }
+  }
+
+  // stores (every lane runs the shuffles; lanes past the row end store nothing)
+#pragma unroll
+  for (int s = 0; s <= D; ++s) {
+    if (s == D && !A.with_rho) break;
+    TS *base = set_base(s);
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const W w = wv[s][i];
+      if (!ODD) {
+        if (active) *reinterpret_cast<W *>(base + (long long)L::opp(i) * A.plane + row0 + x0) = w;
+        continue;
+      }
+      TS *p = base + (long long)i * A.plane;
+      TS *own_opp = base + (long long)L::opp(i) * A.plane + row0 + x0;  // bounced elements
+      auto leaves_wall = [&](int j) { return WALLS && moving<L>(i) && ((m[j] >> i) & 1); };
+      if (L::c(i, 0) == 1) {  // to x + 1
+        const unsigned nb = __shfl_up_sync(0xffffffffu, PK::last_word(w), 1) >> 16;
+        if (!active) continue;
+        const W out = Words<VX>::up(w, nb);
+        if (!ledge) {
+          *reinterpret_cast<W *>(p + row0 + x0) = out;
+        } else {
+#pragma unroll
+          for (int j = 1; j < VX; ++j) st_bits16(p + row0 + x0 + j, PK::bits(out, j));
+        }
+        if (redge) {
+          if (leaves_wall(VX - 1)) st_bits16(own_opp + VX - 1, PK::bits(w, VX - 1));
+          else st_bits16(p + row0 + xr, PK::bits(w, VX - 1));
+        }
+      } else if (L::c(i, 0) == -1) {  // to x - 1
+        const unsigned nb = __shfl_down_sync(0xffffffffu, PK::first_word(w), 1) & 0xffffu;
+        if (!active) continue;
+        const W out = Words<VX>::down(w, nb);
+        if (!redge) {
+          *reinterpret_cast<W *>(p + row0 + x0) = out;
+        } else {
+#pragma unroll
+          for (int j = 0; j < VX - 1; ++j) st_bits16(p + row0 + x0 + j, PK::bits(out, j));
+        }
+        if (ledge) {
+          if (leaves_wall(0)) st_bits16(own_opp, PK::bits(w, 0));
+          else st_bits16(p + row0 + xl, PK::bits(w, 0));
+        }
+      } else {
+        if (!active) continue;
+        const int r = L::c(i, 1) == 1 ? row_yp : L::c(i, 1) == -1 ? row_ym
+                    : L::c(i, 2) == 1 ? row_zp : L::c(i, 2) == -1 ? row_zm : row0;
+        bool any_wall = false;
+#pragma unroll
+        for (int j = 0; j < VX; ++j) any_wall |= leaves_wall(j);
+        if (!any_wall) {
+          *reinterpret_cast<W *>(p + r + x0) = w;
+        } else {
+#pragma unroll
+          for (int j = 0; j < VX; ++j) {
+            if (leaves_wall(j)) st_bits16(own_opp + j, PK::bits(w, j));
+            else st_bits16(p + r + x0 + j, PK::bits(w, j));
+          }
+        }
+      }
+    }
+  }
+}
+
 // FP64 sums and residual over the in-place buffer (see k_reduce).
 template <class L, class TS, bool ODD, bool WALLS, int KIND>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce_aa(const DevArgs A) {
@@ -514,6 +704,16 @@ cudaError_t update_aa_vec_phase(bool walls, const DevArgs &a, cudaStream_t s) {
   const int bx = a.block;
   const int threads = a.nx / VX;
   const dim3 grid((unsigned)((threads + bx - 1) / bx), (unsigned)a.ny, (unsigned)a.nz), block(bx);
+  if constexpr (sizeof(TS) == 2) {  // 16-bit: populations kept packed in registers
+    if (a.scheme2) {
+      if (walls) k_update_aa_vec16p<L, TS, VX, ODD, true, true><<<grid, block, 0, s>>>(a);
+      else k_update_aa_vec16p<L, TS, VX, ODD, false, true><<<grid, block, 0, s>>>(a);
+    } else {
+      if (walls) k_update_aa_vec16p<L, TS, VX, ODD, true, false><<<grid, block, 0, s>>>(a);
+      else k_update_aa_vec16p<L, TS, VX, ODD, false, false><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+  }
   if (a.scheme2) {
     if (walls) k_update_aa_vec<L, TS, VX, ODD, true, true><<<grid, block, 0, s>>>(a);
     else k_update_aa_vec<L, TS, VX, ODD, false, true><<<grid, block, 0, s>>>(a);
