@@ -7,6 +7,9 @@
  * equations (Eq. 2-2): one D2Q5 (2D) or D3Q7 (3D) distribution set per
  * equation, the MRT collision Lambda = M^-1 S_d M (Eq. 4-1 .. 4-3) and the
  * evolution of Eq. 3-21 (diffusive scaling, lattice units dx = dt = c = 1).
+ * Options: the D2Q4 / D3Q6 lattices (Sec. 2.2), Scheme II forcing (Eq. 2-3c),
+ * a non-equilibrium start (the inverse of Eq. 3-16), the in-place AA stream
+ * (one population buffer) and a slab decomposition with its face exchange.
  *
  * Conventions shared by every entry point:
  *   - Every call returns an mdf_status; nothing aborts the process.  On an
