@@ -629,6 +629,7 @@ mdf_status mdf_batch_create(mdf_batch_t *out, int d, int n, const int *side, con
   if (opts.storage != MDF_F32) return bfail(nullptr, MDF_EUNSUPPORTED, "batched cavities use FP32 storage");
   if (opts.q != 0 && opts.q != (d == 2 ? 5 : 7))
     return bfail(nullptr, MDF_EUNSUPPORTED, "batched cavities use D2Q5 / D3Q7");
+  if (opts.inplace) return bfail(nullptr, MDF_EUNSUPPORTED, "batched cavities use two population pools");
   mdf_batch_t b = new (std::nothrow) mdf_batch_s;
   if (!b) return bfail(nullptr, MDF_ENOMEM, "host allocation");
   b->d = d;

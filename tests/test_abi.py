@@ -138,3 +138,16 @@ def test_slab_split_is_checked_without_a_gpu(lib):
         assert lib.mdf_slabs_create(ctypes.byref(s), ctypes.byref(g), 2, ctypes.byref(r), None, ctypes.byref(o),
                                     3) == _lib.EUNSUPPORTED
     assert b"periodic" in lib.mdf_slabs_last_error(None) or b"storage" in lib.mdf_slabs_last_error(None)
+
+
+def test_batch_options_are_checked_without_a_gpu(lib):
+    """Batched cavities take FP32 storage, D2Q5 / D3Q7 and two pools."""
+    from paper_2108_08591_gb300 import _lib
+    b = ctypes.c_void_p()
+    side = (ctypes.c_int * 2)(65, 129)
+    Re = (ctypes.c_double * 2)(100.0, 400.0)
+    for storage, q, inplace in (("f16", 0, 0), ("f32", 4, 0), ("f32", 0, 1)):
+        o = _lib.Opts(_lib.STORAGE[storage], 1, None, 0, 0, q, inplace)
+        st = lib.mdf_batch_create(ctypes.byref(b), 2, 2, ctypes.cast(side, ctypes.c_void_p),
+                                  ctypes.cast(Re, ctypes.c_void_p), 0.1, ctypes.byref(o))
+        assert st == _lib.EUNSUPPORTED, (storage, q, inplace)

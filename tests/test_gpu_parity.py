@@ -248,6 +248,18 @@ def test_scheme2_init_sums_and_residual(storage):
         lat.close()
 
 
+def test_forcing_scheme_is_checked():
+    """Only Eq. 3-21 (0) and Scheme II (2) exist; Scheme I is refused."""
+    from paper_2108_08591_gb300 import Lattice, _lib
+    lat = Lattice((32, 32), s1=1.2)
+    try:
+        for bad in (1, 3, -1):
+            assert lat._lib.mdf_set_forcing(lat._h, bad) == _lib.EINVAL
+        assert lat.forcing == "eq3-21"
+    finally:
+        lat.close()
+
+
 def test_scheme2_without_force_is_eq_3_21():
     """Without a force the two schemes are one update: same bits."""
     shape = (64, 33)
