@@ -471,8 +471,8 @@ def _half_source(pb, F, w):
     return h
 
 
-@pytest.mark.parametrize("d", [2, 3])
-def test_scheme2_is_eq_2_3a_with_implicit_force_derivative(d):
+@pytest.mark.parametrize("d,nq", [(2, 0), (3, 0), (2, 4), (3, 6)])
+def test_scheme2_is_eq_2_3a_with_implicit_force_derivative(d, nq):
     """Scheme II comes from Eq. 2-3a with D_i F replaced by the implicit
     difference (F(x + c_i dt, t + dt) - F(x, t)) / dt and the variable
     fbar = f - dt F / 2.  Undo the change of variable and check Eq. 2-3a
@@ -493,8 +493,8 @@ def test_scheme2_is_eq_2_3a_with_implicit_force_derivative(d):
     F = np.stack([0.03 * np.sin(2 * math.pi * X[a] / n[a] + 6 * rng.uniform())
                   + 0.02 * np.cos(2 * math.pi * X[(a + 1) % d] / n[(a + 1) % d] + 6 * rng.uniform())
                   for a in range(d)])
-    pb2 = O.Problem(d=d, n=n, s1=1.3, s2=0.9, s0=1.1, dx=dx, dt=dt, force=F, scheme=2)
-    pb0 = O.Problem(d=d, n=n, s1=1.3, s2=0.9, s0=1.1, dx=dx, dt=dt, force=F, scheme=0)
+    pb2 = O.Problem(d=d, n=n, s1=1.3, s2=0.9, s0=1.1, dx=dx, dt=dt, force=F, scheme=2, nq=nq)
+    pb0 = O.Problem(d=d, n=n, s1=1.3, s2=0.9, s0=1.1, dx=dx, dt=dt, force=F, scheme=0, nq=nq)
     cint, w, _ = O.lattice(d, pb2.q, 1.0)
     fb = O.run(pb2, O.init(pb2, P, u), 3)  # a non-equilibrium fbar
     fb1 = O.run(pb2, fb.copy(), 1)
@@ -603,8 +603,8 @@ def test_scheme2_four_roll_mill_second_order():
 # --------------------------------------------------------------------------
 # Non-equilibrium seeding (the inverse of Eq. 3-16)
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("d", [2, 3])
-def test_neq_seed_inverts_eq_3_16(d):
+@pytest.mark.parametrize("d,nq", [(2, 0), (3, 0), (2, 4), (3, 6)])
+def test_neq_seed_inverts_eq_3_16(d, nq):
     """f = f^eq(P, u) + f^ne(G) reads back, through Eq. 3-16 (pinned by the
     Poiseuille, four-roll-mill and Couette tests), the traceless part of
     an arbitrary gradient G, with P and u untouched; in physical units."""
@@ -614,7 +614,7 @@ def test_neq_seed_inverts_eq_3_16(d):
     else:
         n = (4, 5, 3)
         P, u = _seeded_fields_3d(n, 13)
-    pb = O.Problem(d=d, n=n, s1=1.35, dx=0.25, dt=0.1)
+    pb = O.Problem(d=d, n=n, s1=1.35, dx=0.25, dt=0.1, nq=nq)
     rng = np.random.default_rng(2108)
     G = rng.normal(scale=0.3, size=(d, d, pb.N))
     f = O.init(pb, P, u, G)
