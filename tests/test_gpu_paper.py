@@ -99,12 +99,14 @@ def test_four_roll_mill_table1(storage):
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])
 def test_scheme2_poiseuille_is_exact(storage):
-    """Sec. 4.1's Poiseuille flow under Scheme II (Eq. 2-3c, 2-7a): the
-    bounce-back of fbar carries the force term Eq. 3-21's wall rule misses,
-    and the steady profile is the parabola itself (the FP64 oracle reaches
-    it to 1e-9 in these 22000 steps), where Eq. 3-21 leaves the printed
-    E(u1) = 5.9427e-4.  FP32 storage: the biased rounding of the force
-    increments (see the Eq. 3-21 test) leaves ~1e-5."""
+    """Sec. 4.1's Poiseuille flow under Scheme II (Eq. 2-3c, 2-7a).
+    - The bounce-back of fbar carries a force term that Eq. 3-21's wall
+      rule lacks.
+    - With the paper's s2 rule (Lambda = 3/16) the steady profile is the
+      parabola itself: the FP64 oracle reaches it to 1e-9 in these 22000
+      steps, where Eq. 3-21 leaves the printed E(u1) = 5.9427e-4.
+    - FP32 storage: the biased rounding of the force increments (see the
+      Eq. 3-21 test) leaves ~1e-5."""
     from paper_2108_08591_gb300 import Lattice
     g = _gold("poiseuille")
     N, nu, F1, s1 = g["N"], g["nu"], g["F1"], g["s1"]

@@ -548,15 +548,19 @@ def test_scheme2_time_dependent_uniform_force_is_trapezoidal():
 
 def test_scheme2_poiseuille_is_exact():
     """Sec. 4.1 Poiseuille flow under Scheme II, with the anti-halfway
-    bounce-back acting on the evolved variable fbar.  In the bulk the steady
-    state of Eq. 2-3c solves the same second-order difference equation as
-    Eq. 3-21 (a uniform force has no implicit difference), which a parabola
-    satisfies exactly.  At a wall, Scheme II's bounce-back of fbar =
-    f - dt F / 2 is Eq. 3-21's bounce-back plus dt w_i Fbar: the force term
-    the Eq. 3-21 wall rule misses, and the source of the O(dx^2) error
-    the paper prints for it (E(u1) = 5.9427e-4 at this size).  So
-    the steady profile is the parabola itself, up to the convergence of
-    the run, and so are du1/dy and S_xy."""
+    bounce-back acting on the evolved variable fbar.
+    - In the bulk, the steady state of Eq. 2-3c solves the same
+      second-order difference equation as Eq. 3-21: a uniform force has no
+      implicit difference. A parabola satisfies it exactly.
+    - At a wall, Scheme II's bounce-back of fbar = f - dt F / 2 is Eq. 3-21's
+      bounce-back plus dt w_i Fbar: a force term that the Eq. 3-21 wall rule
+      lacks.
+    - With the paper's s2 rule, Lambda = (1/s1 - 1/2)(1/s2 - 1/2) = 3/16,
+      and at that value the wall closure is exact too. The steady profile
+      is then the parabola itself, up to the convergence of the run, and so
+      are du1/dy and S_xy.
+    - Eq. 3-21 keeps the printed E(u1) = 5.9427e-4, and another s2 leaves
+      Scheme II an O(dx^2) error as well."""
     g = _gold("paper_numbers.json")["poiseuille"]
     N, nu, F1, s1 = g["N"], g["nu"], g["F1"], g["s1"]
     dx = 1.0 / N
@@ -585,6 +589,11 @@ def test_scheme2_poiseuille_is_exact():
     # a constant, the slip velocity of the Eq. 3-21 wall rule
     du = (out[0][0][0] - un[0]).reshape(N, N)[:, 0]
     assert np.allclose(du, du[0], rtol=0, atol=1e-9 * np.abs(ua).max())
+    # away from Lambda = 3/16 the Scheme II profile is not exact
+    pb = O.Problem(d=2, n=(N, N), s1=s1, s2=1.5, wall=(0, 1, 0), dx=dx, dt=dt, force=F, scheme=2)
+    f = O.init(pb, *synth.rest_state(N * N, 2))
+    O.run(pb, f, 22000)
+    assert O.rel_l2(ua, O.macro(pb, f)[1][0]) > 1e-4
 
 
 def test_scheme2_four_roll_mill_second_order():
@@ -655,3 +664,35 @@ def test_neq_seed_removes_the_initial_layer():
         err[name] = (eG, eu)
     assert err["neq"][0] < 1e-2 and err["eq"][0] > 0.1, err
     assert err["neq"][1] < 0.25 * err["eq"][1], err
+
+
+def _channel_3d_error(q, s2, scheme, H=8, nu=1.0 / 12.0, F=1e-6):
+    cs2 = 0.25 if q == 7 else 1.0 / 3.0
+    s1 = 1.0 / (nu / cs2 + 0.5)
+    n = (3, 3, H)
+    N = 9 * H
+    Fld = np.zeros((3, N))
+    Fld[0] = F
+    z = synth.grid_coords(n)[2] + 0.5
+    ua = F / (2 * nu) * z * (H - z)
+    pb = O.Problem(d=3, n=n, s1=s1, s2=s2, wall=(0, 0, 1), force=Fld, scheme=scheme, nq=q)
+    f = O.init(pb, *synth.rest_state(N, 3))
+    O.run(pb, f, 60 * H * H)
+    return O.rel_l2(ua, O.macro(pb, f)[1][0]), s1
+
+
+def test_scheme2_channel_3d_exact_at_its_magic_rate():
+    """The 3D body-force channel (walls on z) under Scheme II.  As in 2D the
+    steady profile is the exact parabola only at one value of
+    Lambda = (1/s1 - 1/2)(1/s2 - 1/2), which depends on the lattice:
+    3/16 for D3Q6 (the s2 rule of Sec. 4.1) and 1/6 for D3Q7, whose rest
+    weight differs.  Away from it the profile keeps an O(dx^2) error, and
+    Eq. 3-21 keeps one at any s2."""
+    e6, _ = _channel_3d_error(6, None, 2)
+    assert e6 < 1e-8
+    _, s1 = _channel_3d_error(7, None, 2)
+    s2_16 = 1.0 / (1.0 / 6.0 / (1.0 / s1 - 0.5) + 0.5)  # Lambda = 1/6
+    e7, _ = _channel_3d_error(7, s2_16, 2)
+    assert e7 < 1e-8
+    assert _channel_3d_error(7, None, 2)[0] > 1e-4  # Lambda = 3/16 on D3Q7
+    assert _channel_3d_error(7, s2_16, 0)[0] > 1e-4  # Eq. 3-21
