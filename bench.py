@@ -378,7 +378,7 @@ def run_mdf(args):
     # buffered, so step k's read-back and step k+1's upload overlap the
     # updates of the neighbouring steps, as a serving loop would run them;
     # the host clock stops after the last read-back has landed.
-    e2e_steps = max(2, min(args.steps, 10))
+    e2e_steps = max(2, min(args.steps, 20))
     Ph = torch.from_numpy(P).pin_memory()
     uh = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
     outPh = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(2)]
