@@ -696,3 +696,29 @@ def test_scheme2_channel_3d_exact_at_its_magic_rate():
     assert e7 < 1e-8
     assert _channel_3d_error(7, None, 2)[0] > 1e-4  # Lambda = 3/16 on D3Q7
     assert _channel_3d_error(7, s2_16, 0)[0] > 1e-4  # Eq. 3-21
+
+
+@pytest.mark.parametrize("d,q", [(2, 5), (2, 4), (3, 7), (3, 6)])
+@pytest.mark.parametrize("s1", [0.8, 1.2, 1.7])
+def test_shear_wave_decays_at_eq_3_13a_viscosity(d, q, s1):
+    """A small shear wave u_x = A sin(k y) decays as exp(-nu k^2 t) with
+    nu = (1/s1 - 1/2) c_s^2 (Eq. 3-13a), c_s^2 being the lattice's own (1/3,
+    1/2, 1/4, 1/3).  The measured rate matches within the O(k^2) lattice
+    error of a 32-node wavelength."""
+    n = (4, 32) if d == 2 else (4, 32, 3)
+    cv, w, cs2 = O.lattice(d, q, 1.0)
+    N = int(np.prod(n))
+    coords = synth.grid_coords(n)
+    k = 2 * math.pi / n[1]
+    A = 1e-6
+    u = np.zeros((d, N))
+    u[0] = A * np.sin(k * coords[1]).ravel()
+    pb = O.Problem(d=d, n=n, s1=s1, nq=q)
+    f = O.init(pb, np.ones(N), u)
+    steps = 200
+    O.run(pb, f, steps)
+    un = O.macro(pb, f)[1][0]
+    amp = 2 * np.mean(un * np.sin(k * coords[1]).ravel())
+    rate = -math.log(amp / A) / (k * k * steps)
+    nu = (1 / s1 - 0.5) * cs2
+    assert rate == pytest.approx(nu, rel=2e-2), (rate, nu)
