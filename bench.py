@@ -275,12 +275,13 @@ def sampled_oracle_error(shape, s1, P, u, storage, steps, samples=8, seed=77, q=
     lat.init(P, u)
     fl = lat.alloc_fields(("P",))
     lat.step_fields(steps, fl)
-    got = {k: v.cpu().numpy() for k, v in lat.fields(("P", "u", "omega")).items()}
+    names = ("u", "P", "G", "S", "omega")
+    got = {k: v.cpu().numpy() for k, v in lat.fields(names).items()}
     lat.close()
     rng = synth.SplitMix64(seed)
     n = shape[0]
     W = 2 * steps + 1
-    ref, num = {"u": [], "P": [], "omega": []}, {"u": [], "P": [], "omega": []}
+    ref, num = {k: [] for k in names}, {k: [] for k in names}
     for _ in range(samples):
         c = [rng.randint(0, n - 1) for _ in range(d)]
         offs = np.arange(-steps, steps + 1)
@@ -300,11 +301,61 @@ def sampled_oracle_error(shape, s1, P, u, storage, steps, samples=8, seed=77, q=
         mid = (W ** d) // 2
         ref["u"].append(ur[:, mid]); num["u"].append(got["u"][:, g])
         ref["P"].append(Pr[mid] - 1.0); num["P"].append(got["P"][g] - 1.0)
-        ref["omega"].append(D["omega"][:, mid]); num["omega"].append(got["omega"][:, g])
+        for k in ("G", "S", "omega"):
+            ref[k].append(D[k][..., mid]); num[k].append(got[k][..., g])
     err = {k: oracle.rel_l2(np.array(ref[k]), np.array(num[k])) for k in ref}
     err["case"] = (f"{samples} seeded nodes of the full lattice after {steps} updates, "
-                   f"FP64 oracle on periodic {W}^{d} windows; P compared as P - 1")
+                   f"FP64 oracle on periodic {W}^{d} windows; P compared as P - 1; "
+                   "G = du_a/dx_b (Eq. 3-16), S (Eq. 3-17), omega (Eq. 3-18)")
     return err
+
+
+def storage_leg(shape, s1, P, u, storage, steps=5, warmup=3, q=0, oracle_check=True):
+    """A second storage type on the same workload, outside the main timed
+    region: device-timed throughput (fused epilogue update + plain updates per
+    bench step, as the main line), the plain update's roofline fraction at
+    that storage's algorithmic bytes per node, and its sampled FP64 oracle
+    error per field."""
+    import numpy as np
+    import torch
+    from paper_2108_08591_gb300 import Lattice
+    N = int(np.prod(shape))
+    stream = torch.cuda.current_stream()
+    lat = Lattice(shape, s1=s1, storage=storage, stream=stream, q=q)
+    lat.init(P, u)
+    info = lat.info
+    fields = lat.alloc_fields(("P", "u", "G", "div", "S", "sigma", "omega"))
+    for _ in range(warmup):
+        lat.step_fields(1, fields)
+        lat.step(EPI_EVERY - 1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    plain = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(steps)]
+    e0.record(stream)
+    for a, b in plain:
+        lat.step_fields(1, fields)
+        a.record(stream)
+        lat.step(EPI_EVERY - 1)
+        b.record(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    plain_ms = sum(a.elapsed_time(b) for a, b in plain) / (steps * (EPI_EVERY - 1))
+    lat.close()
+    del fields
+    peak, kind = _peaks()
+    achieved = info.bytes_per_update * N / (plain_ms / 1e3) / 1e9
+    out = {"storage": storage, "value": steps * EPI_EVERY * N / (ms / 1e3) / 1e6, "unit": "MLUPS",
+           "steps": steps, "warmup": warmup,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak, "bytes_per_node": info.bytes_per_update,
+                        "avg_launch_ms": plain_ms, "vx": info.vx, "block": info.block,
+                        "peak_source": f"{kind} hbm_gbs (MEASURED_PEAKS.json)"}}
+    if oracle_check:
+        out["fp64_oracle_error"] = sampled_oracle_error(shape, s1, P, u, storage,
+                                                        steps=64 if len(shape) == 2 else 16, q=q)
+    return out
 
 
 def run_mdf(args):
@@ -370,60 +421,29 @@ def run_mdf(args):
     updates_local = args.steps * EPI_EVERY * N
     value, t_max, _ = aggregate(updates_local, elapsed_ms, dist, device="cuda")
 
-    # end to end through the library's Python API with host buffers: every
-    # step copies its inputs (P, u) from pinned host memory to the device,
-    # initialises the lattice from them, runs the step (fused epilogue + plain
-    # updates), writes (P, u) of the final state and copies them back to
-    # pinned host memory.  The copies run on their own streams, double
-    # buffered, so step k's read-back and step k+1's upload overlap the
-    # updates of the neighbouring steps, as a serving loop would run them;
-    # the host clock stops after the last read-back has landed.
+    # end to end through the C-ABI's host-buffer path: every step hands the
+    # library its inputs (P, u) in pinned host memory (mdf_init with
+    # MDF_HOST: the host-to-device copy and the initialisation happen inside
+    # the call), runs the step (fused epilogue + plain updates) and reads
+    # (P, u) of the final state back into pinned host memory (mdf_fields
+    # with MDF_HOST outputs: the kernel, the device-to-host copy and a
+    # synchronisation inside the call).  Timed on the host clock.
     e2e_steps = max(2, min(args.steps, 20))
-    Ph = torch.from_numpy(P).pin_memory()
-    uh = torch.from_numpy(np.ascontiguousarray(u)).pin_memory()
-    outPh = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(2)]
-    outuh = [torch.empty((d, N), dtype=torch.float64).pin_memory() for _ in range(2)]
-    Pd = [torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(2)]
-    ud = [torch.empty((d, N), dtype=torch.float64, device="cuda") for _ in range(2)]
-    oPd = [torch.empty(N, dtype=torch.float64, device="cuda") for _ in range(2)]
-    oud = [torch.empty((d, N), dtype=torch.float64, device="cuda") for _ in range(2)]
-    c_in, c_out = torch.cuda.Stream(), torch.cuda.Stream()
-    ev = {k: [torch.cuda.Event() for _ in range(2)] for k in ("in", "used", "out", "back")}
-
-    def upload(k):
-        b = k % 2
-        with torch.cuda.stream(c_in):
-            if k >= 2:
-                c_in.wait_event(ev["used"][b])  # step k - 2 has initialised from it
-            Pd[b].copy_(Ph, non_blocking=True)
-            ud[b].copy_(uh, non_blocking=True)
-            ev["in"][b].record(c_in)
-
+    Pn = torch.from_numpy(P).pin_memory().numpy()
+    un = torch.from_numpy(np.ascontiguousarray(u)).pin_memory().numpy()
+    outP = torch.empty(N, dtype=torch.float64).pin_memory().numpy()
+    outu = torch.empty((d, N), dtype=torch.float64).pin_memory().numpy()
+    lat.init(Pn, un)  # first host-path call: sizes the library's staging buffer
+    lat.fields_host(("P", "u"), out={"P": outP, "u": outu})
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     t0 = time.perf_counter()
-    upload(0)
     for k in range(e2e_steps):
-        b = k % 2
-        if k + 1 < e2e_steps:
-            upload(k + 1)
-        stream.wait_event(ev["in"][b])
-        lat.init(Pd[b], ud[b])
-        ev["used"][b].record(stream)
+        lat.init(Pn, un)
         bench_step()
-        if k >= 2:
-            stream.wait_event(ev["back"][b])  # step k - 2's result has left oPd[b]
-        lat.fields(("P", "u"), out={"P": oPd[b], "u": oud[b]})
-        ev["out"][b].record(stream)
-        with torch.cuda.stream(c_out):
-            c_out.wait_event(ev["out"][b])
-            outPh[b].copy_(oPd[b], non_blocking=True)
-            outuh[b].copy_(oud[b], non_blocking=True)
-            ev["back"][b].record(c_out)
-    torch.cuda.synchronize()
+        lat.fields_host(("P", "u"), out={"P": outP, "u": outu})
     e2e_s = time.perf_counter() - t0
-    outP, outu = outPh[(e2e_steps - 1) % 2].numpy(), outuh[(e2e_steps - 1) % 2].numpy()
     assert np.isfinite(outP).all() and np.isfinite(outu).all()
     e2e_value, _, _ = aggregate(e2e_steps * EPI_EVERY * N, e2e_s * 1e3, dist, device="cuda")
     lat.close()
@@ -445,6 +465,11 @@ def run_mdf(args):
     oerr = None
     if not args.no_oracle_check:
         oerr = sampled_oracle_error(shape, s1, P, u, args.storage, steps=64 if d == 2 else 16, q=args.q)
+    extra = None
+    if args.storage == "f32" and default_lattice and not args.no_extra_storage:
+        # the 16-bit arm of the same workload: equilibrium-shifted FP16
+        # populations with FP32 node moments
+        extra = storage_leg(shape, s1, P, u, "f16eq", oracle_check=not args.no_oracle_check)
     cpu = None
     if world == 1 and not args.no_cpu_baseline and args.workload == "tg2d" and default_lattice:
         cpu = cpu_oracle_sample()
@@ -475,12 +500,13 @@ def run_mdf(args):
                      "algorithmic_bytes_per_launch": bytes_per_launch,
                      "avg_launch_ms": plain_ms, "kernel_sha": sha},
         "fp64_oracle_error": oerr,
+        "storage_f16eq": extra,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "steps": e2e_steps,
                 "h2d_bytes_per_step": int(P.nbytes + u.nbytes),
                 "d2h_bytes_per_step": int(outP.nbytes + outu.nbytes),
-                "pipeline": "double-buffered copy streams: step k+1's upload and step k's "
-                            "read-back overlap the updates; timed on the host clock"},
+                "path": "C-ABI host buffers: mdf_init(MDF_HOST) from pinned memory, the step, "
+                        "mdf_fields(MDF_HOST) into pinned memory; serial, host clock"},
         "gpu_launches": args.steps * EPI_EVERY,
         "clocks": clocks,
     }
@@ -615,6 +641,8 @@ def main():
     ap.add_argument("--block", type=int, default=None, help="threads per block of the step kernel")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
+    ap.add_argument("--no-extra-storage", action="store_true",
+                    help="skip the FP16 equilibrium-shifted leg of the default line")
     ap.add_argument("--workload", choices=("tg2d", "tg3d", "cavities", "conv", "warmstart"),
                     default="tg2d",
                     help="tg2d: the 4096^2 D2Q5 x 3 line (default); tg3d: 512^3 D3Q7 x 4; "

@@ -248,10 +248,32 @@ mdf_status mdf_fields(mdf_t h, const mdf_fields_t *out);
  */
 mdf_status mdf_fields_host_noalloc(mdf_t h, const mdf_fields_t *out);
 
-/* mdf_moments -- P (Eq. 3-15), u (Eq. 2-7) and rho (nullable) on the device. */
+/*
+ * mdf_moments -- the macroscopic fields of the current state (no step taken):
+ *   P[N]     pressure, Eq. 3-15 with R = 0;
+ *   u[d][N]  velocity u_alpha = sum_i f_{i,alpha}, Eq. 2-7 (Eq. 2-7a under
+ *            Scheme II);
+ *   rho[N]   sum_i f_{i,0} of the alpha = 0 set, a diagnostic (nullable;
+ *            ignored when the set is not carried).
+ * Caller-owned DEVICE arrays of FP64, x-fastest, laid out as mdf_fields_t.
+ * The outputs are FP64 (not FP32) so that P, which sits near P0 = 1, keeps
+ * the digits of its O(U^2) fluctuation; the arithmetic is that of the
+ * storage type.  Stream-ordered on h's stream.  Same as mdf_fields with only
+ * these pointers set.  Errors: MDF_EINVAL for a null P or u.
+ */
 mdf_status mdf_moments(mdf_t h, double *P, double *u, double *rho);
 
-/* mdf_gradients -- Eq. 3-16 .. 3-19 on the device; each pointer nullable. */
+/*
+ * mdf_gradients -- the derived fields of Eq. 3-16 .. 3-19 from the first
+ * moment of f^ne = f - f^eq of the current state (no step taken):
+ *   G[d][d][N]  du_a/dx_b (Eq. 3-16), div[N] (Eq. 3-16a),
+ *   S[k][N]     strain rate (Eq. 3-17), sigma[k][N] viscous stress with
+ *               rho0 = 1 (Eq. 3-17a), k over the d(d+1)/2 pairs a <= b,
+ *   omega[.][N] vorticity (Eq. 3-18, 3-19): one component in 2D, three in 3D.
+ * Caller-owned DEVICE arrays of FP64 (see mdf_moments); each pointer is
+ * nullable, and at least one must be set (else MDF_EINVAL).
+ * Stream-ordered on h's stream; same as mdf_fields with these pointers set.
+ */
 mdf_status mdf_gradients(mdf_t h, double *G, double *div, double *S, double *sigma,
                          double *omega);
 

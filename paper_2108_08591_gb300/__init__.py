@@ -15,14 +15,9 @@ import numpy as np
 from . import _lib
 from ._lib import DEVICE, HOST, MdfError, STORAGE
 
-__all__ = ["Lattice", "Slabs", "CavityBatch", "MdfError", "FIELD_NAMES", "field_shapes", "s2_rule"]
+__all__ = ["Lattice", "Slabs", "CavityBatch", "MdfError", "FIELD_NAMES", "field_shapes"]
 
 FIELD_NAMES = ("P", "u", "rho", "G", "div", "S", "sigma", "omega")
-
-
-def s2_rule(s1: float) -> float:
-    """The paper's default s2 = 8(2 - s1)/(8 - s1) (Sec. 4.1)."""
-    return 8.0 * (2.0 - s1) / (8.0 - s1)
 
 
 def field_shapes(d: int, N: int) -> Dict[str, tuple]:
@@ -212,11 +207,19 @@ class Lattice:
         return out
 
     def moments(self):
-        o = self.fields(("P", "u", "rho") if self.with_rho else ("P", "u"))
+        """(P, u, rho) of the current state as CUDA tensors (mdf_moments);
+        rho is None without the alpha = 0 set."""
+        o = self.alloc_fields(("P", "u", "rho") if self.with_rho else ("P", "u"))
+        self._check(self._lib.mdf_moments(self._h, _ptr(o["P"]), _ptr(o["u"]), _ptr(o.get("rho"))))
         return o["P"], o["u"], o.get("rho")
 
     def gradients(self):
-        return self.fields(("G", "div", "S", "sigma", "omega"))
+        """G, div, S, sigma and omega of the current state as CUDA tensors
+        (mdf_gradients)."""
+        o = self.alloc_fields(("G", "div", "S", "sigma", "omega"))
+        self._check(self._lib.mdf_gradients(self._h, *(_ptr(o[k]) for k in
+                                                       ("G", "div", "S", "sigma", "omega"))))
+        return o
 
     def sums(self) -> np.ndarray:
         out = np.zeros(4)

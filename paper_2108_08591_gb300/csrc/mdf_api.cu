@@ -538,6 +538,8 @@ mdf_status mdf_fields(mdf_t h, const mdf_fields_t *out) {
 }
 
 mdf_status mdf_moments(mdf_t h, double *P, double *u, double *rho) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!P || !u) return fail(h, MDF_EINVAL, "moments: P and u are required");
   mdf_fields_t o{};
   o.P = P; o.u = u; o.rho = rho; o.where = MDF_DEVICE;
   return mdf_fields(h, &o);
@@ -545,6 +547,9 @@ mdf_status mdf_moments(mdf_t h, double *P, double *u, double *rho) {
 
 mdf_status mdf_gradients(mdf_t h, double *G, double *div, double *S, double *sigma,
                          double *omega) {
+  if (check_handle(h)) return MDF_EINVAL;
+  if (!G && !div && !S && !sigma && !omega)
+    return fail(h, MDF_EINVAL, "gradients: no output requested");
   mdf_fields_t o{};
   o.G = G; o.div = div; o.S = S; o.sigma = sigma; o.omega = omega; o.where = MDF_DEVICE;
   return mdf_fields(h, &o);

@@ -241,3 +241,37 @@ def test_nonequilibrium_seed_returns_the_seed_gradient(d, sides, Res):
         g0 = b.fields_host(c, ("G",))["G"]
         assert np.abs(g0).max() < 1e-5 * scale
     b.close()
+
+
+def test_divergence_step_matches_the_fp64_oracle():
+    """The seeded 65^2 draws above cell Re 8 blow up in the FP32 batch at the
+    same 100-step check as in the FP64 oracle, and the draws below the limit
+    stay bounded in both: the divergence belongs to the method at that cell
+    Reynolds number, not to the FP32 storage (Sec. 4.3 cavity, s2 rule of
+    Sec. 4.1)."""
+    import oracle as O
+    from paper_2108_08591_gb300 import CavityBatch
+    draws = synth.cavity_batch()
+    idx = [15, 18, 17, 22, 46]
+    sides = [draws[i][0] for i in idx]
+    Res = [draws[i][1] for i in idx]
+    assert set(sides) == {65}
+    cap = 6000
+    b = CavityBatch(sides, Res, lid_speed=U)
+    steps, status, _ = b.run(tol=1e-14, max_steps=cap, check_every=100)
+    b.close()
+    for c, (N, Re) in enumerate(zip(sides, Res)):
+        s1, s2 = _rates(N, Re)
+        pb = O.Problem(d=2, n=(N, N), s1=s1, s2=s2, wall=(1, 1, 0), lid=True, lid_u=(U, 0, 0))
+        f = O.init(pb, *synth.rest_state(N * N, 2))
+        ref = None
+        for k in range(100, cap + 1, 100):
+            O.run(pb, f, 100)
+            if not np.isfinite(f).all():
+                ref = k
+                break
+        if ref is None:
+            assert status[c] == 6 and steps[c] == cap, (c, Re, status[c], steps[c])
+        else:
+            assert status[c] == 4, (c, Re, status[c], steps[c], ref)
+            assert abs(int(steps[c]) - ref) <= 100, (c, Re, int(steps[c]), ref)

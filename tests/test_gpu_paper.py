@@ -60,6 +60,8 @@ def test_poiseuille_matches_paper(storage, rtol):
     y = (np.arange(N) + 0.5) * dx
     ua = np.repeat(F1 / (2 * nu) * (y - y * y), N) * dt / dx  # lattice velocity
     gy = np.repeat(F1 / (2 * nu) * (1 - 2 * y), N) * dt  # lattice du/dy (per node, per step)
+    print(storage, "E(u1)", _rel(ua, out["u"][0]), "E(G)", _rel(gy, out["G"][0, 1]),
+          "E(S)", _rel(gy / 2, out["S"][1]), "E(omega)", _rel(-gy, out["omega"][0]))
     assert _rel(ua, out["u"][0]) == pytest.approx(g["E_u1"], rel=rtol)
     floor = 1e-8 if storage == "f64" else 3e-2
     assert _rel(gy, out["G"][0, 1]) < floor
@@ -124,6 +126,8 @@ def test_scheme2_poiseuille_is_exact(storage):
     y = (np.arange(N) + 0.5) * dx
     ua = np.repeat(F1 / (2 * nu) * (y - y * y), N) * dt / dx
     gy = np.repeat(F1 / (2 * nu) * (1 - 2 * y), N) * dt
+    print(storage, "scheme II E(u1)", _rel(ua, out["u"][0]), "E(G)", _rel(gy, out["G"][0, 1]),
+          "E(S)", _rel(gy / 2, out["S"][1]))
     bound = 1e-8 if storage == "f64" else 1e-4
     assert _rel(ua, out["u"][0]) < bound
     floor = 1e-8 if storage == "f64" else 3e-2

@@ -7,10 +7,17 @@ P - mean(P)):
   * FP32 storage: u, P within 1e-5.  Derived fields within 1e-4: one FP32
     rounding of a shifted population (|g| ~ 3e-3, ulp ~ 2e-10) against the
     first moment of f^ne (~1e-4 .. 1e-5 at these sizes) gives ~1e-6 per node.
-  * FP16 storage: u within 2e-3.  The pressure fluctuation P' ~ U^2 is
-    carried by populations of size ~U, so rest-shifted FP16 resolves it only
-    to ~2e-3 .. 5e-3 relative: bound 5e-3.  BF16 (8-bit significand):
-    reported, u within 2e-2, P within 5e-2.
+  * Equilibrium-shifted FP16 / BF16 storage (the 16-bit storage the
+    contract names): u and P within 2e-3 (FP16: 1e-4 and 1e-3, below
+    that).  Derived fields are reported per field, with bounds of 1e-2
+    (FP16) and 5e-2 (BF16): the 16-bit rounding lands on f^ne itself, whose
+    first moment they are.
+  * Rest-shifted FP16 / BF16 storage: reported, no contract.  The pressure
+    fluctuation P' ~ U^2 is carried by populations of size ~U, which
+    rest-shifted 16-bit storage resolves only to ~2e-3 .. 5e-3 (FP16) or
+    ~5e-2 (BF16, 8-bit significand) relative.  The bounds below (FP16: u
+    2e-3, P 5e-3; BF16: u 2e-2, P 5e-2) guard against regressions; they are
+    not the 2e-3 contract, which this storage does not meet for P.
 Masks are compared byte for byte.
 """
 import os
@@ -39,10 +46,11 @@ def _built():
 
 
 def _tol(storage):
-    """(u, P - mean P, derived fields) bounds per storage type."""
+    """(u, P - mean P, derived fields) bounds per storage type; the
+    rest-shifted f16 / bf16 rows are reported, not the contract."""
     return {"f64": (1e-10, 1e-10, 1e-8), "f32": (1e-5, 1e-5, 1e-4),
             "f16": (2e-3, 5e-3, 5e-2), "bf16": (2e-2, 5e-2, 3e-1),
-            "f16eq": (1e-4, 1e-3, 1e-2), "bf16eq": (1e-3, 1e-2, 5e-2)}[storage]
+            "f16eq": (1e-4, 1e-3, 1e-2), "bf16eq": (1e-3, 2e-3, 5e-2)}[storage]
 
 
 # --------------------------------------------------------------------------
@@ -739,11 +747,73 @@ def test_zero_steps_and_graph_chunks():
 # --------------------------------------------------------------------------
 # Full size (4096^2, the benchmark's configuration): sampled parity
 # --------------------------------------------------------------------------
+def _sample_points(n, d, count, seed):
+    """Seeded nodes of an n^d lattice plus the nodes where the vector
+    kernels change path: the first and last nodes of a row, of a warp's x
+    span (32 threads x 1, 2 or 4 nodes) and of a block's (64 .. 256 threads),
+    each at a seeded position along the other axes."""
+    rng = synth.SplitMix64(seed)
+    xs = [x for x in (0, 1, 2, 3, 4, 7, 8, 31, 32, 63, 64, 127, 128, 255, 256, 511, 512, 1023,
+                      1024, n - 2, n - 1) if x < n]
+    pts = []
+    for x in sorted(set(xs)):
+        pts.append([x] + [rng.randint(0, n - 1) for _ in range(d - 1)])
+    pts.append([rng.randint(0, n - 1)] + [0] * (d - 1))
+    pts.append([rng.randint(0, n - 1)] + [n - 1] * (d - 1))
+    while len(pts) < count:
+        pts.append([rng.randint(0, n - 1) for _ in range(d)])
+    return pts
+
+
+def _flat(c, n):
+    return c[0] + n * (c[1] + (n * c[2] if len(c) == 3 else 0))
+
+
+def _gather(out, pts, n):
+    """Device fields at the sampled nodes only: {name: array[..., j]} for
+    point j (copying whole 512^3 fields to the host would take minutes)."""
+    import torch
+    idx = torch.tensor([_flat(c, n) for c in pts], dtype=torch.long, device="cuda")
+    return {k: v.index_select(v.dim() - 1, idx).cpu().numpy() for k, v in out.items()}
+
+
+def _sampled_window_errors(shape, s1, P, u, got, steps, pts):
+    """Relative L2 of u, P - 1, G, S and omega on the given nodes of a
+    periodic lattice, against the FP64 oracle on (2 steps + 1)^d windows
+    (after `steps` updates a node depends only on nodes within that many
+    links).  got: fields gathered at pts (column j = point j)."""
+    d = len(shape)
+    n = shape[0]
+    W = 2 * steps + 1
+    offs = np.arange(-steps, steps + 1)
+    keys = ("u", "P", "G", "S", "omega")
+    ref = {k: [] for k in keys}
+    num = {k: [] for k in keys}
+    for g, c in enumerate(pts):
+        axes = [(c[b] + offs) % n for b in range(d)]
+        if d == 2:
+            sel = (axes[1][:, None] * n + axes[0][None, :]).ravel()
+        else:
+            sel = ((axes[2][:, None, None] * n + axes[1][None, :, None]) * n + axes[0][None, None, :]).ravel()
+        pb = O.Problem(d=d, n=(W,) * d, s1=s1)
+        f = O.run(pb, O.init(pb, P[sel], u[:, sel]), steps)
+        Pr, ur, _ = O.macro(pb, f)
+        D = O.derived(pb, f)
+        mid = (W ** d) // 2
+        ref["u"].append(ur[:, mid]); num["u"].append(got["u"][:, g])
+        ref["P"].append(Pr[mid] - 1.0); num["P"].append(got["P"][g] - 1.0)
+        for k in ("G", "S", "omega"):
+            ref[k].append(D[k][..., mid]); num[k].append(got[k][..., g])
+    return {k: rel(np.array(ref[k]), np.array(num[k])) for k in keys}
+
+
 def test_full_size_4096_sampled_parity():
     """4096^2 D2Q5 x 3, FP32 storage, Taylor-Green + 8 modes, run as the
-    benchmark runs it (fused epilogue update, then graph chunks).  After n
-    steps a node depends only on nodes within distance n, so the oracle runs
-    a periodic (2n+1)^2 window around each sampled node."""
+    benchmark runs it (fused epilogue update, then graph chunks), compared
+    with the FP64 oracle at 64 nodes, including every row, warp and block
+    edge of the vector kernel.  After n steps a node depends only on nodes
+    within distance n, so the oracle runs a periodic (2n+1)^2 window around
+    each sampled node."""
     import torch
     from paper_2108_08591_gb300 import Lattice
     n, steps = 4096, 71
@@ -752,7 +822,7 @@ def test_full_size_4096_sampled_parity():
     lat.init(P, u)
     fl = lat.alloc_fields(("P", "u", "G", "div"))
     lat.step_fields(steps, fl)
-    out = lat.fields(("P", "u", "G", "omega", "div"))
+    out = lat.fields(("P", "u", "G", "S", "omega", "div"))
     torch.cuda.synchronize()
     # fields of the initial state from the fused update: f = f^eq there, so
     # f^ne and every gradient vanish up to FP32 storage rounding (~1e-9
@@ -761,86 +831,47 @@ def test_full_size_4096_sampled_parity():
     assert np.abs(fl["div"].cpu().numpy()).max() < 1e-8
     # after 71 updates: divergence identity (exact in exact arithmetic; FP32
     # epilogue arithmetic leaves a few 1e-6 of |G|)
-    got = {k: v.cpu().numpy() for k, v in out.items()}
-    assert np.abs(got["G"]).max() > 1e-6
-    assert np.abs(got["div"]).max() < 5e-5 * np.abs(got["G"]).max()
+    gmax = float(out["G"].abs().max())
+    assert gmax > 1e-6
+    assert float(out["div"].abs().max()) < 5e-5 * gmax
+    pts = _sample_points(n, 2, 64, 77)
+    got = _gather(out, pts, n)
     lat.close()
-    rng = synth.SplitMix64(77)
-    pts = [(rng.randint(0, n - 1), rng.randint(0, n - 1)) for _ in range(12)] + [(0, 0), (n - 1, n - 1)]
-    half = steps
-    ref_u, got_u, ref_P, got_P, ref_w, got_w = [], [], [], [], [], []
-    for cx, cy in pts:
-        Pw, uw = synth.window(n, [P, u], cx, cy, half)
-        W = 2 * half + 1
-        pb = O.Problem(d=2, n=(W, W), s1=S1_TG)
-        f = O.init(pb, Pw, uw)
-        O.run(pb, f, steps)
-        c = half * W + half
-        Pr, ur, _ = O.macro(pb, f)
-        D = O.derived(pb, f)
-        g = cy * n + cx
-        ref_u.append(ur[:, c]); got_u.append(got["u"][:, g])
-        ref_P.append(Pr[c] - 1.0); got_P.append(got["P"][g] - 1.0)
-        ref_w.append(D["omega"][0, c]); got_w.append(got["omega"][0, g])
-    assert rel(np.array(ref_u), np.array(got_u)) < 1e-5
-    assert rel(np.array(ref_P), np.array(got_P)) < 1e-5
-    assert rel(np.array(ref_w), np.array(got_w)) < 1e-3
+    e = _sampled_window_errors((n, n), S1_TG, P, u, got, steps, pts)
+    print("4096^2 f32", e)
+    assert e["u"] < 1e-5 and e["P"] < 1e-5, e
+    assert e["G"] < 1e-3 and e["S"] < 1e-3 and e["omega"] < 1e-3, e
 
 
-def _sampled_window_errors(shape, s1, P, u, got, steps, samples, seed):
-    """Relative L2 of u, P - 1 and omega on sampled nodes of a periodic
-    lattice, against the FP64 oracle on (2 steps + 1)^d windows (after
-    `steps` updates a node depends only on nodes within that many links)."""
-    d = len(shape)
-    n = shape[0]
-    rng = synth.SplitMix64(seed)
-    W = 2 * steps + 1
-    offs = np.arange(-steps, steps + 1)
-    ref = {"u": [], "P": [], "omega": []}
-    num = {"u": [], "P": [], "omega": []}
-    for _ in range(samples):
-        c = [rng.randint(0, n - 1) for _ in range(d)]
-        axes = [(c[b] + offs) % n for b in range(d)]
-        if d == 2:
-            sel = (axes[1][:, None] * n + axes[0][None, :]).ravel()
-            g = c[1] * n + c[0]
-        else:
-            sel = ((axes[2][:, None, None] * n + axes[1][None, :, None]) * n + axes[0][None, None, :]).ravel()
-            g = (c[2] * n + c[1]) * n + c[0]
-        pb = O.Problem(d=d, n=(W,) * d, s1=s1)
-        f = O.run(pb, O.init(pb, P[sel], u[:, sel]), steps)
-        Pr, ur, _ = O.macro(pb, f)
-        D = O.derived(pb, f)
-        mid = (W ** d) // 2
-        ref["u"].append(ur[:, mid]); num["u"].append(got["u"][:, g])
-        ref["P"].append(Pr[mid] - 1.0); num["P"].append(got["P"][g] - 1.0)
-        ref["omega"].append(D["omega"][:, mid]); num["omega"].append(got["omega"][:, g])
-    return {k: rel(np.array(ref[k]), np.array(num[k])) for k in ref}
-
-
-@pytest.mark.parametrize("storage,tol", [("f16eq", (2e-3, 2e-3, 1e-2)), ("bf16eq", (2e-3, 1e-2, 5e-2))])
+@pytest.mark.parametrize("storage,tol", [("f16eq", (2e-3, 2e-3, 1e-2)), ("bf16eq", (2e-3, 2e-3, 5e-2))])
 def test_full_size_4096_equilibrium_shifted_sampled_parity(storage, tol):
     """The 4096^2 workload with equilibrium-shifted 16-bit storage, in the
-    benchmark's launch configuration (2 nodes per thread, 64 threads), at
-    sampled nodes: u within the 2e-3 bound on 16-bit storage."""
+    benchmark's launch configuration, at 64 sampled nodes including the
+    vector kernel's edges: u and P - mean P within the 2e-3 bound on 16-bit
+    storage; G, S and omega reported per field."""
     from paper_2108_08591_gb300 import Lattice
     n, steps = 4096, 40
     P, u = synth.tg_plus_modes(n, U0=0.01, seed=2108)
     lat = Lattice((n, n), s1=S1_TG, storage=storage)
-    assert (lat.info.vx, lat.info.block) == (2, 64)
     lat.init(P, u)
     lat.step(steps)
-    got = {k: v.cpu().numpy() for k, v in lat.fields(("P", "u", "omega")).items()}
+    pts = _sample_points(n, 2, 64, 91)
+    got = _gather(lat.fields(("P", "u", "G", "S", "omega")), pts, n)
     lat.close()
-    e = _sampled_window_errors((n, n), S1_TG, P, u, got, steps, 8, 91)
-    assert e["u"] < tol[0] and e["P"] < tol[1] and e["omega"] < tol[2], e
+    e = _sampled_window_errors((n, n), S1_TG, P, u, got, steps, pts)
+    print("4096^2", storage, e)
+    assert e["u"] < tol[0] and e["P"] < tol[1], e
+    assert e["G"] < tol[2] and e["S"] < tol[2] and e["omega"] < tol[2], e
 
 
-@pytest.mark.parametrize("storage,tol", [("f32", (1e-5, 1e-4, 1e-3)), ("f16", (2e-3, 2e-2, 0.5))])
+@pytest.mark.parametrize("storage,tol", [("f32", (1e-5, 1e-5, 1e-3)), ("f16eq", (2e-3, 2e-3, 1e-2)),
+                                         ("f16", (2e-3, 2e-2, 0.5))])
 def test_full_size_512_cubed_sampled_parity(storage, tol):
     """512^3 D3Q7 x 4 3D Taylor-Green (U0 = 0.05, Re = 1600), in the
-    benchmark's launch configuration (FP32: one node per thread; FP16: 4
-    nodes per thread, populations packed in registers), at sampled nodes."""
+    benchmark's launch configuration, at 48 sampled nodes including the
+    vector kernels' edges.  FP32 and equilibrium-shifted FP16 are held to
+    the contract on u and P; the rest-shifted FP16 row is reported, not the
+    contract (its P and gradient bounds only guard against regressions)."""
     from paper_2108_08591_gb300 import Lattice
     n, steps = 512, 12
     k = 2 * np.pi / n
@@ -850,10 +881,13 @@ def test_full_size_512_cubed_sampled_parity(storage, tol):
     lat = Lattice((n, n, n), s1=s1, storage=storage)
     lat.init(P, u)
     lat.step(steps)
-    got = {k_: v.cpu().numpy() for k_, v in lat.fields(("P", "u", "omega")).items()}
+    pts = _sample_points(n, 3, 48, 93)
+    got = _gather(lat.fields(("P", "u", "G", "S", "omega")), pts, n)
     lat.close()
-    e = _sampled_window_errors((n, n, n), s1, P, u, got, steps, 6, 93)
-    assert e["u"] < tol[0] and e["P"] < tol[1] and e["omega"] < tol[2], e
+    e = _sampled_window_errors((n, n, n), s1, P, u, got, steps, pts)
+    print("512^3", storage, e)
+    assert e["u"] < tol[0] and e["P"] < tol[1], e
+    assert e["G"] < tol[2] and e["omega"] < tol[2], e
 
 
 # --------------------------------------------------------------------------

@@ -31,11 +31,16 @@ def _built():
     _build.build()
 
 
-@pytest.mark.parametrize("shape,storage", [((96, 70), "f32"), ((24, 18, 14), "f64")])
-def test_noalloc_readback_matches_fields_on_two_calls(shape, storage):
+@pytest.mark.parametrize("shape,storage,inplace", [
+    ((96, 70), "f32", False), ((24, 18, 14), "f64", False),
+    # equilibrium-shifted storage: the node moments travel with the populations
+    ((96, 70), "f16eq", False), ((24, 18, 14), "bf16eq", False),
+    # in-place AA stream: the layout parity of the state changes every update
+    ((96, 70), "f32", True), ((24, 18, 14), "f16", True)])
+def test_noalloc_readback_matches_fields_on_two_calls(shape, storage, inplace):
     from paper_2108_08591_gb300 import Lattice
     P, u = synth.smooth_fields(shape, seed=31)
-    lat = Lattice(shape, s1=1.45, storage=storage)
+    lat = Lattice(shape, s1=1.45, storage=storage, inplace=inplace)
     try:
         lat.init(P, u)
         lat.step(17)
@@ -63,11 +68,13 @@ def test_noalloc_rejects_requests_beyond_the_static_buffer():
         lat.init(P, u)
         with pytest.raises(MdfError, match="EINVAL.*static staging buffer"):
             lat.fields_host_noalloc(NAMES)
-        # a request that fits still works: P and u are 3 doubles per node
-        small = Lattice((512, 512), s1=1.2)
+    finally:
+        lat.close()
+    # a request that fits still works: P and u are 3 doubles per node
+    small = Lattice((512, 512), s1=1.2)
+    try:
         small.init(*synth.rest_state(512 * 512, 2))
         out = small.fields_host_noalloc(("P", "u"))
         assert np.allclose(out["P"], 1.0, atol=1e-7) and np.abs(out["u"]).max() < 1e-7
-        small.close()
     finally:
-        lat.close()
+        small.close()
