@@ -45,6 +45,12 @@ WORKLOAD = ("2D Taylor-Green + 8 seeded divergence-free modes (seed 2108), perio
 # the 3D case (--workload tg3d): Taylor-Green vortex, 512^3, D3Q7 x 4 sets,
 # U0 = 0.05, Re = 1600 on U0 and k = 2 pi / 512, epilogue every 200 steps
 TG3D_U0, TG3D_RE = 0.05, 1600.0
+# s2 of the 3D case: the paper's rule 8(2 - s1)/(8 - s1) (Sec. 4.1) gives
+# 0.053 at that s1 = 1.960, which leaves D3Q7 linearly unstable at the flow's
+# speeds (the run blows up within 400 steps); s2 = 1 is stable and leaves the
+# viscosity (set by s1, Eq. 3-13a) unchanged.  The 2D case keeps the rule.
+TG3D_S2 = 1.0
+S2 = -1.0  # the workload's s2 (negative: the paper's rule); set in main()
 KERNEL_SOURCES = ("paper_2108_08591_gb300/csrc/mdf_kernels.cuh",
                   "paper_2108_08591_gb300/csrc/mdf_lattice.cuh")
 
@@ -260,6 +266,7 @@ def _workload(args):
 
 
 def sampled_oracle_error(shape, s1, P, u, storage, steps, samples=8, seed=77, q=0):
+    s2 = S2
     """FP64 oracle error of the GPU fields at full size, on sampled nodes.
 
     After `steps` updates a node depends only on nodes within that many
@@ -271,7 +278,7 @@ def sampled_oracle_error(shape, s1, P, u, storage, steps, samples=8, seed=77, q=
     import synth
     from paper_2108_08591_gb300 import Lattice
     d = len(shape)
-    lat = Lattice(shape, s1=s1, storage=storage, q=q)
+    lat = Lattice(shape, s1=s1, s2=s2, storage=storage, q=q)
     lat.init(P, u)
     fl = lat.alloc_fields(("P",))
     lat.step_fields(steps, fl)
@@ -293,7 +300,7 @@ def sampled_oracle_error(shape, s1, P, u, storage, steps, samples=8, seed=77, q=
             sel = ((axes[2][:, None, None] * n + axes[1][None, :, None]) * n
                    + axes[0][None, None, :]).ravel()
             g = (c[2] * n + c[1]) * n + c[0]
-        pb = oracle.Problem(d=d, n=(W,) * d, s1=s1, nq=q)
+        pb = oracle.Problem(d=d, n=(W,) * d, s1=s1, s2=None if s2 < 0 else s2, nq=q)
         f = oracle.init(pb, P[sel], u[:, sel])
         oracle.run(pb, f, steps)
         Pr, ur, _ = oracle.macro(pb, f)
@@ -321,7 +328,7 @@ def storage_leg(shape, s1, P, u, storage, steps=5, warmup=3, q=0, oracle_check=T
     from paper_2108_08591_gb300 import Lattice
     N = int(np.prod(shape))
     stream = torch.cuda.current_stream()
-    lat = Lattice(shape, s1=s1, storage=storage, stream=stream, q=q)
+    lat = Lattice(shape, s1=s1, s2=S2, storage=storage, stream=stream, q=q)
     lat.init(P, u)
     info = lat.info
     fields = lat.alloc_fields(("P", "u", "G", "div", "S", "sigma", "omega"))
@@ -381,7 +388,7 @@ def run_mdf(args):
     d = len(shape)
     N = int(np.prod(shape))
     stream = torch.cuda.current_stream()
-    lat = Lattice(shape, s1=s1, storage=args.storage, stream=stream, vx=args.vx or 0,
+    lat = Lattice(shape, s1=s1, s2=S2, storage=args.storage, stream=stream, vx=args.vx or 0,
                   block=args.block or 0, q=args.q, inplace=args.inplace)
     lat.init(P, u)
     info = lat.info
@@ -661,11 +668,11 @@ def main():
     ap.add_argument("--grid", type=int, default=4096,
                     help="lattice side (default 4096; smaller sides are profiling cases)")
     args = ap.parse_args()
-    global N_GRID, WORKLOAD, EPI_EVERY
+    global N_GRID, WORKLOAD, EPI_EVERY, S2
     if args.workload == "tg3d":
-        N_GRID, EPI_EVERY = 512, 200
+        N_GRID, EPI_EVERY, S2 = 512, 200, TG3D_S2
         WORKLOAD = (f"3D Taylor-Green vortex, periodic 512^3, D3Q7 x 4 sets, U0 = {TG3D_U0}, "
-                    f"Re = {TG3D_RE:.0f}, FP32 rest-shifted storage, FP32 "
+                    f"Re = {TG3D_RE:.0f}, s2 = {TG3D_S2:g}, FP32 rest-shifted storage, FP32 "
                     "arithmetic, epilogue every 200 steps")
     if args.grid != 4096:
         WORKLOAD = WORKLOAD.replace(f"{N_GRID}x{N_GRID}", f"{args.grid}x{args.grid}").replace(

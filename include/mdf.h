@@ -85,8 +85,11 @@ typedef struct {
     int vx;                  /* x-nodes per thread of the update kernel: 0 = tuned
                                 default; 1 = one node per thread; 2, 4, 8 = vector
                                 widths (FP32: 2, 4; FP16/BF16: 4, 8; FP64: 2;
-                                *EQ: 2, 4).  A width that does not divide nx falls
-                                back to 1. */
+                                *EQ: 2, 4).  In 3D, where wider kernels spill
+                                registers, requests are clamped to 4 (rest-shifted
+                                16-bit, FP32 pull) or 2 (in-place FP32, *EQ);
+                                mdf_info reports the width in use.  A width that
+                                does not divide nx falls back to 1. */
     int block;               /* threads per block of the update kernel: 0 = tuned
                                 default, else a multiple of 32 in [32, 256] */
     int q;                   /* directions per set: 0 = D2Q5 / D3Q7 (default), 4 = D2Q4,

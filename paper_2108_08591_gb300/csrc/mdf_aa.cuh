@@ -128,8 +128,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_aa(const DevArgs A) {
   }
 
   TC M[D + 2];
-  if (A.scheme2) collide_node<L, TC, true>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M);
-  else collide_node<L, TC, false>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M);
+  constexpr bool DZ = dithered<TS>();
+  uint32_t key = 0u;
+  if constexpr (DZ) key = node_key(A.key_base + ((long long)z * A.ny + y) * A.nx + x, launch_step(A));
+  if (A.scheme2) collide_node<L, TC, true, DZ>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M, key);
+  else collide_node<L, TC, false, DZ>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M, key);
 
 #pragma unroll
   for (int a = 0; a < D; ++a)
@@ -423,6 +426,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_aa_vec(const DevArgs A) {
     }
   }
   const TC s1 = TC(A.s1), s2 = TC(A.s2);
+  constexpr bool DZ = dithered<TS>();
+  const int tstep = DZ ? launch_step(A) : 0;
+  const long long n0 = ((long long)z * A.ny + y) * A.nx + x0;
 #pragma unroll
   for (int j = 0; j < VX; ++j) {
     TC gn[D][Q], hn[Q], Fn[D];
@@ -435,7 +441,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_aa_vec(const DevArgs A) {
 #pragma unroll
     for (int a = 0; a < D; ++a) Fn[a] = F[a][j];
     TC M[D + 2];
-    collide_node<L, TC, S2>(gn, hn, A.with_rho != 0, Fn, s1, s2, M);
+    const uint32_t key = DZ ? node_key(A.key_base + n0 + j, tstep) : 0u;
+    collide_node<L, TC, S2, DZ>(gn, hn, A.with_rho != 0, Fn, s1, s2, M, key);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
 #pragma unroll
@@ -731,17 +738,22 @@ cudaError_t update_aa_vec(bool walls, const DevArgs &a, cudaStream_t s) {
 }
 
 // Plain updates with a width built for the storage type that divides nx
-// run the vector kernel (FP32 2 or 4, 16-bit 4 or 8, FP64 2); everything
-// else, and every field-writing update, runs one node per thread.
+// run the vector kernel (FP32 2 or 4, 16-bit 4 or 8, FP64 2; in 3D, where
+// the wider ones spill registers, FP32 2 and 16-bit 4); everything else,
+// and every field-writing update, runs one node per thread.
 template <class L, class TS>
 cudaError_t update_aa_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
   const bool ok = mode == MODE_STEP && a.vx > 1 && a.nx % a.vx == 0 && a.plane < (1LL << 31) - 64;
   if (ok) {
     if constexpr (sizeof(TS) == 4) {
-      if (a.vx == 4) return update_aa_vec<L, TS, 4>(walls, a, s);
+      if constexpr (L::D == 2) {
+        if (a.vx == 4) return update_aa_vec<L, TS, 4>(walls, a, s);
+      }
       if (a.vx == 2) return update_aa_vec<L, TS, 2>(walls, a, s);
     } else if constexpr (sizeof(TS) == 2) {
-      if (a.vx == 8) return update_aa_vec<L, TS, 8>(walls, a, s);
+      if constexpr (L::D == 2) {
+        if (a.vx == 8) return update_aa_vec<L, TS, 8>(walls, a, s);
+      }
       if (a.vx == 4) return update_aa_vec<L, TS, 4>(walls, a, s);
     } else {
       if (a.vx == 2) return update_aa_vec<L, TS, 2>(walls, a, s);

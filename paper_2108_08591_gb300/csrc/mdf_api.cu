@@ -4,6 +4,7 @@
 // kernels of mdf_kernels.cuh; this file only marshals and sequences.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -49,6 +50,15 @@ bool eq_storage(int st) { return st == MDF_F16EQ || st == MDF_BF16EQ; }
 //   Equilibrium-shifted 16-bit: 2 nodes per thread (one FP32 pair), 64
 //       threads in 2D (5.43 TB/s) and 128 in 3D (5.39 TB/s).
 // mdf_autotune() measures the candidates for a given handle instead.
+// Widest vector kernel built for a lattice (wider requests are clamped to
+// it): 8 for 2D 16-bit, 4 otherwise; in 3D, where the wider kernels spill
+// registers, 4 for rest-shifted 16-bit and 2 for in-place FP32 and the
+// equilibrium-shifted codecs.
+int max_vx(int d, int storage, bool inplace) {
+  const bool s16 = storage == MDF_F16 || storage == MDF_BF16;
+  if (d == 2) return s16 ? 8 : 4;
+  return ((inplace && storage == MDF_F32) || eq_storage(storage)) ? 2 : 4;
+}
 int default_vx(int d, int storage) {
   if (eq_storage(storage)) return 2;
   if (d == 3) return (storage == MDF_F16 || storage == MDF_BF16) ? 4 : 1;
@@ -95,6 +105,8 @@ struct mdf_s {
   double *partials = nullptr, *result = nullptr;
   int *nonfinite = nullptr;
   long long step = 0;
+  int *clock = nullptr;     // device copy of `step` for the dither draws of a launch group
+  long long key_base = 0;   // global index of local node 0 (slabs of a larger lattice)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};  // chunk starting from buffer 0 / 1
   void *buf[2] = {nullptr, nullptr};
   bool inplace = false;  // one buffer, AA pattern (buf[1] unused)
@@ -150,6 +162,9 @@ DevArgs base_args(const mdf_t h) {
   a.result = h->result;
   a.nonfinite = h->nonfinite;
   a.uprev = h->uprev;
+  a.clock = h->clock;
+  a.tk = 0;
+  a.key_base = h->key_base;
   return a;
 }
 
@@ -183,6 +198,7 @@ mdf_status one_update(mdf_t h, int mode, const mdf_fields_t *out) {
     a.P = out->P; a.u = out->u; a.rho = out->rho; a.G = out->G; a.div = out->div;
     a.S = out->S; a.sigma = out->sigma; a.omega = out->omega;
   }
+  if (mode != MODE_FIELDS) CU(h, launch_set_clock(h->clock, (int)h->step, h->stream));
   CU(h, launch_update(h, mode, a));
   if (mode != MODE_FIELDS) {
     if (h->inplace) h->parity ^= 1;
@@ -207,7 +223,9 @@ mdf_status build_graph(mdf_t h, int which) {
   cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     for (int k = 0; k < kGraphChunk && e == cudaSuccess; ++k) {
-      e = launch_update(h, MODE_STEP, base_args(h));
+      DevArgs a = base_args(h);
+      a.tk = k;  // the step is *clock + k; the clock is set before each replay
+      e = launch_update(h, MODE_STEP, a);
       if (h->inplace) h->parity ^= 1;
       else std::swap(h->cur, h->nxt);
     }
@@ -237,14 +255,20 @@ mdf_status run_steps(mdf_t h, long long n) {
       mdf_status st = build_graph(h, which);
       if (st != MDF_OK) return st;
     }
+    CU(h, launch_set_clock(h->clock, (int)h->step, h->stream));
     CU(h, cudaGraphLaunch(h->graph[which], h->stream));
     n -= kGraphChunk;  // even chunk: cur/nxt end where they started
     h->step += kGraphChunk;
   }
-  for (; n > 0; --n) {
-    mdf_status st = one_update(h, MODE_STEP, nullptr);
-    if (st != MDF_OK) return st;
+  if (n > 0) CU(h, launch_set_clock(h->clock, (int)h->step, h->stream));
+  for (int k = 0; k < n; ++k) {
+    DevArgs a = base_args(h);
+    a.tk = k;
+    CU(h, launch_update(h, MODE_STEP, a));
+    if (h->inplace) h->parity ^= 1;
+    else std::swap(h->cur, h->nxt);
   }
+  h->step += n;
   return MDF_OK;
 }
 
@@ -347,6 +371,7 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
   }
   h->block = opts.block ? opts.block : (h->inplace ? default_block_aa(d, h->storage) : default_block(d, h->storage));
   h->vx = opts.vx ? opts.vx : (h->inplace ? default_vx_aa(d, h->storage) : default_vx(d, h->storage));
+  h->vx = std::min(h->vx, max_vx(d, h->storage, h->inplace));
 
   const size_t pb = h->pop_bytes();
   cudaError_t e = cudaMalloc(&h->buf[0], pb);
@@ -354,6 +379,8 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, sizeof(double) * kReduceBlocks * 4);
   if (e == cudaSuccess) e = cudaMalloc(&h->result, sizeof(double) * 4);
   if (e == cudaSuccess) e = cudaMalloc(&h->nonfinite, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->clock, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(h->clock, 0, sizeof(int), h->stream);
   if (e == cudaSuccess && h->walls) e = cudaMalloc(&h->mask, (size_t)h->plane);
   if (e == cudaSuccess && h->kmom) e = cudaMalloc(&h->mac[0], h->mom_bytes());
   if (e == cudaSuccess && h->kmom) e = cudaMalloc(&h->mac[1], h->mom_bytes());
@@ -389,7 +416,7 @@ void mdf_destroy(mdf_t h) {
   cudaFree(h->buf[0]); cudaFree(h->buf[1]); cudaFree(h->mask); cudaFree(h->force);
   cudaFree(h->mac[0]); cudaFree(h->mac[1]);
   cudaFree(h->stage); cudaFree(h->uprev); cudaFree(h->partials); cudaFree(h->result);
-  cudaFree(h->nonfinite);
+  cudaFree(h->nonfinite); cudaFree(h->clock);
   delete h;
 }
 
@@ -706,7 +733,7 @@ mdf_status mdf_autotune(mdf_t h, int reps, int *vx_out, int *block_out) {
   // by MDF_F32, F16, BF16, F64, F16EQ, BF16EQ
   const int built[6][2] = {{2, 4}, {4, 8}, {4, 8}, {2, 2}, {2, 4}, {2, 4}};
   for (int k = 0; k < 2; ++k) {
-    const int v = built[h->storage][k];
+    const int v = std::min(built[h->storage][k], max_vx(h->d, h->storage, false));
     bool dup = false;
     for (int j = 0; j < nw; ++j) dup |= widths[j] == v;
     if (!dup && h->nx % v == 0) widths[nw++] = v;
@@ -959,6 +986,9 @@ mdf_status mdf_slabs_create(mdf_slabs_t *out, const mdf_grid *g, int d, const md
       mdf_slabs_destroy(S);
       return st;
     }
+    // global index of local node 0: local layer 1 is global layer s nloc
+    const long long L = d == 2 ? (long long)g->nx : (long long)g->nx * g->ny;
+    h->key_base = ((long long)s * S->nloc - 1) * L;
     S->h.push_back(h);
   }
   *out = S;

@@ -63,6 +63,7 @@ struct BatchArgs {
   int *err;                 // MDF_ETIMEOUT on a barrier or neighbour-wait time-out
   long long timeout;        // barrier spin limit in clock cycles
   int *prog;                // [ntiles] steps completed in the current launch (schedule 2)
+  int *clock;               // steps since the batch was seeded (dither draws of FP32 rounding)
 };
 
 // Bounded grid-wide barrier for a cooperative launch: the last block to
@@ -213,16 +214,18 @@ __device__ __forceinline__ void publish_tile(const BatchArgs &B, int tile, int d
   }
 }
 
-// One update of local node k of cavity C: pull from fin, collide, store to
-// fout; with save, also store the velocity it pulled (for the residual).
+// One update of local node k of cavity C at time step t: pull from fin,
+// collide (dithered FP32 rounding, drawn from the node's index in its own
+// cavity and t, as a single lattice of that cavity draws), store to fout;
+// with save, also store the velocity it pulled (for the residual).
 template <class L>
 __device__ __forceinline__ void batch_update_node(const BatchArgs &B, const float *fin, float *fout,
-                                                  const CavParam &C, int k, bool save) {
+                                                  const CavParam &C, int k, bool save, int t) {
   constexpr int D = L::D, Q = L::Q;
   float g[D][Q], h[Q], F[D] = {}, M[D + 2];
   long long idx;
   batch_pull<L>(B, fin, C, k, g, h, idx);
-  collide_node<L, float>(g, h, B.with_rho != 0, F, C.s1, C.s2, M);
+  collide_node<L, float, false, true>(g, h, B.with_rho != 0, F, C.s1, C.s2, M, node_key(k, t));
   if (save)
 #pragma unroll
     for (int a = 0; a < D; ++a) B.usave[a * B.tot + idx] = M[a];
@@ -255,6 +258,7 @@ __global__ void __launch_bounds__(T) k_batch_chunk(BatchArgs B, int cur, int ste
   const int t0 = SCHED != 1 ? (int)blockIdx.x : (int)((long long)nl * blockIdx.x / gridDim.x);
   const int t1 = SCHED != 1 ? nl : (int)((long long)nl * (blockIdx.x + 1) / gridDim.x);
   const int dt = SCHED != 1 ? (int)gridDim.x : 1;
+  const int tclock = __ldg(B.clock);
   for (int s = 0; s < steps; ++s) {
     const float *fin = B.f[(cur + s) & 1];
     float *fout = B.f[(cur + s + 1) & 1];
@@ -267,7 +271,7 @@ __global__ void __launch_bounds__(T) k_batch_chunk(BatchArgs B, int cur, int ste
 #pragma unroll
       for (int r = 0; r < PER; ++r) {
         const int k = (tile - C.tile0) * kTile + r * T + (int)threadIdx.x;
-        if (k < count) batch_update_node<L>(B, fin, fout, C, k, save);
+        if (k < count) batch_update_node<L>(B, fin, fout, C, k, save, tclock + s);
       }
       if (SCHED == 2) publish_tile(B, tile, s + 1);
     }
@@ -318,6 +322,9 @@ __global__ void __launch_bounds__(kTile) k_batch_residual(BatchArgs B, int cur) 
   }
   if (threadIdx.x == 0) B.badtile[tile] = anybad;
 }
+
+// Advances the batch's step counter by the steps of the chunk just run.
+__global__ void k_batch_tick(int *clock, int steps) { *clock += steps; }
 
 // Per cavity: residual from its tiles' partials (fixed order), step count,
 // status.  One block per cavity.
@@ -598,6 +605,7 @@ template <class L>
 cudaError_t enqueue_period(mdf_batch_t b, int period, double tol, long long max_steps) {
   cudaError_t e = launch_chunk<L>(b, period, 1);
   if (e != cudaSuccess) return e;
+  k_batch_tick<<<1, 1, 0, b->stream>>>(b->B.clock, period);
   const int cur_after = (b->cur + period) & 1;
   k_batch_residual<L><<<b->ntiles, kTile, 0, b->stream>>>(b->B, cur_after);
   k_batch_status<<<b->ncav, 32, 0, b->stream>>>(b->B, period, tol, max_steps);
@@ -691,6 +699,8 @@ mdf_status mdf_batch_create(mdf_batch_t *out, int d, int n, const int *side, con
   if (e == cudaSuccess) e = cudaMalloc(&B.res, sizeof(double) * n);
   if (e == cudaSuccess) e = cudaMalloc(&B.bar, sizeof(unsigned int) * 2);
   if (e == cudaSuccess) e = cudaMalloc(&B.err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&B.clock, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.clock, 0, sizeof(int), b->stream);
   if (e == cudaSuccess) e = cudaMallocHost(&b->host_live, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(B.f[0], 0, popb, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(B.f[1], 0, popb, b->stream);
@@ -723,7 +733,7 @@ void mdf_batch_destroy(mdf_batch_t b) {
   cudaFree(B.f[0]); cudaFree(B.f[1]); cudaFree((void *)B.cav); cudaFree((void *)B.tile_cav);
   cudaFree(B.live); cudaFree(B.n_live); cudaFree(B.usave); cudaFree(B.part); cudaFree(B.badtile);
   cudaFree(B.status); cudaFree(B.steps); cudaFree(B.res); cudaFree(B.bar); cudaFree(B.err);
-  cudaFree(B.prog);
+  cudaFree(B.prog); cudaFree(B.clock);
   cudaFreeHost(b->host_live);
   delete b;
 }
@@ -738,6 +748,8 @@ mdf_status mdf_batch_seed(mdf_batch_t b, int cavity, const double *P, const doub
   if (cavity < -1 || cavity >= b->ncav) return bfail(b, MDF_EINVAL, "cavity %d out of range", cavity);
   const int lo = cavity < 0 ? 0 : cavity, hi = cavity < 0 ? b->ncav : cavity + 1;
   if ((P || u) && cavity < 0) return bfail(b, MDF_EINVAL, "fields need a single cavity");
+  // seeding every cavity restarts the step count of the dither draws
+  if (cavity < 0) BCU(b, cudaMemsetAsync(b->B.clock, 0, sizeof(int), b->stream));
   for (int c = lo; c < hi; ++c) {
     const CavParam &C = b->cav[c];
     const long long nn = b->d == 2 ? (long long)C.N * C.N : (long long)C.N * C.N * C.N;
@@ -855,6 +867,8 @@ mdf_status mdf_batch_step(mdf_batch_t b, long long n) {
   while (n > 0) {
     const int s = (int)std::min<long long>(n, chunk);
     BCU(b, b->d == 2 ? launch_chunk<D2Q5>(b, s, 0) : launch_chunk<D3Q7>(b, s, 0));
+    k_batch_tick<<<1, 1, 0, b->stream>>>(b->B.clock, s);
+    BCU(b, cudaGetLastError());
     b->cur = (b->cur + s) & 1;
     n -= s;
   }

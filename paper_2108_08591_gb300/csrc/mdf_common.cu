@@ -1,5 +1,5 @@
-// Lattice-independent helper kernels: the fixed-order second reduction pass
-// and the padding of body-force fields.
+// Lattice-independent helper kernels: the fixed-order second reduction pass,
+// the padding of body-force fields and the device step counter.
 #include "mdf_internal.h"
 
 namespace mdf {
@@ -27,6 +27,13 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double *_
 
 cudaError_t launch_reduce_final(const DevArgs &a, int nblocks, int k, cudaStream_t s) {
   k_reduce_final<<<1, kReduceThreads, 0, s>>>(a.partials, nblocks, k, a.result);
+  return cudaGetLastError();
+}
+
+__global__ void k_set_clock(int *clock, int value) { *clock = value; }
+
+cudaError_t launch_set_clock(int *clock, int value, cudaStream_t s) {
+  k_set_clock<<<1, 1, 0, s>>>(clock, value);
   return cudaGetLastError();
 }
 

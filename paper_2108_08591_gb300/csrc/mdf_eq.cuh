@@ -223,6 +223,24 @@ __device__ __forceinline__ void relax_encode(T (&g)[L::Q], const T (&Ef)[L::D], 
   }
 }
 
+// VX consecutive 16-bit elements stored with stochastic rounding (one
+// random byte each, see sr_bits16), as one 2/4/8/16-byte access.
+template <class TS, int VX>
+__device__ __forceinline__ void store_sr(TS *p, const float (&v)[VX], const uint32_t (&r)[VX]) {
+  if constexpr (VX == 1) {
+    *reinterpret_cast<unsigned short *>(p) = (unsigned short)sr_bits16<TS>(v[0], r[0]);
+  } else {
+    using Raw = typename std::conditional<VX == 2, uint32_t,
+                typename std::conditional<VX == 4, uint2, uint4>::type>::type;
+    Raw raw;
+    uint32_t *w = reinterpret_cast<uint32_t *>(&raw);
+#pragma unroll
+    for (int k = 0; k < VX / 2; ++k)
+      w[k] = sr_bits16<TS>(v[2 * k], r[2 * k]) | (sr_bits16<TS>(v[2 * k + 1], r[2 * k + 1]) << 16);
+    *reinterpret_cast<Raw *>(p) = raw;
+  }
+}
+
 template <class L, class TS, int VX, int MODE, bool WALLS>
 __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
   constexpr int D = L::D, Q = L::Q, KM = D + 2;
@@ -509,8 +527,16 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
     Mn[D + 1][q] = rr;
   }
 
+  // stochastic rounding of the stored 16-bit parts: one random byte per
+  // population from the node key of (global index, time step)
   TS *__restrict__ fout = static_cast<TS *>(A.fout);
   float *__restrict__ mout = static_cast<float *>(A.mout);
+  uint32_t key[VX];
+  {
+    const int tstep = launch_step(A);
+#pragma unroll
+    for (int j = 0; j < VX; ++j) key[j] = node_key(A.key_base + n0 + j, tstep);
+  }
 #pragma unroll
   for (int s = 0; s <= D; ++s) {
     const int alpha = s == D ? 0 : s + 1;
@@ -521,7 +547,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
       float v[VX];
 #pragma unroll
       for (int q = 0; q < NP; ++q) from_lanes(v + LW * q, G[s][i][q]);
-      VecIO<TS, VX>::store(base + (long long)i * A.plane, v);
+      const int e = s * Q + i;  // byte e & 3 of random word e >> 2
+      uint32_t r[VX];
+#pragma unroll
+      for (int j = 0; j < VX; ++j) r[j] = rand_word(key[j], e >> 2) >> ((e & 3) * 8);
+      store_sr<TS, VX>(base + (long long)i * A.plane, v, r);
     }
   }
 #pragma unroll

@@ -33,6 +33,11 @@ struct DevArgs {
   double *uprev;                 // [d][N] previous velocity (residual)
   double *result;                // [k] final sums
   int *nonfinite;                // set to 1 when a non-finite value is met
+  // dithered rounding of FP32 storage: time step = *clock + tk; the node
+  // key is that of global node index key_base + dense local index
+  const int *clock;              // device step counter of the launch group
+  int tk;                        // this launch's offset in its group
+  long long key_base;            // global index of local node 0 (slabs)
 };
 
 enum Mode { MODE_STEP = 0, MODE_STEP_FIELDS = 1, MODE_FIELDS = 2 };
@@ -99,6 +104,8 @@ inline const LatticeLaunch *lattice_launch(int d, int q) {
   return nullptr;
 }
 
+// Sets the device step counter read by the update kernels of a launch group.
+cudaError_t launch_set_clock(int *clock, int value, cudaStream_t s);
 // Second reduction pass: sums `nblocks` x `k` partials in a fixed order.
 cudaError_t launch_reduce_final(const DevArgs &a, int nblocks, int k, cudaStream_t s);
 // Dense FP64 [d][N] -> padded [d][plane] in FP32 (f64 = false) or FP64.

@@ -27,6 +27,18 @@ namespace mdf {
 template <class TS> struct ComputeOf { using T = float; };
 template <> struct ComputeOf<double> { using T = double; };
 
+// FP32 storage takes the dithered (stochastic) rounding of the collision
+// (mdf_lattice.cuh); the other storage types round to nearest.
+template <class TS> constexpr bool dithered() { return std::is_same<TS, float>::value; }
+
+// Time step of this launch for the dither draws: the lattice's step counter
+// as set on the device before the launch group, plus the launch's offset in
+// the group (launches captured in a CUDA graph read the counter afresh on
+// every replay).
+__device__ __forceinline__ int launch_step(const DevArgs &A) {
+  return (A.clock ? __ldg(A.clock) : 0) + A.tk;
+}
+
 __device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // Index of the node x - c_i (periodic wrap on every axis; walls are masked).
@@ -176,14 +188,17 @@ __device__ __forceinline__ void write_fields(const DevArgs &A, long long n, long
 // So Scheme II is the Eq. 3-21 relaxation below with the equilibrium first
 // moments built from ubar (m4 relaxes towards k m0 there already) and the
 // same w_i Fbar source.
+//
+// DITHER (FP32 storage): the velocity sets' post-collision values are
+// rounded stochastically, with the offsets drawn from `key` (node_key of
+// the node's global index and the time step; see mdf_lattice.cuh).
 template <class L, class TC, bool S2 = false>
-__device__ __forceinline__ void collide_node(TC (&g)[L::D][L::Q], TC (&h)[L::Q], bool with_rho,
-                                             const TC (&F)[L::D], TC s1, TC s2,
-                                             TC (&M)[L::D + 2]) {
+__device__ __forceinline__ void node_moments(const TC (&g)[L::D][L::Q], const TC (&F)[L::D],
+                                             TC (&u)[L::D], TC &Pp) {
   constexpr int D = L::D, Q = L::Q;
   // Eq. 2-7: u_alpha = sum_i f_{i,alpha} (the rest shift has zero sum);
   // Eq. 3-15: P' = (1/d)(sum_alpha sum_i c_{i,alpha} g_{i,alpha} - |u|^2).
-  TC u[D], tr = TC(0), usq = TC(0);
+  TC tr = TC(0), usq = TC(0);
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     TC s = TC(0), t = TC(0);
@@ -199,27 +214,61 @@ __device__ __forceinline__ void collide_node(TC (&g)[L::D][L::Q], TC (&h)[L::Q],
   }
 #pragma unroll
   for (int a = 0; a < D; ++a) usq += u[a] * u[a];
-  const TC Pp = (tr - usq) * TC(1.0 / D);
+  Pp = (tr - usq) * TC(1.0 / D);
+}
+
+// Relaxation of velocity set a (alpha = a + 1) of one node from its moments.
+template <class L, class TC, bool DITHER = false>
+__device__ __forceinline__ void relax_velocity_set(TC (&ga)[L::Q], int a, const TC (&u)[L::D], TC Pp,
+                                                   TC s1, TC s2, TC Fa, uint32_t key) {
+  constexpr int D = L::D, Q = L::Q;
+  TC jeq[D];  // Eq. 3-7a: sum_i c_i f^eq = u_alpha u + P E_alpha (shifted: P')
+#pragma unroll
+  for (int b = 0; b < D; ++b) jeq[b] = u[a] * u[b] + (a == b ? Pp : TC(0));
+  if constexpr (DITHER) {  // population k = a Q + i draws byte k & 3 of word k >> 2
+    float rz[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int k = a * Q + i;
+      rz[i] = rand_scale(rand_word(key, k >> 2), k & 3);
+    }
+    L::template relax<true>(ga, jeq, s1, s2, Fa, rz);
+  } else {
+    L::relax(ga, jeq, s1, s2, Fa);
+  }
+}
+
+// Relaxation of the alpha = 0 set of one node (ubar_0 = rho0 + rho'); r
+// receives rho'.
+template <class L, class TC>
+__device__ __forceinline__ void relax_rho_set(TC (&h)[L::Q], const TC (&u)[L::D], TC s1, TC s2, TC &r) {
+  constexpr int D = L::D, Q = L::Q;
+  r = TC(0);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) r += h[i];
+  TC jeq[D];  // ubar_0 u
+#pragma unroll
+  for (int b = 0; b < D; ++b) jeq[b] = (TC(1) + r) * u[b];
+  L::relax(h, jeq, s1, s2, TC(0));
+}
+
+template <class L, class TC, bool S2 = false, bool DITHER = false>
+__device__ __forceinline__ void collide_node(TC (&g)[L::D][L::Q], TC (&h)[L::Q], bool with_rho,
+                                             const TC (&F)[L::D], TC s1, TC s2,
+                                             TC (&M)[L::D + 2], uint32_t key = 0u) {
+  constexpr int D = L::D;
+  TC u[D], Pp;
+  node_moments<L, TC, S2>(g, F, u, Pp);
 #pragma unroll
   for (int a = 0; a < D; ++a) M[a] = u[a];
   M[D] = Pp;
   M[D + 1] = TC(0);
 #pragma unroll
-  for (int a = 0; a < D; ++a) {
-    TC jeq[D];  // Eq. 3-7a: sum_i c_i f^eq = u_alpha u + P E_alpha (shifted: P')
-#pragma unroll
-    for (int b = 0; b < D; ++b) jeq[b] = u[a] * u[b] + (a == b ? Pp : TC(0));
-    L::relax(g[a], jeq, s1, s2, F[a]);
-  }
+  for (int a = 0; a < D; ++a) relax_velocity_set<L, TC, DITHER>(g[a], a, u, Pp, s1, s2, F[a], key);
   if (with_rho) {
-    TC r = TC(0);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) r += h[i];
-    TC jeq[D];  // ubar_0 u with ubar_0 = rho0 + rho'
-#pragma unroll
-    for (int b = 0; b < D; ++b) jeq[b] = (TC(1) + r) * u[b];
+    TC r;
+    relax_rho_set<L, TC>(h, u, s1, s2, r);
     M[D + 1] = r;
-    L::relax(h, jeq, s1, s2, TC(0));
   }
 }
 
@@ -258,8 +307,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_update(const DevArgs A) {
   }
 
   TC M[D + 2];
-  if (A.scheme2) collide_node<L, TC, true>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M);
-  else collide_node<L, TC, false>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M);
+  constexpr bool DZ = dithered<TS>();
+  uint32_t key = 0u;
+  if constexpr (DZ) key = node_key(A.key_base + ((long long)z * A.ny + y) * A.nx + x, launch_step(A));
+  if (A.scheme2) collide_node<L, TC, true, DZ>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M, key);
+  else collide_node<L, TC, false, DZ>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M, key);
 
   TS *__restrict__ fout = static_cast<TS *>(A.fout);
 #pragma unroll
@@ -493,8 +545,18 @@ __device__ __forceinline__ void pull_all_vec16(const DevArgs &A, const TS *__res
   }
 }
 
+// Register budget of the vector kernel per thread (255: the compiler's
+// choice).  FP32 with 4 nodes per thread is held to VEC_F32X4_REGS, which
+// sets its resident warps at the 128-thread launch.
+#ifndef VEC_F32X4_REGS
+#define VEC_F32X4_REGS 96
+#endif
+template <class TS, int VX> constexpr int vec_max_regs() {
+  return (std::is_same<TS, float>::value && VX == 4) ? VEC_F32X4_REGS : 255;
+}
+
 template <class L, class TS, int VX, int MODE, bool WALLS, bool S2>
-__global__ void __launch_bounds__(kMaxBlock) k_update_vec(const DevArgs A) {
+__global__ void __launch_bounds__(kMaxBlock) __maxnreg__((vec_max_regs<TS, VX>())) k_update_vec(const DevArgs A) {
   using TC = typename ComputeOf<TS>::T;
   constexpr int D = L::D, Q = L::Q;
   const int lane = threadIdx.x & 31;
@@ -545,38 +607,105 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_vec(const DevArgs A) {
     }
   }
   const TC s1 = TC(A.s1), s2 = TC(A.s2);
+  constexpr bool DZ = dithered<TS>();
+  if (MODE != MODE_STEP) {  // fields of the pulled state, node by node
+#pragma unroll
+    for (int j = 0; j < VX; ++j) {
+      TC gn[D][Q], hn[Q], Fn[D];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) gn[a][i] = g[a][i][j];
+        hn[i] = h[i][j];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) Fn[a] = F[a][j];
+      if (active) write_fields<L, TC>(A, n0 + j, N, gn, hn, Fn);
+    }
+    if (MODE == MODE_FIELDS) return;
+  }
+  TS *__restrict__ fout = static_cast<TS *>(A.fout);
+  if constexpr (!DZ) {  // node by node, then every population array stored
+#pragma unroll
+    for (int j = 0; j < VX; ++j) {
+      TC gn[D][Q], hn[Q], Fn[D];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) gn[a][i] = g[a][i][j];
+        hn[i] = h[i][j];
+      }
+#pragma unroll
+      for (int a = 0; a < D; ++a) Fn[a] = F[a][j];
+      TC M[D + 2];
+      collide_node<L, TC, S2>(gn, hn, A.with_rho != 0, Fn, s1, s2, M);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+#pragma unroll
+        for (int a = 0; a < D; ++a) g[a][i][j] = gn[a][i];
+        h[i][j] = hn[i];
+      }
+    }
+    if (!active) return;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        VecIO<TS, VX>::store(fout + ((long long)(a1 + a) * Q + i) * A.plane + row0 + x0, g[a][i]);
+    if (A.with_rho)
+#pragma unroll
+      for (int i = 0; i < Q; ++i) VecIO<TS, VX>::store(fout + (long long)i * A.plane + row0 + x0, h[i]);
+    return;
+  }
+  // With the dither draws (FP32): set by set, with the per-node arithmetic
+  // of collide_node.  The moments of every node first, then each set
+  // relaxed for every node and stored, so that its registers are free for
+  // the next set (the node-by-node order needs ~145 registers here).
+  TC u[VX][D], Pp[VX];
+  uint32_t key[VX];
+  const int tstep = DZ ? launch_step(A) : 0;
 #pragma unroll
   for (int j = 0; j < VX; ++j) {
-    TC gn[D][Q], hn[Q], Fn[D];
+    TC gn[D][Q], Fn[D];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) {
+    for (int a = 0; a < D; ++a) {
+      Fn[a] = F[a][j];
 #pragma unroll
-      for (int a = 0; a < D; ++a) gn[a][i] = g[a][i][j];
-      hn[i] = h[i][j];
+      for (int i = 0; i < Q; ++i) gn[a][i] = g[a][i][j];
     }
-#pragma unroll
-    for (int a = 0; a < D; ++a) Fn[a] = F[a][j];
-    if (MODE != MODE_STEP && active) write_fields<L, TC>(A, n0 + j, N, gn, hn, Fn);
-    if (MODE == MODE_FIELDS) continue;
-    TC M[D + 2];
-    collide_node<L, TC, S2>(gn, hn, A.with_rho != 0, Fn, s1, s2, M);
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-#pragma unroll
-      for (int a = 0; a < D; ++a) g[a][i][j] = gn[a][i];
-      h[i][j] = hn[i];
-    }
+    node_moments<L, TC, S2>(gn, Fn, u[j], Pp[j]);
+    key[j] = DZ ? node_key(A.key_base + n0 + j, tstep) : 0u;
   }
-  if (MODE == MODE_FIELDS || !active) return;
-  TS *__restrict__ fout = static_cast<TS *>(A.fout);
 #pragma unroll
-  for (int a = 0; a < D; ++a)
+  for (int a = 0; a < D; ++a) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i)
-      VecIO<TS, VX>::store(fout + ((long long)(a1 + a) * Q + i) * A.plane + row0 + x0, g[a][i]);
-  if (A.with_rho)
+    for (int j = 0; j < VX; ++j) {
+      TC ga[Q];
 #pragma unroll
-    for (int i = 0; i < Q; ++i) VecIO<TS, VX>::store(fout + (long long)i * A.plane + row0 + x0, h[i]);
+      for (int i = 0; i < Q; ++i) ga[i] = g[a][i][j];
+      relax_velocity_set<L, TC, DZ>(ga, a, u[j], Pp[j], s1, s2, F[a][j], key[j]);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) g[a][i][j] = ga[i];
+    }
+    if (active)
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        VecIO<TS, VX>::store(fout + ((long long)(a1 + a) * Q + i) * A.plane + row0 + x0, g[a][i]);
+  }
+  if (A.with_rho) {
+#pragma unroll
+    for (int j = 0; j < VX; ++j) {
+      TC hn[Q], r;
+#pragma unroll
+      for (int i = 0; i < Q; ++i) hn[i] = h[i][j];
+      relax_rho_set<L, TC>(hn, u[j], s1, s2, r);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) h[i][j] = hn[i];
+    }
+    if (active)
+#pragma unroll
+      for (int i = 0; i < Q; ++i) VecIO<TS, VX>::store(fout + (long long)i * A.plane + row0 + x0, h[i]);
+  }
 }
 
 // Seed (u, P' = P - 1) of node n in the compute type TC: P' is formed in
@@ -863,8 +992,9 @@ cudaError_t update_vec(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Vector widths built per storage type: FP32 2 or 4, 16-bit 4 or 8, FP64 2.
-// A field-writing update, any other width, an x extent not divisible by the
+// Vector widths built per storage type: FP32 2 or 4, 16-bit 4 or 8 (4 only
+// in 3D, where 8 nodes of 28 populations spill registers), FP64 2.  A
+// field-writing update, any other width, an x extent not divisible by the
 // width, or a plane beyond 32-bit offsets runs the scalar kernel.
 template <class L, class TS>
 cudaError_t update_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
@@ -874,7 +1004,9 @@ cudaError_t update_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
       if (a.vx == 4) return update_vec<L, TS, 4>(mode, walls, a, s);
       if (a.vx == 2) return update_vec<L, TS, 2>(mode, walls, a, s);
     } else if constexpr (sizeof(TS) == 2) {
-      if (a.vx == 8) return update_vec<L, TS, 8>(mode, walls, a, s);
+      if constexpr (L::D == 2) {
+        if (a.vx == 8) return update_vec<L, TS, 8>(mode, walls, a, s);
+      }
       if (a.vx == 4) return update_vec<L, TS, 4>(mode, walls, a, s);
     } else {
       if (a.vx == 2) return update_vec<L, TS, 2>(mode, walls, a, s);
@@ -910,7 +1042,9 @@ cudaError_t update_eq_vx(int mode, bool walls, const DevArgs &a, cudaStream_t s)
 // that does not divide nx runs with 1); field-writing updates run with 1.
 template <class L, class TS>
 cudaError_t update_eq_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
-  if (mode == MODE_STEP && a.vx == 4 && a.nx % 4 == 0) return update_eq_vx<L, TS, 4>(mode, walls, a, s);
+  if constexpr (L::D == 2) {  // 3D: 4 nodes of 28 populations spill registers
+    if (mode == MODE_STEP && a.vx == 4 && a.nx % 4 == 0) return update_eq_vx<L, TS, 4>(mode, walls, a, s);
+  }
   if (mode == MODE_STEP && a.vx == 2 && a.nx % 2 == 0) return update_eq_vx<L, TS, 2>(mode, walls, a, s);
   return update_eq_vx<L, TS, 1>(mode, walls, a, s);
 }

@@ -6,6 +6,20 @@
 // The collision is linear in f once f^eq is fixed, so it acts on g exactly as
 // on f with every equilibrium moment shifted the same way (P -> P' = P - P0,
 // ubar_0 -> rho' = ubar_0 - rho0).  Lattice units: dx = dt = c = 1.
+//
+// Rounding.  Each relax() forms the change of every population, delta_i =
+// -(M^-1 S (M g - m^eq))_i + w_i F, at the small scale of the
+// non-equilibrium part and adds it to g_i once, so a post-collision value
+// carries one rounding at the scale of g (~U).  With FP32 storage that one
+// rounding, repeated on a nearly steady field every step, is the same
+// rounding at every step: its errors add up coherently into the slow,
+// large-scale modes (the pressure fluctuation P' ~ U^2 first).  The FP32
+// kernels therefore round that add stochastically: a uniform offset in
+// (-1/2, 1/2) ulp of g_i, drawn from a counter-based hash of (node, time
+// step, set, direction), goes into delta_i before the add, which makes the
+// expected stored value the exact one (dithered rounding).  The draw depends
+// only on the node's global index and the step, so every kernel (vector,
+// scalar, in-place, batched, slab) stores the same bits.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -46,6 +60,60 @@ template <> struct Codec<__nv_bfloat16> {
 };
 
 // ---------------------------------------------------------------------------
+// Dithered rounding of the FP32 populations (see the header comment).
+// ---------------------------------------------------------------------------
+// 32-bit integer mixer: xor-shift / odd-multiply rounds with the constants of
+// the "lowbias32" mixer from C. Wellons' public hash-prospector search.
+__host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+// Random word of node n (global index; its low 32 bits) at time step t.
+__device__ __forceinline__ uint32_t step_key(int t) { return mix32((uint32_t)t * 0x9e3779b9u + 0x632be5abu); }
+__device__ __forceinline__ uint32_t node_key(long long n, int t) { return mix32((uint32_t)n ^ step_key(t)); }
+// Random words of one node for its draws: word 0 is the node key, word k
+// its product with an odd constant folded by a shift (every byte of a word
+// is uniform when the key is).
+__device__ __forceinline__ uint32_t rand_word(uint32_t key, int k) {
+  if (k == 0) return key;
+  const uint32_t x = key * (0x9e3779b9u + 2u * (uint32_t)k);
+  return x ^ (x >> 16);
+}
+// Byte j (0..3) of a random word as the FP32 number 2^-23 (1 + b/256), made
+// by placing the byte in mantissa bits 15..22 under the exponent of 2^-23.
+__device__ __forceinline__ float rand_scale(uint32_t w, int j) {
+  const int sh = 8 * j - 15;
+  const uint32_t m = (sh >= 0 ? w >> sh : w << -sh) & 0x7f8000u;
+  return __uint_as_float(m | (104u << 23));
+}
+// The change dl of a population v with its dither: dl + (b - 127.5)/256
+// ulp(v), where ulp(v) = 2^(E - 23) for v in [2^E, 2^(E+1)): 2^E is v's
+// exponent bits alone (0 for v = 0 or subnormal), and r = rand_scale(...).
+// Uniform in (-1/2, 1/2) ulp with 8-bit resolution (residual bias below
+// ulp/512); the two FMAs round at the scale of dl.
+__device__ __forceinline__ float dithered_change(float dl, float v, float r) {
+  const float p2 = __int_as_float(__float_as_int(v) & 0x7f800000);
+  return __fmaf_rn(r, p2, __fmaf_rn(-1.498046875f * 0x1p-23f, p2, dl));
+}
+
+// Stochastic rounding of an FP32 value to FP16 / BF16 bits with a random
+// byte r: r is added below the bits the 16-bit type keeps (13 for FP16 in
+// its normal range, 16 for BF16) and the value is then truncated toward
+// zero, so it rounds up in magnitude with probability equal to the dropped
+// fraction (8-bit resolution).
+template <class TS> __device__ __forceinline__ uint32_t sr_bits16(float v, uint32_t r);
+template <> __device__ __forceinline__ uint32_t sr_bits16<__half>(float v, uint32_t r) {
+  return __half_as_ushort(__float2half_rz(__int_as_float(__float_as_int(v) + (int)((r & 0xffu) << 5))));
+}
+template <> __device__ __forceinline__ uint32_t sr_bits16<__nv_bfloat16>(float v, uint32_t r) {
+  return (__float_as_uint(v) + ((r & 0xffu) << 8)) >> 16;
+}
+
+// ---------------------------------------------------------------------------
 // D2Q5 (Sec. 2.2): c_0..c_4 = (0,0),(1,0),(0,1),(-1,0),(0,-1);
 // w_0 = 1/3, w_1..4 = 1/6; c_s^2 = 1/3.  MRT basis of Eq. 4-2 (c = 1):
 //   m0 = sum g, m1 = g1 - g3, m2 = g2 - g4, m3 = g1 - g2 + g3 - g4,
@@ -69,9 +137,12 @@ struct D2Q5 {
   static constexpr int UP = 2;
 
   // In-place MRT relaxation of one set: g <- g - M^-1 S (M g - m^eq) + w F.
-  // jeq[b]: equilibrium first moment (shifted); F: source Fbar_alpha.
-  template <class TC>
-  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F) {
+  // jeq[b]: equilibrium first moment (shifted); F: source Fbar_alpha; rz:
+  // random scales (rand_scale) dithering each change before it meets g (DZ,
+  // FP32 only).
+  template <bool DZ = false, class TC>
+  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F,
+                                               const float *rz = nullptr) {
     const TC m0 = g[0] + g[1] + g[2] + g[3] + g[4];
     const TC d1 = s1 * ((g[1] - g[3]) - jeq[0]);
     const TC d2 = s1 * ((g[2] - g[4]) - jeq[1]);
@@ -79,11 +150,17 @@ struct D2Q5 {
     const TC d4 = s2 * ((g[1] + g[2] + g[3] + g[4]) - TC(4) * g[0] + TC(2.0 / 3.0) * m0);
     const TC h1 = TC(0.5) * d1, h2 = TC(0.5) * d2, q3 = TC(0.25) * d3, e4 = TC(0.05) * d4;
     const TC Fw = F * TC(1.0 / 6.0);
-    g[0] = g[0] + TC(0.2) * d4 + F * TC(1.0 / 3.0);
-    g[1] = g[1] - h1 - q3 - e4 + Fw;
-    g[2] = g[2] - h2 + q3 - e4 + Fw;
-    g[3] = g[3] + h1 - q3 - e4 + Fw;
-    g[4] = g[4] + h2 + q3 - e4 + Fw;
+    TC dl[Q];
+    dl[0] = TC(0.2) * d4 + F * TC(1.0 / 3.0);
+    dl[1] = ((Fw - h1) - q3) - e4;
+    dl[2] = ((Fw - h2) + q3) - e4;
+    dl[3] = ((Fw + h1) - q3) - e4;
+    dl[4] = ((Fw + h2) + q3) - e4;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if constexpr (DZ) g[i] = g[i] + dithered_change(dl[i], g[i], rz[i]);
+      else g[i] = g[i] + dl[i];
+    }
   }
 };
 
@@ -110,8 +187,9 @@ struct D3Q7 {
   __host__ __device__ static constexpr double w(int i) { return i == 0 ? 0.25 : 0.125; }
   static constexpr int UP = 5;
 
-  template <class TC>
-  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F) {
+  template <bool DZ = false, class TC>
+  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F,
+                                               const float *rz = nullptr) {
     const TC sx = g[1] + g[2], sy = g[3] + g[4], sz = g[5] + g[6];
     const TC m0 = g[0] + sx + sy + sz;
     const TC d1 = s1 * ((g[1] - g[2]) - jeq[0]);
@@ -124,13 +202,19 @@ struct D3Q7 {
     const TC e4 = d4 * TC(1.0 / 42.0);
     const TC ex = d5 * TC(1.0 / 6.0), eo = d5 * TC(1.0 / 12.0), q6 = TC(0.25) * d6;
     const TC Fw = F * TC(0.125);
-    g[0] = g[0] + d4 * TC(1.0 / 7.0) + F * TC(0.25);
-    g[1] = g[1] - h1 - e4 - ex + Fw;
-    g[2] = g[2] + h1 - e4 - ex + Fw;
-    g[3] = g[3] - h2 - e4 + eo - q6 + Fw;
-    g[4] = g[4] + h2 - e4 + eo - q6 + Fw;
-    g[5] = g[5] - h3 - e4 + eo + q6 + Fw;
-    g[6] = g[6] + h3 - e4 + eo + q6 + Fw;
+    TC dl[Q];
+    dl[0] = d4 * TC(1.0 / 7.0) + F * TC(0.25);
+    dl[1] = ((Fw - h1) - e4) - ex;
+    dl[2] = ((Fw + h1) - e4) - ex;
+    dl[3] = (((Fw - h2) - e4) + eo) - q6;
+    dl[4] = (((Fw + h2) - e4) + eo) - q6;
+    dl[5] = (((Fw - h3) - e4) + eo) + q6;
+    dl[6] = (((Fw + h3) - e4) + eo) + q6;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if constexpr (DZ) g[i] = g[i] + dithered_change(dl[i], g[i], rz[i]);
+      else g[i] = g[i] + dl[i];
+    }
   }
 };
 
@@ -154,17 +238,24 @@ struct D2Q4 {
   __host__ __device__ static constexpr double w(int) { return 0.25; }
   static constexpr int UP = 1;
 
-  template <class TC>
-  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F) {
+  template <bool DZ = false, class TC>
+  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F,
+                                               const float *rz = nullptr) {
     const TC d1 = s1 * ((g[0] - g[2]) - jeq[0]);
     const TC d2 = s1 * ((g[1] - g[3]) - jeq[1]);
     const TC d3 = s2 * ((g[0] + g[2]) - (g[1] + g[3]));
     const TC h1 = TC(0.5) * d1, h2 = TC(0.5) * d2, q3 = TC(0.25) * d3;
     const TC Fw = F * TC(0.25);
-    g[0] = g[0] - h1 - q3 + Fw;
-    g[1] = g[1] - h2 + q3 + Fw;
-    g[2] = g[2] + h1 - q3 + Fw;
-    g[3] = g[3] + h2 + q3 + Fw;
+    TC dl[Q];
+    dl[0] = (Fw - h1) - q3;
+    dl[1] = (Fw - h2) + q3;
+    dl[2] = (Fw + h1) - q3;
+    dl[3] = (Fw + h2) + q3;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if constexpr (DZ) g[i] = g[i] + dithered_change(dl[i], g[i], rz[i]);
+      else g[i] = g[i] + dl[i];
+    }
   }
 };
 
@@ -185,8 +276,9 @@ struct D3Q6 {
   __host__ __device__ static constexpr double w(int) { return 1.0 / 6.0; }
   static constexpr int UP = 4;
 
-  template <class TC>
-  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F) {
+  template <bool DZ = false, class TC>
+  static __device__ __forceinline__ void relax(TC g[Q], const TC jeq[D], TC s1, TC s2, TC F,
+                                               const float *rz = nullptr) {
     const TC sx = g[0] + g[1], sy = g[2] + g[3], sz = g[4] + g[5];
     const TC d1 = s1 * ((g[0] - g[1]) - jeq[0]);
     const TC d2 = s1 * ((g[2] - g[3]) - jeq[1]);
@@ -196,12 +288,18 @@ struct D3Q6 {
     const TC h1 = TC(0.5) * d1, h2 = TC(0.5) * d2, h3 = TC(0.5) * d3;
     const TC ex = d4 * TC(1.0 / 6.0), eo = d4 * TC(1.0 / 12.0), q5 = TC(0.25) * d5;
     const TC Fw = F * TC(1.0 / 6.0);
-    g[0] = g[0] - h1 - ex + Fw;
-    g[1] = g[1] + h1 - ex + Fw;
-    g[2] = g[2] - h2 + eo - q5 + Fw;
-    g[3] = g[3] + h2 + eo - q5 + Fw;
-    g[4] = g[4] - h3 + eo + q5 + Fw;
-    g[5] = g[5] + h3 + eo + q5 + Fw;
+    TC dl[Q];
+    dl[0] = (Fw - h1) - ex;
+    dl[1] = (Fw + h1) - ex;
+    dl[2] = ((Fw - h2) + eo) - q5;
+    dl[3] = ((Fw + h2) + eo) - q5;
+    dl[4] = ((Fw - h3) + eo) + q5;
+    dl[5] = ((Fw + h3) + eo) + q5;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      if constexpr (DZ) g[i] = g[i] + dithered_change(dl[i], g[i], rz[i]);
+      else g[i] = g[i] + dl[i];
+    }
   }
 };
 

@@ -397,7 +397,7 @@ def test_rest_free_scheme2_and_neq_seed(storage):
 
 @pytest.mark.parametrize("d,storage,vx", [
     (2, "f32", 4), (2, "f32", 2), (2, "f16", 8), (2, "bf16", 4), (2, "f64", 2),
-    (3, "f32", 4), (3, "f16", 4), (3, "bf16", 8), (3, "f64", 2),
+    (3, "f32", 4), (3, "f16", 4), (3, "bf16", 4), (3, "f64", 2),
 ])
 @pytest.mark.parametrize("walls", [False, True])
 def test_rest_free_vector_kernel_is_bitwise_the_scalar_kernel(d, storage, vx, walls):
@@ -492,7 +492,7 @@ def test_inplace_aa_is_bitwise_the_pull_stream(storage, case):
 
 @pytest.mark.parametrize("d,storage,vx", [
     (2, "f32", 4), (2, "f32", 2), (2, "f16", 8), (2, "bf16", 4), (2, "f64", 2),
-    (3, "f32", 4), (3, "f16", 8), (3, "bf16", 4), (3, "f64", 2),
+    (3, "f32", 2), (3, "f16", 4), (3, "bf16", 4), (3, "f64", 2),
 ])
 @pytest.mark.parametrize("walls", [False, True])
 def test_inplace_aa_vector_kernel_is_bitwise_the_pull_stream(d, storage, vx, walls):
@@ -777,7 +777,7 @@ def _gather(out, pts, n):
     return {k: v.index_select(v.dim() - 1, idx).cpu().numpy() for k, v in out.items()}
 
 
-def _sampled_window_errors(shape, s1, P, u, got, steps, pts):
+def _sampled_window_errors(shape, s1, P, u, got, steps, pts, s2=None):
     """Relative L2 of u, P - 1, G, S and omega on the given nodes of a
     periodic lattice, against the FP64 oracle on (2 steps + 1)^d windows
     (after `steps` updates a node depends only on nodes within that many
@@ -795,7 +795,7 @@ def _sampled_window_errors(shape, s1, P, u, got, steps, pts):
             sel = (axes[1][:, None] * n + axes[0][None, :]).ravel()
         else:
             sel = ((axes[2][:, None, None] * n + axes[1][None, :, None]) * n + axes[0][None, None, :]).ravel()
-        pb = O.Problem(d=d, n=(W,) * d, s1=s1)
+        pb = O.Problem(d=d, n=(W,) * d, s1=s1, s2=s2)
         f = O.run(pb, O.init(pb, P[sel], u[:, sel]), steps)
         Pr, ur, _ = O.macro(pb, f)
         D = O.derived(pb, f)
@@ -867,9 +867,9 @@ def test_full_size_4096_equilibrium_shifted_sampled_parity(storage, tol):
 @pytest.mark.parametrize("storage,tol", [("f32", (1e-5, 1e-5, 1e-3)), ("f16eq", (2e-3, 2e-3, 1e-2)),
                                          ("f16", (2e-3, 2e-2, 0.5))])
 def test_full_size_512_cubed_sampled_parity(storage, tol):
-    """512^3 D3Q7 x 4 3D Taylor-Green (U0 = 0.05, Re = 1600), in the
-    benchmark's launch configuration, at 48 sampled nodes including the
-    vector kernels' edges.  FP32 and equilibrium-shifted FP16 are held to
+    """512^3 D3Q7 x 4 3D Taylor-Green (U0 = 0.05, Re = 1600, s2 = 1: the
+    s2 rule is unstable at these rates), in the benchmark's launch
+    configuration, at 48 sampled nodes including the vector kernels' edges.  FP32 and equilibrium-shifted FP16 are held to
     the contract on u and P; the rest-shifted FP16 row is reported, not the
     contract (its P and gradient bounds only guard against regressions)."""
     from paper_2108_08591_gb300 import Lattice
@@ -878,13 +878,13 @@ def test_full_size_512_cubed_sampled_parity(storage, tol):
     nu = 0.05 / (k * 1600.0)
     s1 = 1.0 / (4 * nu + 0.5)
     P, u = synth.taylor_green_3d(n, U0=0.05)
-    lat = Lattice((n, n, n), s1=s1, storage=storage)
+    lat = Lattice((n, n, n), s1=s1, s2=1.0, storage=storage)
     lat.init(P, u)
     lat.step(steps)
     pts = _sample_points(n, 3, 48, 93)
     got = _gather(lat.fields(("P", "u", "G", "S", "omega")), pts, n)
     lat.close()
-    e = _sampled_window_errors((n, n, n), s1, P, u, got, steps, pts)
+    e = _sampled_window_errors((n, n, n), s1, P, u, got, steps, pts, s2=1.0)
     print("512^3", storage, e)
     assert e["u"] < tol[0] and e["P"] < tol[1], e
     assert e["G"] < tol[2] and e["omega"] < tol[2], e
@@ -895,8 +895,8 @@ def test_full_size_512_cubed_sampled_parity(storage, tol):
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("d,storage,vx", [
     (2, "f32", 4), (2, "f32", 2), (2, "f16", 8), (2, "bf16", 4), (2, "f64", 2),
-    (3, "f32", 4), (3, "f32", 2), (3, "f16", 4), (3, "bf16", 8), (3, "f64", 2),
-    (2, "f16eq", 2), (2, "f16eq", 4), (2, "bf16eq", 4), (3, "f16eq", 2), (3, "bf16eq", 4),
+    (3, "f32", 4), (3, "f32", 2), (3, "f16", 4), (3, "bf16", 4), (3, "f64", 2),
+    (2, "f16eq", 2), (2, "f16eq", 4), (2, "bf16eq", 4), (3, "f16eq", 2), (3, "bf16eq", 2),
 ])
 @pytest.mark.parametrize("walls", [False, True])
 def test_vector_kernel_is_bitwise_the_scalar_kernel(d, storage, vx, walls):
