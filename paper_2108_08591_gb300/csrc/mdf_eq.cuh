@@ -223,20 +223,44 @@ __device__ __forceinline__ void relax_encode(T (&g)[L::Q], const T (&Ef)[L::D], 
   }
 }
 
-// VX consecutive 16-bit elements stored with stochastic rounding (one
-// random byte each, see sr_bits16), as one 2/4/8/16-byte access.
+// Stochastic rounding of two FP32 values to a packed 16-bit pair in one
+// instruction (cvt.rs, sm_100 family): lo goes to bits 15..0, hi to bits
+// 31..16, and rbits[15:0] / rbits[31:16] are their random bits.
+template <class TS> __device__ __forceinline__ uint32_t cvt_rs_pair(float lo, float hi, uint32_t rbits);
+template <> __device__ __forceinline__ uint32_t cvt_rs_pair<__half>(float lo, float hi, uint32_t rbits) {
+  uint32_t d;
+  asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
+template <> __device__ __forceinline__ uint32_t cvt_rs_pair<__nv_bfloat16>(float lo, float hi, uint32_t rbits) {
+  uint32_t d;
+  asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(rbits));
+  return d;
+}
+// Random word of population e of the node pair (x, x + 1), x even, from
+// the key of its even node: an odd multiple, so each half is uniform.
+__device__ __forceinline__ uint32_t pair_word(uint32_t key, int e) {
+  return key * (0x9e3779b1u + 2u * (uint32_t)e);
+}
+
+// VX consecutive 16-bit elements of population e stored with stochastic
+// rounding, as one 2/4/8/16-byte access; kp[p] is the key of the even node
+// of pair p.  VX = 1 (node x, x0 = x) takes its lane of its pair's word, so
+// every width stores the same bits.
 template <class TS, int VX>
-__device__ __forceinline__ void store_sr(TS *p, const float (&v)[VX], const uint32_t (&r)[VX]) {
+__device__ __forceinline__ void store_sr(TS *p, const float (&v)[VX], const uint32_t (&kp)[(VX + 1) / 2],
+                                         int e, int x0) {
   if constexpr (VX == 1) {
-    *reinterpret_cast<unsigned short *>(p) = (unsigned short)sr_bits16<TS>(v[0], r[0]);
+    const int odd = x0 & 1;
+    const uint32_t d = cvt_rs_pair<TS>(odd ? 0.f : v[0], odd ? v[0] : 0.f, pair_word(kp[0], e));
+    *reinterpret_cast<unsigned short *>(p) = (unsigned short)(odd ? d >> 16 : d);
   } else {
     using Raw = typename std::conditional<VX == 2, uint32_t,
                 typename std::conditional<VX == 4, uint2, uint4>::type>::type;
     Raw raw;
     uint32_t *w = reinterpret_cast<uint32_t *>(&raw);
 #pragma unroll
-    for (int k = 0; k < VX / 2; ++k)
-      w[k] = sr_bits16<TS>(v[2 * k], r[2 * k]) | (sr_bits16<TS>(v[2 * k + 1], r[2 * k + 1]) << 16);
+    for (int k = 0; k < VX / 2; ++k) w[k] = cvt_rs_pair<TS>(v[2 * k], v[2 * k + 1], pair_word(kp[k], e));
     *reinterpret_cast<Raw *>(p) = raw;
   }
 }
@@ -527,15 +551,17 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
     Mn[D + 1][q] = rr;
   }
 
-  // stochastic rounding of the stored 16-bit parts: one random byte per
-  // population from the node key of (global index, time step)
   TS *__restrict__ fout = static_cast<TS *>(A.fout);
   float *__restrict__ mout = static_cast<float *>(A.mout);
-  uint32_t key[VX];
+  // stochastic rounding of the stored 16-bit parts: the random bits of a
+  // node pair (x, x + 1), x even, come from its even node's key of (global
+  // index, time step)
+  uint32_t kp[(VX + 1) / 2];
   {
     const int tstep = launch_step(A);
 #pragma unroll
-    for (int j = 0; j < VX; ++j) key[j] = node_key(A.key_base + n0 + j, tstep);
+    for (int p = 0; p < (VX + 1) / 2; ++p)
+      kp[p] = node_key(A.key_base + n0 + 2 * p - (VX == 1 ? (x0 & 1) : 0), tstep);
   }
 #pragma unroll
   for (int s = 0; s <= D; ++s) {
@@ -547,11 +573,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
       float v[VX];
 #pragma unroll
       for (int q = 0; q < NP; ++q) from_lanes(v + LW * q, G[s][i][q]);
-      const int e = s * Q + i;  // byte e & 3 of random word e >> 2
-      uint32_t r[VX];
-#pragma unroll
-      for (int j = 0; j < VX; ++j) r[j] = rand_word(key[j], e >> 2) >> ((e & 3) * 8);
-      store_sr<TS, VX>(base + (long long)i * A.plane, v, r);
+      store_sr<TS, VX>(base + (long long)i * A.plane, v, kp, s * Q + i, x0);
     }
   }
 #pragma unroll

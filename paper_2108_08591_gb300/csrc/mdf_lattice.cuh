@@ -76,12 +76,10 @@ __host__ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 __device__ __forceinline__ uint32_t step_key(int t) { return mix32((uint32_t)t * 0x9e3779b9u + 0x632be5abu); }
 __device__ __forceinline__ uint32_t node_key(long long n, int t) { return mix32((uint32_t)n ^ step_key(t)); }
 // Random words of one node for its draws: word 0 is the node key, word k
-// its product with an odd constant folded by a shift (every byte of a word
-// is uniform when the key is).
+// its product with a distinct odd constant (a bijection, so every byte of a
+// word is uniform when the key is).
 __device__ __forceinline__ uint32_t rand_word(uint32_t key, int k) {
-  if (k == 0) return key;
-  const uint32_t x = key * (0x9e3779b9u + 2u * (uint32_t)k);
-  return x ^ (x >> 16);
+  return k == 0 ? key : key * (0x9e3779b9u + 2u * (uint32_t)k);
 }
 // Byte j (0..3) of a random word as the FP32 number 2^-23 (1 + b/256), made
 // by placing the byte in mantissa bits 15..22 under the exponent of 2^-23.
@@ -98,19 +96,6 @@ __device__ __forceinline__ float rand_scale(uint32_t w, int j) {
 __device__ __forceinline__ float dithered_change(float dl, float v, float r) {
   const float p2 = __int_as_float(__float_as_int(v) & 0x7f800000);
   return __fmaf_rn(r, p2, __fmaf_rn(-1.498046875f * 0x1p-23f, p2, dl));
-}
-
-// Stochastic rounding of an FP32 value to FP16 / BF16 bits with a random
-// byte r: r is added below the bits the 16-bit type keeps (13 for FP16 in
-// its normal range, 16 for BF16) and the value is then truncated toward
-// zero, so it rounds up in magnitude with probability equal to the dropped
-// fraction (8-bit resolution).
-template <class TS> __device__ __forceinline__ uint32_t sr_bits16(float v, uint32_t r);
-template <> __device__ __forceinline__ uint32_t sr_bits16<__half>(float v, uint32_t r) {
-  return __half_as_ushort(__float2half_rz(__int_as_float(__float_as_int(v) + (int)((r & 0xffu) << 5))));
-}
-template <> __device__ __forceinline__ uint32_t sr_bits16<__nv_bfloat16>(float v, uint32_t r) {
-  return (__float_as_uint(v) + ((r & 0xffu) << 8)) >> 16;
 }
 
 // ---------------------------------------------------------------------------
