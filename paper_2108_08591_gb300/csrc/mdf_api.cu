@@ -337,7 +337,10 @@ mdf_status mdf_create(mdf_t *out, const mdf_grid *g, int d, const mdf_rates *r,
   h->nsets = d + h->with_rho;
   h->storage = opts.storage;
   h->nx = g->nx; h->ny = g->ny; h->nz = g->nz;
-  h->px = (g->nx + 31) / 32 * 32;
+  // x pitch: 128-byte rows; the equilibrium-shifted codecs store x in tiles
+  // of 64 nodes (mdf_eq.cuh), so their pitch is a multiple of 64
+  const int pitch = eq_storage(opts.storage) ? 64 : 32;
+  h->px = (g->nx + pitch - 1) / pitch * pitch;
   h->plane = (long long)h->px * g->ny * g->nz;
   h->N = (long long)g->nx * g->ny * g->nz;
   h->s0 = r->s0; h->s1 = s1; h->s2 = s2;

@@ -19,6 +19,20 @@
 
 namespace mdf {
 
+// Memory layout.  x is cut into tiles of 64 nodes (the x pitch is a
+// multiple of 64).  For each row (z, y) and tile, the nk arrays of the
+// tile (populations: set-major, direction within set; moments: slot by
+// slot) lie one after the other, 64 elements each:
+//     element k of node x in row r:  ((r px/64 + x/64) nk + k) 64 + x mod 64.
+// A thread's nodes share one tile, so every array it touches sits at a
+// compile-time offset (k 64 elements) from a few per-row pointers, and a
+// warp's 64 nodes of one array are one contiguous 128-byte (16-bit) or
+// 256-byte (FP32) span.
+constexpr int kEqTile = 64;
+__host__ __device__ __forceinline__ long long eq_off(int px, long long row, int x, int nk) {
+  return ((row * (px / kEqTile) + (x / kEqTile)) * (long long)nk) * kEqTile + (x & (kEqTile - 1));
+}
+
 // FP16 keeps |s| in its normal range (6e-5 .. 65504) for non-equilibrium
 // parts between ~4e-9 and 4; BF16 has the FP32 exponent range.
 template <class TS> struct EqScale;
@@ -43,15 +57,14 @@ __device__ __forceinline__ float geq_m(int alpha, int i, const float (&M)[L::D +
   return wi * (ua + (cu * ua + cP) * ics2);
 }
 
+// The KM moment slots of VX nodes from a tile pointer (slots >= K read 0).
 template <int KM, int VX>
-__device__ __forceinline__ void load_moments(const DevArgs &A, int K, int off,
-                                             float (&M)[KM][VX]) {
-  const float *min = static_cast<const float *>(A.min);
+__device__ __forceinline__ void load_moments(const float *mt, int K, float (&M)[KM][VX]) {
 #pragma unroll
   for (int k = 0; k < KM; ++k) {
     if (k < K) {
       float v[VX];
-      VecIO<float, VX>::load(min + (long long)k * A.plane + off, v);
+      VecIO<float, VX>::load(mt + k * kEqTile, v);
 #pragma unroll
       for (int j = 0; j < VX; ++j) M[k][j] = v[j];
     } else {
@@ -276,45 +289,55 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
   const bool active = x0 < A.nx;
   if (!active) x0 = A.nx - VX;
   const int y = blockIdx.y, z = blockIdx.z;
-  const int row0 = (z * A.ny + y) * A.px;
-  const int row_ym = (z * A.ny + wrap(y - 1, A.ny)) * A.px;
-  const int row_yp = (z * A.ny + wrap(y + 1, A.ny)) * A.px;
-  const int row_zm = D == 3 ? (wrap(z - 1, A.nz) * A.ny + y) * A.px : row0;
-  const int row_zp = D == 3 ? (wrap(z + 1, A.nz) * A.ny + y) * A.px : row0;
+  const long long rc = (long long)z * A.ny + y;  // this row and the rows the pulls come from
+  const long long rym = (long long)z * A.ny + wrap(y - 1, A.ny);
+  const long long ryp = (long long)z * A.ny + wrap(y + 1, A.ny);
+  const long long rzm = D == 3 ? (long long)wrap(z - 1, A.nz) * A.ny + y : rc;
+  const long long rzp = D == 3 ? (long long)wrap(z + 1, A.nz) * A.ny + y : rc;
   const bool ledge = lane == 0 || x0 == 0;
   const bool redge = lane == 31 || x0 + VX >= A.nx;
   const int xl = x0 == 0 ? A.nx - 1 : x0 - 1;
   const int xr = x0 + VX >= A.nx ? 0 : x0 + VX;
   const int K = moment_slots(D, A.with_rho);
+  const int NK = (D + A.with_rho) * Q;  // population arrays per tile
   const TS *__restrict__ fin = static_cast<const TS *>(A.fin);
   const float *__restrict__ min = static_cast<const float *>(A.min);
   const int a1 = A.with_rho;
+  // tile pointers: array k of the thread's nodes (or of an x-edge node) is
+  // at pointer + k * kEqTile
+  const TS *Pc = fin + eq_off(A.px, rc, x0, NK), *Pym = fin + eq_off(A.px, rym, x0, NK);
+  const TS *Pyp = fin + eq_off(A.px, ryp, x0, NK), *Pzm = fin + eq_off(A.px, rzm, x0, NK);
+  const TS *Pzp = fin + eq_off(A.px, rzp, x0, NK);
+  const TS *Pl = fin + eq_off(A.px, rc, xl, NK), *Pr = fin + eq_off(A.px, rc, xr, NK);
 
   uint8_t m[VX];
   if (WALLS) {
 #pragma unroll
-    for (int j = 0; j < VX; ++j) m[j] = A.mask[row0 + x0 + j];
+    for (int j = 0; j < VX; ++j) m[j] = A.mask[rc * A.px + x0 + j];
   }
   float Mo[KM][VX], Mym[KM][VX], Myp[KM][VX], Mzm[KM][VX], Mzp[KM][VX], Mxl[KM], Mxr[KM];
-  load_moments<KM, VX>(A, K, row0 + x0, Mo);
-  load_moments<KM, VX>(A, K, row_ym + x0, Mym);
-  load_moments<KM, VX>(A, K, row_yp + x0, Myp);
+  load_moments<KM, VX>(min + eq_off(A.px, rc, x0, K), K, Mo);
+  load_moments<KM, VX>(min + eq_off(A.px, rym, x0, K), K, Mym);
+  load_moments<KM, VX>(min + eq_off(A.px, ryp, x0, K), K, Myp);
   if (D == 3) {
-    load_moments<KM, VX>(A, K, row_zm + x0, Mzm);
-    load_moments<KM, VX>(A, K, row_zp + x0, Mzp);
+    load_moments<KM, VX>(min + eq_off(A.px, rzm, x0, K), K, Mzm);
+    load_moments<KM, VX>(min + eq_off(A.px, rzp, x0, K), K, Mzp);
   }
+  {
+    const float *Ml = min + eq_off(A.px, rc, xl, K), *Mr = min + eq_off(A.px, rc, xr, K);
 #pragma unroll
-  for (int k = 0; k < KM; ++k) {
-    float l = __shfl_up_sync(0xffffffffu, Mo[k][VX - 1], 1);
-    float r = __shfl_down_sync(0xffffffffu, Mo[k][0], 1);
-    if (k < K) {
-      if (ledge) l = __ldg(min + (long long)k * A.plane + row0 + xl);
-      if (redge) r = __ldg(min + (long long)k * A.plane + row0 + xr);
-    } else {
-      l = r = 0.f;
+    for (int k = 0; k < KM; ++k) {
+      float l = __shfl_up_sync(0xffffffffu, Mo[k][VX - 1], 1);
+      float r = __shfl_down_sync(0xffffffffu, Mo[k][0], 1);
+      if (k < K) {
+        if (ledge) l = __ldg(Ml + k * kEqTile);
+        if (redge) r = __ldg(Mr + k * kEqTile);
+      } else {
+        l = r = 0.f;
+      }
+      Mxl[k] = l;
+      Mxr[k] = r;
     }
-    Mxl[k] = l;
-    Mxr[k] = r;
   }
 
   // ---- pull: every population word is loaded before any is decoded, so
@@ -328,12 +351,12 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
     if (alpha == 0 && !A.with_rho) break;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const TS *p = fin + ((long long)(alpha == 0 ? 0 : a1 + alpha - 1) * Q + i) * A.plane;
-      const int r = L::c(i, 1) == 1 ? row_ym : L::c(i, 1) == -1 ? row_yp
-                  : L::c(i, 2) == 1 ? row_zm : L::c(i, 2) == -1 ? row_zp : row0;
-      wv[s][i] = Packed16<TS, VX>::load(p + r + x0);
-      if (L::c(i, 0) == 1) edge[s][0] = ledge ? ldg_bits16(p + row0 + xl) : 0u;
-      if (L::c(i, 0) == -1) edge[s][1] = redge ? ldg_bits16(p + row0 + xr) : 0u;
+      const int k = ((alpha == 0 ? 0 : a1 + alpha - 1) * Q + i) * kEqTile;
+      const TS *p = L::c(i, 1) == 1 ? Pym : L::c(i, 1) == -1 ? Pyp
+                  : L::c(i, 2) == 1 ? Pzm : L::c(i, 2) == -1 ? Pzp : Pc;
+      wv[s][i] = Packed16<TS, VX>::load(p + k);
+      if (L::c(i, 0) == 1) edge[s][0] = ledge ? ldg_bits16(Pl + k) : 0u;
+      if (L::c(i, 0) == -1) edge[s][1] = redge ? ldg_bits16(Pr + k) : 0u;
     }
   }
   // ---- decode, direction by direction (source terms shared by the sets)
@@ -395,7 +418,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
     for (int s = 0; s <= D; ++s) {
       const int alpha = s == D ? 0 : s + 1;
       if (alpha == 0 && !A.with_rho) break;
-      const TS *base = fin + (long long)(alpha == 0 ? 0 : a1 + alpha - 1) * Q * A.plane;
+      const TS *base = Pc + (alpha == 0 ? 0 : a1 + alpha - 1) * Q * kEqTile;
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         const int o = L::opp(i);
@@ -407,7 +430,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
             float un[D];
 #pragma unroll
             for (int b = 0; b < D; ++b) un[b] = Mo[b][j];
-            const float own = Codec<TS>::load(base + (long long)o * A.plane + row0 + x0 + j);
+            const float own = Codec<TS>::load(base + o * kEqTile + j);
             float w = -vfma(eq_inner<L, float>(alpha, o, un, Mo[D][j], Mo[D + 1][j]), swo, own);
             if (alpha >= 1 && i == L::opp(L::UP) && (m[j] & 0x80u)) w = vadd(w, lid);
             float v[LW];
@@ -426,7 +449,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
 #pragma unroll
   for (int a = 0; a < D; ++a) {
     if (A.force) {
-      VecIO<float, VX>::load(static_cast<const float *>(A.force) + a * A.plane + row0 + x0, Fr[a]);
+      VecIO<float, VX>::load(static_cast<const float *>(A.force) + a * A.plane + rc * A.px + x0, Fr[a]);
     } else {
 #pragma unroll
       for (int j = 0; j < VX; ++j) Fr[a][j] = 0.f;
@@ -567,22 +590,23 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
   for (int s = 0; s <= D; ++s) {
     const int alpha = s == D ? 0 : s + 1;
     if (alpha == 0 && !A.with_rho) break;
-    TS *base = fout + (long long)(alpha == 0 ? 0 : a1 + alpha - 1) * Q * A.plane + row0 + x0;
+    TS *base = fout + eq_off(A.px, rc, x0, NK) + (alpha == 0 ? 0 : a1 + alpha - 1) * Q * kEqTile;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       float v[VX];
 #pragma unroll
       for (int q = 0; q < NP; ++q) from_lanes(v + LW * q, G[s][i][q]);
-      store_sr<TS, VX>(base + (long long)i * A.plane, v, kp, s * Q + i, x0);
+      store_sr<TS, VX>(base + i * kEqTile, v, kp, s * Q + i, x0);
     }
   }
+  float *mo = mout + eq_off(A.px, rc, x0, K);
 #pragma unroll
   for (int k = 0; k < KM; ++k) {
     if (k < K) {
       float v[VX];
 #pragma unroll
       for (int q = 0; q < NP; ++q) from_lanes(v + LW * q, Mn[k][q]);
-      VecIO<float, VX>::store(mout + (long long)k * A.plane + row0 + x0, v);
+      VecIO<float, VX>::store(mo + k * kEqTile, v);
     }
   }
 }
@@ -616,9 +640,11 @@ __global__ void __launch_bounds__(kMaxBlock) k_init_eq(const DevArgs A) {
   init_moments<L>(A, N, n, M0);
   float *mout = static_cast<float *>(A.mout);
   const int K = moment_slots(D, A.with_rho);
-  for (int k = 0; k < K; ++k) mout[k * A.plane + idx] = M0[k];
+  const long long row = (long long)z * A.ny + y;
+  for (int k = 0; k < K; ++k) mout[eq_off(A.px, row, x, K) + k * kEqTile] = M0[k];
   TS *fout = static_cast<TS *>(A.fout);
   const int nsets = D + A.with_rho;
+  TS *fn = fout + eq_off(A.px, row, x, nsets * Q);
   for (int a = 0; a < nsets; ++a) {
     const int alpha = a + 1 - A.with_rho;
 #pragma unroll
@@ -642,8 +668,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_init_eq(const DevArgs A) {
         if (A.Gin) target += narrow_f64(fne_at<L>(A, N, tn, alpha, i));
         if (half) target -= float(0.5 * L::w(i)) * __ldg(Fa + ((long long)tz * A.ny + ty) * A.px + tx);
       }
-      Codec<TS>::store(fout + ((long long)a * Q + i) * A.plane + idx,
-                       (target - geq_m<L>(alpha, i, M0)) * EqScale<TS>::s);
+      Codec<TS>::store(fn + (a * Q + i) * kEqTile, (target - geq_m<L>(alpha, i, M0)) * EqScale<TS>::s);
     }
   }
 }
@@ -658,26 +683,31 @@ __device__ __forceinline__ void pull_node_eq(const DevArgs &A, int x, int y, int
   const int K = moment_slots(D, A.with_rho);
   const float *min = static_cast<const float *>(A.min);
   const TS *fin = static_cast<const TS *>(A.fin);
+  const int nsets = D + A.with_rho;
+  const long long row = (long long)z * A.ny + y;
   float Mo[D + 2];
 #pragma unroll
-  for (int k = 0; k < D + 2; ++k) Mo[k] = k < K ? __ldg(min + k * A.plane + idx) : 0.f;
-  const int nsets = D + A.with_rho;
+  for (int k = 0; k < D + 2; ++k) Mo[k] = k < K ? __ldg(min + eq_off(A.px, row, x, K) + k * kEqTile) : 0.f;
   for (int a = 0; a < nsets; ++a) {
     const int alpha = a + 1 - A.with_rho;
-    const TS *base = fin + (long long)a * Q * A.plane;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       if (WALLS && i != 0 && ((m >> L::opp(i)) & 1)) {
-        float w = -(Codec<TS>::load(base + (long long)L::opp(i) * A.plane + idx) * EqScale<TS>::inv +
+        float w = -(Codec<TS>::load(fin + eq_off(A.px, row, x, nsets * Q) + (a * Q + L::opp(i)) * kEqTile) *
+                        EqScale<TS>::inv +
                     geq_m<L>(alpha, L::opp(i), Mo));
         if (alpha >= 1 && i == L::opp(L::UP) && (m & 0x80u)) w += float(2.0 * L::w(i) * A.lid_u[alpha - 1]);
         g[a][i] = w;
-      } else {
-        const long long src = pull_src<L>(A, x, y, z, i);
+      } else {  // from the node x - c_i (periodic wrap)
+        const int sx = wrap(x - L::c(i, 0), A.nx);
+        const int sy = wrap(y - L::c(i, 1), A.ny);
+        const int sz = D == 3 ? wrap(z - L::c(i, 2), A.nz) : z;
+        const long long srow = (long long)sz * A.ny + sy;
         float Ms[D + 2];
 #pragma unroll
-        for (int k = 0; k < D + 2; ++k) Ms[k] = k < K ? __ldg(min + k * A.plane + src) : 0.f;
-        g[a][i] = Codec<TS>::load(base + (long long)i * A.plane + src) * EqScale<TS>::inv +
+        for (int k = 0; k < D + 2; ++k) Ms[k] = k < K ? __ldg(min + eq_off(A.px, srow, sx, K) + k * kEqTile) : 0.f;
+        g[a][i] = Codec<TS>::load(fin + eq_off(A.px, srow, sx, nsets * Q) + (a * Q + i) * kEqTile) *
+                      EqScale<TS>::inv +
                   geq_m<L>(alpha, i, Ms);
       }
     }
