@@ -488,6 +488,10 @@ def run_mdf(args):
                   else f"k_update_aa<{kname},{tname},even+odd,MODE_STEP,periodic>")
     elif args.storage.endswith("eq"):
         kernel = f"k_update_eq<{kname},{tname},VX={info.vx},MODE_STEP,periodic>"
+    elif info.vx == 4 and args.storage == "f32":
+        kernel = f"k_update_vec_f32x4<{kname},MODE_STEP,periodic>"
+    elif info.vx > 1 and d == 3 and args.storage in ("f16", "bf16"):
+        kernel = f"k_update_vec16p<{kname},{tname},VX={info.vx},periodic>"
     elif info.vx > 1:
         kernel = f"k_update_vec<{kname},{tname},VX={info.vx},MODE_STEP,periodic>"
     else:

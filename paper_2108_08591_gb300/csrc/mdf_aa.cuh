@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_aa(const DevArgs A) {
   constexpr bool DZ = dithered<TS>();
   uint32_t key = 0u;
   if constexpr (DZ) key = node_key(A.key_base + ((long long)z * A.ny + y) * A.nx + x, launch_step(A));
-  if (A.scheme2) collide_node<L, TC, true, DZ>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M, key);
-  else collide_node<L, TC, false, DZ>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M, key);
+  if (A.scheme2) collide_node<L, TC, true, DZ>(g, h, A.with_rho != 0, F, rate<TC>(A.s1, A.s1f), rate<TC>(A.s2, A.s2f), M, key);
+  else collide_node<L, TC, false, DZ>(g, h, A.with_rho != 0, F, rate<TC>(A.s1, A.s1f), rate<TC>(A.s2, A.s2f), M, key);
 
 #pragma unroll
   for (int a = 0; a < D; ++a)
@@ -425,7 +425,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_aa_vec(const DevArgs A) {
       for (int j = 0; j < VX; ++j) F[a][j] = TC(0);
     }
   }
-  const TC s1 = TC(A.s1), s2 = TC(A.s2);
+  const TC s1 = rate<TC>(A.s1, A.s1f), s2 = rate<TC>(A.s2, A.s2f);
   constexpr bool DZ = dithered<TS>();
   const int tstep = DZ ? launch_step(A) : 0;
   const long long n0 = ((long long)z * A.ny + y) * A.nx + x0;
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_aa_vec16p(const DevArgs A)
       for (int j = 0; j < VX; ++j) F[a][j] = 0.f;
     }
   }
-  const float s1 = float(A.s1), s2 = float(A.s2);
+  const float s1 = A.s1f, s2 = A.s2f;
 #pragma unroll
   for (int j = 0; j < VX; ++j) {
     float gn[D][Q], hn[Q], Fn[D];

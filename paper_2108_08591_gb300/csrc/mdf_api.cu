@@ -155,6 +155,7 @@ DevArgs base_args(const mdf_t h) {
   a.vx = h->vx;
   a.block = h->block;
   a.s1 = h->s1; a.s2 = h->s2;
+  a.s1f = (float)h->s1; a.s2f = (float)h->s2;
   for (int b = 0; b < 3; ++b) a.lid_u[b] = h->bc.lid ? h->bc.lid_u[b] : 0.0;
   a.min = h->mac[h->cur_index()];
   a.mout = h->mac[1 - h->cur_index()];

@@ -256,6 +256,21 @@ __device__ __forceinline__ uint32_t pair_word(uint32_t key, int e) {
   return key * (0x9e3779b1u + 2u * (uint32_t)e);
 }
 
+// Moments of the x - 1 and x + VX neighbours of a thread's nodes: from the
+// neighbouring lanes, or, at a warp or row edge, from the loaded El / Er.
+template <int KM, int VX>
+__device__ __forceinline__ void settle_edge_moments(const float (&Mo)[KM][VX], const float (&El)[KM],
+                                                    const float (&Er)[KM], int K, bool ledge, bool redge,
+                                                    float (&Mxl)[KM], float (&Mxr)[KM]) {
+#pragma unroll
+  for (int k = 0; k < KM; ++k) {
+    const float l = __shfl_up_sync(0xffffffffu, Mo[k][VX - 1], 1);
+    const float r = __shfl_down_sync(0xffffffffu, Mo[k][0], 1);
+    Mxl[k] = k < K ? (ledge ? El[k] : l) : 0.f;
+    Mxr[k] = k < K ? (redge ? Er[k] : r) : 0.f;
+  }
+}
+
 // VX consecutive 16-bit elements of population e stored with stochastic
 // rounding, as one 2/4/8/16-byte access; kp[p] is the key of the even node
 // of pair p.  VX = 1 (node x, x0 = x) takes its lane of its pair's word, so
@@ -315,6 +330,9 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
 #pragma unroll
     for (int j = 0; j < VX; ++j) m[j] = A.mask[rc * A.px + x0 + j];
   }
+  // ---- every load of the thread is issued before any value is used (moments
+  // of the node and its pull sources, the x-edge moments, the population
+  // words and their x-edge words), so that all are in flight together
   float Mo[KM][VX], Mym[KM][VX], Myp[KM][VX], Mzm[KM][VX], Mzp[KM][VX], Mxl[KM], Mxr[KM];
   load_moments<KM, VX>(min + eq_off(A.px, rc, x0, K), K, Mo);
   load_moments<KM, VX>(min + eq_off(A.px, rym, x0, K), K, Mym);
@@ -323,25 +341,21 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
     load_moments<KM, VX>(min + eq_off(A.px, rzm, x0, K), K, Mzm);
     load_moments<KM, VX>(min + eq_off(A.px, rzp, x0, K), K, Mzp);
   }
+  float El[KM], Er[KM];  // x - 1 and x + VX moments, read by the warp's edge lanes
   {
     const float *Ml = min + eq_off(A.px, rc, xl, K), *Mr = min + eq_off(A.px, rc, xr, K);
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
-      float l = __shfl_up_sync(0xffffffffu, Mo[k][VX - 1], 1);
-      float r = __shfl_down_sync(0xffffffffu, Mo[k][0], 1);
-      if (k < K) {
-        if (ledge) l = __ldg(Ml + k * kEqTile);
-        if (redge) r = __ldg(Mr + k * kEqTile);
-      } else {
-        l = r = 0.f;
-      }
-      Mxl[k] = l;
-      Mxr[k] = r;
+      El[k] = (k < K && ledge) ? __ldg(Ml + k * kEqTile) : 0.f;
+      Er[k] = (k < K && redge) ? __ldg(Mr + k * kEqTile) : 0.f;
     }
   }
-
-  // ---- pull: every population word is loaded before any is decoded, so
-  // all of a thread's reads are in flight together
+  // In 3D (28 words and five moment rows per thread, ~124 registers) the
+  // x-neighbour moments are settled before the population words are
+  // requested, which keeps fewer values live (measured faster there; so is
+  // this register path against staging the moment rows in shared memory);
+  // in 2D everything is requested first.
+  if constexpr (D == 3) settle_edge_moments<KM, VX>(Mo, El, Er, K, ledge, redge, Mxl, Mxr);
   using PW = typename Packed16<TS, VX>::W;
   PW wv[D + 1][Q];
   unsigned edge[D + 1][2];  // per set: x - 1 value of the +x pull, x + VX value of the -x pull
@@ -359,6 +373,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
       if (L::c(i, 0) == -1) edge[s][1] = redge ? ldg_bits16(Pr + k) : 0u;
     }
   }
+  if constexpr (D == 2) settle_edge_moments<KM, VX>(Mo, El, Er, K, ledge, redge, Mxl, Mxr);
   // ---- decode, direction by direction (source terms shared by the sets)
   T G[D + 1][Q][NP];  // [velocity sets 0..D-1, continuity set D][i][lane group]
 #pragma unroll
@@ -478,7 +493,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_eq(const DevArgs A) {
   if (MODE == MODE_FIELDS || !active) return;
 
   // ---- collide + encode
-  const float s1 = float(A.s1), s2 = float(A.s2);
+  const float s1 = A.s1f, s2 = A.s2f;
   float kf[6];
   if constexpr (Q == 5) {
     kf[0] = (1.f - s1) * 0.5f;

@@ -23,6 +23,7 @@ struct DevArgs {
   int vx;                        // x-nodes per thread of the update kernel (1: scalar)
   int block;                     // threads per block of the update kernel
   double s1, s2;                 // relaxation rates (s0 never acts: m0 = m0eq)
+  float s1f, s2f;                // the same rates rounded to FP32 on the host
   double lid_u[3];               // lid velocity
   // derived-field outputs (dense [N] layout), each nullable
   double *P, *u, *rho, *G, *div, *S, *sigma, *omega;

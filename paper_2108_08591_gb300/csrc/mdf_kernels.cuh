@@ -27,6 +27,13 @@ namespace mdf {
 template <class TS> struct ComputeOf { using T = float; };
 template <> struct ComputeOf<double> { using T = double; };
 
+// A relaxation rate in the compute type (the FP32 copy is rounded on the
+// host, so no kernel converts from FP64).
+template <class TC> __device__ __forceinline__ TC rate(double d, float f) {
+  if constexpr (std::is_same<TC, double>::value) return d;
+  else return f;
+}
+
 // FP32 storage takes the dithered (stochastic) rounding of the collision
 // (mdf_lattice.cuh); the other storage types round to nearest.
 template <class TS> constexpr bool dithered() { return std::is_same<TS, float>::value; }
@@ -310,8 +317,8 @@ __global__ void __launch_bounds__(kMaxBlock) k_update(const DevArgs A) {
   constexpr bool DZ = dithered<TS>();
   uint32_t key = 0u;
   if constexpr (DZ) key = node_key(A.key_base + ((long long)z * A.ny + y) * A.nx + x, launch_step(A));
-  if (A.scheme2) collide_node<L, TC, true, DZ>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M, key);
-  else collide_node<L, TC, false, DZ>(g, h, A.with_rho != 0, F, TC(A.s1), TC(A.s2), M, key);
+  if (A.scheme2) collide_node<L, TC, true, DZ>(g, h, A.with_rho != 0, F, rate<TC>(A.s1, A.s1f), rate<TC>(A.s2, A.s2f), M, key);
+  else collide_node<L, TC, false, DZ>(g, h, A.with_rho != 0, F, rate<TC>(A.s1, A.s1f), rate<TC>(A.s2, A.s2f), M, key);
 
   TS *__restrict__ fout = static_cast<TS *>(A.fout);
 #pragma unroll
@@ -545,18 +552,25 @@ __device__ __forceinline__ void pull_all_vec16(const DevArgs &A, const TS *__res
   }
 }
 
-// Register budget of the vector kernel per thread (255: the compiler's
-// choice).  FP32 with 4 nodes per thread is held to VEC_F32X4_REGS, which
-// sets its resident warps at the 128-thread launch.
-#ifndef VEC_F32X4_REGS
-#define VEC_F32X4_REGS 96
-#endif
-template <class TS, int VX> constexpr int vec_max_regs() {
-  return (std::is_same<TS, float>::value && VX == 4) ? VEC_F32X4_REGS : 255;
+// Register budget of the FP32 vector kernel with 4 nodes per thread, which
+// sets its resident warps at the 128-thread launch (the other widths and
+// types take the compiler's choice).
+constexpr int kVecF32x4Regs = 96;
+
+template <class L, class TS, int VX, int MODE, bool WALLS, bool S2>
+__device__ __forceinline__ void update_vec_body(const DevArgs &A);
+
+template <class L, class TS, int VX, int MODE, bool WALLS, bool S2>
+__global__ void __launch_bounds__(kMaxBlock) k_update_vec(const DevArgs A) {
+  update_vec_body<L, TS, VX, MODE, WALLS, S2>(A);
+}
+template <class L, int MODE, bool WALLS, bool S2>
+__global__ void __maxnreg__(kVecF32x4Regs) k_update_vec_f32x4(const DevArgs A) {
+  update_vec_body<L, float, 4, MODE, WALLS, S2>(A);
 }
 
 template <class L, class TS, int VX, int MODE, bool WALLS, bool S2>
-__global__ void __launch_bounds__(kMaxBlock) __maxnreg__((vec_max_regs<TS, VX>())) k_update_vec(const DevArgs A) {
+__device__ __forceinline__ void update_vec_body(const DevArgs &A) {
   using TC = typename ComputeOf<TS>::T;
   constexpr int D = L::D, Q = L::Q;
   const int lane = threadIdx.x & 31;
@@ -606,7 +620,7 @@ __global__ void __launch_bounds__(kMaxBlock) __maxnreg__((vec_max_regs<TS, VX>()
       for (int j = 0; j < VX; ++j) F[a][j] = TC(0);
     }
   }
-  const TC s1 = TC(A.s1), s2 = TC(A.s2);
+  const TC s1 = rate<TC>(A.s1, A.s1f), s2 = rate<TC>(A.s2, A.s2f);
   constexpr bool DZ = dithered<TS>();
   if (MODE != MODE_STEP) {  // fields of the pulled state, node by node
 #pragma unroll
@@ -980,14 +994,22 @@ cudaError_t update_vec(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
       if (walls) k_update_vec16p<L, TS, VX, true, false><<<grid, block, 0, s>>>(a);
       else k_update_vec16p<L, TS, VX, false, false><<<grid, block, 0, s>>>(a);
     }
-    return cudaGetLastError();
-  }
-  if (a.scheme2) {
-    if (walls) k_update_vec<L, TS, VX, MODE_STEP, true, true><<<grid, block, 0, s>>>(a);
-    else k_update_vec<L, TS, VX, MODE_STEP, false, true><<<grid, block, 0, s>>>(a);
+  } else if constexpr (std::is_same<TS, float>::value && VX == 4) {  // the register-budgeted build
+    if (a.scheme2) {
+      if (walls) k_update_vec_f32x4<L, MODE_STEP, true, true><<<grid, block, 0, s>>>(a);
+      else k_update_vec_f32x4<L, MODE_STEP, false, true><<<grid, block, 0, s>>>(a);
+    } else {
+      if (walls) k_update_vec_f32x4<L, MODE_STEP, true, false><<<grid, block, 0, s>>>(a);
+      else k_update_vec_f32x4<L, MODE_STEP, false, false><<<grid, block, 0, s>>>(a);
+    }
   } else {
-    if (walls) k_update_vec<L, TS, VX, MODE_STEP, true, false><<<grid, block, 0, s>>>(a);
-    else k_update_vec<L, TS, VX, MODE_STEP, false, false><<<grid, block, 0, s>>>(a);
+    if (a.scheme2) {
+      if (walls) k_update_vec<L, TS, VX, MODE_STEP, true, true><<<grid, block, 0, s>>>(a);
+      else k_update_vec<L, TS, VX, MODE_STEP, false, true><<<grid, block, 0, s>>>(a);
+    } else {
+      if (walls) k_update_vec<L, TS, VX, MODE_STEP, true, false><<<grid, block, 0, s>>>(a);
+      else k_update_vec<L, TS, VX, MODE_STEP, false, false><<<grid, block, 0, s>>>(a);
+    }
   }
   return cudaGetLastError();
 }

@@ -98,6 +98,17 @@ __device__ __forceinline__ float dithered_change(float dl, float v, float r) {
   return __fmaf_rn(r, p2, __fmaf_rn(-1.498046875f * 0x1p-23f, p2, dl));
 }
 
+// g <- g + dl: the change of a population added once, dithered for FP32
+// storage (DZ) with the random scale rz[i].
+template <bool DZ, class TC>
+__device__ __forceinline__ void add_change(TC &g, TC dl, const float *rz, int i) {
+  if constexpr (DZ) g = g + dithered_change(dl, g, rz[i]);
+  else g = g + dl;
+}
+// Round-to-nearest storage (16-bit rest-shifted, FP64): the change of each
+// population is added term by term, g - h1 - ... + w F, in the order that
+// keeps fewest values live; the stored rounding dominates there.
+
 // ---------------------------------------------------------------------------
 // D2Q5 (Sec. 2.2): c_0..c_4 = (0,0),(1,0),(0,1),(-1,0),(0,-1);
 // w_0 = 1/3, w_1..4 = 1/6; c_s^2 = 1/3.  MRT basis of Eq. 4-2 (c = 1):
@@ -135,16 +146,18 @@ struct D2Q5 {
     const TC d4 = s2 * ((g[1] + g[2] + g[3] + g[4]) - TC(4) * g[0] + TC(2.0 / 3.0) * m0);
     const TC h1 = TC(0.5) * d1, h2 = TC(0.5) * d2, q3 = TC(0.25) * d3, e4 = TC(0.05) * d4;
     const TC Fw = F * TC(1.0 / 6.0);
-    TC dl[Q];
-    dl[0] = TC(0.2) * d4 + F * TC(1.0 / 3.0);
-    dl[1] = ((Fw - h1) - q3) - e4;
-    dl[2] = ((Fw - h2) + q3) - e4;
-    dl[3] = ((Fw + h1) - q3) - e4;
-    dl[4] = ((Fw + h2) + q3) - e4;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if constexpr (DZ) g[i] = g[i] + dithered_change(dl[i], g[i], rz[i]);
-      else g[i] = g[i] + dl[i];
+    if constexpr (DZ) {
+      add_change<DZ>(g[0], TC(0.2) * d4 + F * TC(1.0 / 3.0), rz, 0);
+      add_change<DZ>(g[1], ((Fw - h1) - q3) - e4, rz, 1);
+      add_change<DZ>(g[2], ((Fw - h2) + q3) - e4, rz, 2);
+      add_change<DZ>(g[3], ((Fw + h1) - q3) - e4, rz, 3);
+      add_change<DZ>(g[4], ((Fw + h2) + q3) - e4, rz, 4);
+    } else {
+      g[0] = g[0] + TC(0.2) * d4 + F * TC(1.0 / 3.0);
+      g[1] = g[1] - h1 - q3 - e4 + Fw;
+      g[2] = g[2] - h2 + q3 - e4 + Fw;
+      g[3] = g[3] + h1 - q3 - e4 + Fw;
+      g[4] = g[4] + h2 + q3 - e4 + Fw;
     }
   }
 };
@@ -187,18 +200,22 @@ struct D3Q7 {
     const TC e4 = d4 * TC(1.0 / 42.0);
     const TC ex = d5 * TC(1.0 / 6.0), eo = d5 * TC(1.0 / 12.0), q6 = TC(0.25) * d6;
     const TC Fw = F * TC(0.125);
-    TC dl[Q];
-    dl[0] = d4 * TC(1.0 / 7.0) + F * TC(0.25);
-    dl[1] = ((Fw - h1) - e4) - ex;
-    dl[2] = ((Fw + h1) - e4) - ex;
-    dl[3] = (((Fw - h2) - e4) + eo) - q6;
-    dl[4] = (((Fw + h2) - e4) + eo) - q6;
-    dl[5] = (((Fw - h3) - e4) + eo) + q6;
-    dl[6] = (((Fw + h3) - e4) + eo) + q6;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if constexpr (DZ) g[i] = g[i] + dithered_change(dl[i], g[i], rz[i]);
-      else g[i] = g[i] + dl[i];
+    if constexpr (DZ) {
+      add_change<DZ>(g[0], d4 * TC(1.0 / 7.0) + F * TC(0.25), rz, 0);
+      add_change<DZ>(g[1], ((Fw - h1) - e4) - ex, rz, 1);
+      add_change<DZ>(g[2], ((Fw + h1) - e4) - ex, rz, 2);
+      add_change<DZ>(g[3], (((Fw - h2) - e4) + eo) - q6, rz, 3);
+      add_change<DZ>(g[4], (((Fw + h2) - e4) + eo) - q6, rz, 4);
+      add_change<DZ>(g[5], (((Fw - h3) - e4) + eo) + q6, rz, 5);
+      add_change<DZ>(g[6], (((Fw + h3) - e4) + eo) + q6, rz, 6);
+    } else {
+      g[0] = g[0] + d4 * TC(1.0 / 7.0) + F * TC(0.25);
+      g[1] = g[1] - h1 - e4 - ex + Fw;
+      g[2] = g[2] + h1 - e4 - ex + Fw;
+      g[3] = g[3] - h2 - e4 + eo - q6 + Fw;
+      g[4] = g[4] + h2 - e4 + eo - q6 + Fw;
+      g[5] = g[5] - h3 - e4 + eo + q6 + Fw;
+      g[6] = g[6] + h3 - e4 + eo + q6 + Fw;
     }
   }
 };
@@ -231,15 +248,16 @@ struct D2Q4 {
     const TC d3 = s2 * ((g[0] + g[2]) - (g[1] + g[3]));
     const TC h1 = TC(0.5) * d1, h2 = TC(0.5) * d2, q3 = TC(0.25) * d3;
     const TC Fw = F * TC(0.25);
-    TC dl[Q];
-    dl[0] = (Fw - h1) - q3;
-    dl[1] = (Fw - h2) + q3;
-    dl[2] = (Fw + h1) - q3;
-    dl[3] = (Fw + h2) + q3;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if constexpr (DZ) g[i] = g[i] + dithered_change(dl[i], g[i], rz[i]);
-      else g[i] = g[i] + dl[i];
+    if constexpr (DZ) {
+      add_change<DZ>(g[0], (Fw - h1) - q3, rz, 0);
+      add_change<DZ>(g[1], (Fw - h2) + q3, rz, 1);
+      add_change<DZ>(g[2], (Fw + h1) - q3, rz, 2);
+      add_change<DZ>(g[3], (Fw + h2) + q3, rz, 3);
+    } else {
+      g[0] = g[0] - h1 - q3 + Fw;
+      g[1] = g[1] - h2 + q3 + Fw;
+      g[2] = g[2] + h1 - q3 + Fw;
+      g[3] = g[3] + h2 + q3 + Fw;
     }
   }
 };
@@ -273,17 +291,20 @@ struct D3Q6 {
     const TC h1 = TC(0.5) * d1, h2 = TC(0.5) * d2, h3 = TC(0.5) * d3;
     const TC ex = d4 * TC(1.0 / 6.0), eo = d4 * TC(1.0 / 12.0), q5 = TC(0.25) * d5;
     const TC Fw = F * TC(1.0 / 6.0);
-    TC dl[Q];
-    dl[0] = (Fw - h1) - ex;
-    dl[1] = (Fw + h1) - ex;
-    dl[2] = ((Fw - h2) + eo) - q5;
-    dl[3] = ((Fw + h2) + eo) - q5;
-    dl[4] = ((Fw - h3) + eo) + q5;
-    dl[5] = ((Fw + h3) + eo) + q5;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if constexpr (DZ) g[i] = g[i] + dithered_change(dl[i], g[i], rz[i]);
-      else g[i] = g[i] + dl[i];
+    if constexpr (DZ) {
+      add_change<DZ>(g[0], (Fw - h1) - ex, rz, 0);
+      add_change<DZ>(g[1], (Fw + h1) - ex, rz, 1);
+      add_change<DZ>(g[2], ((Fw - h2) + eo) - q5, rz, 2);
+      add_change<DZ>(g[3], ((Fw + h2) + eo) - q5, rz, 3);
+      add_change<DZ>(g[4], ((Fw - h3) + eo) + q5, rz, 4);
+      add_change<DZ>(g[5], ((Fw + h3) + eo) + q5, rz, 5);
+    } else {
+      g[0] = g[0] - h1 - ex + Fw;
+      g[1] = g[1] + h1 - ex + Fw;
+      g[2] = g[2] - h2 + eo - q5 + Fw;
+      g[3] = g[3] + h2 + eo - q5 + Fw;
+      g[4] = g[4] - h3 + eo + q5 + Fw;
+      g[5] = g[5] + h3 + eo + q5 + Fw;
     }
   }
 };

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(kMaxBlock) k_update_vec16p(const DevArgs A) {
       for (int j = 0; j < VX; ++j) F[a][j] = 0.f;
     }
   }
-  const float s1 = float(A.s1), s2 = float(A.s2);
+  const float s1 = A.s1f, s2 = A.s2f;
 #pragma unroll
   for (int j = 0; j < VX; ++j) {
     float gn[D][Q], hn[Q], Fn[D];

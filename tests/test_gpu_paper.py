@@ -36,14 +36,15 @@ def _rel(a, b):
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(a.ravel()))
 
 
-@pytest.mark.parametrize("storage,rtol", [("f64", 2e-3), ("f32", 3e-2)])
+@pytest.mark.parametrize("storage,rtol", [("f64", 2e-3), ("f32", 2e-3)])
 def test_poiseuille_matches_paper(storage, rtol):
     """Sec. 4.1: E(u1) = 5.9427e-4 at 32^2, s1 = 1.2; the gradient, strain
     rate and vorticity exact for the linear shear (the paper quotes ~1e-16;
-    storage rounding sets the floor here).  With FP32 storage the force
-    increment per step (~4e-7) is small next to the stored populations
-    (~7e-5), so each addition drops low bits with a bias: u carries ~1e-5
-    relative error, which moves the 6e-4 error E(u1) by ~2 % (bound 3 %)."""
+    storage rounding sets the floor here).  The force increment per step
+    (~4e-7) enters each population's change at the non-equilibrium scale
+    and FP32 storage rounds the one add stochastically, so the FP32 run
+    keeps E(u1) within 3e-5 of the FP64 one and the gradients at ~5e-7
+    (bound 1e-5); with round-to-nearest they were 1.8 % and 1.3e-5 off."""
     from paper_2108_08591_gb300 import Lattice
     g = _gold("poiseuille")
     N, nu, F1, s1 = g["N"], g["nu"], g["F1"], g["s1"]
@@ -63,7 +64,7 @@ def test_poiseuille_matches_paper(storage, rtol):
     print(storage, "E(u1)", _rel(ua, out["u"][0]), "E(G)", _rel(gy, out["G"][0, 1]),
           "E(S)", _rel(gy / 2, out["S"][1]), "E(omega)", _rel(-gy, out["omega"][0]))
     assert _rel(ua, out["u"][0]) == pytest.approx(g["E_u1"], rel=rtol)
-    floor = 1e-8 if storage == "f64" else 3e-2
+    floor = 1e-8 if storage == "f64" else 1e-5
     assert _rel(gy, out["G"][0, 1]) < floor
     assert _rel(gy / 2, out["S"][1]) < floor
     assert _rel(-gy, out["omega"][0]) < floor
@@ -107,8 +108,9 @@ def test_scheme2_poiseuille_is_exact(storage):
     - With the paper's s2 rule (Lambda = 3/16) the steady profile is the
       parabola itself: the FP64 oracle reaches it to 1e-9 in these 22000
       steps, where Eq. 3-21 leaves the printed E(u1) = 5.9427e-4.
-    - FP32 storage: the biased rounding of the force increments (see the
-      Eq. 3-21 test) leaves ~1e-5."""
+    - FP32 storage (force increments at the small scale, stochastic
+      rounding of the add; see the Eq. 3-21 test): ~7e-8 on u, ~5e-7 on
+      the gradients."""
     from paper_2108_08591_gb300 import Lattice
     g = _gold("poiseuille")
     N, nu, F1, s1 = g["N"], g["nu"], g["F1"], g["s1"]
@@ -128,9 +130,9 @@ def test_scheme2_poiseuille_is_exact(storage):
     gy = np.repeat(F1 / (2 * nu) * (1 - 2 * y), N) * dt
     print(storage, "scheme II E(u1)", _rel(ua, out["u"][0]), "E(G)", _rel(gy, out["G"][0, 1]),
           "E(S)", _rel(gy / 2, out["S"][1]))
-    bound = 1e-8 if storage == "f64" else 1e-4
+    bound = 1e-8 if storage == "f64" else 1e-6
     assert _rel(ua, out["u"][0]) < bound
-    floor = 1e-8 if storage == "f64" else 3e-2
+    floor = 1e-8 if storage == "f64" else 1e-5
     assert _rel(gy, out["G"][0, 1]) < floor
     assert _rel(gy / 2, out["S"][1]) < floor
 
