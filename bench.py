@@ -53,6 +53,10 @@ TG3D_S2 = 1.0
 S2 = -1.0  # the workload's s2 (negative: the paper's rule); set in main()
 KERNEL_SOURCES = ("paper_2108_08591_gb300/csrc/mdf_kernels.cuh",
                   "paper_2108_08591_gb300/csrc/mdf_lattice.cuh")
+# sources of the equilibrium-shifted update (its recorded traffic is keyed
+# by their hash)
+EQ_SOURCES = KERNEL_SOURCES + ("paper_2108_08591_gb300/csrc/mdf_eq.cuh",
+                               "paper_2108_08591_gb300/csrc/mdf_pack16.cuh")
 
 
 def _dist():
@@ -90,23 +94,26 @@ def aggregate(local_updates: float, local_ms: float, dist=None, device="cpu"):
     return total / (t_max / 1e3) / 1e6, t_max, world
 
 
-def _kernel_sha() -> str:
+def _kernel_sha(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in sources:
         with open(os.path.join(ROOT, p), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel_sha: str):
-    """DRAM bytes per launch of the step kernel from the committed ncu
-    summary, or None when the kernel changed since it was captured."""
+def _traffic(kernel_sha: str, leg: str = ""):
+    """DRAM bytes per launch of the step kernel (or of a storage leg's
+    kernel) from the committed ncu summary, or None when the kernel changed
+    since it was captured."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             t = json.load(fh)
     except (OSError, ValueError):
         return None
+    if leg:
+        t = t.get(leg) or {}
     if t.get("kernel_sha") != kernel_sha:
         return None
     return t.get("dram_bytes_per_launch_4096")
@@ -353,10 +360,13 @@ def storage_leg(shape, s1, P, u, storage, steps=5, warmup=3, q=0, oracle_check=T
     del fields
     peak, kind = _peaks()
     achieved = info.bytes_per_update * N / (plain_ms / 1e3) / 1e9
+    sha = _kernel_sha(EQ_SOURCES) if storage.endswith("eq") else _kernel_sha()
+    traffic = _traffic(sha, storage) if (N_GRID == 4096 and len(shape) == 2) else None
     out = {"storage": storage, "value": steps * EPI_EVERY * N / (ms / 1e3) / 1e6, "unit": "MLUPS",
            "steps": steps, "warmup": warmup,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak, "bytes_per_node": info.bytes_per_update,
+                        "frac": achieved / peak, "traffic": traffic, "kernel_sha": sha,
+                        "bytes_per_node": info.bytes_per_update,
                         "avg_launch_ms": plain_ms, "vx": info.vx, "block": info.block,
                         "peak_source": f"{kind} hbm_gbs (MEASURED_PEAKS.json)"}}
     if oracle_check:
