@@ -571,7 +571,7 @@ def run_cavities(args):
     sched_default = b.schedule()
     ms_default = timed()
     t0 = time.perf_counter()
-    sched = b.autotune(reps=20)  # untimed: chooses the persistent kernel's launch shape
+    sched = b.autotune(reps=60)  # untimed: chooses the persistent kernel's launch shape
     tune_s = time.perf_counter() - t0
     ms = timed()
     mlups = nodes.sum() / (ms / 1e3) / 1e6

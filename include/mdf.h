@@ -431,18 +431,22 @@ mdf_status mdf_batch_set_timeout(mdf_batch_t b, long long cycles);
  * nodes of a 128-node tile, `threads` apart), `grid` co-resident blocks (0:
  * the most that fit, MDF_EINVAL above that) and `sched` 0 (live tiles dealt
  * round-robin to the blocks, a grid barrier between steps), 1 (one
- * contiguous run of tiles per block, grid barrier) or 2 (round-robin, no
+ * contiguous run of tiles per block, grid barrier), 2 (round-robin, no
  * grid barrier: a tile starts a step once the tiles within one neighbour
- * stride of it have finished the previous one).  Every schedule computes
- * the same bits; only the speed differs. */
+ * stride of it have finished the previous one) or 3 (round-robin but for
+ * the last eight rounds of each step, whose tiles the blocks claim one at a
+ * time from an atomic ticket counter; grid barrier).  Every schedule
+ * computes the same bits; only the speed differs.  MDF_EINVAL for other
+ * values.  A new batch starts with 64 threads, schedule 3 and the largest
+ * grid. */
 mdf_status mdf_batch_set_schedule(mdf_batch_t b, int threads, int grid, int sched);
 
 /* mdf_batch_get_schedule -- the launch shape in use (any pointer may be NULL). */
 mdf_status mdf_batch_get_schedule(mdf_batch_t b, int *threads, int *grid, int *sched);
 
 /* mdf_batch_autotune -- time `reps` (rounded up to even; < 2: 20) steps of
- * every schedule candidate (threads 128 / 64 / 32, schedules 0 / 1 / 2, grids
- * of 1, 2, 3, 4, 6, 8, 12, 16 blocks per SM up to the co-resident limit) on
+ * every schedule candidate (threads 128 / 64 / 32, schedules 0 .. 3, grids
+ * of 1, 2, 3, 4, 6, 8, 12, 16, 24, 32 blocks per SM up to the co-resident limit) on
  * the current state with all cavities live, keep the fastest and restore
  * the state (bit for bit; step counts and statuses are not touched).
  * Needs one extra population pool of device memory while it runs. */

@@ -42,6 +42,22 @@ struct CavParam {
   unsigned long long mN;   // ceil(2^64 / N): floor(k / N) = mulhi(k, mN) for k < 2^32
 };
 
+// Word offsets in the barrier buffer, each counter on its own 128-byte line
+// so that the arrivals, the polled generation and the tickets of even and
+// odd steps do not share a line.
+constexpr int kBarGen = 0, kBarArrive = 32, kBarTicket = 64, kBarWords = 128;
+// Schedule 3: rounds of tiles, at the end of every step, that blocks claim
+// from a ticket counter instead of taking them round-robin (8 measured
+// fastest on 64 cavities, against 1 .. 24 and all tiles claimed).
+#ifndef MDF_BATCH_TAIL_ROUNDS
+#define MDF_BATCH_TAIL_ROUNDS 8
+#endif
+constexpr int kDynRounds = MDF_BATCH_TAIL_ROUNDS;
+// Sleep between polls of the barrier's generation, in nanoseconds.
+#ifndef MDF_BATCH_BAR_SLEEP
+#define MDF_BATCH_BAR_SLEEP 256
+#endif
+
 enum CavStatus { CAV_RUNNING = 0, CAV_CONVERGED = 1, CAV_DIVERGED = 2, CAV_MAXSTEPS = 3 };
 
 struct BatchArgs {
@@ -59,38 +75,43 @@ struct BatchArgs {
   int *status;              // [ncav]
   long long *steps;         // [ncav]
   double *res;              // [ncav]
-  unsigned int *bar;        // [0] arrivals, [1] generation
+  unsigned int *bar;        // [kBarArrive] arrivals, [kBarGen] generation, [kBarTicket + 32 (s & 1)]
+                            // tile tickets of step s (schedule 3); one 128-byte line each
   int *err;                 // MDF_ETIMEOUT on a barrier or neighbour-wait time-out
   long long timeout;        // barrier spin limit in clock cycles
   int *prog;                // [ntiles] steps completed in the current launch (schedule 2)
   int *clock;               // steps since the batch was seeded (dither draws of FP32 rounding)
 };
 
-// Bounded grid-wide barrier for a cooperative launch: the last block to
-// arrive advances the generation; the others spin on it, give up after
-// `timeout` cycles (or when another block already gave up), and report.
-__device__ __forceinline__ bool grid_barrier(const BatchArgs &B) {
+// Bounded grid-wide barrier for a cooperative launch after step s: the
+// last block to arrive clears the ticket counter of step s + 1 and advances
+// the generation; the others poll it, give up after `timeout` cycles (or
+// when another block already gave up), and report.
+__device__ __forceinline__ bool grid_barrier(const BatchArgs &B, int s) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int *gen = B.bar + 1;
+    volatile unsigned int *gen = B.bar + kBarGen;
     volatile int *err = B.err;
     const unsigned int g = *gen;
     __threadfence();
-    const unsigned int arrived = atomicAdd(B.bar, 1u) + 1u;
-    if (arrived == gridDim.x) {
-      atomicExch(B.bar, 0u);
+    const bool last = atomicAdd(B.bar + kBarArrive, 1u) + 1u == gridDim.x;
+    if (last) {
+      atomicExch(B.bar + kBarArrive, 0u);
+      atomicExch(B.bar + kBarTicket + 32 * ((s + 1) & 1), 0u);
       __threadfence();
-      atomicAdd(B.bar + 1, 1u);
+      atomicAdd(B.bar + kBarGen, 1u);
     } else {
       const long long t0 = clock64();
-      while (*gen == g) {
-        if (*err) break;
-        if (clock64() - t0 > B.timeout) {
-          atomicCAS(B.err, 0, (int)MDF_ETIMEOUT);
-          break;
+      for (unsigned int k = 0; *gen == g; ++k) {
+        if ((k & 15) == 0) {  // from the first poll on, every 16th
+          if (*err) break;
+          if (clock64() - t0 > B.timeout) {
+            atomicCAS(B.err, 0, (int)MDF_ETIMEOUT);
+            break;
+          }
         }
-        __nanosleep(64);
+        __nanosleep(MDF_BATCH_BAR_SLEEP);
       }
     }
     __threadfence();
@@ -249,33 +270,83 @@ __device__ __forceinline__ void batch_update_node(const BatchArgs &B, const floa
 // stays on consecutive nodes); blocks take live tiles round-robin (SCHED 0)
 // or one contiguous run of the live list each (SCHED 1), with a grid
 // barrier between steps, or round-robin with per-tile step counters and
-// neighbour waits instead of the barrier (SCHED 2).  Every schedule does the
-// same arithmetic per node, so all give the same bits.
+// neighbour waits instead of the barrier (SCHED 2).  SCHED 3 deals all but
+// the last kDynRounds rounds of tiles round-robin and lets the blocks claim
+// the rest one tile at a time from the step's ticket counter, so that a
+// block that ran slow takes fewer of the tiles before the barrier.  Every
+// schedule does the same arithmetic per node, so all give the same bits.
+// Schedule 3 of D2Q5 at 128 threads is held to the 12 co-resident blocks
+// per SM (40 registers) that schedules 0 .. 2 reach unconstrained, so its
+// ticket logic costs no occupancy; 0 leaves the register count free.
+template <class L, int T>
+constexpr int batch_min_blocks() {
+  return L::D == 2 && T == 128 ? 12 : 0;
+}
+
 template <class L, int T, int SCHED>
-__global__ void __launch_bounds__(T) k_batch_chunk(BatchArgs B, int cur, int steps, int save_first) {
+__global__ void __launch_bounds__(T, SCHED == 3 ? batch_min_blocks<L, T>() : 0)
+    k_batch_chunk(BatchArgs B, int cur, int steps, int save_first) {
   constexpr int PER = kTile / T;
   const int nl = *B.n_live;
-  const int t0 = SCHED != 1 ? (int)blockIdx.x : (int)((long long)nl * blockIdx.x / gridDim.x);
-  const int t1 = SCHED != 1 ? nl : (int)((long long)nl * (blockIdx.x + 1) / gridDim.x);
-  const int dt = SCHED != 1 ? (int)gridDim.x : 1;
+  const int G = (int)gridDim.x;
+  const int nstat = SCHED == 3 ? max(0, nl / G - kDynRounds) * G : nl;  // tiles dealt round-robin
+  const int t0 = SCHED != 1 ? (int)blockIdx.x : (int)((long long)nl * blockIdx.x / G);
+  const int t1 = SCHED != 1 ? nl : (int)((long long)nl * (blockIdx.x + 1) / G);
+  const int dt = SCHED != 1 ? G : 1;
   const int tclock = __ldg(B.clock);
+  __shared__ int next_ticket;
   for (int s = 0; s < steps; ++s) {
     const float *fin = B.f[(cur + s) & 1];
     float *fout = B.f[(cur + s + 1) & 1];
     const bool save = save_first && s == 0;
-    for (int t = t0; t < t1; t += dt) {
-      const int tile = B.live[t];
+    auto update_tile = [&](int tile) {
       const CavParam C = B.cav[B.tile_cav[tile]];
       const long long count = node_count<L>(C.N);
-      if (SCHED == 2 && !wait_neighbours<L>(B, C, tile, s, count)) return;
 #pragma unroll
       for (int r = 0; r < PER; ++r) {
         const int k = (tile - C.tile0) * kTile + r * T + (int)threadIdx.x;
         if (k < count) batch_update_node<L>(B, fin, fout, C, k, save, tclock + s);
       }
-      if (SCHED == 2) publish_tile(B, tile, s + 1);
+    };
+    if (SCHED != 3) {
+      for (int t = t0; t < t1; t += dt) {
+        const int tile = B.live[t];
+        if (SCHED == 2) {
+          const CavParam &C = B.cav[B.tile_cav[tile]];
+          if (!wait_neighbours<L>(B, C, tile, s, node_count<L>(C.N))) return;
+        }
+        update_tile(tile);
+        if (SCHED == 2) publish_tile(B, tile, s + 1);
+      }
+    } else {
+      // live-list positions blockIdx.x, + G, ... below nstat, then claimed
+      // tickets; thread 0 claims the following ticket while the block
+      // updates the current tile and publishes it afterwards
+      unsigned int *ticket = B.bar + kBarTicket + 32 * (s & 1);
+      int pos = (int)blockIdx.x;
+      if (pos >= nstat) {
+        if (threadIdx.x == 0) next_ticket = (int)atomicAdd(ticket, 1u);
+        __syncthreads();
+        pos = nstat + next_ticket;
+      }
+      while (pos < nl) {
+        int npos = pos + G;
+        const bool claim = npos >= nstat;  // the same in every thread
+        int claimed = 0;
+        if (claim) {
+          __syncthreads();  // every thread has read next_ticket
+          if (threadIdx.x == 0) claimed = (int)atomicAdd(ticket, 1u);
+        }
+        update_tile(B.live[pos]);
+        if (claim) {
+          if (threadIdx.x == 0) next_ticket = claimed;
+          __syncthreads();
+          npos = nstat + next_ticket;
+        }
+        pos = npos;
+      }
     }
-    if (SCHED != 2 && s + 1 < steps && !grid_barrier(B)) return;
+    if (SCHED != 2 && s + 1 < steps && !grid_barrier(B, s)) return;
   }
 }
 
@@ -479,8 +550,8 @@ struct mdf_batch_s {
   BatchArgs B{};
   int cur = 0;
   int grid = 0;      // blocks of the persistent kernel
-  int threads = 128; // threads per block (kTile / threads nodes per thread)
-  int sched = 0;     // 0: tiles round-robin over blocks, 1: contiguous runs
+  int threads = 64;  // threads per block (kTile / threads nodes per thread)
+  int sched = 3;     // 0: round-robin, 1: contiguous runs, 2: neighbour waits, 3: claimed tail
   int *host_live = nullptr;
   cudaGraphExec_t graph = nullptr;
   int graph_period = 0, graph_cur = 0;
@@ -534,6 +605,11 @@ cudaError_t launch_chunk_s(mdf_batch_t b, int steps, int save_first) {
       cudaError_t e = cudaMemsetAsync(b->B.prog, 0, sizeof(int) * (size_t)b->ntiles, b->stream);
       return e != cudaSuccess ? e : launch_chunk_t<L, T, 2>(b, steps, save_first);
     }
+    case 3: {  // so do the tickets of the first two steps
+      cudaError_t e = cudaMemsetAsync(b->B.bar + kBarTicket, 0, sizeof(unsigned int) * (kBarWords - kBarTicket),
+                                      b->stream);
+      return e != cudaSuccess ? e : launch_chunk_t<L, T, 3>(b, steps, save_first);
+    }
   }
   return cudaErrorInvalidValue;
 }
@@ -555,6 +631,7 @@ cudaError_t occupancy_t(int sched, int *per) {
     case 0: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_batch_chunk<L, T, 0>, T, 0);
     case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_batch_chunk<L, T, 1>, T, 0);
     case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_batch_chunk<L, T, 2>, T, 0);
+    case 3: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per, k_batch_chunk<L, T, 3>, T, 0);
   }
   return cudaErrorInvalidValue;
 }
@@ -596,7 +673,7 @@ mdf_status all_live(mdf_batch_t b) {
   BCU(b, cudaMemcpyAsync(b->B.live, live.data(), sizeof(int) * b->ntiles, cudaMemcpyHostToDevice, b->stream));
   BCU(b, cudaMemcpyAsync(b->B.n_live, &b->ntiles, sizeof(int), cudaMemcpyHostToDevice, b->stream));
   BCU(b, cudaMemsetAsync(b->B.err, 0, sizeof(int), b->stream));
-  BCU(b, cudaMemsetAsync(b->B.bar, 0, sizeof(unsigned int) * 2, b->stream));
+  BCU(b, cudaMemsetAsync(b->B.bar, 0, sizeof(unsigned int) * kBarWords, b->stream));
   BCU(b, cudaStreamSynchronize(b->stream));  // `live` leaves scope
   return MDF_OK;
 }
@@ -697,7 +774,7 @@ mdf_status mdf_batch_create(mdf_batch_t *out, int d, int n, const int *side, con
   if (e == cudaSuccess) e = cudaMalloc(&B.status, sizeof(int) * n);
   if (e == cudaSuccess) e = cudaMalloc(&B.steps, sizeof(long long) * n);
   if (e == cudaSuccess) e = cudaMalloc(&B.res, sizeof(double) * n);
-  if (e == cudaSuccess) e = cudaMalloc(&B.bar, sizeof(unsigned int) * 2);
+  if (e == cudaSuccess) e = cudaMalloc(&B.bar, sizeof(unsigned int) * kBarWords);
   if (e == cudaSuccess) e = cudaMalloc(&B.err, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&B.clock, sizeof(int));
   if (e == cudaSuccess) e = cudaMemsetAsync(B.clock, 0, sizeof(int), b->stream);
@@ -705,7 +782,7 @@ mdf_status mdf_batch_create(mdf_batch_t *out, int d, int n, const int *side, con
   if (e == cudaSuccess) e = cudaMemsetAsync(B.f[0], 0, popb, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(B.f[1], 0, popb, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(B.usave, 0, sizeof(float) * d * (size_t)b->tot, b->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(B.bar, 0, sizeof(unsigned int) * 2, b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(B.bar, 0, sizeof(unsigned int) * kBarWords, b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(B.err, 0, sizeof(int), b->stream);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync((void *)B.cav, b->cav.data(), sizeof(CavParam) * n, cudaMemcpyHostToDevice, b->stream);
@@ -795,7 +872,7 @@ mdf_status mdf_batch_run(mdf_batch_t b, double tol, long long max_steps, int che
   BCU(b, cudaMemcpyAsync(B.live, live.data(), sizeof(int) * b->ntiles, cudaMemcpyHostToDevice, b->stream));
   BCU(b, cudaMemcpyAsync(B.n_live, &b->ntiles, sizeof(int), cudaMemcpyHostToDevice, b->stream));
   BCU(b, cudaMemsetAsync(B.err, 0, sizeof(int), b->stream));
-  BCU(b, cudaMemsetAsync(B.bar, 0, sizeof(unsigned int) * 2, b->stream));
+  BCU(b, cudaMemsetAsync(B.bar, 0, sizeof(unsigned int) * kBarWords, b->stream));
   BCU(b, cudaStreamSynchronize(b->stream));
   // one convergence period as a graph (on a non-legacy stream), else direct launches
   if (b->graph && (b->graph_period != check_every || b->graph_tol != tol || b->graph_max != max_steps ||
@@ -943,7 +1020,7 @@ mdf_status mdf_batch_set_schedule(mdf_batch_t b, int threads, int grid, int sche
   if (!b) return MDF_EINVAL;
   if (threads != 32 && threads != 64 && threads != 128)
     return bfail(b, MDF_EINVAL, "threads per block must be 32, 64 or 128 (got %d)", threads);
-  if (sched < 0 || sched > 2) return bfail(b, MDF_EINVAL, "schedule must be 0, 1 or 2 (got %d)", sched);
+  if (sched < 0 || sched > 3) return bfail(b, MDF_EINVAL, "schedule must be 0, 1, 2 or 3 (got %d)", sched);
   int gmax = 0;
   BCU(b, max_grid(b, threads, sched, &gmax));
   if (grid < 0 || grid > gmax)
@@ -984,24 +1061,24 @@ mdf_status mdf_batch_autotune(mdf_batch_t b, int reps, int *threads_out, int *gr
   int best_threads = old_threads, best_sched = old_sched, best_grid = old_grid;
   float best = 1e30f;
   const int threads_c[3] = {128, 64, 32};
-  const int mult_c[8] = {1, 2, 3, 4, 6, 8, 12, 16};
+  const int mult_c[10] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32};
   bool warmed = false;
   for (int ti = 0; ti < 3 && st == MDF_OK; ++ti)
-    for (int sc = 0; sc < 3 && st == MDF_OK; ++sc) {
+    for (int sc = 0; sc < 4 && st == MDF_OK; ++sc) {
       int gmax = 0;
       if (max_grid(b, threads_c[ti], sc, &gmax) != cudaSuccess) {
         st = bfail(b, MDF_ECUDA, "autotune: occupancy query failed");
         break;
       }
       int last = 0;
-      for (int mi = 0; mi < 8 && st == MDF_OK; ++mi) {
+      for (int mi = 0; mi < 10 && st == MDF_OK; ++mi) {
         const int g = std::min(gmax, mult_c[mi] * sms);
         if (g == last) continue;
         last = g;
         b->threads = threads_c[ti];
         b->sched = sc;
         b->grid = g;
-        cudaError_t e = cudaMemsetAsync(b->B.bar, 0, sizeof(unsigned int) * 2, b->stream);
+        cudaError_t e = cudaMemsetAsync(b->B.bar, 0, sizeof(unsigned int) * kBarWords, b->stream);
         if (e == cudaSuccess && !warmed) {
           e = b->d == 2 ? launch_chunk<D2Q5>(b, 2, 0) : launch_chunk<D3Q7>(b, 2, 0);
           warmed = true;

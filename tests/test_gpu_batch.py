@@ -65,12 +65,12 @@ def test_batch_matches_oracle():
     b.close()
 
 
-@pytest.mark.parametrize("graph,sched", [(False, 0), (True, 0), (True, 2)])
+@pytest.mark.parametrize("graph,sched", [(False, 0), (True, 0), (True, 2), (True, 3)])
 def test_batch_run_to_steady_state(graph, sched):
     """Low-Re cavities converge; the residual and the step count follow the
     definition; the final state equals a plain run of the same length (with
-    the grid-barrier and the neighbour-wait schedules, cavities retiring at
-    different periods)."""
+    the grid-barrier, the neighbour-wait and the claimed-tail schedules,
+    cavities retiring at different periods)."""
     import torch
     from paper_2108_08591_gb300 import CavityBatch, Lattice
     sides, Res = [12, 16, 21], [5.0, 10.0, 20.0]
@@ -139,14 +139,15 @@ def test_barrier_timeout_is_reported_not_hung():
                                          (3, [10, 13], [50.0, 200.0])])
 def test_every_schedule_gives_the_same_bits(d, sides, Res):
     """Threads per block 128 / 64 / 32 (1, 2, 4 nodes per thread), both tile
-    orders with a grid barrier and the barrier-free neighbour-wait schedule,
+    orders with a grid barrier, the claimed-tail order and the barrier-free
+    neighbour-wait schedule,
     a one-block and the largest grid: the same arithmetic per node, so the
     same bits after 40 updates in one launch."""
     from paper_2108_08591_gb300 import CavityBatch
     names = ("P", "u", "G")
     ref = None
     for threads in (128, 64, 32):
-        for sched in (0, 1, 2):
+        for sched in (0, 1, 2, 3):
             for grid in (1, 0):
                 b = CavityBatch(sides, Res, lid_speed=U, d=d)
                 b.set_schedule(threads, grid, sched)
@@ -174,7 +175,7 @@ def test_autotune_keeps_the_state_and_the_bits():
     before = [b.fields_host(c, ("P", "u")) for c in range(3)]
     best = b.autotune(reps=6)
     assert best == b.schedule()
-    assert best["threads"] in (32, 64, 128) and best["sched"] in (0, 1, 2) and best["grid"] >= 1
+    assert best["threads"] in (32, 64, 128) and best["sched"] in (0, 1, 2, 3) and best["grid"] >= 1
     after = [b.fields_host(c, ("P", "u")) for c in range(3)]
     for c in range(3):
         for k in ("P", "u"):
@@ -194,7 +195,7 @@ def test_schedule_rejects_bad_arguments():
     from paper_2108_08591_gb300 import CavityBatch
     from paper_2108_08591_gb300._lib import MdfError
     b = CavityBatch([17], [100.0], lid_speed=U)
-    for args in ((96, 0, 0), (128, 0, 3), (128, -1, 0), (128, 10 ** 7, 0)):
+    for args in ((96, 0, 0), (128, 0, 4), (128, 0, -1), (128, -1, 0), (128, 10 ** 7, 0)):
         with pytest.raises(MdfError, match="EINVAL"):
             b.set_schedule(*args)
     b.close()
