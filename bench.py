@@ -615,17 +615,22 @@ def run_conv(args):
     rows = []
     shapes = [(8, 256, 32, 32), (8, 128, 64, 64), (8, 64, 128, 128), (8, 32, 256, 256),
               (8, 256, 96, 32), (8, 64, 384, 128), (8, 256, 16, 32), (8, 256, 64, 16)]
-    for kern in ("tcgen05-halo", "tcgen05", "mma.sync"):
+    # backward = dgrad (the forward kernel on flipped weights) + the default
+    # tcgen05 weight gradient; with the halo kernel also + the mma.sync one
+    for kern, wgrad in (("tcgen05-halo", "tcgen05"), ("tcgen05-halo", "mma.sync"), ("tcgen05", "tcgen05"),
+                        ("mma.sync", "tcgen05")):
         set_conv_kernel(kern)
-        set_wgrad_kernel("mma.sync")  # the default weight gradient (the faster here)
+        set_wgrad_kernel(wgrad)
         for (B, H, Cin, Cout) in shapes:
             g = torch.Generator(device="cuda").manual_seed(1)
             x = torch.randn(B, H, H, Cin, device="cuda", generator=g).to(torch.bfloat16)
             w = (0.05 * torch.randn(Cout, 3, 3, Cin, device="cuda", generator=g)).to(torch.bfloat16)
             dz = torch.randn(B, H, H, Cout, device="cuda", generator=g).to(torch.bfloat16)
             flops = 2.0 * B * H * H * Cout * 9 * Cin
-            for name, fn, mult in (("fwd", lambda: conv3x3_bf16(x, w, out_fp32=False), 1),
-                                   ("bwd", lambda: conv3x3_bf16_backward(x, w, dz), 2)):
+            ops = (("bwd", lambda: conv3x3_bf16_backward(x, w, dz), 2),)
+            if wgrad == "tcgen05":
+                ops = (("fwd", lambda: conv3x3_bf16(x, w, out_fp32=False), 1),) + ops
+            for name, fn, mult in ops:
                 for _ in range(max(3, args.warmup)):
                     fn()
                 torch.cuda.synchronize()
@@ -641,10 +646,11 @@ def run_conv(args):
                 e1.record()
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / args.steps
-                rows.append({"kernel": kern, "B": B, "H": H, "Cin": Cin, "Cout": Cout, "op": name,
-                             "ms": ms, "tflops": mult * flops / ms / 1e9})
+                rows.append({"kernel": kern, "wgrad": wgrad if name == "bwd" else None, "B": B, "H": H,
+                             "Cin": Cin, "Cout": Cout, "op": name, "ms": ms, "tflops": mult * flops / ms / 1e9})
                 del graph
     set_conv_kernel("tcgen05-halo")
+    set_wgrad_kernel("tcgen05")
     print(json.dumps({"workload": "conv", "unit": "TFLOP/s", "timing": "CUDA graph of --steps calls",
                       "rows": rows}), flush=True)
     return 0

@@ -525,16 +525,19 @@ mdf_status mdf_nn_set_tc_tile(int bn, int stages);
  * mdf_nn_set_tc_tile's bn. */
 mdf_status mdf_nn_set_halo_tile(int mt, int kc);
 
-/* Weight-gradient kernel, process-wide: which = 0 the mma.sync split-K
- * kernel (the default), 1 the tcgen05 kernel (nine TMEM accumulators, one
- * staged x halo per pixel chunk; Cin % 16 != 0 falls back to 0).  Both
- * accumulate in FP32; the tcgen05 one is the slower on this GPU. */
+/* Weight-gradient kernel, process-wide: which = 1 the tcgen05 kernel (the
+ * default: TMA-loaded dz and shifted x boxes, the taps of one kernel row
+ * per CTA in three TMEM accumulators; Cin % 16 != 0 or Cout % 8 != 0 falls
+ * back to 0), 0 the mma.sync split-K kernel.  Both accumulate in FP32. */
 mdf_status mdf_nn_set_wgrad_kernel(int which);
 
-/* Input-channel tile of the tcgen05 weight-gradient kernel, process-wide:
- * 16 or 32 (used when it divides into Cin's 16-channel steps), 0 keeps the
- * automatic choice. */
-mdf_status mdf_nn_set_wgrad_tile(int bn);
+/* Launch shape of the tcgen05 weight-gradient kernel, process-wide: input
+ * channel tile bn 16, 32 or 64 (a tile that does not divide Cin falls back
+ * to 32 or 16; 0 keeps the automatic choice, the largest that divides) and
+ * the CTAs per SM that its pipeline depth leaves shared memory for (1 .. 16;
+ * 0 keeps the default 3); the pixel split fills one wave of the CTAs that
+ * fit.  MDF_EINVAL otherwise. */
+mdf_status mdf_nn_set_wgrad_tile(int bn, int ctas_per_sm);
 
 /* Read and clear the tcgen05 kernel's time-out flag (1 when a bounded
  * mbarrier wait gave up) of the current device; synchronises the device. */

@@ -495,8 +495,15 @@ def set_conv_kernel(which: str):
 
 
 def set_wgrad_kernel(which: str):
-    """Weight-gradient kernel: 'mma.sync' (default) or 'tcgen05'."""
+    """Weight-gradient kernel: 'tcgen05' (default) or 'mma.sync'."""
     _lib.check(_lib.load().mdf_nn_set_wgrad_kernel({"mma.sync": 0, "tcgen05": 1}[which]))
+
+
+def set_wgrad_tile(bn: int = 0, ctas_per_sm: int = 0):
+    """Launch shape of the tcgen05 weight gradient: input-channel tile 16,
+    32 or 64 (0: automatic) and the CTAs per SM its pipeline depth leaves
+    room for (0: the default)."""
+    _lib.check(_lib.load().mdf_nn_set_wgrad_tile(int(bn), int(ctas_per_sm)))
 
 
 def conv_timeout_flag() -> int:

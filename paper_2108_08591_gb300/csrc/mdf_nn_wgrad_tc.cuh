@@ -1,80 +1,139 @@
-// Weight gradient of the 3x3 convolution on the 5th-generation tensor cores.
+// Weight gradient of the 3x3 convolution on the 5th-generation tensor cores,
+// fed by the Tensor Memory Accelerator.
 //
 // dW[o][t][ci] = sum_p dz[p][o] x[p + s_t][ci]: for every tap t a GEMM over
 // pixel positions p (the K dimension) with M = output channels o and N =
-// input channels ci.  Pixels are taken in the padded column-strip positions
-// of the forward halo kernel (strip width <= 64, pitch P = width + 2), so
-// tap (kh, kw) of position p reads x at position p + kh P + kw: one staged
-// x halo per chunk of KP positions serves all nine taps as start offsets.
+// input channels ci.
 //
-// Both operands come straight from NHWC memory with the pixel index
-// outermost, i.e. MN-major: rows of 16 bytes (8 channels of one position),
-// consecutive positions 16 bytes apart inside an 8-channel column.  Staged
-// as such, a K step of 16 positions is a 256-byte advance of the start
-// address, and the tap shift a 16-byte one.  dz rows of the discarded pad
-// columns (and of positions past the image) are zero, so their x values do
-// not contribute.  Nine FP32 accumulators (one per tap, BN columns each)
-// live in TMEM; M is 128 output channels (rows past Cout stay zero).  The
-// pixel chunks are split over CTAs; each writes its partial sums to
-// part[split][Cout][9 Cin] for the split reduction.
+// A chunk is a block of `rows` image rows x TW columns of one image
+// (TW x rows = 128 positions, TW the power of two in {16, 32, 64} that
+// covers the width, or 64 with column strips).  The taps are split over
+// CTAs by kernel row kh: per chunk the CTA of row kh loads, with one TMA box
+// per 8-channel column,
+//   * dz at the chunk's positions (A, M = output channels), and
+//   * for kw = 0, 1, 2, x at the same positions shifted by (kh - 1, kw - 1)
+//     (B, N = input channels),
+// so tap (kh, kw) is a plain GEMM of the chunk: no pad columns and no start
+// offsets.  Boxes that reach past the image edges (the -1 and +1 shifts,
+// ragged strips and rows) are filled with zeros by the TMA unit, which is
+// the convolution's zero padding; dz positions past the image are zero, so
+// nothing outside it contributes.
 //
-// Warp-specialised like the forward kernels: warps 0-3 load with cp.async
-// and signal a stage's `full` mbarrier, one lane of warp 4 issues the
-// 9 x KP / 16 MMAs of a chunk and commits them to the stage's `empty`
-// mbarrier; warps 0-3 then read TMEM and store the partial sums.  Every wait
-// is bounded; a time-out raises the error flag and the CTA still drains its
-// copies and MMAs before freeing TMEM.
+// Both operands are MN-major with the 32-, 64- or 128-byte swizzle: a box
+// of W channels (W = 16, 32 or 64) x TW x rows lands in shared memory as 128
+// rows (positions) of 2W bytes, in groups of 8 rows that the TMA unit and
+// the tensor cores swizzle alike, so a K step of 16 positions is an advance
+// of two groups.  A (M = 128 output channels) is 128 / W such boxes side by
+// side; the ones past Cout are never loaded: the MMA reads whatever lies
+// there, and the D rows they make are never stored (each D row depends only
+// on its own A row).  The shared memory allocation covers the full 128-row
+// read of every stage.
+//
+// Three FP32 accumulators of BN columns live in TMEM (64 to 256 columns), so
+// several CTAs share an SM.  One thread issues the TMA boxes of a stage
+// against its `full` mbarrier (expected bytes), one thread issues the
+// 3 x 128 / 16 MMAs of a chunk and commits them to the stage's `empty`
+// mbarrier, and the four warps then read TMEM and store the partial sums
+// part[split][Cout][9 Cin] of their split of the chunks.  Every wait is
+// bounded; after a time-out the CTA raises the error flag, waits (bounded)
+// for the boxes it issued and its MMAs, and frees TMEM.
 #pragma once
+
+#include <cuda.h>  // CUtensorMap (the tensor maps are encoded on the host)
 
 #include "mdf_nn_halo.cuh"
 
 namespace mdfnn {
 
-constexpr int WG_KP = 64;  // pixel positions per chunk (K per stage)
-constexpr int WG_RB = ((WG_KP + 2 * 66 + 2) + 7) & ~7;  // x-halo rows per 8-channel column
+constexpr int WG_K = 128;        // positions per chunk (K per stage)
+constexpr int WG_THREADS = 128;  // producer lane, MMA lane, four epilogue warps
 
-struct WgradTcArgs {
-  const bf16 *x;   // [B][H][W][Cin]
-  const bf16 *dz;  // [B][H][W][Cout]
+struct WgradTmaArgs {
   float *part;     // [splits][Cout][9 Cin]
   int B, H, W, Cin, Cout;
-  int splits;
+  int TW, rows;    // chunk: rows x TW positions (TW x rows = WG_K)
+  int strips, rblocks;
+  int splits;      // pixel splits; the grid's z is 3 x splits (kernel rows)
+  int wa, na;      // dz box width in channels, boxes per stage (shared memory layout)
 };
 
-template <int BN, int S>
-constexpr size_t wgrad_tc_smem_bytes() {
-  return (size_t)S * (16 * WG_KP * 16 + (BN / 8) * WG_RB * 16) + (2 * S + 1) * 8 + 16;
+// Chunk width of an image of width W: the power of two in {16, 32, 64}
+// covering W, or 64 (column strips).
+__host__ __device__ inline int wgrad_tw(int W) { return W <= 16 ? 16 : W <= 32 ? 32 : 64; }
+
+// dz box width for Cout output channels, and the boxes of the first M tile.
+__host__ __device__ inline int wgrad_wa(int Cout) { return Cout >= 64 ? 64 : Cout >= 32 ? 32 : 16; }
+__host__ __device__ inline int wgrad_na(int Cout) {
+  const int m = Cout < 128 ? Cout : 128, w = wgrad_wa(Cout);
+  return (m + w - 1) / w;
+}
+
+// Shared memory of S stages: the A boxes of all stages first (na boxes of
+// 256 wa bytes each), then the B boxes (three of 256 BN bytes each), then
+// the mbarriers, from a 1024-byte aligned base (1 KB of slack).  The MMA
+// reads 32 KB from each stage's A start, so the data area reaches at least
+// 32 KB past the last stage's A start, plus 4 KB (every address an A
+// descriptor can form, with the two byte offsets taken either way round).
+__host__ __device__ inline size_t wgrad_tma_data_bytes(int BN, int S, int wa, int na) {
+  const size_t as = (size_t)na * 256 * wa, a = S * as, b = (size_t)S * 3 * 256 * BN;
+  const size_t reach = (size_t)(S - 1) * as + 32768 + 4096;
+  return a + b > reach ? a + b : reach;
+}
+__host__ __device__ inline size_t wgrad_tma_smem_bytes(int BN, int S, int wa, int na) {
+  return 1024 + wgrad_tma_data_bytes(BN, S, wa, na) + (2 * S + 1) * 8 + 16;
+}
+
+// Swizzle field of a tcgen05 shared-memory descriptor for rows of `bytes`
+// (32, 64 or 128) bytes.
+__host__ __device__ constexpr uint32_t umma_swizzle(int bytes) { return bytes == 128 ? 2u : bytes == 64 ? 4u : 6u; }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+// One box of a 4D tensor map (c0 innermost) into shared memory, completing
+// on `bar` with its byte count.  c0 is a channel offset, a multiple of 8
+// (16 bytes); the other coordinates may lie outside the tensor (zero fill).
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            int c3, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
 }
 
 template <int BN, int S>
-__global__ void __launch_bounds__(HX_THREADS) k_conv_wgrad_tc(WgradTcArgs a, int *err) {
-  static_assert(BN == 16 || BN == 32, "N tile");
-  constexpr int LAG = S >= 3 ? S - 1 : 1;  // copy groups in flight
-  static_assert(LAG >= 1 && LAG < S, "look-ahead");
-  constexpr int A_BYTES = 16 * WG_KP * 16;      // 128 output channels x KP positions
-  constexpr int NCB = BN / 8;                   // 8-channel columns of the x halo
-  constexpr int B_BYTES = NCB * WG_RB * 16;
-  constexpr int STAGE = A_BYTES + B_BYTES;
-  constexpr uint32_t TCOLS = 9 * BN <= 256 ? 256 : 512;
-  extern __shared__ __align__(1024) uint8_t smem[];
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * STAGE);
+__global__ void __launch_bounds__(WG_THREADS)
+    k_conv_wgrad_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dzmap,
+                     WgradTmaArgs a, int *err) {
+  static_assert(BN == 16 || BN == 32 || BN == 64, "N tile");
+  static_assert(S >= 2 && S <= 8, "stages");
+  constexpr uint32_t BBOX = 256 * BN;  // bytes of one shifted x box (128 positions x BN channels)
+  constexpr uint32_t TCOLS = 3 * BN <= 64 ? 64 : 3 * BN <= 128 ? 128 : 256;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // the swizzle pattern repeats every 1024 bytes of the shared address
+  uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  const uint32_t abox = 256u * (uint32_t)a.wa, astage = abox * (uint32_t)a.na;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + wgrad_tma_data_bytes(BN, S, a.wa, a.na));
   uint64_t *empty = full + S;
   uint64_t *done = empty + S;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  const uint32_t a0 = smem_u32(smem), b0 = a0 + (uint32_t)S * astage;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const HaloGeom g = halo_geom(a.H, a.W, 1);
-  const int tiles = (a.H * g.P + WG_KP - 1) / WG_KP;
-  const long long NQ = (long long)a.B * g.strips * tiles;
-  const int split = blockIdx.z;
+  const int split = blockIdx.z / 3, kh = blockIdx.z - 3 * (blockIdx.z / 3);
+  const long long NQ = (long long)a.B * a.strips * a.rblocks;
   const long long q0 = NQ * split / a.splits, q1 = NQ * (split + 1) / a.splits;
   const int NL = (int)(q1 - q0);  // chunks of this CTA (>= 1)
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * 128;
-  const int mcores = min(16, (a.Cout - m0) / 8);  // real 8-channel columns of dz
-  const int R = WG_KP + 2 * g.P + 2;
+  const int mrem = min(128, a.Cout - m0);
+  const int na = (mrem + a.wa - 1) / a.wa;  // dz boxes this CTA loads (<= a.na)
+  const uint32_t stage_bytes = (uint32_t)na * abox + 3 * BBOX;
   const long long limit = 2000000000LL;
 
-  if (warp == 4) {
+  if (warp == 2) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"(TCOLS));
@@ -82,111 +141,55 @@ __global__ void __launch_bounds__(HX_THREADS) k_conv_wgrad_tc(WgradTcArgs a, int
   }
   if (tid == 0) {
     for (int k = 0; k < S; ++k) {
-      mbar_init(&full[k], 128);
+      mbar_init(&full[k], 1);
       mbar_init(&empty[k], 1);
     }
     mbar_init(done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  // dz columns past Cout are zero in every stage and never rewritten
-  for (int k = tid; k < S * (16 - mcores) * WG_KP; k += blockDim.x) {
-    const int st = k / ((16 - mcores) * WG_KP), rem = k - st * ((16 - mcores) * WG_KP);
-    const int core = mcores + rem / WG_KP, row = rem - (rem / WG_KP) * WG_KP;
-    *reinterpret_cast<uint4 *>(smem + st * STAGE + core * (WG_KP * 16) + row * 16) = make_uint4(0, 0, 0, 0);
-  }
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   const uint32_t tmem = *tmem_slot;
 
   bool ok = true;
-  if (warp < 4) {
-    // ---------------- producers
-    const int rr = tid & 7;
-    const int acore = tid >> 3;  // dz: 16 columns x 8 rows per pass
-    const int bcore = (tid >> 3) % NCB, brg = (tid >> 3) / NCB;
-    constexpr int BROWS = 8 * (16 / NCB);  // x-halo rows per pass
+  if (tid == 0) {
+    // ---------------- producer: the boxes of chunk i into stage i % S
+    int issued = 0;
     for (int i = 0; i < NL; ++i) {
       const int s = i % S;
       if (i >= S && !mbar_wait(&empty[s], (uint32_t)((i / S - 1) & 1), limit)) {
         ok = false;
         break;
       }
-      const long long qq = q0 + i;
-      const int kt = (int)(qq % tiles);
-      const long long bs = qq / tiles;
-      const int strip = (int)(bs % g.strips), b = (int)(bs / g.strips);
-      const int o0 = kt * WG_KP, col0 = strip * g.TW, TWs = min(g.TW, a.W - col0);
-      uint8_t *sa = smem + s * STAGE, *sb = sa + A_BYTES;
-      if (acore < mcores) {  // dz rows: positions o0 + row, zero outside the image or in pad columns
-        int pr = (o0 + rr) / g.P, pc = (o0 + rr) - pr * g.P;
-        for (int row = rr; row < WG_KP; row += 8) {
-          const bool v = pr < a.H && pc < TWs;
-          const bf16 *src = v ? a.dz + (((size_t)b * a.H + pr) * a.W + col0 + pc) * a.Cout + m0 + acore * 8 : a.dz;
-          cp_async16(sa + acore * (WG_KP * 16) + row * 16, src, v);
-          pc += 8;
-          while (pc >= g.P) {
-            pc -= g.P;
-            ++pr;
-          }
-        }
-      }
-      {  // x halo rows: padded positions o0 + row
-        const int r0 = brg * 8 + rr;
-        int pr = (o0 + r0) / g.P, pc = (o0 + r0) - pr * g.P;
-        const int ci = n0 + bcore * 8;
-        for (int row = r0; row < R; row += BROWS) {
-          const int h = pr - 1, w = col0 + pc - 1;
-          const bool v = ci < a.Cin && (unsigned)h < (unsigned)a.H && (unsigned)w < (unsigned)a.W;
-          const bf16 *src = v ? a.x + (((size_t)b * a.H + h) * a.W + w) * a.Cin + ci : a.x;
-          cp_async16(sb + bcore * (WG_RB * 16) + row * 16, src, v);
-          pc += BROWS;
-          while (pc >= g.P) {
-            pc -= g.P;
-            ++pr;
-          }
-        }
-      }
-      cp_async_commit();
-      if (i >= LAG) {
-        cp_async_wait<LAG>();
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        mbar_arrive(&full[(i - LAG) % S]);
-      }
-    }
-    cp_async_wait<0>();
-    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-    if (ok)
-      for (int u = NL > LAG ? NL - LAG : 0; u < NL; ++u) mbar_arrive(&full[u % S]);
-    // ---------------- epilogue: lane = output channel, 9 BN columns
-    if (!mbar_wait(done, 0u, limit)) ok = false;
-    asm volatile("tcgen05.fence::after_thread_sync;\n");
-    if (__all_sync(0xffffffffu, ok)) {
-      const int o = m0 + warp * 32 + lane;
-      float *dst0 = a.part + ((size_t)split * a.Cout + o) * 9 * a.Cin + n0;
-#pragma unroll 1
-      for (int t = 0; t < 9; ++t) {
-#pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 16) {
-          float v[16];
-          tc_ld<16>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * BN + c0), v);
-          if (o < a.Cout && n0 + c0 < a.Cin) {
-            float4 *d = reinterpret_cast<float4 *>(dst0 + t * a.Cin + c0);
+      const long long q = q0 + i;
+      const int rb = (int)(q % a.rblocks);
+      const long long bs = q / a.rblocks;
+      const int strip = (int)(bs % a.strips), b = (int)(bs / a.strips);
+      const int r0 = rb * a.rows, c0 = strip * a.TW;
+      mbar_expect_tx(&full[s], stage_bytes);
+      const uint32_t sa = a0 + (uint32_t)s * astage, sb = b0 + (uint32_t)s * 3 * BBOX;
+      for (int j = 0; j < na; ++j) tma_load_4d(sa + j * abox, &dzmap, m0 + a.wa * j, c0, r0, b, &full[s]);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
-          }
-        }
-      }
+      for (int kw = 0; kw < 3; ++kw)
+        tma_load_4d(sb + kw * BBOX, &xmap, n0, c0 + kw - 1, r0 + kh - 1, b, &full[s]);
+      issued = i + 1;
     }
-  } else if (lane == 0) {
-    // ---------------- MMA issuer: A = dz (MN-major, M = output channels),
-    // B = x halo (MN-major, N = input channels), K = positions
+    // every box issued has landed before the CTA can leave (on the normal
+    // path the MMA lane already consumed them all and these return at once)
+    for (int i = issued > S ? issued - S : 0; i < issued; ++i)
+      if (!mbar_wait(&full[i % S], (uint32_t)((i / S) & 1), limit)) ok = false;
+  } else if (tid == 32) {
+    // ---------------- MMA issuer: A = dz (M = output channels), B = shifted
+    // x (N = input channels), K = the chunk's 128 positions.  Swizzled
+    // MN-major descriptors: stride byte offset = the next group of 8
+    // positions (8 rows of the box), leading byte offset = the next box
+    // along M (B is one box wide; its leading offset is set to the group
+    // stride so that every address the descriptor can form stays inside
+    // the box).  A K step of 16 positions advances two groups.
     const uint32_t idesc = umma_idesc_bf16(128, BN) | (1u << 15) | (1u << 16);
-    // leading byte offset: K-adjacent core matrices (8 positions) 128 B
-    // apart; stride byte offset: MN-adjacent core matrices, dz columns KP x
-    // 16 B apart, halo columns RB x 16 B apart
-    const uint32_t k_st = 128, a_mn = WG_KP * 16, b_mn = WG_RB * 16;
+    const uint32_t ag = 16u * (uint32_t)a.wa, bg = 16u * BN;  // bytes of 8 rows
+    const uint64_t aswz = (uint64_t)umma_swizzle(2 * a.wa) << 61, bswz = (uint64_t)umma_swizzle(2 * BN) << 61;
     for (int i = 0; i < NL; ++i) {
       const int s = i % S;
       if (!mbar_wait(&full[s], (uint32_t)((i / S) & 1), limit)) {
@@ -194,28 +197,46 @@ __global__ void __launch_bounds__(HX_THREADS) k_conv_wgrad_tc(WgradTcArgs a, int
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n");
-      // descriptors of the stage, advanced through their start-address field
-      // (address / 16; shared memory stays below 256 KB, so no carry)
-      const uint32_t sa = smem_u32(smem + s * STAGE), sb = sa + A_BYTES;
-      const uint64_t da = umma_smem_desc(sa, k_st, a_mn), db = umma_smem_desc(sb, k_st, b_mn);
-#pragma unroll 1
-      for (int t = 0; t < 9; ++t) {
-        const int kh = t / 3, kw = t - 3 * (t / 3);
-        const uint64_t dbt = db + (uint64_t)(kh * g.P + kw);  // tap shift: rows of 16 B
+      const uint32_t sa = a0 + (uint32_t)s * astage, sb = b0 + (uint32_t)s * 3 * BBOX;
+      const uint64_t da = umma_smem_desc(sa, abox, ag) | aswz;
 #pragma unroll
-        for (int ks = 0; ks < WG_KP / 16; ++ks)
-          tc_mma(tmem + (uint32_t)(t * BN), da + (uint64_t)(ks * 16), dbt + (uint64_t)(ks * 16), idesc,
-                 (i > 0 || ks > 0) ? 1u : 0u);
+      for (int kw = 0; kw < 3; ++kw) {
+        const uint64_t db = umma_smem_desc(sb + kw * BBOX, bg, bg) | bswz;
+#pragma unroll
+        for (int ks = 0; ks < WG_K / 16; ++ks)
+          tc_mma(tmem + (uint32_t)(kw * BN), da + (uint64_t)(ks * (2 * ag >> 4)), db + (uint64_t)(ks * (2 * bg >> 4)),
+                 idesc, (i > 0 || ks > 0) ? 1u : 0u);
       }
       tc_commit(&empty[s]);
     }
-    tc_commit(done);
-    if (!mbar_wait(done, 0u, limit)) ok = false;
+    tc_commit(done);  // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+  // ---------------- epilogue: lane = output channel, three taps of BN columns
+  if (!mbar_wait(done, 0u, limit)) ok = false;
+  asm volatile("tcgen05.fence::after_thread_sync;\n");
+  if (__all_sync(0xffffffffu, ok)) {
+    const int o = m0 + warp * 32 + lane;
+    float *dst0 = a.part + ((size_t)split * a.Cout + o) * 9 * a.Cin + n0;
+#pragma unroll 1
+    for (int kw = 0; kw < 3; ++kw) {
+      const int t = 3 * kh + kw;
+#pragma unroll 1
+      for (int c = 0; c < BN; c += 16) {
+        float v[16];
+        tc_ld<16>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kw * BN + c), v);
+        if (o < a.Cout && n0 + c < a.Cin) {
+          float4 *d = reinterpret_cast<float4 *>(dst0 + t * a.Cin + c);
+#pragma unroll
+          for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+        }
+      }
+    }
   }
   if (!ok) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n");
   __syncthreads();
-  if (warp == 4) {
+  if (warp == 2) {
     asm volatile("tcgen05.fence::after_thread_sync;\n");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS));
   }

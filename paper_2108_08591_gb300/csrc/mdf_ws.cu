@@ -106,13 +106,15 @@ mdf_status wfail(mdf_ws_t w, mdf_status st, const char *fmt, ...) {
 // gathers, 0 = mma.sync.
 int g_conv_kernel = 2;
 int g_halo_mt = 0, g_halo_kc = 0;  // halo kernel tile override (0 = automatic)
-// Weight-gradient kernel: 0 = mma.sync split-K (default), 1 = tcgen05 with
-// nine TMEM accumulators (needs Cin % 16 == 0, else 0).  The tcgen05 one
-// measured 1.7-3.6x slower on the network's layers: with all nine taps in
-// TMEM only one or two CTAs fit per SM, too few to hide the loads of its
-// small per-chunk MMA batches.
-int g_wgrad_kernel = 0;
+// Weight-gradient kernel: 1 = tcgen05 fed by TMA, one kernel row of taps per
+// CTA (default; needs Cin % 16 == 0 and Cout % 8 == 0, else 0), 0 = mma.sync
+// split-K.  On the network's layers the tcgen05 one measured 1.4-3.3x
+// faster.
+int g_wgrad_kernel = 1;
 int g_wgrad_bn = 0;  // tcgen05 weight-gradient channel tile override (0 = automatic)
+int g_wgrad_ctas = 3;  // tcgen05 weight-gradient CTAs per SM its stage count leaves room for
+constexpr int kMaxSmemOptin = 227 * 1024;  // dynamic shared memory a CTA may opt in to
+constexpr int kSmemPerSm = 228 * 1024;     // shared memory of an SM (1 KB of it reserved per CTA)
 std::mutex g_tc_mu;
 std::map<int, int *> g_tc_err;  // per-device error flag of the tcgen05 kernel
 
@@ -249,19 +251,97 @@ cudaError_t conv_fwd(cudaStream_t s, const bf16 *x, const bf16 *w, const float *
 
 int pix_per_split(long long M) { return M >= 8192 ? 2048 : 256; }
 
+// Streaming multiprocessors of the current device (152 when the query fails).
+int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n < 1)
+    return 152;
+  return n;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no
+// link against the driver library); null when unavailable.
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                   CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Tensor map of an NHWC BF16 tensor [B][H][W][C] (C % 8 == 0, 16-byte
+// aligned base) with boxes of bc channels (16, 32 or 64: rows of 32, 64 or
+// 128 bytes, swizzled at that width) x TW columns x `rows` rows x one
+// image; coordinates outside the tensor read as zero.
+bool nhwc_map(CUtensorMap *m, const bf16 *p, int B, int H, int W, int C, int bc, int TW, int rows) {
+  EncodeTiledFn fn = encode_tiled();
+  if (!fn || C % 8 != 0 || (reinterpret_cast<uintptr_t>(p) & 15u) != 0) return false;
+  const CUtensorMapSwizzle swz = bc == 64   ? CU_TENSOR_MAP_SWIZZLE_128B
+                                 : bc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                            : CU_TENSOR_MAP_SWIZZLE_32B;
+  const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+  const cuuint32_t box[4] = {(cuuint32_t)bc, (cuuint32_t)TW, (cuuint32_t)rows, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(p), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BN, int S>
-cudaError_t launch_wgrad_tc(cudaStream_t s, const WgradTcArgs &a, int *err) {
+cudaError_t launch_wgrad_tma(cudaStream_t s, const CUtensorMap &xm, const CUtensorMap &dm, const WgradTmaArgs &a,
+                             int *err) {
   static bool configured = false;
-  const size_t smem = wgrad_tc_smem_bytes<BN, S>();
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_tc<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_tma<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxSmemOptin);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((unsigned)((a.Cin + BN - 1) / BN), (unsigned)((a.Cout + 127) / 128), (unsigned)a.splits);
-  k_conv_wgrad_tc<BN, S><<<grid, HX_THREADS, smem, s>>>(a, err);
+  dim3 grid((unsigned)((a.Cin + BN - 1) / BN), (unsigned)((a.Cout + 127) / 128), (unsigned)(3 * a.splits));
+  k_conv_wgrad_tma<BN, S><<<grid, WG_THREADS, wgrad_tma_smem_bytes(BN, S, a.wa, a.na), s>>>(xm, dm, a, err);
   return cudaGetLastError();
+}
+
+// Stages of the TMA weight gradient: the most (up to 4) whose shared memory
+// still lets g_wgrad_ctas CTAs share an SM, at least 2.
+int wgrad_stages(int bn, int wa, int na) {
+  const size_t budget = (size_t)kSmemPerSm / (size_t)std::max(1, g_wgrad_ctas);
+  for (int S = 4; S > 2; --S) {
+    const size_t b = wgrad_tma_smem_bytes(bn, S, wa, na);
+    if (b + 1024 <= budget && b <= (size_t)kMaxSmemOptin) return S;
+  }
+  return 2;
+}
+
+// CTAs of the TMA weight gradient that fit on one SM: shared memory (1 KB
+// reserved per CTA), TMEM columns (512 per SM) and threads.
+int wgrad_fit(int bn, int S, int wa, int na) {
+  const int by_smem = (int)((size_t)kSmemPerSm / (wgrad_tma_smem_bytes(bn, S, wa, na) + 1024));
+  const int tcols = 3 * bn <= 64 ? 64 : 3 * bn <= 128 ? 128 : 256;
+  return std::max(1, std::min(std::min(by_smem, 512 / tcols), 2048 / WG_THREADS));
+}
+
+template <int BN>
+cudaError_t launch_wgrad_tma_s(cudaStream_t s, int S, const CUtensorMap &xm, const CUtensorMap &dm,
+                               const WgradTmaArgs &a, int *err) {
+  switch (S) {
+    case 4: return launch_wgrad_tma<BN, 4>(s, xm, dm, a, err);
+    case 3: return launch_wgrad_tma<BN, 3>(s, xm, dm, a, err);
+    default: return launch_wgrad_tma<BN, 2>(s, xm, dm, a, err);
+  }
 }
 
 cudaError_t conv_wgrad(cudaStream_t s, const bf16 *x, const bf16 *dz, float *part, float *dw,
@@ -269,19 +349,28 @@ cudaError_t conv_wgrad(cudaStream_t s, const bf16 *x, const bf16 *dz, float *par
   const long long M = (long long)B * H * W;
   const int pps = pix_per_split(M);
   const int splits = (int)((M + pps - 1) / pps);
-  if (g_wgrad_kernel == 1 && Cin % 16 == 0) {
+  CUtensorMap xm, dm;
+  const int TW = wgrad_tw(W), rows = WG_K / TW;
+  int bn = g_wgrad_bn ? g_wgrad_bn : (Cin % 64 == 0 ? 64 : Cin % 32 == 0 ? 32 : 16);
+  if (Cin % bn != 0) bn = Cin % 32 == 0 ? 32 : 16;
+  const int wa = wgrad_wa(Cout), na = wgrad_na(Cout);
+  if (g_wgrad_kernel == 1 && Cin % 16 == 0 && Cout % 8 == 0 && nhwc_map(&xm, x, B, H, W, Cin, bn, TW, rows) &&
+      nhwc_map(&dm, dz, B, H, W, Cout, wa, TW, rows)) {
     int *err = tc_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
-    // split the pixel chunks for about two CTAs per SM, within the partial
-    // buffer sized for the mma.sync kernel's splits
-    const HaloGeom g = halo_geom(H, W, 1);
-    const long long nq = (long long)B * g.strips * ((H * g.P + WG_KP - 1) / WG_KP);
-    const int bn = g_wgrad_bn ? g_wgrad_bn : (Cin % 32 == 0 ? 32 : 16);
-    const long long tiles = (long long)((Cin + bn - 1) / bn) * ((Cout + 127) / 128);
-    long long sp = (2 * 152 + tiles - 1) / tiles;
+    // split the chunks so that one wave fills every SM with the CTAs that
+    // fit there (each tile has three kernel-row CTAs per split), within the
+    // partial buffer sized for the mma.sync kernel's splits
+    const int strips = (W + TW - 1) / TW, rblocks = (H + rows - 1) / rows;
+    const long long nq = (long long)B * strips * rblocks;
+    const int S = wgrad_stages(bn, wa, na);
+    const long long tiles = 3LL * ((Cin + bn - 1) / bn) * ((Cout + 127) / 128);
+    long long sp = ((long long)wgrad_fit(bn, S, wa, na) * sm_count() + tiles - 1) / tiles;
     sp = std::min<long long>(std::min<long long>(sp, splits), nq);
-    WgradTcArgs a{x, dz, part, B, H, W, Cin, Cout, (int)std::max<long long>(1, sp)};
-    cudaError_t e = bn == 32 ? launch_wgrad_tc<32, 3>(s, a, err) : launch_wgrad_tc<16, 3>(s, a, err);
+    WgradTmaArgs a{part, B, H, W, Cin, Cout, TW, rows, strips, rblocks, (int)std::max<long long>(1, sp), wa, na};
+    cudaError_t e = bn == 64   ? launch_wgrad_tma_s<64>(s, S, xm, dm, a, err)
+                    : bn == 32 ? launch_wgrad_tma_s<32>(s, S, xm, dm, a, err)
+                               : launch_wgrad_tma_s<16>(s, S, xm, dm, a, err);
     if (e != cudaSuccess) return e;
     const long long n = (long long)Cout * 9 * Cin;
     k_sum_splits<<<grid1(n), 256, 0, s>>>(part, a.splits, n, dw, 0);
@@ -668,9 +757,11 @@ mdf_status mdf_nn_set_wgrad_kernel(int which) {
 }
 
 // tcgen05 weight-gradient channel tile override (0 = automatic), process-wide.
-mdf_status mdf_nn_set_wgrad_tile(int bn) {
-  if (bn != 0 && bn != 16 && bn != 32) return MDF_EINVAL;
+mdf_status mdf_nn_set_wgrad_tile(int bn, int ctas_per_sm) {
+  if (bn != 0 && bn != 16 && bn != 32 && bn != 64) return MDF_EINVAL;
+  if (ctas_per_sm < 0 || ctas_per_sm > 16) return MDF_EINVAL;
   g_wgrad_bn = bn;
+  g_wgrad_ctas = ctas_per_sm ? ctas_per_sm : 3;
   return MDF_OK;
 }
 

@@ -60,13 +60,18 @@ def test_conv_forward(kernel, B, H, W, Cin, Cout):
     assert np.all(np.abs(got - r) <= 2.0 ** -8 * np.abs(r) + 1e-6)
 
 
-@pytest.fixture(params=["tcgen05", "mma.sync"])
+@pytest.fixture(params=["tcgen05", "tcgen05-bn16", "tcgen05-bn64", "mma.sync"])
 def wgrad_kernel(request):
-    from paper_2108_08591_gb300 import conv_timeout_flag, set_wgrad_kernel
-    set_wgrad_kernel(request.param)
+    """The weight-gradient kernels; the tcgen05 one also with its 16- and
+    64-channel tiles and the deepest pipeline (one CTA per SM)."""
+    from paper_2108_08591_gb300 import conv_timeout_flag, set_wgrad_kernel, set_wgrad_tile
+    kern, _, tile = request.param.partition("-bn")
+    set_wgrad_kernel(kern)
+    set_wgrad_tile(int(tile) if tile else 0, 1 if tile else 0)
     yield request.param
     assert conv_timeout_flag() == 0
-    set_wgrad_kernel("mma.sync")
+    set_wgrad_kernel("tcgen05")
+    set_wgrad_tile(0, 0)
 
 
 # shapes: ragged channel tiles, Cin 8 (tcgen05 wgrad falls back), several
