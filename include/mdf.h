@@ -533,11 +533,12 @@ mdf_status mdf_nn_set_wgrad_kernel(int which);
 
 /* Launch shape of the tcgen05 weight-gradient kernel, process-wide: input
  * channel tile bn 16, 32 or 64 (a tile that does not divide Cin falls back
- * to 32 or 16; 0 keeps the automatic choice, the largest that divides) and
- * the CTAs per SM that its pipeline depth leaves shared memory for (1 .. 16;
- * 0 keeps the default 3); the pixel split fills one wave of the CTAs that
- * fit.  MDF_EINVAL otherwise. */
-mdf_status mdf_nn_set_wgrad_tile(int bn, int ctas_per_sm);
+ * to 32 or 16; 0 keeps the automatic choice, the largest that divides), the
+ * CTAs per SM that its pipeline depth leaves shared memory for (1 .. 16; 0
+ * keeps the default 3) and the pixel positions per pipeline stage kc, 64
+ * or 128 (0: 128); the pixel split fills one wave of the CTAs that fit.
+ * MDF_EINVAL otherwise. */
+mdf_status mdf_nn_set_wgrad_tile(int bn, int ctas_per_sm, int kc);
 
 /* Read and clear the tcgen05 kernel's time-out flag (1 when a bounded
  * mbarrier wait gave up) of the current device; synchronises the device. */

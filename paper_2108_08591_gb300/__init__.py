@@ -499,11 +499,11 @@ def set_wgrad_kernel(which: str):
     _lib.check(_lib.load().mdf_nn_set_wgrad_kernel({"mma.sync": 0, "tcgen05": 1}[which]))
 
 
-def set_wgrad_tile(bn: int = 0, ctas_per_sm: int = 0):
+def set_wgrad_tile(bn: int = 0, ctas_per_sm: int = 0, kc: int = 0):
     """Launch shape of the tcgen05 weight gradient: input-channel tile 16,
-    32 or 64 (0: automatic) and the CTAs per SM its pipeline depth leaves
-    room for (0: the default)."""
-    _lib.check(_lib.load().mdf_nn_set_wgrad_tile(int(bn), int(ctas_per_sm)))
+    32 or 64, the CTAs per SM its pipeline depth leaves room for and the
+    pixel positions per stage, 64 or 128 (0: automatic, each)."""
+    _lib.check(_lib.load().mdf_nn_set_wgrad_tile(int(bn), int(ctas_per_sm), int(kc)))
 
 
 def conv_timeout_flag() -> int:

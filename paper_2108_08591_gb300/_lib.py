@@ -125,7 +125,7 @@ SIGNATURES = {
     "mdf_nn_set_tc_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "mdf_nn_set_halo_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
     "mdf_nn_set_wgrad_kernel": (ctypes.c_int, [ctypes.c_int]),
-    "mdf_nn_set_wgrad_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int]),
+    "mdf_nn_set_wgrad_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "mdf_nn_conv_error": (ctypes.c_int, [DP]),
 }
 

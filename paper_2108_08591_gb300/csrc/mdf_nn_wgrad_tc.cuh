@@ -6,8 +6,8 @@
 // input channels ci.
 //
 // A chunk is a block of `rows` image rows x TW columns of one image
-// (TW x rows = 128 positions, TW the power of two in {16, 32, 64} that
-// covers the width, or 64 with column strips).  The taps are split over
+// (TW x rows = KC = 64 or 128 positions, TW the power of two in {16, 32,
+// 64} that covers the width, or 64 with column strips).  The taps are split over
 // CTAs by kernel row kh: per chunk the CTA of row kh loads, with one TMA box
 // per 8-channel column,
 //   * dz at the chunk's positions (A, M = output channels), and
@@ -20,7 +20,7 @@
 // nothing outside it contributes.
 //
 // Both operands are MN-major with the 32-, 64- or 128-byte swizzle: a box
-// of W channels (W = 16, 32 or 64) x TW x rows lands in shared memory as 128
+// of W channels (W = 16, 32 or 64) x TW x rows lands in shared memory as KC
 // rows (positions) of 2W bytes, in groups of 8 rows that the TMA unit and
 // the tensor cores swizzle alike, so a K step of 16 positions is an advance
 // of two groups.  A (M = 128 output channels) is 128 / W such boxes side by
@@ -32,7 +32,7 @@
 // Three FP32 accumulators of BN columns live in TMEM (64 to 256 columns), so
 // several CTAs share an SM.  One thread issues the TMA boxes of a stage
 // against its `full` mbarrier (expected bytes), one thread issues the
-// 3 x 128 / 16 MMAs of a chunk and commits them to the stage's `empty`
+// 3 x KC / 16 MMAs of a chunk and commits them to the stage's `empty`
 // mbarrier, and the four warps then read TMEM and store the partial sums
 // part[split][Cout][9 Cin] of their split of the chunks.  Every wait is
 // bounded; after a time-out the CTA raises the error flag, waits (bounded)
@@ -45,13 +45,12 @@
 
 namespace mdfnn {
 
-constexpr int WG_K = 128;        // positions per chunk (K per stage)
 constexpr int WG_THREADS = 128;  // producer lane, MMA lane, four epilogue warps
 
 struct WgradTmaArgs {
   float *part;     // [splits][Cout][9 Cin]
   int B, H, W, Cin, Cout;
-  int TW, rows;    // chunk: rows x TW positions (TW x rows = WG_K)
+  int TW, rows;    // chunk: rows x TW positions (TW x rows = KC of the kernel)
   int strips, rblocks;
   int splits;      // pixel splits; the grid's z is 3 x splits (kernel rows)
   int wa, na;      // dz box width in channels, boxes per stage (shared memory layout)
@@ -68,19 +67,20 @@ __host__ __device__ inline int wgrad_na(int Cout) {
   return (m + w - 1) / w;
 }
 
-// Shared memory of S stages: the A boxes of all stages first (na boxes of
-// 256 wa bytes each), then the B boxes (three of 256 BN bytes each), then
-// the mbarriers, from a 1024-byte aligned base (1 KB of slack).  The MMA
-// reads 32 KB from each stage's A start, so the data area reaches at least
-// 32 KB past the last stage's A start, plus 4 KB (every address an A
-// descriptor can form, with the two byte offsets taken either way round).
-__host__ __device__ inline size_t wgrad_tma_data_bytes(int BN, int S, int wa, int na) {
-  const size_t as = (size_t)na * 256 * wa, a = S * as, b = (size_t)S * 3 * 256 * BN;
-  const size_t reach = (size_t)(S - 1) * as + 32768 + 4096;
+// Shared memory of S stages of KC positions: the A boxes of all stages
+// first (na boxes of 2 KC wa bytes each), then the B boxes (three of 2 KC BN
+// bytes each), then the mbarriers, from a 1024-byte aligned base (1 KB of
+// slack).  The MMA reads 128 A rows, 256 KC bytes, from each stage's A
+// start, so the data area reaches that far past the last stage's A start,
+// plus 4 KB (every address an A descriptor can form, with the two byte
+// offsets taken either way round).
+__host__ __device__ inline size_t wgrad_tma_data_bytes(int KC, int BN, int S, int wa, int na) {
+  const size_t as = (size_t)na * 2 * KC * wa, a = S * as, b = (size_t)S * 3 * 2 * KC * BN;
+  const size_t reach = (size_t)(S - 1) * as + 256 * (size_t)KC + 4096;
   return a + b > reach ? a + b : reach;
 }
-__host__ __device__ inline size_t wgrad_tma_smem_bytes(int BN, int S, int wa, int na) {
-  return 1024 + wgrad_tma_data_bytes(BN, S, wa, na) + (2 * S + 1) * 8 + 16;
+__host__ __device__ inline size_t wgrad_tma_smem_bytes(int KC, int BN, int S, int wa, int na) {
+  return 1024 + wgrad_tma_data_bytes(KC, BN, S, wa, na) + (2 * S + 1) * 8 + 16;
 }
 
 // Swizzle field of a tcgen05 shared-memory descriptor for rows of `bytes`
@@ -104,19 +104,20 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-template <int BN, int S>
+template <int KC, int BN, int S>
 __global__ void __launch_bounds__(WG_THREADS)
     k_conv_wgrad_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dzmap,
                      WgradTmaArgs a, int *err) {
   static_assert(BN == 16 || BN == 32 || BN == 64, "N tile");
   static_assert(S >= 2 && S <= 8, "stages");
-  constexpr uint32_t BBOX = 256 * BN;  // bytes of one shifted x box (128 positions x BN channels)
+  static_assert(KC == 64 || KC == 128, "positions per chunk");
+  constexpr uint32_t BBOX = 2 * KC * BN;  // bytes of one shifted x box (KC positions x BN channels)
   constexpr uint32_t TCOLS = 3 * BN <= 64 ? 64 : 3 * BN <= 128 ? 128 : 256;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // the swizzle pattern repeats every 1024 bytes of the shared address
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  const uint32_t abox = 256u * (uint32_t)a.wa, astage = abox * (uint32_t)a.na;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + wgrad_tma_data_bytes(BN, S, a.wa, a.na));
+  const uint32_t abox = 2u * KC * (uint32_t)a.wa, astage = abox * (uint32_t)a.na;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + wgrad_tma_data_bytes(KC, BN, S, a.wa, a.na));
   uint64_t *empty = full + S;
   uint64_t *done = empty + S;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(WG_THREADS)
       if (!mbar_wait(&full[i % S], (uint32_t)((i / S) & 1), limit)) ok = false;
   } else if (tid == 32) {
     // ---------------- MMA issuer: A = dz (M = output channels), B = shifted
-    // x (N = input channels), K = the chunk's 128 positions.  Swizzled
+    // x (N = input channels), K = the chunk's KC positions.  Swizzled
     // MN-major descriptors: stride byte offset = the next group of 8
     // positions (8 rows of the box), leading byte offset = the next box
     // along M (B is one box wide; its leading offset is set to the group
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(WG_THREADS)
       for (int kw = 0; kw < 3; ++kw) {
         const uint64_t db = umma_smem_desc(sb + kw * BBOX, bg, bg) | bswz;
 #pragma unroll
-        for (int ks = 0; ks < WG_K / 16; ++ks)
+        for (int ks = 0; ks < KC / 16; ++ks)
           tc_mma(tmem + (uint32_t)(kw * BN), da + (uint64_t)(ks * (2 * ag >> 4)), db + (uint64_t)(ks * (2 * bg >> 4)),
                  idesc, (i > 0 || ks > 0) ? 1u : 0u);
       }

@@ -113,6 +113,7 @@ int g_halo_mt = 0, g_halo_kc = 0;  // halo kernel tile override (0 = automatic)
 int g_wgrad_kernel = 1;
 int g_wgrad_bn = 0;  // tcgen05 weight-gradient channel tile override (0 = automatic)
 int g_wgrad_ctas = 3;  // tcgen05 weight-gradient CTAs per SM its stage count leaves room for
+int g_wgrad_kc = 0;    // tcgen05 weight-gradient positions per chunk (0 = automatic)
 constexpr int kMaxSmemOptin = 227 * 1024;  // dynamic shared memory a CTA may opt in to
 constexpr int kSmemPerSm = 228 * 1024;     // shared memory of an SM (1 KB of it reserved per CTA)
 std::mutex g_tc_mu;
@@ -300,48 +301,63 @@ bool nhwc_map(CUtensorMap *m, const bf16 *p, int B, int H, int W, int C, int bc,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN, int S>
+template <int KC, int BN, int S>
 cudaError_t launch_wgrad_tma(cudaStream_t s, const CUtensorMap &xm, const CUtensorMap &dm, const WgradTmaArgs &a,
                              int *err) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_tma<BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_tma<KC, BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          kMaxSmemOptin);
     if (e != cudaSuccess) return e;
     configured = true;
   }
   dim3 grid((unsigned)((a.Cin + BN - 1) / BN), (unsigned)((a.Cout + 127) / 128), (unsigned)(3 * a.splits));
-  k_conv_wgrad_tma<BN, S><<<grid, WG_THREADS, wgrad_tma_smem_bytes(BN, S, a.wa, a.na), s>>>(xm, dm, a, err);
+  k_conv_wgrad_tma<KC, BN, S>
+      <<<grid, WG_THREADS, wgrad_tma_smem_bytes(KC, BN, S, a.wa, a.na), s>>>(xm, dm, a, err);
   return cudaGetLastError();
 }
 
-// Stages of the TMA weight gradient: the most (up to 4) whose shared memory
-// still lets g_wgrad_ctas CTAs share an SM, at least 2.
-int wgrad_stages(int bn, int wa, int na) {
+// Pipeline of the TMA weight gradient: chunks of g_wgrad_kc positions (128
+// when automatic: on every layer of the network it measured fastest or
+// within 2 % of 64) and the most stages, up to 4, whose shared memory still
+// lets g_wgrad_ctas CTAs share an SM, at least 2.
+void wgrad_pipeline(int bn, int wa, int na, int *kc, int *stages) {
   const size_t budget = (size_t)kSmemPerSm / (size_t)std::max(1, g_wgrad_ctas);
+  *kc = g_wgrad_kc ? g_wgrad_kc : 128;
+  *stages = 2;
   for (int S = 4; S > 2; --S) {
-    const size_t b = wgrad_tma_smem_bytes(bn, S, wa, na);
-    if (b + 1024 <= budget && b <= (size_t)kMaxSmemOptin) return S;
+    const size_t b = wgrad_tma_smem_bytes(*kc, bn, S, wa, na);
+    if (b + 1024 <= budget && b <= (size_t)kMaxSmemOptin) {
+      *stages = S;
+      break;
+    }
   }
-  return 2;
 }
 
 // CTAs of the TMA weight gradient that fit on one SM: shared memory (1 KB
 // reserved per CTA), TMEM columns (512 per SM) and threads.
-int wgrad_fit(int bn, int S, int wa, int na) {
-  const int by_smem = (int)((size_t)kSmemPerSm / (wgrad_tma_smem_bytes(bn, S, wa, na) + 1024));
+int wgrad_fit(int kc, int bn, int S, int wa, int na) {
+  const int by_smem = (int)((size_t)kSmemPerSm / (wgrad_tma_smem_bytes(kc, bn, S, wa, na) + 1024));
   const int tcols = 3 * bn <= 64 ? 64 : 3 * bn <= 128 ? 128 : 256;
   return std::max(1, std::min(std::min(by_smem, 512 / tcols), 2048 / WG_THREADS));
 }
 
-template <int BN>
+template <int KC, int BN>
 cudaError_t launch_wgrad_tma_s(cudaStream_t s, int S, const CUtensorMap &xm, const CUtensorMap &dm,
                                const WgradTmaArgs &a, int *err) {
   switch (S) {
-    case 4: return launch_wgrad_tma<BN, 4>(s, xm, dm, a, err);
-    case 3: return launch_wgrad_tma<BN, 3>(s, xm, dm, a, err);
-    default: return launch_wgrad_tma<BN, 2>(s, xm, dm, a, err);
+    case 4: return launch_wgrad_tma<KC, BN, 4>(s, xm, dm, a, err);
+    case 3: return launch_wgrad_tma<KC, BN, 3>(s, xm, dm, a, err);
+    default: return launch_wgrad_tma<KC, BN, 2>(s, xm, dm, a, err);
   }
+}
+
+template <int KC>
+cudaError_t launch_wgrad_tma_b(cudaStream_t s, int bn, int S, const CUtensorMap &xm, const CUtensorMap &dm,
+                               const WgradTmaArgs &a, int *err) {
+  return bn == 64   ? launch_wgrad_tma_s<KC, 64>(s, S, xm, dm, a, err)
+         : bn == 32 ? launch_wgrad_tma_s<KC, 32>(s, S, xm, dm, a, err)
+                    : launch_wgrad_tma_s<KC, 16>(s, S, xm, dm, a, err);
 }
 
 cudaError_t conv_wgrad(cudaStream_t s, const bf16 *x, const bf16 *dz, float *part, float *dw,
@@ -350,10 +366,12 @@ cudaError_t conv_wgrad(cudaStream_t s, const bf16 *x, const bf16 *dz, float *par
   const int pps = pix_per_split(M);
   const int splits = (int)((M + pps - 1) / pps);
   CUtensorMap xm, dm;
-  const int TW = wgrad_tw(W), rows = WG_K / TW;
   int bn = g_wgrad_bn ? g_wgrad_bn : (Cin % 64 == 0 ? 64 : Cin % 32 == 0 ? 32 : 16);
   if (Cin % bn != 0) bn = Cin % 32 == 0 ? 32 : 16;
   const int wa = wgrad_wa(Cout), na = wgrad_na(Cout);
+  int kc = 128, S = 2;
+  wgrad_pipeline(bn, wa, na, &kc, &S);
+  const int TW = wgrad_tw(W), rows = kc / TW;
   if (g_wgrad_kernel == 1 && Cin % 16 == 0 && Cout % 8 == 0 && nhwc_map(&xm, x, B, H, W, Cin, bn, TW, rows) &&
       nhwc_map(&dm, dz, B, H, W, Cout, wa, TW, rows)) {
     int *err = tc_error_flag();
@@ -363,14 +381,12 @@ cudaError_t conv_wgrad(cudaStream_t s, const bf16 *x, const bf16 *dz, float *par
     // partial buffer sized for the mma.sync kernel's splits
     const int strips = (W + TW - 1) / TW, rblocks = (H + rows - 1) / rows;
     const long long nq = (long long)B * strips * rblocks;
-    const int S = wgrad_stages(bn, wa, na);
     const long long tiles = 3LL * ((Cin + bn - 1) / bn) * ((Cout + 127) / 128);
-    long long sp = ((long long)wgrad_fit(bn, S, wa, na) * sm_count() + tiles - 1) / tiles;
+    long long sp = (long long)wgrad_fit(kc, bn, S, wa, na) * sm_count() / tiles;  // no second wave
     sp = std::min<long long>(std::min<long long>(sp, splits), nq);
     WgradTmaArgs a{part, B, H, W, Cin, Cout, TW, rows, strips, rblocks, (int)std::max<long long>(1, sp), wa, na};
-    cudaError_t e = bn == 64   ? launch_wgrad_tma_s<64>(s, S, xm, dm, a, err)
-                    : bn == 32 ? launch_wgrad_tma_s<32>(s, S, xm, dm, a, err)
-                               : launch_wgrad_tma_s<16>(s, S, xm, dm, a, err);
+    cudaError_t e = kc == 128 ? launch_wgrad_tma_b<128>(s, bn, S, xm, dm, a, err)
+                              : launch_wgrad_tma_b<64>(s, bn, S, xm, dm, a, err);
     if (e != cudaSuccess) return e;
     const long long n = (long long)Cout * 9 * Cin;
     k_sum_splits<<<grid1(n), 256, 0, s>>>(part, a.splits, n, dw, 0);
@@ -757,11 +773,13 @@ mdf_status mdf_nn_set_wgrad_kernel(int which) {
 }
 
 // tcgen05 weight-gradient channel tile override (0 = automatic), process-wide.
-mdf_status mdf_nn_set_wgrad_tile(int bn, int ctas_per_sm) {
+mdf_status mdf_nn_set_wgrad_tile(int bn, int ctas_per_sm, int kc) {
   if (bn != 0 && bn != 16 && bn != 32 && bn != 64) return MDF_EINVAL;
   if (ctas_per_sm < 0 || ctas_per_sm > 16) return MDF_EINVAL;
+  if (kc != 0 && kc != 64 && kc != 128) return MDF_EINVAL;
   g_wgrad_bn = bn;
   g_wgrad_ctas = ctas_per_sm ? ctas_per_sm : 3;
+  g_wgrad_kc = kc;
   return MDF_OK;
 }
 

@@ -60,18 +60,29 @@ def test_conv_forward(kernel, B, H, W, Cin, Cout):
     assert np.all(np.abs(got - r) <= 2.0 ** -8 * np.abs(r) + 1e-6)
 
 
-@pytest.fixture(params=["tcgen05", "tcgen05-bn16", "tcgen05-bn64", "mma.sync"])
+WGRAD_VARIANTS = {  # kernel, channel tile, CTAs per SM, positions per stage
+    "tcgen05": ("tcgen05", 0, 0, 0),
+    "tcgen05-bn16": ("tcgen05", 16, 1, 0),
+    "tcgen05-bn64": ("tcgen05", 64, 1, 0),
+    "tcgen05-k64": ("tcgen05", 0, 4, 64),
+    "tcgen05-k128": ("tcgen05", 32, 2, 128),
+    "mma.sync": ("mma.sync", 0, 0, 0),
+}
+
+
+@pytest.fixture(params=list(WGRAD_VARIANTS))
 def wgrad_kernel(request):
     """The weight-gradient kernels; the tcgen05 one also with its 16- and
-    64-channel tiles and the deepest pipeline (one CTA per SM)."""
+    64-channel tiles, both pipeline stage lengths and shallow and deep
+    pipelines."""
     from paper_2108_08591_gb300 import conv_timeout_flag, set_wgrad_kernel, set_wgrad_tile
-    kern, _, tile = request.param.partition("-bn")
+    kern, bn, ctas, kc = WGRAD_VARIANTS[request.param]
     set_wgrad_kernel(kern)
-    set_wgrad_tile(int(tile) if tile else 0, 1 if tile else 0)
+    set_wgrad_tile(bn, ctas, kc)
     yield request.param
     assert conv_timeout_flag() == 0
     set_wgrad_kernel("tcgen05")
-    set_wgrad_tile(0, 0)
+    set_wgrad_tile(0, 0, 0)
 
 
 # shapes: ragged channel tiles, Cin 8 (tcgen05 wgrad falls back), several
