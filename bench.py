@@ -609,8 +609,8 @@ def run_conv(args):
     repeated --steps times inside one CUDA graph (host launch cost excluded),
     inputs L2-resident (the network's working set), CUDA-event timed."""
     import torch
-    from paper_2108_08591_gb300 import (_build, conv3x3_bf16, conv3x3_bf16_backward, set_conv_kernel,
-                                        set_wgrad_kernel)
+    from paper_2108_08591_gb300 import (_build, conv3x3_bf16, conv3x3_bf16_backward, conv3x3_bf16_wgrad,
+                                        set_conv_kernel, set_wgrad_kernel)
     _build.build()
     rows = []
     shapes = [(8, 256, 32, 32), (8, 128, 64, 64), (8, 64, 128, 128), (8, 32, 256, 256),
@@ -628,6 +628,8 @@ def run_conv(args):
             dz = torch.randn(B, H, H, Cout, device="cuda", generator=g).to(torch.bfloat16)
             flops = 2.0 * B * H * H * Cout * 9 * Cin
             ops = (("bwd", lambda: conv3x3_bf16_backward(x, w, dz), 2),)
+            if kern == "tcgen05-halo":  # the weight gradient alone, once per weight-gradient kernel
+                ops = (("wgrad", lambda: conv3x3_bf16_wgrad(x, dz), 1),) + ops
             if wgrad == "tcgen05":
                 ops = (("fwd", lambda: conv3x3_bf16(x, w, out_fp32=False), 1),) + ops
             for name, fn, mult in ops:
@@ -646,7 +648,7 @@ def run_conv(args):
                 e1.record()
                 torch.cuda.synchronize()
                 ms = e0.elapsed_time(e1) / args.steps
-                rows.append({"kernel": kern, "wgrad": wgrad if name == "bwd" else None, "B": B, "H": H,
+                rows.append({"kernel": kern, "wgrad": wgrad if name != "fwd" else None, "B": B, "H": H,
                              "Cin": Cin, "Cout": Cout, "op": name, "ms": ms, "tflops": mult * flops / ms / 1e9})
                 del graph
     set_conv_kernel("tcgen05-halo")

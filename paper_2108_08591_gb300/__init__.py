@@ -528,6 +528,21 @@ def conv3x3_bf16(x, w, bias=None, relu=False, out_fp32=True):
     return y
 
 
+def conv3x3_bf16_wgrad(x, dz):
+    """dw fp32 [Cout, 3, 3, Cin] of the library's weight-gradient kernel
+    (the one set_wgrad_kernel selects) for NHWC bf16 x and dz."""
+    import torch
+    lib = _lib.load()
+    B, H, W, Cin = x.shape
+    Cout = dz.shape[3]
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    part = torch.empty(int(lib.mdf_nn_wgrad_scratch(B, H, W, Cin, Cout)), dtype=torch.float32, device=x.device)
+    dw = torch.empty((Cout, 3, 3, Cin), dtype=torch.float32, device=x.device)
+    _lib.check(lib.mdf_nn_conv_wgrad(x.data_ptr(), dz.data_ptr(), dw.data_ptr(), part.data_ptr(), B, H, W,
+                                     Cin, Cout, s))
+    return dw
+
+
 def conv3x3_bf16_backward(x, w, dz):
     """(dx bf16, dw fp32) of the library's convolution kernels."""
     import torch

@@ -91,13 +91,15 @@ def wgrad_kernel(request):
                                             (1, 5, 66, 32, 16), (3, 5, 9, 8, 16), (1, 12, 130, 32, 48),
                                             (2, 9, 9, 64, 136)])
 def test_conv_backward(kernel, wgrad_kernel, B, H, W, Cin, Cout):
-    from paper_2108_08591_gb300 import conv3x3_bf16_backward
+    import torch
+    from paper_2108_08591_gb300 import conv3x3_bf16_backward, conv3x3_bf16_wgrad
     x, xn = _bf16((B, H, W, Cin), 3)
     w, wn = _bf16((Cout, 3, 3, Cin), 4)
     dz, dzn = _bf16((B, H, W, Cout), 5)
     dx_ref, dw_ref, _ = onn.conv3x3_backward(xn, wn, dzn)
     dx, dw = conv3x3_bf16_backward(x, w, dz)
     assert _rel(dw_ref, dw.cpu().numpy()) < 1e-5
+    assert torch.equal(conv3x3_bf16_wgrad(x, dz), dw)  # the same kernel alone
     got = dx.float().cpu().numpy()
     assert np.all(np.abs(got - dx_ref) <= 2.0 ** -8 * np.abs(dx_ref) + 1e-5)
 
