@@ -72,6 +72,21 @@ def test_invalid_arguments_are_rejected_without_a_gpu(lib):
     lib.mdf_destroy(None)
 
 
+def test_network_kernel_choices_are_checked_without_a_gpu(lib):
+    """The process-wide kernel and tile setters validate their arguments on
+    the host (they launch nothing)."""
+    from paper_2108_08591_gb300 import _lib
+    for bad in ((24, 0, 0), (128, 0, 0), (32, -1, 0), (32, 17, 0), (32, 0, 96), (0, 0, 32)):
+        assert lib.mdf_nn_set_wgrad_tile(*bad) == _lib.EINVAL, bad
+    for good in ((0, 0, 0), (16, 1, 64), (64, 4, 128)):
+        assert lib.mdf_nn_set_wgrad_tile(*good) == _lib.OK, good
+    assert lib.mdf_nn_set_wgrad_tile(0, 0, 0) == _lib.OK
+    assert lib.mdf_nn_set_wgrad_kernel(2) == _lib.EINVAL
+    assert lib.mdf_nn_set_wgrad_kernel(1) == _lib.OK
+    assert lib.mdf_nn_set_conv_kernel(3) == _lib.EINVAL
+    assert lib.mdf_nn_set_conv_kernel(2) == _lib.OK
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     """The ctypes mirrors have the header's sizes and field offsets (a C
     program built with gcc against include/mdf.h prints them)."""
