@@ -108,7 +108,7 @@ int g_conv_kernel = 2;
 int g_halo_mt = 0, g_halo_kc = 0;  // halo kernel tile override (0 = automatic)
 // Weight-gradient kernel: 1 = tcgen05 fed by TMA, one kernel row of taps per
 // CTA (default; needs Cin % 16 == 0 and Cout % 8 == 0, else 0), 0 = mma.sync
-// split-K.  On the network's layers the tcgen05 one measured 1.4-3.3x
+// split-K.  On the network's layers the tcgen05 one measured 2.1-3.9x
 // faster.
 int g_wgrad_kernel = 1;
 int g_wgrad_bn = 0;  // tcgen05 weight-gradient channel tile override (0 = automatic)
