@@ -527,13 +527,16 @@ mdf_status mdf_nn_set_halo_tile(int mt, int kc);
 
 /* Weight-gradient kernel, process-wide: which = 1 the tcgen05 kernel (the
  * default: TMA-loaded dz and shifted x boxes, the taps of one kernel row
- * per CTA in three TMEM accumulators; Cin % 16 != 0 or Cout % 8 != 0 falls
- * back to 0), 0 the mma.sync split-K kernel.  Both accumulate in FP32. */
+ * per CTA in three TMEM accumulators, M = output channels, or input
+ * channels where that pads fewer of the 128 rows and Cout % 32 == 0;
+ * Cin % 16 != 0 or Cout % 8 != 0 falls back to 0), 0 the mma.sync split-K
+ * kernel.  Both accumulate in FP32. */
 mdf_status mdf_nn_set_wgrad_kernel(int which);
 
-/* Launch shape of the tcgen05 weight-gradient kernel, process-wide: input
- * channel tile bn 16, 32 or 64 (a tile that does not divide Cin falls back
- * to 32 or 16; 0 keeps the automatic choice, the largest that divides), the
+/* Launch shape of the tcgen05 weight-gradient kernel, process-wide: N tile
+ * bn 16, 32 or 64 channels (of Cin, or of Cout where the roles are
+ * swapped; a tile that does not divide them falls back to the largest that
+ * does; 0 keeps the automatic choice, the largest that divides), the
  * CTAs per SM that its pipeline depth leaves shared memory for (1 .. 16; 0
  * keeps the default 3) and the pixel positions per pipeline stage kc, 64
  * or 128 (0: 128); the pixel split fills one wave of the CTAs that fit.

@@ -500,8 +500,8 @@ def set_wgrad_kernel(which: str):
 
 
 def set_wgrad_tile(bn: int = 0, ctas_per_sm: int = 0, kc: int = 0):
-    """Launch shape of the tcgen05 weight gradient: input-channel tile 16,
-    32 or 64, the CTAs per SM its pipeline depth leaves room for and the
+    """Launch shape of the tcgen05 weight gradient: N tile of 16, 32 or 64
+    channels, the CTAs per SM its pipeline depth leaves room for and the
     pixel positions per stage, 64 or 128 (0: automatic, each)."""
     _lib.check(_lib.load().mdf_nn_set_wgrad_tile(int(bn), int(ctas_per_sm), int(kc)))
 

@@ -14,7 +14,10 @@
 //   * for kw = 0, 1, 2, x at the same positions shifted by (kh - 1, kw - 1)
 //     (B, N = input channels),
 // so tap (kh, kw) is a plain GEMM of the chunk: no pad columns and no start
-// offsets.  Boxes that reach past the image edges (the -1 and +1 shifts,
+// offsets.  Layers with fewer output than input channels (where fewer of
+// the 128 M rows would be padding the other way round) swap the roles: A =
+// the three shifted x blocks (M = input channels), B = dz (N = output
+// channels), and the epilogue stores the accumulators transposed.  Boxes that reach past the image edges (the -1 and +1 shifts,
 // ragged strips and rows) are filled with zeros by the TMA unit, which is
 // the convolution's zero padding; dz positions past the image are zero, so
 // nothing outside it contributes.
@@ -53,34 +56,37 @@ struct WgradTmaArgs {
   int TW, rows;    // chunk: rows x TW positions (TW x rows = KC of the kernel)
   int strips, rblocks;
   int splits;      // pixel splits; the grid's z is 3 x splits (kernel rows)
-  int wa, na;      // dz box width in channels, boxes per stage (shared memory layout)
+  int wa, na;      // A box width in channels, A boxes per copy in the first M tile (layout)
 };
 
 // Chunk width of an image of width W: the power of two in {16, 32, 64}
 // covering W, or 64 (column strips).
 __host__ __device__ inline int wgrad_tw(int W) { return W <= 16 ? 16 : W <= 32 ? 32 : 64; }
 
-// dz box width for Cout output channels, and the boxes of the first M tile.
-__host__ __device__ inline int wgrad_wa(int Cout) { return Cout >= 64 ? 64 : Cout >= 32 ? 32 : 16; }
-__host__ __device__ inline int wgrad_na(int Cout) {
-  const int m = Cout < 128 ? Cout : 128, w = wgrad_wa(Cout);
+// A box width for an M extent of C channels (Cout, or Cin when the roles
+// are swapped), and the boxes of the first M tile.
+__host__ __device__ inline int wgrad_wa(int C) { return C >= 64 ? 64 : C >= 32 ? 32 : 16; }
+__host__ __device__ inline int wgrad_na(int C) {
+  const int m = C < 128 ? C : 128, w = wgrad_wa(C);
   return (m + w - 1) / w;
 }
 
 // Shared memory of S stages of KC positions: the A boxes of all stages
-// first (na boxes of 2 KC wa bytes each), then the B boxes (three of 2 KC BN
-// bytes each), then the mbarriers, from a 1024-byte aligned base (1 KB of
-// slack).  The MMA reads 128 A rows, 256 KC bytes, from each stage's A
-// start, so the data area reaches that far past the last stage's A start,
+// first (na boxes of 2 KC wa bytes per copy; one copy, or three shifted
+// copies when SWAP), then the B boxes (three shifted copies of 2 KC BN
+// bytes, or one when SWAP), then the mbarriers, from a 1024-byte aligned
+// base (1 KB of slack).  The MMA reads 128 A rows, 256 KC bytes, from every
+// A copy's start, so the data area reaches that far past the last one,
 // plus 4 KB (every address an A descriptor can form, with the two byte
 // offsets taken either way round).
-__host__ __device__ inline size_t wgrad_tma_data_bytes(int KC, int BN, int S, int wa, int na) {
-  const size_t as = (size_t)na * 2 * KC * wa, a = S * as, b = (size_t)S * 3 * 2 * KC * BN;
-  const size_t reach = (size_t)(S - 1) * as + 256 * (size_t)KC + 4096;
+__host__ __device__ inline size_t wgrad_tma_data_bytes(bool swap, int KC, int BN, int S, int wa, int na) {
+  const size_t ac = (size_t)na * 2 * KC * wa, as = (swap ? 3 : 1) * ac;
+  const size_t a = S * as, b = (size_t)S * (swap ? 1 : 3) * 2 * KC * BN;
+  const size_t reach = (size_t)S * as - ac + 256 * (size_t)KC + 4096;
   return a + b > reach ? a + b : reach;
 }
-__host__ __device__ inline size_t wgrad_tma_smem_bytes(int KC, int BN, int S, int wa, int na) {
-  return 1024 + wgrad_tma_data_bytes(KC, BN, S, wa, na) + (2 * S + 1) * 8 + 16;
+__host__ __device__ inline size_t wgrad_tma_smem_bytes(bool swap, int KC, int BN, int S, int wa, int na) {
+  return 1024 + wgrad_tma_data_bytes(swap, KC, BN, S, wa, na) + (2 * S + 1) * 8 + 16;
 }
 
 // Swizzle field of a tcgen05 shared-memory descriptor for rows of `bytes`
@@ -104,20 +110,25 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
       : "memory");
 }
 
-template <int KC, int BN, int S>
+// SWAP = false: A = dz (M = output channels), B = x (N = input channels),
+// three shifted B copies.  SWAP = true, for layers with more input than
+// output channels: A = x (M = input channels), three shifted A copies, B =
+// dz (N = output channels); the accumulators hold dW transposed.
+template <bool SWAP, int KC, int BN, int S>
 __global__ void __launch_bounds__(WG_THREADS)
     k_conv_wgrad_tma(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dzmap,
                      WgradTmaArgs a, int *err) {
   static_assert(BN == 16 || BN == 32 || BN == 64, "N tile");
   static_assert(S >= 2 && S <= 8, "stages");
   static_assert(KC == 64 || KC == 128, "positions per chunk");
-  constexpr uint32_t BBOX = 2 * KC * BN;  // bytes of one shifted x box (KC positions x BN channels)
+  constexpr int NA = SWAP ? 3 : 1, NB = SWAP ? 1 : 3;  // copies of A and of B per stage
+  constexpr uint32_t BBOX = 2 * KC * BN;                // bytes of one B box (KC positions x BN channels)
   constexpr uint32_t TCOLS = 3 * BN <= 64 ? 64 : 3 * BN <= 128 ? 128 : 256;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // the swizzle pattern repeats every 1024 bytes of the shared address
   uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  const uint32_t abox = 2u * KC * (uint32_t)a.wa, astage = abox * (uint32_t)a.na;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + wgrad_tma_data_bytes(KC, BN, S, a.wa, a.na));
+  const uint32_t abox = 2u * KC * (uint32_t)a.wa, acopy = abox * (uint32_t)a.na, astage = NA * acopy;
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem + wgrad_tma_data_bytes(SWAP, KC, BN, S, a.wa, a.na));
   uint64_t *empty = full + S;
   uint64_t *done = empty + S;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
@@ -129,9 +140,9 @@ __global__ void __launch_bounds__(WG_THREADS)
   const long long q0 = NQ * split / a.splits, q1 = NQ * (split + 1) / a.splits;
   const int NL = (int)(q1 - q0);  // chunks of this CTA (>= 1)
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * 128;
-  const int mrem = min(128, a.Cout - m0);
-  const int na = (mrem + a.wa - 1) / a.wa;  // dz boxes this CTA loads (<= a.na)
-  const uint32_t stage_bytes = (uint32_t)na * abox + 3 * BBOX;
+  const int mrem = min(128, (SWAP ? a.Cin : a.Cout) - m0);
+  const int na = (mrem + a.wa - 1) / a.wa;  // A boxes per copy this CTA loads (<= a.na)
+  const uint32_t stage_bytes = (uint32_t)(NA * na) * abox + NB * BBOX;
   const long long limit = 2000000000LL;
 
   if (warp == 2) {
@@ -155,7 +166,8 @@ __global__ void __launch_bounds__(WG_THREADS)
 
   bool ok = true;
   if (tid == 0) {
-    // ---------------- producer: the boxes of chunk i into stage i % S
+    // ---------------- producer: the boxes of chunk i into stage i % S; the
+    // x boxes are shifted by (kh - 1, kw - 1)
     int issued = 0;
     for (int i = 0; i < NL; ++i) {
       const int s = i % S;
@@ -169,11 +181,19 @@ __global__ void __launch_bounds__(WG_THREADS)
       const int strip = (int)(bs % a.strips), b = (int)(bs / a.strips);
       const int r0 = rb * a.rows, c0 = strip * a.TW;
       mbar_expect_tx(&full[s], stage_bytes);
-      const uint32_t sa = a0 + (uint32_t)s * astage, sb = b0 + (uint32_t)s * 3 * BBOX;
-      for (int j = 0; j < na; ++j) tma_load_4d(sa + j * abox, &dzmap, m0 + a.wa * j, c0, r0, b, &full[s]);
+      const uint32_t sa = a0 + (uint32_t)s * astage, sb = b0 + (uint32_t)s * NB * BBOX;
+      if constexpr (SWAP) {
 #pragma unroll
-      for (int kw = 0; kw < 3; ++kw)
-        tma_load_4d(sb + kw * BBOX, &xmap, n0, c0 + kw - 1, r0 + kh - 1, b, &full[s]);
+        for (int kw = 0; kw < 3; ++kw)
+          for (int j = 0; j < na; ++j)
+            tma_load_4d(sa + kw * acopy + j * abox, &xmap, m0 + a.wa * j, c0 + kw - 1, r0 + kh - 1, b, &full[s]);
+        tma_load_4d(sb, &dzmap, n0, c0, r0, b, &full[s]);
+      } else {
+        for (int j = 0; j < na; ++j) tma_load_4d(sa + j * abox, &dzmap, m0 + a.wa * j, c0, r0, b, &full[s]);
+#pragma unroll
+        for (int kw = 0; kw < 3; ++kw)
+          tma_load_4d(sb + kw * BBOX, &xmap, n0, c0 + kw - 1, r0 + kh - 1, b, &full[s]);
+      }
       issued = i + 1;
     }
     // every box issued has landed before the CTA can leave (on the normal
@@ -181,8 +201,7 @@ __global__ void __launch_bounds__(WG_THREADS)
     for (int i = issued > S ? issued - S : 0; i < issued; ++i)
       if (!mbar_wait(&full[i % S], (uint32_t)((i / S) & 1), limit)) ok = false;
   } else if (tid == 32) {
-    // ---------------- MMA issuer: A = dz (M = output channels), B = shifted
-    // x (N = input channels), K = the chunk's KC positions.  Swizzled
+    // ---------------- MMA issuer, K = the chunk's KC positions.  Swizzled
     // MN-major descriptors: stride byte offset = the next group of 8
     // positions (8 rows of the box), leading byte offset = the next box
     // along M (B is one box wide; its leading offset is set to the group
@@ -198,11 +217,11 @@ __global__ void __launch_bounds__(WG_THREADS)
         break;
       }
       asm volatile("tcgen05.fence::after_thread_sync;\n");
-      const uint32_t sa = a0 + (uint32_t)s * astage, sb = b0 + (uint32_t)s * 3 * BBOX;
-      const uint64_t da = umma_smem_desc(sa, abox, ag) | aswz;
+      const uint32_t sa = a0 + (uint32_t)s * astage, sb = b0 + (uint32_t)s * NB * BBOX;
 #pragma unroll
       for (int kw = 0; kw < 3; ++kw) {
-        const uint64_t db = umma_smem_desc(sb + kw * BBOX, bg, bg) | bswz;
+        const uint64_t da = umma_smem_desc(sa + (SWAP ? kw * acopy : 0u), abox, ag) | aswz;
+        const uint64_t db = umma_smem_desc(sb + (SWAP ? 0u : kw * BBOX), bg, bg) | bswz;
 #pragma unroll
         for (int ks = 0; ks < KC / 16; ++ks)
           tc_mma(tmem + (uint32_t)(kw * BN), da + (uint64_t)(ks * (2 * ag >> 4)), db + (uint64_t)(ks * (2 * bg >> 4)),
@@ -213,12 +232,11 @@ __global__ void __launch_bounds__(WG_THREADS)
     tc_commit(done);  // arrives once every MMA issued above has completed
   }
   __syncwarp();
-  // ---------------- epilogue: lane = output channel, three taps of BN columns
+  // ---------------- epilogue: lane = M row, three taps of BN columns
   if (!mbar_wait(done, 0u, limit)) ok = false;
   asm volatile("tcgen05.fence::after_thread_sync;\n");
   if (__all_sync(0xffffffffu, ok)) {
-    const int o = m0 + warp * 32 + lane;
-    float *dst0 = a.part + ((size_t)split * a.Cout + o) * 9 * a.Cin + n0;
+    const int r = m0 + warp * 32 + lane;  // output channel, or input channel when SWAP
 #pragma unroll 1
     for (int kw = 0; kw < 3; ++kw) {
       const int t = 3 * kh + kw;
@@ -226,10 +244,19 @@ __global__ void __launch_bounds__(WG_THREADS)
       for (int c = 0; c < BN; c += 16) {
         float v[16];
         tc_ld<16>(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(kw * BN + c), v);
-        if (o < a.Cout && n0 + c < a.Cin) {
-          float4 *d = reinterpret_cast<float4 *>(dst0 + t * a.Cin + c);
+        if constexpr (SWAP) {  // dW[n0 + c + k][t][r]: consecutive lanes, consecutive addresses
+          if (r < a.Cin) {
+            float *dst = a.part + (((size_t)split * a.Cout + n0 + c) * 9 + t) * a.Cin + r;
 #pragma unroll
-          for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+            for (int k = 0; k < 16; ++k)
+              if (n0 + c + k < a.Cout) dst[(size_t)k * 9 * a.Cin] = v[k];
+          }
+        } else {  // dW[r][t][n0 + c .. + 15]
+          if (r < a.Cout && n0 + c < a.Cin) {
+            float4 *d = reinterpret_cast<float4 *>(a.part + (((size_t)split * a.Cout + r) * 9 + t) * a.Cin + n0 + c);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+          }
         }
       }
     }

@@ -108,7 +108,7 @@ int g_conv_kernel = 2;
 int g_halo_mt = 0, g_halo_kc = 0;  // halo kernel tile override (0 = automatic)
 // Weight-gradient kernel: 1 = tcgen05 fed by TMA, one kernel row of taps per
 // CTA (default; needs Cin % 16 == 0 and Cout % 8 == 0, else 0), 0 = mma.sync
-// split-K.  On the network's layers the tcgen05 one measured 2.1-3.9x
+// split-K.  On the network's layers the tcgen05 one measured 1.8-3.9x
 // faster.
 int g_wgrad_kernel = 1;
 int g_wgrad_bn = 0;  // tcgen05 weight-gradient channel tile override (0 = automatic)
@@ -301,19 +301,20 @@ bool nhwc_map(CUtensorMap *m, const bf16 *p, int B, int H, int W, int C, int bc,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int KC, int BN, int S>
+template <bool SWAP, int KC, int BN, int S>
 cudaError_t launch_wgrad_tma(cudaStream_t s, const CUtensorMap &xm, const CUtensorMap &dm, const WgradTmaArgs &a,
                              int *err) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_tma<KC, BN, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kMaxSmemOptin);
+    cudaError_t e = cudaFuncSetAttribute(k_conv_wgrad_tma<SWAP, KC, BN, S>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmemOptin);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  dim3 grid((unsigned)((a.Cin + BN - 1) / BN), (unsigned)((a.Cout + 127) / 128), (unsigned)(3 * a.splits));
-  k_conv_wgrad_tma<KC, BN, S>
-      <<<grid, WG_THREADS, wgrad_tma_smem_bytes(KC, BN, S, a.wa, a.na), s>>>(xm, dm, a, err);
+  const int nn = SWAP ? a.Cout : a.Cin, mm = SWAP ? a.Cin : a.Cout;
+  dim3 grid((unsigned)((nn + BN - 1) / BN), (unsigned)((mm + 127) / 128), (unsigned)(3 * a.splits));
+  k_conv_wgrad_tma<SWAP, KC, BN, S>
+      <<<grid, WG_THREADS, wgrad_tma_smem_bytes(SWAP, KC, BN, S, a.wa, a.na), s>>>(xm, dm, a, err);
   return cudaGetLastError();
 }
 
@@ -321,12 +322,12 @@ cudaError_t launch_wgrad_tma(cudaStream_t s, const CUtensorMap &xm, const CUtens
 // when automatic: on every layer of the network it measured fastest or
 // within 2 % of 64) and the most stages, up to 4, whose shared memory still
 // lets g_wgrad_ctas CTAs share an SM, at least 2.
-void wgrad_pipeline(int bn, int wa, int na, int *kc, int *stages) {
+void wgrad_pipeline(bool swap, int bn, int wa, int na, int *kc, int *stages) {
   const size_t budget = (size_t)kSmemPerSm / (size_t)std::max(1, g_wgrad_ctas);
   *kc = g_wgrad_kc ? g_wgrad_kc : 128;
   *stages = 2;
   for (int S = 4; S > 2; --S) {
-    const size_t b = wgrad_tma_smem_bytes(*kc, bn, S, wa, na);
+    const size_t b = wgrad_tma_smem_bytes(swap, *kc, bn, S, wa, na);
     if (b + 1024 <= budget && b <= (size_t)kMaxSmemOptin) {
       *stages = S;
       break;
@@ -336,28 +337,42 @@ void wgrad_pipeline(int bn, int wa, int na, int *kc, int *stages) {
 
 // CTAs of the TMA weight gradient that fit on one SM: shared memory (1 KB
 // reserved per CTA), TMEM columns (512 per SM) and threads.
-int wgrad_fit(int kc, int bn, int S, int wa, int na) {
-  const int by_smem = (int)((size_t)kSmemPerSm / (wgrad_tma_smem_bytes(kc, bn, S, wa, na) + 1024));
+int wgrad_fit(bool swap, int kc, int bn, int S, int wa, int na) {
+  const int by_smem = (int)((size_t)kSmemPerSm / (wgrad_tma_smem_bytes(swap, kc, bn, S, wa, na) + 1024));
   const int tcols = 3 * bn <= 64 ? 64 : 3 * bn <= 128 ? 128 : 256;
   return std::max(1, std::min(std::min(by_smem, 512 / tcols), 2048 / WG_THREADS));
 }
 
-template <int KC, int BN>
+template <bool SWAP, int KC, int BN>
 cudaError_t launch_wgrad_tma_s(cudaStream_t s, int S, const CUtensorMap &xm, const CUtensorMap &dm,
                                const WgradTmaArgs &a, int *err) {
   switch (S) {
-    case 4: return launch_wgrad_tma<KC, BN, 4>(s, xm, dm, a, err);
-    case 3: return launch_wgrad_tma<KC, BN, 3>(s, xm, dm, a, err);
-    default: return launch_wgrad_tma<KC, BN, 2>(s, xm, dm, a, err);
+    case 4: return launch_wgrad_tma<SWAP, KC, BN, 4>(s, xm, dm, a, err);
+    case 3: return launch_wgrad_tma<SWAP, KC, BN, 3>(s, xm, dm, a, err);
+    default: return launch_wgrad_tma<SWAP, KC, BN, 2>(s, xm, dm, a, err);
   }
 }
 
-template <int KC>
+template <bool SWAP, int KC>
 cudaError_t launch_wgrad_tma_b(cudaStream_t s, int bn, int S, const CUtensorMap &xm, const CUtensorMap &dm,
                                const WgradTmaArgs &a, int *err) {
-  return bn == 64   ? launch_wgrad_tma_s<KC, 64>(s, S, xm, dm, a, err)
-         : bn == 32 ? launch_wgrad_tma_s<KC, 32>(s, S, xm, dm, a, err)
-                    : launch_wgrad_tma_s<KC, 16>(s, S, xm, dm, a, err);
+  return bn == 64   ? launch_wgrad_tma_s<SWAP, KC, 64>(s, S, xm, dm, a, err)
+         : bn == 32 ? launch_wgrad_tma_s<SWAP, KC, 32>(s, S, xm, dm, a, err)
+                    : launch_wgrad_tma_s<SWAP, KC, 16>(s, S, xm, dm, a, err);
+}
+
+template <bool SWAP>
+cudaError_t launch_wgrad_tma_k(cudaStream_t s, int kc, int bn, int S, const CUtensorMap &xm, const CUtensorMap &dm,
+                               const WgradTmaArgs &a, int *err) {
+  return kc == 128 ? launch_wgrad_tma_b<SWAP, 128>(s, bn, S, xm, dm, a, err)
+                   : launch_wgrad_tma_b<SWAP, 64>(s, bn, S, xm, dm, a, err);
+}
+
+// Largest of 64, 32, 16 channels that divides C (C % 16 == 0), or the
+// override when it divides.
+int wgrad_tile(int C) {
+  if (g_wgrad_bn && C % g_wgrad_bn == 0) return g_wgrad_bn;
+  return C % 64 == 0 ? 64 : C % 32 == 0 ? 32 : 16;
 }
 
 cudaError_t conv_wgrad(cudaStream_t s, const bf16 *x, const bf16 *dz, float *part, float *dw,
@@ -365,15 +380,22 @@ cudaError_t conv_wgrad(cudaStream_t s, const bf16 *x, const bf16 *dz, float *par
   const long long M = (long long)B * H * W;
   const int pps = pix_per_split(M);
   const int splits = (int)((M + pps - 1) / pps);
+  // orientation: M (128-row MMA tiles) on the channel count that leaves
+  // fewer of its rows as padding (output channels on a tie), unless that
+  // leaves N tiles of 16 output channels, whose MMAs are too small (64 -> 16
+  // measured 83 us swapped against 63 us); the N tile divides the other one
+  const long long pad_out = ((Cout + 127) / 128) * 128LL * Cin, pad_in = ((Cin + 127) / 128) * 128LL * Cout;
+  const bool swap = pad_in < pad_out && Cout % 32 == 0;
+  const int mext = swap ? Cin : Cout, next = swap ? Cout : Cin;
   CUtensorMap xm, dm;
-  int bn = g_wgrad_bn ? g_wgrad_bn : (Cin % 64 == 0 ? 64 : Cin % 32 == 0 ? 32 : 16);
-  if (Cin % bn != 0) bn = Cin % 32 == 0 ? 32 : 16;
-  const int wa = wgrad_wa(Cout), na = wgrad_na(Cout);
+  const int bn = next % 16 == 0 ? wgrad_tile(next) : 16;
+  const int wa = wgrad_wa(mext), na = wgrad_na(mext);
   int kc = 128, S = 2;
-  wgrad_pipeline(bn, wa, na, &kc, &S);
+  wgrad_pipeline(swap, bn, wa, na, &kc, &S);
   const int TW = wgrad_tw(W), rows = kc / TW;
-  if (g_wgrad_kernel == 1 && Cin % 16 == 0 && Cout % 8 == 0 && nhwc_map(&xm, x, B, H, W, Cin, bn, TW, rows) &&
-      nhwc_map(&dm, dz, B, H, W, Cout, wa, TW, rows)) {
+  if (g_wgrad_kernel == 1 && Cin % 16 == 0 && Cout % 8 == 0 &&
+      nhwc_map(&xm, x, B, H, W, Cin, swap ? wa : bn, TW, rows) &&
+      nhwc_map(&dm, dz, B, H, W, Cout, swap ? bn : wa, TW, rows)) {
     int *err = tc_error_flag();
     if (!err) return cudaErrorMemoryAllocation;
     // split the chunks so that one wave fills every SM with the CTAs that
@@ -381,12 +403,12 @@ cudaError_t conv_wgrad(cudaStream_t s, const bf16 *x, const bf16 *dz, float *par
     // partial buffer sized for the mma.sync kernel's splits
     const int strips = (W + TW - 1) / TW, rblocks = (H + rows - 1) / rows;
     const long long nq = (long long)B * strips * rblocks;
-    const long long tiles = 3LL * ((Cin + bn - 1) / bn) * ((Cout + 127) / 128);
-    long long sp = (long long)wgrad_fit(kc, bn, S, wa, na) * sm_count() / tiles;  // no second wave
+    const long long tiles = 3LL * ((next + bn - 1) / bn) * ((mext + 127) / 128);
+    long long sp = (long long)wgrad_fit(swap, kc, bn, S, wa, na) * sm_count() / tiles;  // no second wave
     sp = std::min<long long>(std::min<long long>(sp, splits), nq);
     WgradTmaArgs a{part, B, H, W, Cin, Cout, TW, rows, strips, rblocks, (int)std::max<long long>(1, sp), wa, na};
-    cudaError_t e = kc == 128 ? launch_wgrad_tma_b<128>(s, bn, S, xm, dm, a, err)
-                              : launch_wgrad_tma_b<64>(s, bn, S, xm, dm, a, err);
+    cudaError_t e = swap ? launch_wgrad_tma_k<true>(s, kc, bn, S, xm, dm, a, err)
+                         : launch_wgrad_tma_k<false>(s, kc, bn, S, xm, dm, a, err);
     if (e != cudaSuccess) return e;
     const long long n = (long long)Cout * 9 * Cin;
     k_sum_splits<<<grid1(n), 256, 0, s>>>(part, a.splits, n, dw, 0);

@@ -86,10 +86,12 @@ def wgrad_kernel(request):
 
 
 # shapes: ragged channel tiles, Cin 8 (tcgen05 wgrad falls back), several
-# column strips, more than 128 output channels (two M tiles)
+# column strips, more than 128 output channels (two M tiles), more input
+# than output channels (the tcgen05 weight gradient's swapped roles: 96 ->
+# 32, and 160 -> 32 with two M tiles of input channels)
 @pytest.mark.parametrize("B,H,W,Cin,Cout", [(2, 10, 7, 16, 40), (1, 8, 8, 96, 32), (2, 16, 16, 32, 64),
                                             (1, 5, 66, 32, 16), (3, 5, 9, 8, 16), (1, 12, 130, 32, 48),
-                                            (2, 9, 9, 64, 136)])
+                                            (2, 9, 9, 64, 136), (1, 6, 20, 160, 32)])
 def test_conv_backward(kernel, wgrad_kernel, B, H, W, Cin, Cout):
     import torch
     from paper_2108_08591_gb300 import conv3x3_bf16_backward, conv3x3_bf16_wgrad
