@@ -87,7 +87,7 @@ typedef struct {
                                 widths (FP32: 2, 4; FP16/BF16: 4, 8; FP64: 2;
                                 *EQ: 2, 4).  In 3D, where wider kernels spill
                                 registers, requests are clamped to 4 (rest-shifted
-                                16-bit, FP32 pull) or 2 (in-place FP32, *EQ);
+                                16-bit, FP64) or 2 (FP32, *EQ);
                                 mdf_info reports the width in use.  A width that
                                 does not divide nx falls back to 1. */
     int block;               /* threads per block of the update kernel: 0 = tuned

@@ -52,12 +52,14 @@ bool eq_storage(int st) { return st == MDF_F16EQ || st == MDF_BF16EQ; }
 // mdf_autotune() measures the candidates for a given handle instead.
 // Widest vector kernel built for a lattice (wider requests are clamped to
 // it): 8 for 2D 16-bit, 4 otherwise; in 3D, where the wider kernels spill
-// registers, 4 for rest-shifted 16-bit and 2 for in-place FP32 and the
-// equilibrium-shifted codecs.
+// registers (FP32 with 4 nodes per thread: 424-1012 B at the 96-register
+// budget of the 2D kernel), 4 for rest-shifted 16-bit and FP64 and 2 for
+// FP32 and the equilibrium-shifted codecs.
 int max_vx(int d, int storage, bool inplace) {
+  (void)inplace;
   const bool s16 = storage == MDF_F16 || storage == MDF_BF16;
   if (d == 2) return s16 ? 8 : 4;
-  return ((inplace && storage == MDF_F32) || eq_storage(storage)) ? 2 : 4;
+  return (storage == MDF_F32 || eq_storage(storage)) ? 2 : 4;
 }
 int default_vx(int d, int storage) {
   if (eq_storage(storage)) return 2;

@@ -1014,8 +1014,9 @@ cudaError_t update_vec(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Vector widths built per storage type: FP32 2 or 4, 16-bit 4 or 8 (4 only
-// in 3D, where 8 nodes of 28 populations spill registers), FP64 2.  A
+// Vector widths built per storage type: FP32 2 or 4 (2 only in 3D, where
+// 4 nodes spill registers), 16-bit 4 or 8 (4 only in 3D, where 8 nodes of
+// 28 populations spill registers), FP64 2.  A
 // field-writing update, any other width, an x extent not divisible by the
 // width, or a plane beyond 32-bit offsets runs the scalar kernel.
 template <class L, class TS>
@@ -1023,7 +1024,9 @@ cudaError_t update_t(int mode, bool walls, const DevArgs &a, cudaStream_t s) {
   const bool ok = mode == MODE_STEP && a.vx > 1 && a.nx % a.vx == 0 && a.plane < (1LL << 31) - 64;
   if (ok) {
     if constexpr (sizeof(TS) == 4) {
-      if (a.vx == 4) return update_vec<L, TS, 4>(mode, walls, a, s);
+      if constexpr (L::D == 2) {
+        if (a.vx == 4) return update_vec<L, TS, 4>(mode, walls, a, s);
+      }
       if (a.vx == 2) return update_vec<L, TS, 2>(mode, walls, a, s);
     } else if constexpr (sizeof(TS) == 2) {
       if constexpr (L::D == 2) {
