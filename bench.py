@@ -375,6 +375,30 @@ def storage_leg(shape, s1, P, u, storage, steps=5, warmup=3, q=0, oracle_check=T
     return out
 
 
+def tg3d_leg(oracle_check=True):
+    """The 512^3 D3Q7 x 4 Taylor-Green workload (FP32 rest-shifted storage,
+    s2 = TG3D_S2, epilogue every 200 updates) as a short extra leg of the
+    default line: two bench steps after one warm-up step, through
+    storage_leg, with its sampled FP64 oracle error after 16 updates."""
+    import synth
+    global S2, EPI_EVERY
+    saved = (S2, EPI_EVERY)
+    S2, EPI_EVERY = TG3D_S2, 200
+    try:
+        n = 512
+        nu = TG3D_U0 / (2 * math.pi / n * TG3D_RE)
+        P, u = synth.taylor_green_3d(n, U0=TG3D_U0)
+        out = storage_leg((n,) * 3, 1.0 / (nu / _cs2(3, 0) + 0.5), P, u, "f32", steps=2, warmup=1,
+                          oracle_check=oracle_check)
+        out["workload"] = (f"3D Taylor-Green vortex, periodic 512^3, D3Q7 x 4 sets, U0 = {TG3D_U0}, "
+                           f"Re = {TG3D_RE:.0f}, s2 = {TG3D_S2:g}, FP32 rest-shifted storage, "
+                           "epilogue every 200 steps")
+        out["kernel"] = "k_update<D3Q7,float,MODE_STEP,periodic>"
+        return out
+    finally:
+        S2, EPI_EVERY = saved
+
+
 def run_mdf(args):
     import numpy as np
     import torch
@@ -487,6 +511,10 @@ def run_mdf(args):
         # the 16-bit arm of the same workload: equilibrium-shifted FP16
         # populations with FP32 node moments
         extra = storage_leg(shape, s1, P, u, "f16eq", oracle_check=not args.no_oracle_check)
+    leg3d = None
+    if (args.workload == "tg2d" and N_GRID == 4096 and args.storage == "f32" and default_lattice
+            and not args.no_extra_storage):
+        leg3d = tg3d_leg(oracle_check=not args.no_oracle_check)
     cpu = None
     if world == 1 and not args.no_cpu_baseline and args.workload == "tg2d" and default_lattice:
         cpu = cpu_oracle_sample()
@@ -522,6 +550,7 @@ def run_mdf(args):
                      "avg_launch_ms": plain_ms, "kernel_sha": sha},
         "fp64_oracle_error": oerr,
         "storage_f16eq": extra,
+        "workload_tg3d": leg3d,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "MLUPS", "steps": e2e_steps,
                 "h2d_bytes_per_step": int(P.nbytes + u.nbytes),
@@ -671,7 +700,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true")
     ap.add_argument("--no-extra-storage", action="store_true",
-                    help="skip the FP16 equilibrium-shifted leg of the default line")
+                    help="skip the extra legs of the default line (FP16 equilibrium-shifted, 512^3 3D)")
     ap.add_argument("--workload", choices=("tg2d", "tg3d", "cavities", "conv", "warmstart"),
                     default="tg2d",
                     help="tg2d: the 4096^2 D2Q5 x 3 line (default); tg3d: 512^3 D3Q7 x 4; "
